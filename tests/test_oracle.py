@@ -1,0 +1,298 @@
+"""Pins of the CPU oracle against facts fixed by the mathematics.
+
+The paper (Sec. 1) names the variable-coefficient Poisson solve but prints no
+worked example, so every pin here is a closed form, an invariant, a brute-force
+dense solve or a finite difference:
+
+* sampled sine modes are exact eigenvectors of the constant-beta operator with
+  the wall placed h/2 outside the last cell centre (pins signs, the h^2
+  scaling and the doubled wall coefficient);
+* a layered beta whose exact continuous solution has constant flux makes the
+  discrete operator vanish away from walls only with harmonic face means
+  (pins the face rule and the x/y/z face orientation);
+* symmetry and negative definiteness of A for a rough beta;
+* the multigrid result equals a dense direct solve (8^3, anisotropic and a
+  coarsest level big enough to take the conjugate-gradient branch);
+* the manufactured smooth solution converges at second order;
+* after one red-black pass the updated colour satisfies its own equations;
+* restriction and prolongation identities and R A_fine P = 2 A_coarse;
+* the adjoint against central finite differences, the Euler identity of a
+  degree-1 homogeneous face rule and the self-adjointness of the solve.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1008_2801_gb300 import inputs
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+def _rough_beta(shape, seed=0):
+    return np.exp(_rng(seed).uniform(-2.0, 2.0, shape))
+
+
+def _mode(shape, h, k):
+    nz, ny, nx = shape
+    z, y, x = inputs.cell_centres((nx, ny, nz), h)
+    Lx, Ly, Lz = nx * h, ny * h, nz * h
+    return (np.sin(k[0] * np.pi * x / Lx) * np.sin(k[1] * np.pi * y / Ly)
+            * np.sin(k[2] * np.pi * z / Lz)) * np.ones(shape)
+
+
+def _eig(shape, h, k, beta):
+    nz, ny, nx = shape
+    lam = 0.0
+    for kd, nd in zip(k, (nx, ny, nz)):
+        lam -= 4.0 * beta * np.sin(kd * np.pi * h / (2.0 * nd * h)) ** 2 / h ** 2
+    return lam
+
+
+@pytest.mark.parametrize("shape,k", [((8, 8, 8), (1, 1, 1)),
+                                     ((12, 6, 10), (2, 1, 3)),
+                                     ((16, 16, 16), (3, 2, 5))])
+def test_sine_modes_are_exact_eigenvectors(shape, k):
+    beta0 = 1.7
+    h = 1.0 / 16
+    beta = np.full(shape, beta0)
+    faces = O.face_beta(beta)
+    u = _mode(shape, h, k)
+    lam = _eig(shape, h, k, beta0)
+    Au = O.apply(faces, h, u)
+    assert np.max(np.abs(Au - lam * u)) <= 1e-12 * abs(lam) * np.max(np.abs(u))
+    # and the multigrid solve of A phi = u returns u / lam
+    phi, info = O.solve(beta, u, h, tol=1e-13)
+    assert info["status"] == "ok"
+    err = np.linalg.norm(phi - u / lam) / np.linalg.norm(u / lam)
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_layered_beta_needs_harmonic_faces(axis):
+    # beta piecewise constant in one direction.  The continuous solution of
+    # (beta phi')' = 0 with flux q has phi' = q / beta; integrating it between
+    # cell centres gives the cell-centre values below.  Away from the walls
+    # the discrete operator must vanish on them.
+    n = 12
+    h = 1.0 / n
+    layers = np.exp(_rng(3).uniform(-2, 2, n))
+    # exact integral of q / beta(s) from the first centre to each centre
+    phi1 = np.zeros(n)
+    for i in range(1, n):
+        phi1[i] = phi1[i - 1] + 0.5 * h / layers[i - 1] + 0.5 * h / layers[i]
+    shape = (n, n, n)
+    beta = np.empty(shape)
+    phi = np.empty(shape)
+    sl = [None, None, None]
+    for c in range(n):
+        idx = [slice(None)] * 3
+        idx[2 - axis] = c
+        beta[tuple(idx)] = layers[c]
+        phi[tuple(idx)] = phi1[c]
+    faces = O.face_beta(beta)
+    Aphi = O.apply(faces, h, phi)
+    inner = Aphi[1:-1, 1:-1, 1:-1]
+    scale = np.max(np.abs(phi)) * np.max(layers) / h ** 2
+    assert np.max(np.abs(inner)) <= 1e-13 * scale
+    # the arithmetic mean would not satisfy it: check the test can fail
+    bx, by, bz = faces
+    arith = [b.copy() for b in faces]
+    a = [arith[0][:, :, 1:-1], arith[1][:, 1:-1, :], arith[2][1:-1, :, :]][axis]
+    lo = [beta[:, :, :-1], beta[:, :-1, :], beta[:-1, :, :]][axis]
+    hi = [beta[:, :, 1:], beta[:, 1:, :], beta[1:, :, :]][axis]
+    a[...] = 0.5 * (lo + hi)
+    bad = O.apply(tuple(arith), h, phi)[1:-1, 1:-1, 1:-1]
+    assert np.max(np.abs(bad)) > 1e-3 * scale
+
+
+def test_operator_symmetric_negative_definite():
+    shape = (7, 10, 9)
+    h = 0.1
+    beta = _rough_beta(shape, 1)
+    faces = O.face_beta(beta)
+    r = _rng(2)
+    for _ in range(4):
+        u = r.standard_normal(shape)
+        v = r.standard_normal(shape)
+        Au, Av = O.apply(faces, h, u), O.apply(faces, h, v)
+        lhs, rhs = np.vdot(u, Av), np.vdot(Au, v)
+        assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(u) * np.linalg.norm(Av)
+        assert np.vdot(u, Au) < 0
+
+
+def test_dense_matrix_symmetric_and_definite():
+    shape = (4, 5, 6)
+    beta = _rough_beta(shape, 4)
+    A = O.dense_matrix(O.face_beta(beta), 0.25, shape)
+    assert np.max(np.abs(A - A.T)) <= 1e-12 * np.max(np.abs(A))
+    assert np.max(np.linalg.eigvalsh(0.5 * (A + A.T))) < 0
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 4, 8), (13, 13, 13)])
+def test_multigrid_equals_dense_solve(shape):
+    nz, ny, nx = shape
+    d = inputs.stellar((nx, ny, nz), 11)
+    h = d["dx"]
+    A = O.dense_matrix(O.face_beta(d["beta"]), h, shape)
+    x = np.linalg.solve(A, d["f"].ravel()).reshape(shape)
+    phi, info = O.solve(d["beta"], d["f"], h, tol=1e-14)
+    assert info["status"] == "ok"
+    assert np.linalg.norm(phi - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_levels_rule():
+    assert O.levels((64, 64, 64)) == [(64, 64, 64), (32, 32, 32), (16, 16, 16),
+                                      (8, 8, 8), (4, 4, 4), (2, 2, 2)]
+    assert O.levels((48, 128, 128))[-1] == (3, 8, 8)
+    assert O.levels((32, 128, 128))[-1] == (2, 8, 8)
+    assert O.levels((10, 6, 14)) == [(10, 6, 14), (5, 3, 7)]
+    assert O.levels((33, 33, 33)) == [(33, 33, 33)]
+    assert O.levels((2, 8, 8)) == [(2, 8, 8)]
+
+
+def test_manufactured_second_order():
+    errs = []
+    for n in (16, 32, 64):
+        d = inputs.manufactured(n)
+        phi, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-12)
+        assert info["status"] == "ok"
+        e = phi - d["phi_exact"]
+        errs.append((np.sqrt(np.mean(e ** 2)), np.max(np.abs(e))))
+    for (l2a, mxa), (l2b, mxb) in zip(errs, errs[1:]):
+        assert np.log2(l2a / l2b) >= 1.8
+        assert np.log2(mxa / mxb) >= 1.8
+
+
+def test_rbgs_pass_solves_own_colour():
+    shape = (6, 7, 9)
+    h = 0.2
+    r = _rng(5)
+    beta = _rough_beta(shape, 5)
+    faces = O.face_beta(beta)
+    f = r.standard_normal(shape)
+    phi = r.standard_normal(shape)
+    k, j, i = np.indices(shape)
+    red = (i + j + k) % 2 == 0
+    for color, mask in ((0, red), (1, ~red)):
+        new = O.rbgs_pass(faces, h, f, phi, color)
+        assert np.array_equal(new[~mask], phi[~mask])
+        res = O.residual(faces, h, f, new)
+        scale = np.max(np.abs(f)) + np.max(np.abs(O.apply(faces, h, new)))
+        assert np.max(np.abs(res[mask])) <= 1e-13 * scale
+        assert np.max(np.abs(res[~mask])) > 1e-3 * scale
+        phi = new
+
+
+def test_transfer_identities():
+    shape = (6, 8, 10)
+    r = _rng(6)
+    e = r.standard_normal((3, 4, 5))
+    # R P = I for piecewise-constant P and 8-child averaging R
+    assert np.allclose(O.restrict(O.prolong_add(e, np.zeros(shape))), e, rtol=0, atol=1e-15)
+    # averaging a linear function gives its value at the coarse centre
+    nz, ny, nx = shape
+    z, y, x = inputs.cell_centres((nx, ny, nz), 1.0)
+    lin = 0.3 + 1.1 * x - 0.7 * y + 2.3 * z + 0 * x * y * z
+    zc, yc, xc = inputs.cell_centres((nx // 2, ny // 2, nz // 2), 2.0)
+    want = 0.3 + 1.1 * xc - 0.7 * yc + 2.3 * zc + 0 * xc * yc * zc
+    assert np.allclose(O.restrict(lin), want, rtol=0, atol=1e-13)
+
+
+def test_galerkin_identity_of_coarse_faces():
+    # With piecewise-constant P and mean-of-8 R, R A_h P = 2 A_2h exactly when
+    # the coarse face coefficient is the mean of the 4 fine faces it covers.
+    shape = (8, 6, 10)
+    h = 0.1
+    beta = _rough_beta(shape, 7)
+    faces = O.face_beta(beta)
+    cfaces = O.coarsen_faces(*faces)
+    e = _rng(8).standard_normal((4, 3, 5))
+    lhs = O.restrict(O.apply(faces, h, O.prolong_add(e, np.zeros(shape))))
+    rhs = 2.0 * O.apply(cfaces, 2 * h, e)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+
+
+def _loss(beta, f, tgt, h):
+    phi, info = O.solve(beta, f, h, tol=1e-14, max_cycles=400)
+    assert info["status"] == "ok"
+    return 0.5 * np.sum((phi - tgt) ** 2), phi
+
+
+def _central(bp, bm, fp, fm, tgt, h, eps):
+    # (L+ - L-) / (2 eps) written as sum (phi+ - phi-)(mean(phi+-) - tgt) / (2 eps)
+    # to avoid cancelling two large sums
+    pp = _loss(bp, fp, tgt, h)[1]
+    pm = _loss(bm, fm, tgt, h)[1]
+    return np.sum((pp - pm) * (0.5 * (pp + pm) - tgt)) / (2 * eps)
+
+
+def test_adjoint_matches_central_differences():
+    n = 16
+    d = inputs.stellar(n, 21, nrhs=1)
+    beta, f, tgt, h = d["beta"], d["f_batch"][0], d["phi_target"][0], d["dx"]
+    L0, phi = _loss(beta, f, tgt, h)
+    lam, dbeta, _ = O.adjoint(beta, h, phi, phi - tgt, tol=1e-14)
+    r = _rng(9)
+    for _ in range(6):
+        c = tuple(r.integers(0, n, 3))
+        eps = 1e-4 * beta[c]
+        bp, bm = beta.copy(), beta.copy()
+        bp[c] += eps
+        bm[c] -= eps
+        fd = _central(bp, bm, f, f, tgt, h, eps)
+        assert abs(fd - dbeta[c]) <= 1e-6 * abs(dbeta).max(), (c, fd, dbeta[c])
+        # L is exactly quadratic in f, so a large central step has no
+        # truncation error and keeps rounding noise small
+        eps = 1e-1
+        fp, fm = f.copy(), f.copy()
+        fp[c] += eps
+        fm[c] -= eps
+        fd = _central(beta, beta, fp, fm, tgt, h, eps)
+        assert abs(fd - lam[c]) <= 1e-6 * abs(lam).max(), (c, fd, lam[c])
+    # a wall cell too (the wall-face branch of the gradient)
+    c = (0, 0, n - 1)
+    eps = 1e-4 * beta[c]
+    bp, bm = beta.copy(), beta.copy()
+    bp[c] += eps
+    bm[c] -= eps
+    fd = _central(bp, bm, f, f, tgt, h, eps)
+    assert abs(fd - dbeta[c]) <= 1e-6 * abs(dbeta).max()
+
+
+def test_adjoint_euler_identity_and_self_adjointness():
+    n = 12
+    d = inputs.stellar(n, 22, nrhs=2)
+    beta, h = d["beta"], d["dx"]
+    fs, tg = d["f_batch"], d["phi_target"]
+    phis = np.stack([O.solve(beta, fs[b], h, tol=1e-14)[0] for b in range(2)])
+    g = phis - tg
+    lam, dbeta, infos = O.adjoint(beta, h, phis, g, tol=1e-14)
+    assert all(i["status"] == "ok" for i in infos)
+    # beta_face is degree-1 homogeneous in beta and phi(c beta) = phi / c, so
+    # sum_i beta_i dL/dbeta_i = dL/dc at c = 1 = -g . phi
+    lhs = np.sum(beta * dbeta)
+    rhs = -np.sum(g * phis)
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs)
+    # <A^-1 g, f> = <g, A^-1 f>
+    assert abs(np.vdot(lam[0], fs[1]) - np.vdot(g[0], O.solve(beta, fs[1], h, tol=1e-14)[0])) \
+        <= 1e-11 * np.linalg.norm(lam[0]) * np.linalg.norm(fs[1])
+
+
+def test_zero_rhs_and_nonfinite():
+    shape = (4, 4, 4)
+    beta = np.ones(shape)
+    phi, info = O.solve(beta, np.zeros(shape), 0.25, phi0=np.ones(shape))
+    assert info["status"] == "ok" and not phi.any()
+    f = np.ones(shape)
+    f[1, 2, 3] = np.nan
+    _, info = O.solve(beta, f, 0.25)
+    assert info["status"] == "nonfinite"
+
+
+def test_not_converged_reports_history():
+    d = inputs.stellar(16, 23)
+    phi, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-14, max_cycles=2)
+    assert info["status"] == "not_converged" and info["cycles"] == 2
+    assert info["hist"][2] < info["hist"][1] < info["hist"][0] == 1.0
