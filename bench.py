@@ -1,0 +1,501 @@
+#!/usr/bin/env python3
+"""Throughput of the multigrid Poisson solve on GB300.
+
+One step = one Poisson solve of a MAESTRO-like time step on the 256^3
+stellar-profile workload (beta = 1/rho with rho = (1 + (r/0.3)^2)^-1.5 times
+1% noise, f ~ U[-1, 1] minus its mean): set beta (face coefficients, coarse
+levels, coarsest inverse) and solve div(beta grad phi) = f from phi = 0 to a
+relative residual of 1e-10 with FP64 V(2,2) cycles.  Inputs are resident in
+HBM when the timed region starts; the working set (~1 GB) is far larger than
+L2.  value = cells / second over all ranks (each rank solves its own box:
+independent problems, weak scaling, no collective on the data path).
+
+Printed beside it (one JSON line): the same solve in mixed precision, the
+end-to-end rate through the C ABI with host buffers, the dominant kernel's
+roofline from CUDA events recorded inside the timed graph replays, the CPU
+oracle timed on this machine's host cores, and (unless --no-extra) the 512^3
+FP64-vs-mixed, 64-box batched and 8-RHS adjoint workloads.
+
+--impl reference times the CPU oracle on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MG solves: cells/s to 1e-10 rel residual, FP64 vs mixed; smoother HBM GB/s"
+TOL = 1e-10
+WORKLOAD = "stellar-profile beta (rho_c=1, core 0.3, 1% noise), f~U[-1,1] mean removed, 256^3, dx=1/256, Dirichlet walls, V(2,2) RBGS to 1e-10 rel residual"
+
+# compulsory bytes per cell of one launch (kernel table)
+BYTES_PER_CELL = {("sweep", 8): 56, ("sweep", 4): 28, ("pass", 8): 44, ("pass", 4): 22,
+                  ("restrict", 8): 41, ("restrict", 4): 20.5, ("refine", 8): 60}
+# FP64 flops per cell of one launch: a Gauss-Seidel update is 6 FMA + 1 sub +
+# 1 mul = 14 flop; a sweep updates every cell, a single-colour pass half
+FLOPS_PER_CELL = {"sweep": 14, "pass": 7}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--size", type=int, default=256)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------- distributed ----
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def dist_init(backend):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x, device):
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+    return float(x)
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers ----
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp64_alu_peak_tflops():
+    # 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (maximum SM clock)
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("kernels.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1008_2801_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu capture, if the kernels have
+    not changed since it was taken (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        if t.get("kernel_hash") == kernel_source_hash() and kernel in t.get("per_launch", {}):
+            return t["per_launch"][kernel]
+    except Exception:
+        pass
+    return None
+
+
+def oracle_time(beta, f, dx, tol):
+    import oracle
+    t0 = time.perf_counter()
+    phi, info = oracle.solve(beta, f, dx, tol=tol)
+    return time.perf_counter() - t0, phi, info
+
+
+# -------------------------------------------------------------- GPU arm ----
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1008_2801_gb300 import BatchSolver, Solver, inputs
+
+    rank, world = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.size
+    d = inputs.stellar(n, 2)
+    N = n ** 3
+    beta = torch.from_numpy(d["beta"]).to(dev)
+    f = torch.from_numpy(d["f"]).to(dev)
+    phi = torch.zeros_like(f)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(solver, steps, warm):
+        def step():
+            phi.zero_()
+            solver.set_beta(beta)
+            return solver.solve(f, phi=phi, tol=TOL)[1]
+        for _ in range(warm):
+            st = step()
+        solver.read_profile(reset=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        clk = ClockSampler(local)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            st = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = clk.stop()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        return ms, st, solver.read_profile(reset=True), clocks
+
+    s64 = Solver((n, n, n), d["dx"], precision="fp64", device=dev)
+    s64.profile(True)
+    ms, st64, prof, clocks = timed(s64, args.steps, max(args.warmup, 3))
+    ms_max = max_over_ranks(ms, dev)
+    value = world * N / (ms_max / 1e3)
+    phi64 = phi.cpu().numpy()
+
+    # dominant level-0 kernel of the FP64 step and its roofline
+    fine = {k: v for k, v in prof.items() if k != "kernels" and v["launches"]}
+    dom = max(fine, key=lambda k: fine[k]["ms"])
+    peaks, peaks_src = measured_peaks()
+    kt = fine[dom]["ms"] / fine[dom]["launches"] / 1e3
+    roof = None
+    if dom in FLOPS_PER_CELL:
+        flops = FLOPS_PER_CELL[dom] * N
+        peak = fp64_alu_peak_tflops()
+        ach = flops / kt / 1e12
+        byt = BYTES_PER_CELL[(dom, 8)] * N
+        roof = {"bound": "alu", "kernel": f"k_rbgs_{dom} (FP64, finest level)",
+                "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4),
+                "peak_source": "FP64 FMA units x max SM clock (152 SM x 2 FMA/clk x 2.07 GHz)",
+                "traffic": stored_traffic(f"rbgs_{dom}_f64"),
+                "algorithmic_bytes": byt, "algorithmic_flops": flops,
+                "launch_ms": round(kt * 1e3, 4), "launches": fine[dom]["launches"],
+                "hbm_view": {"achieved_gbs": round(byt / kt / 1e9, 1),
+                             "peak_gbs": peaks["hbm_gbs"],
+                             "frac": round(byt / kt / 1e9 / peaks["hbm_gbs"], 4),
+                             "peak_source": peaks_src}}
+    else:
+        byt = BYTES_PER_CELL.get((dom, 8), 48) * N
+        ach = byt / kt / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                "traffic": stored_traffic(dom), "peak_source": peaks_src,
+                "launch_ms": round(kt * 1e3, 4)}
+    stage_ms = {k: round(v["ms"] / max(args.steps, 1), 4) for k, v in fine.items()}
+
+    out = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "cells_per_gpu": N, "tol": TOL,
+                      "step": "mg_set_beta + mg_solve (phi0 = 0)", "cycles": st64["cycles"],
+                      "rel_resid": st64["rel_resid"],
+                      "l2": "inputs larger than L2 (working set ~1 GB > 129 MB)",
+                      "parallelism": f"independent box per GPU x {world}"},
+           "roofline": roof, "stage_ms_per_step": stage_ms,
+           "gpu_launches": prof["kernels"], "clocks": clocks}
+    s64.close()
+
+    # mixed precision on the same input
+    smx = Solver((n, n, n), d["dx"], precision="mixed", device=dev)
+    smx.profile(True)
+    msm, stm, profm, _ = timed(smx, args.steps, max(args.warmup, 3))
+    msm = max_over_ranks(msm, dev)
+    phimx = phi.cpu().numpy()
+    finem = {k: v for k, v in profm.items() if k != "kernels" and v["launches"]}
+    mixed = {"value": world * N / (msm / 1e3), "unit": "cells/s", "ms_per_step": msm,
+             "steps": stm["cycles"], "rel_resid": stm["rel_resid"],
+             "speedup_vs_fp64": ms_max / msm,
+             "stage_ms_per_step": {k: round(v["ms"] / max(args.steps, 1), 4)
+                                   for k, v in finem.items()}}
+    if "sweep" in finem:
+        kt32 = finem["sweep"]["ms"] / finem["sweep"]["launches"] / 1e3
+        b32 = BYTES_PER_CELL[("sweep", 4)] * N
+        mixed["roofline"] = {"bound": "hbm", "kernel": "k_rbgs_sweep (FP32, finest level)",
+                             "achieved": round(b32 / kt32 / 1e9, 1), "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": round(b32 / kt32 / 1e9 / peaks["hbm_gbs"], 4),
+                             "traffic": stored_traffic("rbgs_sweep_f32"),
+                             "launch_ms": round(kt32 * 1e3, 4), "peak_source": peaks_src}
+    out["mixed"] = mixed
+    smx.close()
+
+    # end to end through the C ABI with host (pinned) buffers
+    bh = torch.from_numpy(d["beta"]).pin_memory()
+    fh = torch.from_numpy(d["f"]).pin_memory()
+    ph = torch.zeros(f.shape, dtype=torch.float64).pin_memory()
+    se = Solver((n, n, n), d["dx"], precision="fp64", device=dev)
+    tot = 0.0
+    for it in range(max(args.warmup, 3) + args.steps):
+        ph.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        se.set_beta(bh)
+        se.solve(fh, phi=ph, tol=TOL)
+        t1 = time.perf_counter()
+        if it >= max(args.warmup, 3):
+            tot += t1 - t0
+    e2e_ms = max_over_ranks(tot / args.steps * 1e3, dev)
+    out["e2e"] = {"value": world * N / (e2e_ms / 1e3), "unit": "cells/s", "ms_per_step": e2e_ms,
+                  "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N,
+                  "path": "mg_set_beta + mg_solve on pinned host buffers (copies inside)"}
+    se.close()
+
+    # CPU oracle on this machine's host cores (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        t, ref10, info = oracle_time(d["beta"], d["f"], d["dx"], TOL)
+        out["cpu_baseline"] = {"value": N / t, "unit": "cells/s", "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"one full oracle solve of the {n}^3 workload to 1e-10 "
+                                         f"({info['cycles']} V-cycles, {t:.1f} s)"}
+        ref, _ = oracle.solve(d["beta"], d["f"], d["dx"], tol=1e-13, phi0=ref10)
+        nr = np.linalg.norm(ref)
+        out["error_vs_oracle"] = {"fp64": float(np.linalg.norm(phi64 - ref) / nr),
+                                  "mixed": float(np.linalg.norm(phimx - ref) / nr),
+                                  "reference": "oracle at 1e-13 rel residual"}
+    if rank == 0 and not args.no_extra:
+        out["extra"] = run_extra(dev, args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_extra(dev, args):
+    """512^3 FP64 vs mixed, 64 uneven boxes (batched vs sequential) and the
+    8-RHS adjoint; each timed once after one warm-up (not part of value)."""
+    import numpy as np
+    import torch
+
+    from paper_1008_2801_gb300 import BatchSolver, MGSolve, Solver, inputs
+
+    ex = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def time_once(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = ev(), ev()
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b), r
+
+    # 512^3
+    d = inputs.config(3)
+    beta = torch.from_numpy(d["beta"]).to(dev)
+    f = torch.from_numpy(d["f"]).to(dev)
+    del d
+    N = f.numel()
+    res = {}
+    sols = {}
+    for prec in ("fp64", "mixed"):
+        s = Solver(tuple(f.shape), 1 / 512, precision=prec, device=dev)
+        phi = torch.zeros_like(f)
+
+        def go():
+            phi.zero_()
+            s.set_beta(beta)
+            return s.solve(f, phi=phi, tol=TOL)[1]
+        ms, st = time_once(go)
+        res[prec] = {"cells_per_s": N / (ms / 1e3), "ms": ms, "cycles": st["cycles"],
+                     "rel_resid": st["rel_resid"]}
+        sols[prec] = phi.clone()
+        s.close()
+    res["mixed_vs_fp64_rel_l2"] = ((sols["mixed"] - sols["fp64"]).norm() /
+                                   sols["fp64"].norm()).item()
+    res["speedup_mixed"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    ex["512^3"] = res
+    del beta, f, sols
+    torch.cuda.empty_cache()
+
+    # 64 uneven boxes
+    d = inputs.config(4)
+    shapes = [tuple(int(v) for v in dims[::-1]) for dims in d["dims"]]
+    bp = torch.from_numpy(np.concatenate([b.ravel() for b in d["beta"]])).to(dev)
+    fp = torch.from_numpy(np.concatenate([x.ravel() for x in d["f"]])).to(dev)
+    N = fp.numel()
+    res = {"boxes": len(shapes), "cells": N}
+    for prec in ("fp64", "mixed"):
+        bs = BatchSolver(shapes, d["dx"], precision=prec, device=dev)
+        phi = torch.zeros_like(fp)
+
+        def go():
+            phi.zero_()
+            bs.set_beta(bp)
+            return bs.solve(fp, phi, tol=TOL)[1]
+        ms, sts = time_once(go)
+        res[f"batched_{prec}"] = {"cells_per_s": N / (ms / 1e3), "ms": ms,
+                                  "max_cycles": max(s["cycles"] for s in sts),
+                                  "all_ok": all(s["status"] == "ok" for s in sts)}
+        bs.close()
+    solvers = [Solver(sh, d["dx"], precision="fp64", device=dev) for sh in shapes]
+    offs = np.cumsum([0] + [int(np.prod(sh)) for sh in shapes])
+
+    def seq():
+        for i, s in enumerate(solvers):
+            s.set_beta(bp[offs[i]:offs[i + 1]].view(shapes[i]))
+            s.solve(fp[offs[i]:offs[i + 1]].view(shapes[i]), tol=TOL)
+    ms, _ = time_once(seq)
+    res["sequential_fp64"] = {"cells_per_s": N / (ms / 1e3), "ms": ms}
+    for s in solvers:
+        s.close()
+    ex["batched_64"] = res
+    del bp, fp
+
+    # adjoint, 128^3 x 8 right-hand sides
+    d = inputs.config(5)
+    beta = torch.from_numpy(d["beta"]).to(dev).requires_grad_(True)
+    fb = torch.from_numpy(d["f"]).to(dev).requires_grad_(True)
+    tgt = torch.from_numpy(d["phi_target"]).to(dev)
+    s = Solver(tuple(beta.shape), d["dx"], precision="fp64", device=dev)
+
+    def fwd_bwd():
+        beta.grad = None
+        fb.grad = None
+        phi = MGSolve.apply(fb, beta, s, TOL)
+        (0.5 * ((phi - tgt) ** 2).sum()).backward()
+        return phi
+    ms, _ = time_once(fwd_bwd)
+    ex["adjoint_128^3_x8"] = {"ms_forward_backward": ms,
+                              "cells_per_s": 2 * fb.numel() / (ms / 1e3),
+                              "note": "8 forward + 8 adjoint solves, cells counted per solve"}
+    s.close()
+    return ex
+
+
+# --------------------------------------------------------- reference arm ----
+
+def run_reference(args):
+    rank, world = dist_init("gloo")
+    if rank != 0:
+        return
+    import oracle
+    from paper_1008_2801_gb300 import inputs
+    n = args.size
+    d = inputs.stellar(n, 2)
+    N = n ** 3
+    oracle.build()
+    steps, warm = args.steps, max(args.warmup, 1)
+    t_first, _, info = oracle_time(d["beta"], d["f"], d["dx"], TOL)
+    cycles = info["cycles"]
+    budget = 240.0
+    full = (steps + warm) * t_first <= budget
+    times = []
+    for it in range(warm - 1 + steps):
+        if full:
+            t, _, _ = oracle_time(d["beta"], d["f"], d["dx"], TOL)
+            eff = t
+        else:
+            m = max(1, int(budget / (steps + warm) / (t_first / cycles)))
+            t0 = time.perf_counter()
+            oracle.solve(d["beta"], d["f"], d["dx"], tol=1e-300, max_cycles=m)
+            t = time.perf_counter() - t0
+            eff = t / m * cycles
+        if it >= warm - 1:
+            times.append(eff)
+    ms = sum(times) / len(times) * 1e3
+    v = N / (ms / 1e3)
+    sample = (f"full oracle solve of the {n}^3 workload to 1e-10 ({cycles} V-cycles) per step"
+              if full else f"{m} oracle V-cycles per step, scaled to the {cycles} a full solve needs")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": N, "tol": TOL},
+        "cpu_baseline": {"value": v, "unit": "cells/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -1,0 +1,196 @@
+/*
+ * mg.h -- C ABI of the GB300 multigrid solver for the cell-centred
+ * variable-coefficient Poisson equation
+ *
+ *        div(beta grad phi) = f        on a box, phi = 0 on its walls.
+ *
+ * This is the linear solve of a MAESTRO time step (paper Sec. 1: the
+ * velocity constraint of the low-Mach approximation gives a variable-
+ * coefficient Poisson equation to be solved every step; paper Sec. 3: these
+ * solves are what limits MAESTRO's scaling).  The paper does not name a
+ * discretisation; the library implements:
+ *
+ *   - cell (i, j, k) of an (nx, ny, nz) box with spacing dx has its centre at
+ *     ((i+1/2)dx, (j+1/2)dx, (k+1/2)dx); arrays are C order (nz, ny, nx),
+ *     x fastest (the torch shape (nz, ny, nx));
+ *   - face coefficients: harmonic mean 2 a b / (a + b) of the two cells' beta;
+ *     a wall face takes 2 beta of its cell (the wall is dx/2 from the centre);
+ *   - (A phi)_c = sum over the 6 faces of beta_face (phi_nbr - phi_c) / dx^2,
+ *     phi_nbr = 0 outside the box; A is symmetric negative definite;
+ *   - geometric multigrid V(nu1, nu2) cycles, red-black Gauss-Seidel
+ *     smoothing (red = (i+j+k) even first), restriction = mean of 8 children,
+ *     piecewise-constant prolongation, coarse face = mean of 4 fine faces,
+ *     all dimensions halved while all are even and >= 4, coarsest level
+ *     (at most MG_MAX_BOTTOM cells) solved exactly with a dense inverse;
+ *   - convergence: ||f - A phi||_2 <= tol * ||f||_2 (unweighted discrete L2).
+ *
+ * Conventions for every call below.
+ *   - Pointers to f, phi, beta and gradients are float64, contiguous, C order
+ *     (nz, ny, nx) (batched calls: boxes packed back to back).  They may be
+ *     device pointers on the context's device or host pointers (pageable or
+ *     pinned); host buffers are copied in and out inside the call.  The
+ *     caller owns them; the library never frees or retains them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     ordered on it; calls that return a convergence status synchronise it.
+ *   - The library owns its hierarchy (allocated in *_create with cudaMalloc)
+ *     and frees it in *_destroy.
+ *   - Every int-returning call returns an mg_status; mg_last_error() gives a
+ *     thread-local message for the last failure.  On MG_ERR_CUDA the CUDA
+ *     error is in the message; the context must then be destroyed.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef MG_H
+#define MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+typedef struct mg_batch mg_batch;
+
+enum mg_status {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,   /* bad size, pointer, option or call order */
+    MG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    MG_ERR_OOM = 3,           /* device allocation failed */
+    MG_ERR_NOT_CONVERGED = 4, /* max_cycles reached or the residual stalled; phi = last iterate */
+    MG_ERR_DIVERGED = 5,      /* residual grew by more than 1e3 over its start */
+    MG_ERR_NONFINITE = 6,     /* NaN/Inf in f, beta or the residual */
+    MG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+    MG_ERR_UNSUPPORTED = 8    /* shape or option outside what is implemented */
+};
+
+/* boundary conditions: homogeneous Dirichlet (phi = 0 on every wall) */
+enum { MG_BC_DIRICHLET0 = 0 };
+
+/* precision of the V-cycles */
+enum {
+    MG_FP64 = 0,  /* everything in FP64 */
+    MG_MIXED = 1  /* FP32 V-cycles inside an FP64 iterative-refinement loop:
+                     FP64 residual, solution update and norm; FP32 smoothing,
+                     residual, transfers and coarsest solve */
+};
+
+#define MG_MAX_BOTTOM 1024   /* most cells allowed on the coarsest level */
+#define MG_MAX_HIST 128      /* residual-history entries kept in mg_stats */
+
+typedef struct {
+    int precision;    /* MG_FP64 (default) or MG_MIXED */
+    int nu1, nu2;     /* pre- and post-smoothing sweeps (default 2, 2; 0..8) */
+    int max_cycles;   /* V-cycles (FP64) or refinement steps (mixed); default 100 */
+    int use_graph;    /* 1 (default): replay each V-cycle as a captured CUDA graph */
+    int smoother;     /* 0 auto (default), 1 single-colour in-place passes,
+                         2 fused two-colour out-of-place sweeps */
+    int reserved[10];
+} mg_opts;
+
+typedef struct {
+    int cycles;                /* V-cycles (FP64) or refinement steps (mixed) run */
+    int status;                /* mg_status of the solve */
+    double norm_f;             /* ||f||_2 */
+    double rel_resid0;         /* ||f - A phi0|| / ||f|| before the first cycle */
+    double rel_resid;          /* ||f - A phi|| / ||f|| at return */
+    double hist[MG_MAX_HIST];  /* rel_resid after cycle c (hist[0] = rel_resid0) */
+    float t_setup_ms;          /* mg_set_beta wall time of the last set-up */
+    float t_solve_ms;          /* wall time of this call */
+} mg_stats;
+
+/* Fill *opts with the defaults above. */
+void mg_default_opts(mg_opts *opts);
+
+/* Create a solver for an n = {nx, ny, nz} box with spacing dx > 0 on the
+ * current CUDA device.  Builds the level list and allocates the hierarchy;
+ * runs no kernel.  opts may be NULL (defaults).  Errors: INVALID_ARG (n < 1,
+ * dx <= 0, bad options), UNSUPPORTED (bc != MG_BC_DIRICHLET0, or a coarsest
+ * level above MG_MAX_BOTTOM cells, e.g. a 33^3 box), OOM, CUDA. */
+int mg_create(mg_ctx **out, const int n[3], double dx, int bc, const mg_opts *opts);
+
+/* Set cell beta (nx*ny*nz values, all > 0 and finite).  Computes face
+ * coefficients on every level, inverse diagonals and the coarsest-level
+ * inverse, and keeps a device copy of beta for mg_adjoint.  Asynchronous.
+ * Errors: INVALID_ARG (NULL). Non-positive or non-finite beta is not checked
+ * here; it surfaces as MG_ERR_NONFINITE in the next solve. */
+int mg_set_beta(mg_ctx *ctx, const double *beta_cell, void *stream);
+
+/* Solve A phi = f.  phi holds the initial guess on entry (zeros for none)
+ * and the solution on return.  tol > 0 is the relative residual target.
+ * st may be NULL.  Synchronises the stream once per cycle to read the
+ * residual norm.  Returns OK, NOT_CONVERGED or DIVERGED (phi = last iterate),
+ * NONFINITE (phi unspecified), INVALID_ARG (no beta set, NULL, tol <= 0), CUDA.
+ * f = 0 gives phi = 0 and OK. */
+int mg_solve(mg_ctx *ctx, const double *f, double *phi, double tol, mg_stats *st,
+             void *stream);
+
+/* Same as mg_solve for nrhs right-hand sides packed back to back (each
+ * nx*ny*nz values) that share beta; st may be NULL or an array of nrhs.
+ * Returns the worst status over the right-hand sides. */
+int mg_solve_multi(mg_ctx *ctx, int nrhs, const double *f, double *phi, double tol,
+                   mg_stats *st, void *stream);
+
+/* Adjoint of mg_solve for a loss L(phi) with dL/dphi = g (nrhs right-hand
+ * sides packed as in mg_solve_multi, phi the forward solutions):
+ *   dLdf  (written)      = lambda, the solution of A lambda = g (A = A^T);
+ *   dLdbeta (ADDED TO)   += sum over right-hand sides and over the 6 faces of
+ *       each cell of dL/dbeta_face * d beta_face / d beta_cell, with
+ *       dL/dbeta_face = (lambda_n - lambda_c)(phi_n - phi_c)/dx^2 inside and
+ *       lambda_c phi_c / dx^2 on walls, d beta_face/d beta_c =
+ *       2 beta_n^2 / (beta_c + beta_n)^2 inside and 2 on walls.
+ * The forward beta must still be the one set.  Returns as mg_solve_multi. */
+int mg_adjoint(mg_ctx *ctx, int nrhs, const double *phi, const double *g, double *dLdf,
+               double *dLdbeta, double tol, mg_stats *st, void *stream);
+
+/* Level list of a context: *nlev levels, dims[3*l .. 3*l+2] = (nx, ny, nz)
+ * of level l (dims may be NULL; room for 32 levels). */
+int mg_levels(const mg_ctx *ctx, int *nlev, int *dims);
+
+void mg_destroy(mg_ctx *ctx);
+
+/* ---- many independent boxes (the grids of one MultiFAB level, paper Sec. 2:
+ * a level is a union of disjoint rectangular grids whose data are distributed
+ * and worked on independently).  Every stage of a V-cycle runs as one launch
+ * over the tiles of all boxes still active at that level; a box whose
+ * residual meets tol stops being updated.  Box b has dims n[b] and spacing
+ * dx[b]; its arrays are packed at element offset off[b] = sum_{c<b} cells(c). */
+int mg_batch_create(mg_batch **out, int nbox, const int (*n)[3], const double *dx, int bc,
+                    const mg_opts *opts);
+int mg_batch_set_beta(mg_batch *b, const double *beta_packed, void *stream);
+/* st may be NULL or an array of nbox; returns the worst status over boxes. */
+int mg_solve_batched(mg_batch *b, const double *f_packed, double *phi_packed, double tol,
+                     mg_stats *st, void *stream);
+void mg_batch_destroy(mg_batch *b);
+
+/* ---- measurement -------------------------------------------------------
+ * With profiling on, the solver records CUDA events around each stage class
+ * below (as event nodes inside the captured V-cycle graph, so the times are
+ * those of the real solve) and accumulates the device time between them.
+ * `kernels` counts every kernel launched by the context (graph nodes count
+ * once per replay).  Profiling takes effect at the next solve. */
+enum {
+    MG_PROF_SWEEP = 0,     /* finest level: fused red+black sweeps */
+    MG_PROF_PASS = 1,      /* finest level: single-colour passes */
+    MG_PROF_RESTRICT = 2,  /* finest level: residual + restriction */
+    MG_PROF_PROLONG = 3,   /* finest level: prolongation + correction */
+    MG_PROF_NORM = 4,      /* finest level: residual norm */
+    MG_PROF_COARSE = 5,    /* every coarser level and the coarsest solve */
+    MG_PROF_REFINE = 6,    /* mixed precision: FP64 refinement step */
+    MG_PROF_NKIND = 16
+};
+typedef struct {
+    double ms[MG_PROF_NKIND];          /* summed device time per stage class */
+    long long launches[MG_PROF_NKIND]; /* timed launches per stage class */
+    long long kernels;                 /* kernels launched (all classes) */
+    long long cells[MG_PROF_NKIND];    /* cells processed per launch (finest level) */
+} mg_profile;
+int mg_profile_enable(mg_ctx *ctx, int on);
+int mg_profile_read(mg_ctx *ctx, mg_profile *out, int reset);
+int mg_batch_profile_enable(mg_batch *b, int on);
+int mg_batch_profile_read(mg_batch *b, mg_profile *out, int reset);
+
+const char *mg_error_string(int status);
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

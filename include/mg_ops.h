@@ -1,0 +1,125 @@
+/*
+ * mg_ops.h -- single-stage entry points of the multigrid solver in mg.h.
+ *
+ * Each call runs one stage of the V-cycle on one box, on arrays the caller
+ * owns, so the stages can be checked one at a time and reused by callers
+ * that drive their own cycle.  Definitions are the ones stated in mg.h
+ * (paper Sec. 1 names the variable-coefficient Poisson solve; the stage
+ * definitions are this library's reading of it).
+ *
+ * LEVEL LAYOUT.  Every array of an (nx, ny, nz) level holds
+ * mg_layout_elems(n) elements of the stage's precision and uses
+ *     row pitch  P = round_up(nx + 1, 8),  plane pitch Q = P * (ny + 1),
+ *     element (i, j, k) at offset (k + 1) * Q + j * P + i.
+ * Cell arrays (phi, f, invD, r) use i < nx, j < ny, k < nz; x-face weights
+ * use i <= nx (face i lies between cells i-1 and i), y-face weights j <= ny,
+ * z-face weights k <= nz.  Every element outside those ranges (the guard
+ * plane below k = 0, the row j = ny, the columns i >= nx, the plane k = nz
+ * of cell arrays) must be zero in phi arrays; the library never writes them.
+ * Face "weights" are beta_face / h^2, so A phi = sum_f w_f (phi_nbr - phi_c).
+ *
+ * Precision: `prec` is MG_OPS_F64 (double arrays) or MG_OPS_F32 (float).
+ * All calls are asynchronous on `stream`; pointers are device pointers.
+ * Return: MG_OK, MG_ERR_INVALID_ARG (bad size/pointer/precision), MG_ERR_CUDA.
+ */
+#ifndef MG_OPS_H
+#define MG_OPS_H
+
+#include "mg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { MG_OPS_F64 = 0, MG_OPS_F32 = 1 };
+
+/* Pitches and total elements of the level layout of an n = {nx, ny, nz} box. */
+int mg_layout(const int n[3], long long *P, long long *Q, long long *elems);
+
+/* Face weights from cell beta (contiguous (nz, ny, nx) float64):
+ * w = harmonic mean of the two cells' beta / h^2, wall faces 2 beta / h^2.
+ * Writes FP64 weights wx, wy, wz in the level layout. */
+int mg_op_face_weights(const int n[3], double h, const double *beta, double *wx, double *wy,
+                       double *wz, void *stream);
+
+/* Coarse weights of an all-even fine level n: w_c = (mean of the 4 fine faces
+ * covering the coarse face) / 4, i.e. the coarse face beta is the mean of the
+ * fine ones and the coarse spacing is 2h.  FP64. */
+int mg_op_coarsen_weights(const int n_fine[3], const double *wx, const double *wy,
+                          const double *wz, double *cwx, double *cwy, double *cwz,
+                          void *stream);
+
+/* invD = 1 / (sum of the 6 face weights of each cell), FP64. */
+int mg_op_inv_diag(const int n[3], const double *wx, const double *wy, const double *wz,
+                   double *invD, void *stream);
+
+/* Round FP64 level arrays to FP32 (weights and inverse diagonal). */
+int mg_op_round_f32(const int n[3], const double *wx, const double *wy, const double *wz,
+                    const double *invD, float *wx32, float *wy32, float *wz32,
+                    float *invD32, void *stream);
+
+/* One red (color 0) or black (color 1) Gauss-Seidel pass in place: every cell
+ * with (i+j+k) % 2 == color gets phi = (sum_f w_f phi_nbr - f) * invD. */
+int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
+                    const void *invD, const void *f, void *phi, int color, void *stream);
+
+/* One full red-then-black sweep as the solver runs it by default (fused,
+ * out of place: reads phi_in, writes phi_out; phi_in is not modified).
+ * Equal to a red pass followed by a black pass. */
+int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
+                     const void *invD, const void *f, const void *phi_in, void *phi_out,
+                     void *stream);
+
+/* r = f - A phi (cell array). */
+int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
+                   const void *f, const void *phi, void *r, void *stream);
+
+/* Fused residual and restriction of an all-even level n: fc = mean over the
+ * 8 children of (f - A phi); phic (coarse solution) is set to zero. */
+int mg_op_residual_restrict(int prec, const int n_fine[3], const void *wx, const void *wy,
+                            const void *wz, const void *f, const void *phi, void *fc,
+                            void *phic, void *stream);
+
+/* phi += coarse value of each cell's parent (piecewise-constant
+ * prolongation) for an all-even fine level n. */
+int mg_op_prolong_add(int prec, const int n_fine[3], const void *phic, void *phi,
+                      void *stream);
+
+/* Exact coarsest-level solve set-up: Ainv = A^{-1} as a dense row-major
+ * (N, N) FP64 matrix, N = nx*ny*nz <= MG_MAX_BOTTOM, dense index
+ * (k*ny + j)*nx + i.  work: N*N doubles of scratch. */
+int mg_op_bottom_inverse(const int n[3], const double *wx, const double *wy,
+                         const double *wz, double *work, double *Ainv, void *stream);
+
+/* phi = Ainv f on the coarsest level (Ainv in the stage precision). */
+int mg_op_bottom_solve(int prec, const int n[3], const void *Ainv, const void *f, void *phi,
+                       void *stream);
+
+/* Residual norm: *out (device double) = ||f - A phi||_2, reduced in a fixed
+ * order.  `partials` is caller-owned device scratch of at least
+ * mg_op_norm_scratch(n) doubles. */
+long long mg_op_norm_scratch(const int n[3]);
+int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy,
+                        const void *wz, const void *f, const void *phi, double *partials,
+                        double *out, void *stream);
+
+/* Mixed-precision refinement step on the finest level (FP64 x, f, weights;
+ * FP32 correction e and scaled residual r32):
+ *   x_out = x_in + (*c_e) e;  r = f - A64 x_out;  r32 = r / (*c_r);
+ *   *out = ||r||_2 (fixed-order reduction through `partials`).
+ * c_e and c_r are device doubles.  x_in and x_out must differ. */
+int mg_op_refine(const int n[3], const double *wx, const double *wy, const double *wz,
+                 const double *f, const double *x_in, double *x_out, const float *e,
+                 float *r32, const double *c_e, const double *c_r, double *partials,
+                 double *out, void *stream);
+
+/* Beta gradient of one right-hand side (see mg_adjoint): dbeta += chain of
+ * the face products of phi and lambda.  beta, phi, lambda, dbeta are
+ * contiguous (nz, ny, nx) float64. */
+int mg_op_beta_grad(const int n[3], double h, const double *beta, const double *phi,
+                    const double *lambda, double *dbeta, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_OPS_H */

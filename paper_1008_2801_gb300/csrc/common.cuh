@@ -1,0 +1,136 @@
+// common.cuh -- level descriptors, tile bookkeeping and reductions shared by
+// the solver's kernels and host driver.
+//
+// Storage of one (nx, ny, nz) level (any precision T): every array holds
+// (nz + 2) * Q elements with row pitch P = round_up(nx + 1, 8) and plane pitch
+// Q = P * (ny + 1); the element of logical position (i, j, k) sits at offset
+// (k + 1) Q + j P + i.  Device pointers in the descriptors below point at
+// logical (0, 0, 0), so position (i, j, k) is ptr[k Q + j P + i] for cell
+// arrays and for face arrays alike (x face i between cells i-1 and i, y face j,
+// z face k).  Outside the box (i = -1 or nx, j = -1 or ny, k = -1 or nz) the
+// solution arrays hold zeros that are never written: the stencil reads the
+// homogeneous Dirichlet neighbour value 0 there without a branch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg.h"
+
+namespace mg {
+
+constexpr int MG_BOTTOM_CELLS = MG_MAX_BOTTOM;  // dense coarsest-level limit
+
+constexpr int kTX = 32;   // tile width  (threads along x)
+constexpr int kTY = 8;    // tile height (threads along y)
+constexpr int kThreads = kTX * kTY;
+constexpr int kSweepZ = 32;   // planes per CTA of the fused red-black sweep
+
+inline __host__ __device__ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+inline __host__ __device__ long long pitch_row(int nx) { return round_up((long long)nx + 1, 8); }
+inline __host__ __device__ long long pitch_plane(int nx, int ny) { return pitch_row(nx) * (ny + 1); }
+inline __host__ __device__ long long level_elems(int nx, int ny, int nz)
+{
+    return pitch_plane(nx, ny) * (nz + 2);
+}
+
+// One box at one level, as the cycle kernels see it.
+template <class T>
+struct Box {
+    T *phi;          // solution / correction
+    T *phi2;         // second solution buffer (out-of-place sweeps)
+    T *f;            // right-hand side
+    const T *wx, *wy, *wz;   // face weights beta_face / h^2
+    const T *invD;   // 1 / sum of the six weights
+    const T *ainv;   // coarsest level only: dense A^{-1}, row-major n x n
+    T *phic;         // next-coarser level solution (zeroed by restriction)
+    T *fc;           // next-coarser level right-hand side
+    int nx, ny, nz;
+    int P;           // row pitch
+    long long Q;     // plane pitch
+    int cP;          // coarse row pitch
+    long long cQ;    // coarse plane pitch
+    int box;         // index of the box in its batch
+};
+
+// Index spaces that kernels tile: all cells, red-black pairs along x
+// (ceil(nx/2) per row), the cells of the next-coarser level, or pairs along x
+// with z cut into chunks of kSweepZ planes (the fused sweep marches in z).
+enum TileKind { TK_CELL = 0, TK_PAIR = 1, TK_COARSE = 2, TK_SWEEP = 3, TK_NKIND = 4 };
+
+inline __host__ __device__ void tile_extent(int kind, int nx, int ny, int nz, int &ex, int &ey,
+                                            int &ez)
+{
+    if (kind == TK_PAIR) { ex = (nx + 1) / 2; ey = ny; ez = nz; }
+    else if (kind == TK_COARSE) { ex = nx / 2; ey = ny / 2; ez = nz / 2; }
+    else if (kind == TK_SWEEP) { ex = (nx + 1) / 2; ey = ny; ez = (nz + kSweepZ - 1) / kSweepZ; }
+    else { ex = nx; ey = ny; ez = nz; }
+}
+
+inline __host__ __device__ int tiles_of(int kind, int nx, int ny, int nz)
+{
+    int ex, ey, ez;
+    tile_extent(kind, nx, ny, nz, ex, ey, ez);
+    return ((ex + kTX - 1) / kTX) * ((ey + kTY - 1) / kTY) * ez;
+}
+
+// A set of boxes launched together (one box, or every box of a batch that is
+// active at a level).  tstart[kind] is a device prefix array of nbox + 1 tile
+// offsets for each tile kind; one CTA handles one tile.
+template <class T>
+struct BoxSet {
+    const Box<T> *boxes;
+    const int *tstart[TK_NKIND];
+    int ntiles[TK_NKIND];
+    int nbox;
+};
+
+// Last box b with tstart[b] <= t (tstart ascending, tstart[0] = 0).
+__device__ __forceinline__ int find_box(const int *__restrict__ tstart, int nbox, int t)
+{
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tstart + mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Position of this thread inside tile `local` of a box (kind's index space).
+struct TilePos {
+    int x, y, z;
+};
+__device__ __forceinline__ TilePos tile_pos(int kind, int nx, int ny, int nz, int local)
+{
+    int ex, ey, ez;
+    tile_extent(kind, nx, ny, nz, ex, ey, ez);
+    int ntx = (ex + kTX - 1) / kTX, nty = (ey + kTY - 1) / kTY;
+    int tx = local % ntx;
+    local /= ntx;
+    int ty = local % nty;
+    int tz = local / nty;
+    TilePos p;
+    p.x = tx * kTX + (int)threadIdx.x;
+    p.y = ty * kTY + (int)threadIdx.y;
+    p.z = tz;
+    return p;
+}
+
+// Fixed-order block sum of one double per thread (blockDim = kTX x kTY):
+// warp shuffles, then warp 0 adds the 8 warp sums in order.  Result valid in
+// thread (0, 0).
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double warp_part[kThreads / 32];
+    int tid = threadIdx.y * kTX + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) warp_part[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < kThreads / 32; ++w) s += warp_part[w];
+    return s;
+}
+
+}  // namespace mg

@@ -1,0 +1,96 @@
+// kernels.h -- host launchers of the solver's CUDA kernels (kernels.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace mg {
+
+// Kernels launched by this library so far (all threads, all contexts).
+long long launch_counter();
+
+// ---- V-cycle stages over a set of boxes (one CTA per tile) --------------
+// `active` (nullable, indexed by Box::box) skips boxes whose flag is 0.
+
+// One red (0) or black (1) Gauss-Seidel pass in place on Box::phi.
+template <class T>
+cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, cudaStream_t st);
+
+// Fused red+black sweep, out of place: Box::phi -> Box::phi2 (src_is_phi2
+// swaps the roles).
+template <class T>
+cudaError_t launch_rbgs_sweep(const BoxSet<T> &S, const int *active, int src_is_phi2,
+                              cudaStream_t st);
+
+// fc = mean over 8 children of (f - A phi); phic = 0.
+template <class T>
+cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStream_t st);
+
+// phi += phic[parent].
+template <class T>
+cudaError_t launch_prolong(const BoxSet<T> &S, const int *active, cudaStream_t st);
+
+// r = f - A phi written to Box::phi2 (used by the single-stage entry point).
+template <class T>
+cudaError_t launch_residual_field(const BoxSet<T> &S, cudaStream_t st);
+
+// Residual norm of level 0: partial sums, then out[Box::box] (see below).
+
+// Per-tile partial sums of squares: mode 0 = residual f - A phi, mode 1 = f.
+template <class T>
+cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode,
+                                 double *partials, cudaStream_t st);
+
+// out[Box::box] = sqrt(sum of the box's partials), fixed order; inactive
+// boxes keep their old value.  copy and inv (nullable) receive the same value
+// and its reciprocal (0 for a zero norm).
+template <class T>
+cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const double *partials,
+                               double *out, double *copy, double *inv, cudaStream_t st);
+
+// Coarsest level: phi = Ainv f (dense, one warp per row).
+template <class T>
+cudaError_t launch_bottom(const BoxSet<T> &S, const int *active, int max_cells, cudaStream_t st);
+
+// Mixed-precision refinement on the finest level of every box:
+// x_out = x_in + c_e[b] e; r = f - A x_out; r32 = r * c_r_inv[b]; partial sums
+// of r^2.  S64: phi/phi2 = x_in/x_out (swapped by x_in_is_phi2), f, weights.
+// S32: phi = e, f = r32.
+cudaError_t launch_refine(const BoxSet<double> &S64, const BoxSet<float> &S32, const int *active,
+                          int x_in_is_phi2, const double *c_e, const double *c_r_inv,
+                          double *partials, cudaStream_t st);
+
+// ---- moving data between packed user arrays and the level layout --------
+// user[off[b] + (k*ny + j)*nx + i] -> level 0 f (to_f) or phi of box b.
+cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,
+                        int to_f, cudaStream_t st);
+// level 0 phi (side[b] == 0, or side == NULL) or phi2 (side[b] == 1) -> user.
+cudaError_t launch_unpack(const BoxSet<double> &S, const long long *off, double *user,
+                          const int *side, cudaStream_t st);
+// phi = 0 inside the box (active boxes only).
+template <class T>
+cudaError_t launch_zero(const BoxSet<T> &S, const int *active, cudaStream_t st);
+// Mixed-precision scales per box: init -> se = 0, sr = normf, sr_inv = 1/normf;
+// otherwise (active boxes) se = sr, sr = norm, sr_inv = 1/norm.
+cudaError_t launch_scales(int nbox, const int *active, int init, const double *norm,
+                          const double *normf, double *se, double *sr, double *sr_inv,
+                          cudaStream_t st);
+
+// ---- set-up (one box per launch) -----------------------------------------
+cudaError_t launch_face_weights(int nx, int ny, int nz, double inv_h2, const double *beta,
+                                double *wx, double *wy, double *wz, cudaStream_t st);
+cudaError_t launch_coarsen(int nx, int ny, int nz, const double *wx, const double *wy,
+                           const double *wz, double *cwx, double *cwy, double *cwz,
+                           cudaStream_t st);
+cudaError_t launch_inv_diag(int nx, int ny, int nz, const double *wx, const double *wy,
+                            const double *wz, double *invD, cudaStream_t st);
+cudaError_t launch_round_f32(int nx, int ny, int nz, const double *wx, const double *wy,
+                             const double *wz, const double *invD, float *wx32, float *wy32,
+                             float *wz32, float *invD32, cudaStream_t st);
+cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, const double *wy,
+                                  const double *wz, double *work, double *inv64, float *inv32,
+                                  cudaStream_t st);
+cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double *beta,
+                             const double *phi, const double *lam, double *dbeta,
+                             cudaStream_t st);
+
+}  // namespace mg

@@ -1,0 +1,105 @@
+// solver.h -- host-side hierarchy and cycle driver shared by mg_ctx (one box)
+// and mg_batch (many boxes).
+#pragma once
+
+#include <array>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mg.h"
+
+namespace mg {
+
+int set_error(int code, const char *fmt, ...);
+
+// Arrays of one box at one level, in one precision.
+template <class T>
+struct LevelBufs {
+    T *phi = nullptr, *phi2 = nullptr, *f = nullptr;
+    T *wx = nullptr, *wy = nullptr, *wz = nullptr, *invD = nullptr;
+};
+
+// All levels of all boxes in one precision, plus the launch sets.
+template <class T>
+struct Hier {
+    std::vector<std::vector<LevelBufs<T>>> lv;  // [box][level]
+    std::vector<T *> ainv;                      // [box] dense coarsest-level inverse
+    std::vector<BoxSet<T>> smooth;              // [level]: boxes not yet at their bottom
+    BoxSet<T> fine{};                           // level 0 of every box
+    BoxSet<T> bottom{};                         // coarsest level of every box
+    cudaGraphExec_t graph = nullptr;            // captured V-cycle (+ fine norm for FP64)
+};
+
+// A timed stretch of one stage class: events recorded before and after it.
+struct ProfSlot {
+    int kind;
+    cudaEvent_t b, e;
+};
+
+struct Solver {
+    int dev = 0;
+    int nbox = 0;
+    mg_opts opts{};
+    std::vector<std::array<int, 3>> n;              // [box] fine dims (nx, ny, nz)
+    std::vector<double> dx;                          // [box]
+    std::vector<std::vector<std::array<int, 3>>> dims;  // [box][level]
+    std::vector<int> nlev;                           // [box]
+    int maxlev = 0;
+    int max_bottom = 0;                              // most cells on a coarsest level
+    std::vector<long long> off;                      // [box+1] packed cell offsets
+    long long total = 0;                             // packed cells
+
+    char *arena = nullptr;                           // every level array, zero-filled
+    char *desc = nullptr;                            // launch-set descriptors
+    Hier<double> h64;
+    Hier<float> h32;
+    bool has32 = false;
+
+    double *beta = nullptr;        // packed copy of cell beta
+    double *work = nullptr;        // coarsest-level inverse scratch
+    double *partials = nullptr;    // per-tile partial sums
+    double *dnorm = nullptr;       // [nbox] last residual norm
+    double *dnormf = nullptr;      // [nbox] ||f||
+    double *dinv = nullptr;        // [nbox] scratch reciprocal
+    double *se = nullptr, *sr = nullptr, *sr_inv = nullptr;  // mixed scales
+    int *active = nullptr;         // [nbox] device flags
+    const long long *doff = nullptr;  // [nbox + 1] device copy of off
+    int *dside = nullptr;          // [nbox] device: 1 if the solution ended in phi2
+    double *hnorm = nullptr;       // pinned [2 * nbox]
+    int *hactive = nullptr;        // pinned [nbox]
+    int *hside = nullptr;          // pinned [nbox]
+    double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;  // packed staging
+    cudaStream_t cap = nullptr;    // capture stream
+    cudaEvent_t ev_setup0 = nullptr, ev_setup1 = nullptr;
+    bool beta_set = false;
+    float t_setup_ms = 0.f;
+    bool setup_pending = false;
+
+    // measurement (mg_profile_*)
+    bool prof = false;                    // record stage events
+    bool graph_prof = false;              // graphs were captured with events
+    std::vector<ProfSlot> slots64, slots32;  // event slots inside the graphs
+    std::vector<ProfSlot> direct;         // slots of direct launches since the last collect
+    std::vector<const std::vector<ProfSlot> *> pending;  // graph slot lists to collect
+    std::vector<cudaEvent_t> ev_free;     // reusable events
+    std::vector<ProfSlot> *rec = nullptr; // where begin/end append (capture or direct)
+    bool capturing = false;
+    double prof_ms[MG_PROF_NKIND] = {};
+    long long prof_n[MG_PROF_NKIND] = {};
+    long long kernels = 0;                // kernels launched by this solver
+    long long cap_kernels = 0;            // kernels enqueued into graph captures
+    long long graph_kernels64 = 0, graph_kernels32 = 0;
+};
+
+int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
+                  const mg_opts *opts);
+void solver_destroy(Solver *s);
+int solver_set_beta(Solver *s, const double *beta_packed, cudaStream_t st);
+// Solve every box; f/phi packed.  zero_guess ignores phi's input.
+int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *st,
+                 cudaStream_t stream, bool zero_guess);
+int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, double *dLdf,
+                   double *dLdbeta, double tol, mg_stats *st, cudaStream_t stream);
+
+}  // namespace mg

@@ -1,0 +1,299 @@
+"""Python front end of the GB300 multigrid solver (torch tensors in, out).
+
+Tensors are float64 with shape (nz, ny, nx) (x fastest), on the solver's CUDA
+device or on the host (host tensors are copied in and out inside the call).
+All arithmetic runs in libmgpu.so; this module only passes pointers and the
+current CUDA stream.
+
+The equation is the variable-coefficient Poisson equation of the paper's
+Sec. 1, div(beta grad phi) = f, with phi = 0 on the box walls.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import MGError, check
+
+PRECISIONS = {"fp64": _lib.MG_FP64, "mixed": _lib.MG_MIXED}
+SMOOTHERS = {"auto": 0, "passes": 1, "fused": 2}
+
+
+def _stream_of(t: torch.Tensor):
+    if t.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, name, numel=None, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if t.is_cuda and device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, solver on {device}")
+
+
+def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother):
+    o = _lib.mg_opts()
+    _lib.load().mg_default_opts(ctypes.byref(o))
+    o.precision = PRECISIONS[precision]
+    o.nu1, o.nu2, o.max_cycles = nu1, nu2, max_cycles
+    o.use_graph = 1 if use_graph else 0
+    o.smoother = SMOOTHERS[smoother]
+    return o
+
+
+def _stats_dict(s: _lib.mg_stats):
+    n = max(0, min(s.cycles + 1, _lib.MG_MAX_HIST))
+    return {"status": _lib.STATUS_NAMES.get(s.status, str(s.status)), "cycles": s.cycles,
+            "norm_f": s.norm_f, "rel_resid0": s.rel_resid0, "rel_resid": s.rel_resid,
+            "hist": list(s.hist[:n]), "t_setup_ms": s.t_setup_ms, "t_solve_ms": s.t_solve_ms}
+
+
+_SOFT = (_lib.MG_OK, _lib.MG_ERR_NOT_CONVERGED)
+
+
+def _profile_dict(p: _lib.mg_profile):
+    out = {"kernels": p.kernels}
+    for k, name in enumerate(_lib.PROF_NAMES):
+        out[name] = {"ms": p.ms[k], "launches": p.launches[k], "cells": p.cells[k]}
+    return out
+
+
+class Solver:
+    """Multigrid solver for one (nz, ny, nx) box with cubic cells of size dx.
+
+    precision: "fp64" (everything FP64) or "mixed" (FP32 V-cycles inside an
+    FP64 iterative-refinement loop).  Not thread-safe.
+    """
+
+    def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
+                 use_graph=True, smoother="auto", device=None):
+        L = _lib.load()
+        self.shape = tuple(int(v) for v in shape)
+        nz, ny, nx = self.shape
+        self.dx = float(dx)
+        self.precision = precision
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self._h = ctypes.c_void_p()
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother)
+        with torch.cuda.device(self.device):
+            check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, 0,
+                              ctypes.byref(o)), "mg_create")
+        self._beta = None
+
+    @property
+    def numel(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    def levels(self):
+        n = ctypes.c_int()
+        dims = (ctypes.c_int * 96)()
+        check(_lib.load().mg_levels(self._h, ctypes.byref(n), dims), "mg_levels")
+        return [(dims[3 * i + 2], dims[3 * i + 1], dims[3 * i]) for i in range(n.value)]
+
+    def set_beta(self, beta: torch.Tensor):
+        _check_tensor(beta, "beta", self.numel, self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().mg_set_beta(self._h, _ptr(beta), _stream_of(beta)), "mg_set_beta")
+        self._beta = beta
+
+    def solve(self, f: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-10,
+              raise_on=("invalid_arg", "cuda", "oom", "nonfinite", "diverged", "timeout",
+                        "unsupported")):
+        """Solve A phi = f; returns (phi, stats).  phi (if given) is the initial
+        guess and is overwritten.  A leading batch dimension solves several
+        right-hand sides with the same beta."""
+        _check_tensor(f, "f", device=self.device)
+        if f.numel() % self.numel:
+            raise ValueError("f must hold whole boxes")
+        nrhs = f.numel() // self.numel
+        if phi is None:
+            phi = torch.zeros_like(f)
+        _check_tensor(phi, "phi", f.numel(), self.device)
+        st = (_lib.mg_stats * nrhs)()
+        L = _lib.load()
+        with torch.cuda.device(self.device):
+            if nrhs == 1:
+                rc = L.mg_solve(self._h, _ptr(f), _ptr(phi), float(tol), st, _stream_of(f))
+            else:
+                rc = L.mg_solve_multi(self._h, nrhs, _ptr(f), _ptr(phi), float(tol), st,
+                                      _stream_of(f))
+        stats = [_stats_dict(s) for s in st]
+        if _lib.STATUS_NAMES.get(rc) in raise_on:
+            raise MGError(rc, "mg_solve")
+        return phi, (stats[0] if nrhs == 1 else stats)
+
+    def adjoint(self, phi: torch.Tensor, g: torch.Tensor, tol: float = 1e-10,
+                dbeta: torch.Tensor | None = None):
+        """Returns (dL/df = lambda, dL/dbeta) for dL/dphi = g (see mg_adjoint)."""
+        _check_tensor(phi, "phi", device=self.device)
+        _check_tensor(g, "g", phi.numel(), self.device)
+        nrhs = phi.numel() // self.numel
+        lam = torch.empty_like(g)
+        if dbeta is None:
+            dbeta = torch.zeros(self.shape, dtype=torch.float64, device=phi.device)
+        _check_tensor(dbeta, "dbeta", self.numel, self.device)
+        st = (_lib.mg_stats * nrhs)()
+        with torch.cuda.device(self.device):
+            rc = _lib.load().mg_adjoint(self._h, nrhs, _ptr(phi), _ptr(g), _ptr(lam),
+                                        _ptr(dbeta), float(tol), st, _stream_of(phi))
+        if rc not in _SOFT:
+            raise MGError(rc, "mg_adjoint")
+        return lam, dbeta
+
+    def profile(self, on: bool = True):
+        """Record per-stage device times (CUDA events inside the V-cycle graph)."""
+        check(_lib.load().mg_profile_enable(self._h, 1 if on else 0), "mg_profile_enable")
+
+    def read_profile(self, reset: bool = False):
+        p = _lib.mg_profile()
+        check(_lib.load().mg_profile_read(self._h, ctypes.byref(p), 1 if reset else 0),
+              "mg_profile_read")
+        return _profile_dict(p)
+
+    def close(self):
+        if self._h:
+            _lib.load().mg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Independent boxes of uneven size solved together (one launch per stage
+    over the tiles of every active box).  shapes: list of (nz, ny, nx); arrays
+    are packed back to back in box order (see ``pack``/``unpack``)."""
+
+    def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
+                 use_graph=True, smoother="auto", device=None):
+        L = _lib.load()
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        nb = len(self.shapes)
+        dxs = [float(dx)] * nb if isinstance(dx, (int, float)) else [float(v) for v in dx]
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        n = (ctypes.c_int * (3 * nb))(*[v for s in self.shapes for v in (s[2], s[1], s[0])])
+        d = (ctypes.c_double * nb)(*dxs)
+        self._h = ctypes.c_void_p()
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother)
+        with torch.cuda.device(self.device):
+            check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, 0, ctypes.byref(o)),
+                  "mg_batch_create")
+        self.sizes = [s[0] * s[1] * s[2] for s in self.shapes]
+        self.total = sum(self.sizes)
+
+    def pack(self, arrays):
+        return torch.cat([a.reshape(-1) for a in arrays])
+
+    def unpack(self, packed):
+        out, o = [], 0
+        for s, k in zip(self.shapes, self.sizes):
+            out.append(packed[o:o + k].view(s))
+            o += k
+        return out
+
+    def set_beta(self, beta_packed: torch.Tensor):
+        _check_tensor(beta_packed, "beta", self.total, self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().mg_batch_set_beta(self._h, _ptr(beta_packed),
+                                                _stream_of(beta_packed)), "mg_batch_set_beta")
+        self._beta = beta_packed
+
+    def solve(self, f_packed, phi_packed=None, tol=1e-10):
+        _check_tensor(f_packed, "f", self.total, self.device)
+        if phi_packed is None:
+            phi_packed = torch.zeros_like(f_packed)
+        _check_tensor(phi_packed, "phi", self.total, self.device)
+        st = (_lib.mg_stats * len(self.shapes))()
+        with torch.cuda.device(self.device):
+            rc = _lib.load().mg_solve_batched(self._h, _ptr(f_packed), _ptr(phi_packed),
+                                              float(tol), st, _stream_of(f_packed))
+        if rc not in _SOFT:
+            raise MGError(rc, "mg_solve_batched")
+        return phi_packed, [_stats_dict(s) for s in st]
+
+    def profile(self, on: bool = True):
+        check(_lib.load().mg_batch_profile_enable(self._h, 1 if on else 0),
+              "mg_batch_profile_enable")
+
+    def read_profile(self, reset: bool = False):
+        p = _lib.mg_profile()
+        check(_lib.load().mg_batch_profile_read(self._h, ctypes.byref(p), 1 if reset else 0),
+              "mg_batch_profile_read")
+        return _profile_dict(p)
+
+    def close(self):
+        if self._h:
+            _lib.load().mg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MGSolve(torch.autograd.Function):
+    """phi = A(beta)^{-1} f as a differentiable op.
+
+    Forward: set beta, solve (f may carry a leading right-hand-side dim).
+    Backward: the adjoint solve A lambda = dL/dphi gives dL/df = lambda and
+    the face products give dL/dbeta (summed over right-hand sides).
+    """
+
+    @staticmethod
+    def forward(ctx, f, beta, solver: Solver, tol: float = 1e-10):
+        solver.set_beta(beta)
+        phi, _ = solver.solve(f.contiguous(), tol=tol)
+        ctx.solver, ctx.tol = solver, tol
+        ctx.save_for_backward(phi, beta)
+        return phi
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        phi, beta = ctx.saved_tensors
+        solver = ctx.solver
+        if solver._beta is not beta:
+            solver.set_beta(beta)
+        lam, dbeta = solver.adjoint(phi, grad_phi.contiguous(), tol=ctx.tol)
+        return lam, dbeta, None, None
+
+
+_cache: dict = {}
+
+
+def solve(f: torch.Tensor, beta: torch.Tensor, dx: float, tol: float = 1e-10,
+          precision: str = "fp64"):
+    """Functional form: phi with div(beta grad phi) = f (differentiable in f
+    and beta).  Solvers are cached per (shape, dx, precision, device)."""
+    shape = tuple(beta.shape)
+    key = (shape, float(dx), precision, f.device)
+    s = _cache.get(key)
+    if s is None:
+        s = _cache[key] = Solver(shape, dx, precision=precision, device=f.device)
+    return MGSolve.apply(f, beta, s, tol)

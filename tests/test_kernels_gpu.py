@@ -1,0 +1,216 @@
+"""Per-stage parity of the CUDA kernels with the CPU oracle (GPU).
+
+Every stage is called through the C ABI (include/mg_ops.h) on the same
+seeded inputs the oracle gets, and compared element by element.
+
+Tolerances, from the arithmetic: each output is a sum of at most 8 products
+(plus one multiply by a stored reciprocal), so its rounding error is below
+about 10 u * (sum of |terms|), u = 2^-53 in FP64 and 2^-24 in FP32.  The
+tests allow 1e-13 (FP64) and 1e-5 (FP32) times that term scale, i.e. 100x
+headroom; the FP32 kernels are compared with the FP64 oracle.
+
+Shapes span several tiles with ragged tails: tiles are 32 x 8 cells (64 x 8
+for the fused sweep, which also cuts z into chunks of 32 planes).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_2801_gb300 import inputs
+from paper_1008_2801_gb300 import ops as K
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1, 1), (3, 2, 5), (5, 7, 9), (20, 17, 33), (70, 20, 130)]
+EVEN = [(2, 2, 2), (4, 6, 8), (18, 10, 34), (66, 20, 130)]
+
+
+def _case(shape, seed):
+    nz, ny, nx = shape
+    d = inputs.stellar((nx, ny, nz), seed)
+    r = np.random.default_rng(seed + 100)
+    phi = r.uniform(-1, 1, shape)
+    return d["beta"], d["f"], phi, d["dx"]
+
+
+def _t(a, dev, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
+
+
+def _level(shape, data, dev, dtype=torch.float64, kind="cell"):
+    return K.put(K.level(shape, dtype, dev), shape, _t(data, dev, dtype), kind)
+
+
+def _weights(beta, h, shape, dev, dtype=torch.float64):
+    w = K.face_weights(_t(beta, dev), h)
+    if dtype == torch.float32:
+        invD = K.inv_diag(w, shape)
+        w32, inv32 = K.round_f32(w, invD, shape)
+        return w32, inv32
+    return w, K.inv_diag(w, shape)
+
+
+def _tol(dtype):
+    return 1e-13 if dtype == torch.float64 else 1e-5
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_face_weights_and_inverse_diagonal(cuda_device, shape):
+    beta, _, _, h = _case(shape, 1)
+    w = K.face_weights(_t(beta, cuda_device), h)
+    faces = O.face_beta(beta)
+    for wt, fo, kind in zip(w, faces, "xyz"):
+        got = K.get(wt, shape, kind).cpu().numpy()
+        want = fo / h ** 2
+        assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-15
+    invD = K.get(K.inv_diag(w, shape), shape).cpu().numpy()
+    bx, by, bz = faces
+    D = (bx[:, :, :-1] + bx[:, :, 1:] + by[:, :-1, :] + by[:, 1:, :] + bz[:-1] + bz[1:]) / h ** 2
+    assert np.max(np.abs(invD * D - 1.0)) <= 1e-14
+
+
+@pytest.mark.parametrize("shape", EVEN)
+def test_coarsened_weights(cuda_device, shape):
+    beta, _, _, h = _case(shape, 2)
+    w = K.face_weights(_t(beta, cuda_device), h)
+    cw = K.coarsen_weights(w, shape)
+    c = tuple(s // 2 for s in shape)
+    for wt, fo, kind in zip(cw, O.coarsen_faces(*O.face_beta(beta)), "xyz"):
+        got = K.get(wt, c, kind).cpu().numpy()
+        want = fo / (2 * h) ** 2
+        assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-14
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_single_colour_passes(cuda_device, shape, dtype):
+    beta, f, phi, h = _case(shape, 3)
+    w, invD = _weights(beta, h, shape, cuda_device, dtype)
+    ft = _level(shape, f, cuda_device, dtype)
+    pt = _level(shape, phi, cuda_device, dtype)
+    faces = O.face_beta(beta)
+    ref = phi
+    for color in (0, 1):
+        K.rbgs_pass(w, invD, ft, pt, shape, color)
+        ref = O.rbgs_pass(faces, h, f, ref, color)
+        got = K.get(pt, shape).cpu().double().numpy()
+        scale = np.max(np.abs(ref)) + np.max(np.abs(f)) * h * h / np.min(faces[0])
+        assert np.max(np.abs(got - ref)) <= _tol(dtype) * scale, color
+    # the guard cells around the box stay zero
+    full = pt.cpu()
+    assert not full[0].any() and not full[-1].any()
+    assert not full[:, shape[1]].any() and not full[:, :, shape[2]:].any()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fused_sweep_equals_red_then_black(cuda_device, shape, dtype):
+    beta, f, phi, h = _case(shape, 4)
+    w, invD = _weights(beta, h, shape, cuda_device, dtype)
+    ft = _level(shape, f, cuda_device, dtype)
+    pin = _level(shape, phi, cuda_device, dtype)
+    before = pin.clone()
+    out = K.rbgs_sweep(w, invD, ft, pin, shape)
+    assert torch.equal(pin, before)  # out of place
+    faces = O.face_beta(beta)
+    ref = O.rbgs_pass(faces, h, f, O.rbgs_pass(faces, h, f, phi, 0), 1)
+    got = K.get(out, shape).cpu().double().numpy()
+    scale = np.max(np.abs(ref)) + np.max(np.abs(f)) * h * h / np.min(faces[0])
+    assert np.max(np.abs(got - ref)) <= _tol(dtype) * scale
+    # and equals the two single-colour passes on the GPU
+    p2 = _level(shape, phi, cuda_device, dtype)
+    K.rbgs_pass(w, invD, ft, p2, shape, 0)
+    K.rbgs_pass(w, invD, ft, p2, shape, 1)
+    assert torch.allclose(K.get(out, shape), K.get(p2, shape), rtol=0,
+                          atol=_tol(dtype) * scale)
+    full = out.cpu()
+    assert not full[0].any() and not full[-1].any() and not full[:, :, shape[2]:].any()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_residual_and_norm(cuda_device, shape, dtype):
+    beta, f, phi, h = _case(shape, 5)
+    w, _ = _weights(beta, h, shape, cuda_device, dtype)
+    ft = _level(shape, f, cuda_device, dtype)
+    pt = _level(shape, phi, cuda_device, dtype)
+    faces = O.face_beta(beta)
+    ref = O.residual(faces, h, f, phi)
+    got = K.get(K.residual(w, ft, pt, shape), shape).cpu().double().numpy()
+    scale = np.max(np.abs(f)) + 2 * 6 * np.max(faces[0]) / h ** 2 * np.max(np.abs(phi))
+    assert np.max(np.abs(got - ref)) <= _tol(dtype) * scale
+    nrm = K.residual_norm(w, ft, pt, shape).item()
+    want = O.norm2(ref)
+    assert abs(nrm - want) <= _tol(dtype) * scale * np.sqrt(ref.size)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", EVEN)
+def test_residual_restrict_and_prolong(cuda_device, shape, dtype):
+    beta, f, phi, h = _case(shape, 6)
+    w, _ = _weights(beta, h, shape, cuda_device, dtype)
+    ft = _level(shape, f, cuda_device, dtype)
+    pt = _level(shape, phi, cuda_device, dtype)
+    faces = O.face_beta(beta)
+    c = tuple(s // 2 for s in shape)
+    fc, phic = K.residual_restrict(w, ft, pt, shape)
+    ref = O.restrict(O.residual(faces, h, f, phi))
+    got = K.get(fc, c).cpu().double().numpy()
+    scale = np.max(np.abs(f)) + 2 * 6 * np.max(faces[0]) / h ** 2 * np.max(np.abs(phi))
+    assert np.max(np.abs(got - ref)) <= _tol(dtype) * scale
+    assert not K.get(phic, c).any()
+    # prolongation: phi += coarse value of the parent
+    e = np.random.default_rng(7).uniform(-1, 1, c)
+    et = _level(c, e, cuda_device, dtype)
+    K.prolong_add(et, pt, shape)
+    want = O.prolong_add(e, phi)
+    got = K.get(pt, shape).cpu().double().numpy()
+    assert np.max(np.abs(got - want)) <= _tol(dtype) * 2
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (3, 8, 8), (7, 3, 5), (4, 16, 16)])
+def test_coarsest_level_inverse_and_solve(cuda_device, shape):
+    beta, f, _, h = _case(shape, 8)
+    w = K.face_weights(_t(beta, cuda_device), h)
+    ainv = K.bottom_inverse(w, shape)
+    A = O.dense_matrix(O.face_beta(beta), h, shape)
+    got = ainv.cpu().numpy()
+    want = np.linalg.inv(A)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    for dtype in (torch.float64, torch.float32):
+        ft = _level(shape, f, cuda_device, dtype)
+        phi = K.bottom_solve(ainv.to(dtype), ft, shape)
+        x = np.linalg.solve(A, f.ravel()).reshape(shape)
+        g = K.get(phi, shape).cpu().double().numpy()
+        assert np.max(np.abs(g - x)) <= (1e-12 if dtype == torch.float64 else 1e-5) * \
+            np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("shape", [(5, 7, 9), (20, 17, 33), (70, 20, 130)])
+def test_refinement_step(cuda_device, shape):
+    beta, f, x, h = _case(shape, 9)
+    w = K.face_weights(_t(beta, cuda_device), h)
+    e = np.random.default_rng(10).uniform(-1, 1, shape).astype(np.float32)
+    c_e, c_r = 0.37, 2.5
+    x_out, r32, nrm = K.refine(w, _level(shape, f, cuda_device), _level(shape, x, cuda_device),
+                               _level(shape, e, cuda_device, torch.float32), c_e, c_r, shape)
+    faces = O.face_beta(beta)
+    xo = x + c_e * e.astype(np.float64)
+    r = O.residual(faces, h, f, xo)
+    gx = K.get(x_out, shape).cpu().numpy()
+    assert np.max(np.abs(gx - xo)) <= 1e-15 * np.max(np.abs(xo))
+    scale = np.max(np.abs(f)) + 12 * np.max(faces[0]) / h ** 2 * np.max(np.abs(xo))
+    gr = K.get(r32, shape).cpu().double().numpy()
+    assert np.max(np.abs(gr - r / c_r)) <= 1e-13 * scale / c_r + 6e-8 * np.max(np.abs(r / c_r))
+    assert abs(nrm.item() - O.norm2(r)) <= 1e-13 * scale * np.sqrt(r.size)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 7, 9), (20, 17, 33)])
+def test_beta_gradient_assembly(cuda_device, shape):
+    beta, _, phi, h = _case(shape, 11)
+    lam = np.random.default_rng(12).uniform(-1, 1, shape)
+    got = K.beta_grad(_t(beta, cuda_device), _t(phi, cuda_device), _t(lam, cuda_device), h)
+    want = O.beta_grad(beta, h, phi, lam)
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(got.cpu().numpy() - want)) <= 1e-13 * scale

@@ -1,0 +1,209 @@
+"""Whole solves through the C ABI against the CPU oracle (GPU).
+
+Parity bar for a solve: the GPU solution phi must satisfy
+||f - A phi|| <= tol ||f|| with the residual computed by the oracle's own
+operator, and (where the oracle solve at relative residual 1e-13 is
+affordable) ||phi - phi_oracle|| <= 1e-9 ||phi_oracle||.  Full-size cases
+use the residual property, which holds at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_2801_gb300 import BatchSolver, MGError, Solver, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _dev(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def _rel_resid(beta, f, phi, h):
+    r = O.residual(O.face_beta(beta), h, f, phi)
+    return O.norm2(r) / O.norm2(f)
+
+
+def _solve(beta, f, h, dev, precision="fp64", tol=TOL, **kw):
+    shape = f.shape
+    with Solver(shape, h, precision=precision, device=dev, **kw) as s:
+        s.set_beta(_dev(beta, dev))
+        phi, st = s.solve(_dev(f, dev), tol=tol)
+        return phi.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_manufactured_64(cuda_device, precision):
+    d = inputs.manufactured(64)
+    phi, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, precision)
+    assert st["status"] == "ok" and st["rel_resid"] <= TOL
+    assert _rel_resid(d["beta"], d["f"], phi, d["dx"]) <= TOL * 1.01
+    ref, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-13)
+    assert np.linalg.norm(phi - ref) <= 1e-9 * np.linalg.norm(ref)
+    # both carry the same discretisation error against the exact solution
+    e_gpu = np.max(np.abs(phi - d["phi_exact"]))
+    e_ref = np.max(np.abs(ref - d["phi_exact"]))
+    assert abs(e_gpu - e_ref) <= 1e-6 * e_ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(10, 6, 14), (24, 40, 56), (64, 64, 64), (16, 32, 128)])
+def test_stellar_reduced(cuda_device, shape, precision):
+    nz, ny, nx = shape
+    d = inputs.stellar((nx, ny, nz), 2)
+    phi, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, precision)
+    assert st["status"] == "ok"
+    assert _rel_resid(d["beta"], d["f"], phi, d["dx"]) <= TOL * 1.01
+    ref, _ = O.solve(d["beta"], d["f"], d["dx"], tol=1e-13)
+    assert np.linalg.norm(phi - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stellar_256_full_size(cuda_device, precision):
+    d = inputs.config(2)
+    phi, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, precision)
+    assert st["status"] == "ok"
+    assert _rel_resid(d["beta"], d["f"], phi, d["dx"]) <= TOL * 1.01
+    ref, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-13)
+    assert info["status"] == "ok"
+    assert np.linalg.norm(phi - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_stellar_512_full_size_mixed_and_fp64(cuda_device):
+    d = inputs.config(3)
+    out = {}
+    for precision in ("mixed", "fp64"):
+        phi, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, precision)
+        assert st["status"] == "ok", st
+        assert _rel_resid(d["beta"], d["f"], phi, d["dx"]) <= TOL * 1.01
+        out[precision] = phi
+    # two independent solves at 1e-10 agree far below the 1e-9 bar
+    diff = np.linalg.norm(out["mixed"] - out["fp64"]) / np.linalg.norm(out["fp64"])
+    assert diff <= 1e-9
+
+
+def test_initial_guess_and_zero_rhs(cuda_device):
+    d = inputs.stellar(16, 3)
+    beta = _dev(d["beta"], cuda_device)
+    with Solver((16, 16, 16), d["dx"], device=cuda_device) as s:
+        s.set_beta(beta)
+        phi, st = s.solve(_dev(d["f"], cuda_device))
+        assert st["status"] == "ok"
+        # starting from the solution converges at once
+        phi2, st2 = s.solve(_dev(d["f"], cuda_device), phi=phi.clone())
+        assert st2["cycles"] == 0 and torch.equal(phi2, phi)
+        z, st3 = s.solve(torch.zeros_like(phi), phi=torch.ones_like(phi))
+        assert st3["status"] == "ok" and not z.any()
+
+
+def test_host_buffers_match_device_buffers(cuda_device):
+    d = inputs.stellar((20, 12, 36), 4)
+    shape = d["f"].shape
+    with Solver(shape, d["dx"], device=cuda_device) as s:
+        s.set_beta(torch.from_numpy(d["beta"]))   # host beta
+        ph, st = s.solve(torch.from_numpy(d["f"].copy()))
+        pd, _ = s.solve(_dev(d["f"], cuda_device))
+        assert st["status"] == "ok"
+        assert torch.equal(ph, pd.cpu())
+        pin = torch.from_numpy(d["f"].copy()).pin_memory()
+        pp, _ = s.solve(pin)
+        assert torch.equal(pp, pd.cpu())
+
+
+def test_graph_and_smoother_options_agree(cuda_device):
+    d = inputs.stellar(32, 5)
+    base, _ = _solve(d["beta"], d["f"], d["dx"], cuda_device)
+    nog, _ = _solve(d["beta"], d["f"], d["dx"], cuda_device, use_graph=False)
+    assert np.array_equal(base, nog)
+    passes, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, smoother="passes")
+    assert st["status"] == "ok"
+    assert np.linalg.norm(passes - base) <= 1e-9 * np.linalg.norm(base)
+    odd, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, nu1=3, nu2=1)
+    assert st["status"] == "ok"
+    assert np.linalg.norm(odd - base) <= 1e-9 * np.linalg.norm(base)
+
+
+def test_deterministic_run_to_run(cuda_device):
+    d = inputs.stellar(48, 6)
+    a, _ = _solve(d["beta"], d["f"], d["dx"], cuda_device)
+    b, _ = _solve(d["beta"], d["f"], d["dx"], cuda_device)
+    assert np.array_equal(a, b)
+
+
+def test_faults_are_reported_not_raised_on_device(cuda_device):
+    d = inputs.stellar(16, 7)
+    beta = _dev(d["beta"], cuda_device)
+    f = _dev(d["f"], cuda_device)
+    with Solver((16, 16, 16), d["dx"], device=cuda_device, max_cycles=2) as s:
+        with pytest.raises(MGError) as ei:
+            s.solve(f)                   # beta not set yet
+        assert ei.value.name == "invalid_arg"
+        s.set_beta(beta)
+        phi, st = s.solve(f)             # two cycles are not enough
+        assert st["status"] == "not_converged" and st["cycles"] == 2
+        assert st["hist"][2] < st["hist"][1] < 1.0
+        assert _rel_resid(d["beta"], d["f"], phi.cpu().numpy(), d["dx"]) == \
+            pytest.approx(st["rel_resid"], rel=1e-6)
+        bad = f.clone()
+        bad[3, 4, 5] = float("nan")
+        with pytest.raises(MGError) as ei:
+            s.solve(bad)
+        assert ei.value.name == "nonfinite"
+        with pytest.raises(MGError) as ei:
+            s.solve(f, tol=0.0)
+        assert ei.value.name == "invalid_arg"
+    with pytest.raises(MGError) as ei:
+        Solver((33, 33, 33), 1 / 33, device=cuda_device)
+    assert ei.value.name == "unsupported"
+    with pytest.raises(MGError) as ei:
+        Solver((8, 8, 8), -1.0, device=cuda_device)
+    assert ei.value.name == "invalid_arg"
+
+
+def test_multi_rhs_matches_single(cuda_device):
+    d = inputs.stellar(24, 8, nrhs=3)
+    with Solver((24, 24, 24), d["dx"], device=cuda_device) as s:
+        s.set_beta(_dev(d["beta"], cuda_device))
+        fb = _dev(d["f_batch"], cuda_device)
+        phis, sts = s.solve(fb)
+        assert all(st["status"] == "ok" for st in sts)
+        for b in range(3):
+            one, _ = s.solve(fb[b].contiguous())
+            assert torch.equal(one, phis[b])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_reduced_vs_oracle(cuda_device, precision):
+    d = inputs.batched(12, 40, sizes=(8, 12, 16, 24, 32), dx=1 / 32)
+    shapes = [tuple(int(v) for v in dims[::-1]) for dims in d["dims"]]
+    bs = BatchSolver(shapes, d["dx"], precision=precision, device=cuda_device)
+    bs.set_beta(_dev(np.concatenate([b.ravel() for b in d["beta"]]), cuda_device))
+    f = _dev(np.concatenate([x.ravel() for x in d["f"]]), cuda_device)
+    phi, sts = bs.solve(f, tol=TOL)
+    parts = bs.unpack(phi.cpu())
+    for b in range(len(shapes)):
+        assert sts[b]["status"] == "ok"
+        ref, _ = O.solve(d["beta"][b], d["f"][b], d["dx"], tol=1e-13)
+        got = parts[b].numpy()
+        assert _rel_resid(d["beta"][b], d["f"][b], got, d["dx"]) <= TOL * 1.01
+        assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+    bs.close()
+
+
+def test_batched_full_size(cuda_device):
+    d = inputs.config(4)
+    shapes = [tuple(int(v) for v in dims[::-1]) for dims in d["dims"]]
+    for precision in ("fp64", "mixed"):
+        bs = BatchSolver(shapes, d["dx"], precision=precision, device=cuda_device)
+        bs.set_beta(_dev(np.concatenate([b.ravel() for b in d["beta"]]), cuda_device))
+        f = _dev(np.concatenate([x.ravel() for x in d["f"]]), cuda_device)
+        phi, sts = bs.solve(f, tol=TOL)
+        parts = bs.unpack(phi.cpu())
+        for b in range(0, len(shapes), 7):
+            assert sts[b]["status"] == "ok"
+            assert _rel_resid(d["beta"][b], d["f"][b], parts[b].numpy(), d["dx"]) <= TOL * 1.01
+        assert all(s["status"] == "ok" for s in sts)
+        bs.close()
