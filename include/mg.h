@@ -82,7 +82,11 @@ typedef struct {
     int use_graph;    /* 1 (default): replay each V-cycle as a captured CUDA graph */
     int smoother;     /* 0 auto (default), 1 single-colour in-place passes,
                          2 fused two-colour out-of-place sweeps */
-    int reserved[10];
+    int coarse_cells; /* levels of at most this many cells run inside one CTA
+                         per box (the coarse end of the V-cycle as a single
+                         launch); 0 default (4096 in FP32 V-cycles, 1024 in
+                         FP64 ones, whose FP64 rate per SM is low), -1 off */
+    int reserved[9];
 } mg_opts;
 
 typedef struct {

@@ -49,9 +49,10 @@ int mg_op_coarsen_weights(const int n_fine[3], const double *wx, const double *w
                           const double *wz, double *cwx, double *cwy, double *cwz,
                           void *stream);
 
-/* invD = 1 / (sum of the 6 face weights of each cell), FP64. */
+/* D = sum of the 6 face weights of each cell (the negated diagonal of A),
+ * invD = 1 / D, FP64.  D may be NULL. */
 int mg_op_inv_diag(const int n[3], const double *wx, const double *wy, const double *wz,
-                   double *invD, void *stream);
+                   double *invD, double *D, void *stream);
 
 /* Round FP64 level arrays to FP32 (weights and inverse diagonal). */
 int mg_op_round_f32(const int n[3], const double *wx, const double *wy, const double *wz,
@@ -63,22 +64,27 @@ int mg_op_round_f32(const int n[3], const double *wx, const double *wy, const do
 int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
                     const void *invD, const void *f, void *phi, int color, void *stream);
 
-/* One full red-then-black sweep as the solver runs it by default (fused,
- * out of place: reads phi_in, writes phi_out; phi_in is not modified).
- * Equal to a red pass followed by a black pass. */
+/* One full red-then-black sweep as the solver runs it on large levels
+ * (fused, out of place: reads phi_in, writes phi_out; phi_in is not
+ * modified).  Equal to a red pass followed by a black pass.  Each CTA marches
+ * through zc planes (zc <= 0: 32). */
 int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                     const void *invD, const void *f, const void *phi_in, void *phi_out,
+                     const void *invD, const void *f, const void *phi_in, void *phi_out, int zc,
                      void *stream);
+
+/* In the residual stages below, D (nullable) is the stored diagonal of
+ * mg_op_inv_diag in the stage precision; when NULL it is summed from the six
+ * weights of each cell. */
 
 /* r = f - A phi (cell array). */
 int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                   const void *f, const void *phi, void *r, void *stream);
+                   const void *D, const void *f, const void *phi, void *r, void *stream);
 
 /* Fused residual and restriction of an all-even level n: fc = mean over the
  * 8 children of (f - A phi); phic (coarse solution) is set to zero. */
 int mg_op_residual_restrict(int prec, const int n_fine[3], const void *wx, const void *wy,
-                            const void *wz, const void *f, const void *phi, void *fc,
-                            void *phic, void *stream);
+                            const void *wz, const void *D, const void *f, const void *phi,
+                            void *fc, void *phic, void *stream);
 
 /* phi += coarse value of each cell's parent (piecewise-constant
  * prolongation) for an all-even fine level n. */
@@ -100,18 +106,19 @@ int mg_op_bottom_solve(int prec, const int n[3], const void *Ainv, const void *f
  * mg_op_norm_scratch(n) doubles. */
 long long mg_op_norm_scratch(const int n[3]);
 int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy,
-                        const void *wz, const void *f, const void *phi, double *partials,
-                        double *out, void *stream);
+                        const void *wz, const void *D, const void *f, const void *phi,
+                        double *partials, double *out, void *stream);
 
-/* Mixed-precision refinement step on the finest level (FP64 x, f, weights;
- * FP32 correction e and scaled residual r32):
- *   x_out = x_in + (*c_e) e;  r = f - A64 x_out;  r32 = r / (*c_r);
- *   *out = ||r||_2 (fixed-order reduction through `partials`).
- * c_e and c_r are device doubles.  x_in and x_out must differ. */
+/* Mixed-precision refinement step on the finest level (FP64 x, f, weights,
+ * D; FP32 correction e and scaled residual r32):
+ *   x += (*c_e) e  (in place);  r = f - A64 x;  r32 = float(r) * float(1/(*c_r));
+ *   *out = (*c_r) * ||r32||_2  (= ||r||_2 to FP32 accuracy; fixed-order
+ *   reduction through `partials`).
+ * c_e and c_r are device doubles, c_r > 0. */
 int mg_op_refine(const int n[3], const double *wx, const double *wy, const double *wz,
-                 const double *f, const double *x_in, double *x_out, const float *e,
-                 float *r32, const double *c_e, const double *c_r, double *partials,
-                 double *out, void *stream);
+                 const double *D, const double *f, double *x, const float *e, float *r32,
+                 const double *c_e, const double *c_r, double *partials, double *out,
+                 void *stream);
 
 /* Beta gradient of one right-hand side (see mg_adjoint): dbeta += chain of
  * the face products of phi and lambda.  beta, phi, lambda, dbeta are

@@ -38,7 +38,8 @@ STATUS_NAMES = {
 
 class mg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("max_cycles", c_int),
-                ("use_graph", c_int), ("smoother", c_int), ("reserved", c_int * 10)]
+                ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
+                ("reserved", c_int * 9)]
 
 
 class mg_stats(ctypes.Structure):
@@ -88,17 +89,17 @@ _SIGS = {
     "mg_op_face_weights": (c_int, [c_int3, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p]),
     "mg_op_coarsen_weights": (c_int, [c_int3] + [c_void_p] * 7),
-    "mg_op_inv_diag": (c_int, [c_int3] + [c_void_p] * 5),
+    "mg_op_inv_diag": (c_int, [c_int3] + [c_void_p] * 6),
     "mg_op_round_f32": (c_int, [c_int3] + [c_void_p] * 9),
     "mg_op_rbgs_pass": (c_int, [c_int, c_int3] + [c_void_p] * 6 + [c_int, c_void_p]),
-    "mg_op_rbgs_sweep": (c_int, [c_int, c_int3] + [c_void_p] * 8),
-    "mg_op_residual": (c_int, [c_int, c_int3] + [c_void_p] * 7),
-    "mg_op_residual_restrict": (c_int, [c_int, c_int3] + [c_void_p] * 8),
+    "mg_op_rbgs_sweep": (c_int, [c_int, c_int3] + [c_void_p] * 7 + [c_int, c_void_p]),
+    "mg_op_residual": (c_int, [c_int, c_int3] + [c_void_p] * 8),
+    "mg_op_residual_restrict": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_prolong_add": (c_int, [c_int, c_int3, c_void_p, c_void_p, c_void_p]),
     "mg_op_bottom_inverse": (c_int, [c_int3] + [c_void_p] * 6),
     "mg_op_bottom_solve": (c_int, [c_int, c_int3] + [c_void_p] * 4),
     "mg_op_norm_scratch": (c_ll, [c_int3]),
-    "mg_op_residual_norm": (c_int, [c_int, c_int3] + [c_void_p] * 8),
+    "mg_op_residual_norm": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_refine": (c_int, [c_int3] + [c_void_p] * 13),
     "mg_op_beta_grad": (c_int, [c_int3, c_double] + [c_void_p] * 5),
 }

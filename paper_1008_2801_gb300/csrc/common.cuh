@@ -24,7 +24,8 @@ constexpr int MG_BOTTOM_CELLS = MG_MAX_BOTTOM;  // dense coarsest-level limit
 constexpr int kTX = 32;   // tile width  (threads along x)
 constexpr int kTY = 8;    // tile height (threads along y)
 constexpr int kThreads = kTX * kTY;
-constexpr int kSweepZ = 32;   // planes per CTA of the fused red-black sweep
+constexpr int kSweepZ = 32;   // default planes per CTA of the fused red-black sweep
+constexpr int kColZ = 16;     // planes per thread of the column kernels (norms)
 
 inline __host__ __device__ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 inline __host__ __device__ long long pitch_row(int nx) { return round_up((long long)nx + 1, 8); }
@@ -42,6 +43,7 @@ struct Box {
     T *f;            // right-hand side
     const T *wx, *wy, *wz;   // face weights beta_face / h^2
     const T *invD;   // 1 / sum of the six weights
+    const T *D;      // sum of the six weights (FP64 levels; NULL: summed on the fly)
     const T *ainv;   // coarsest level only: dense A^{-1}, row-major n x n
     T *phic;         // next-coarser level solution (zeroed by restriction)
     T *fc;           // next-coarser level right-hand side
@@ -51,26 +53,30 @@ struct Box {
     int cP;          // coarse row pitch
     long long cQ;    // coarse plane pitch
     int box;         // index of the box in its batch
+    int zc;          // planes per CTA of the fused sweep (chosen on the host)
 };
 
 // Index spaces that kernels tile: all cells, red-black pairs along x
-// (ceil(nx/2) per row), the cells of the next-coarser level, or pairs along x
-// with z cut into chunks of kSweepZ planes (the fused sweep marches in z).
-enum TileKind { TK_CELL = 0, TK_PAIR = 1, TK_COARSE = 2, TK_SWEEP = 3, TK_NKIND = 4 };
+// (ceil(nx/2) per row), the cells of the next-coarser level, pairs along x
+// with z cut into chunks of kSweepZ planes (the fused sweep marches in z), or
+// cells with z cut into chunks of kColZ planes (one thread per column chunk).
+enum TileKind { TK_CELL = 0, TK_PAIR = 1, TK_COARSE = 2, TK_SWEEP = 3, TK_COLZ = 4, TK_NKIND = 5 };
 
+// zc: planes per CTA of the fused sweep (TK_SWEEP only).
 inline __host__ __device__ void tile_extent(int kind, int nx, int ny, int nz, int &ex, int &ey,
-                                            int &ez)
+                                            int &ez, int zc = kSweepZ)
 {
     if (kind == TK_PAIR) { ex = (nx + 1) / 2; ey = ny; ez = nz; }
     else if (kind == TK_COARSE) { ex = nx / 2; ey = ny / 2; ez = nz / 2; }
-    else if (kind == TK_SWEEP) { ex = (nx + 1) / 2; ey = ny; ez = (nz + kSweepZ - 1) / kSweepZ; }
+    else if (kind == TK_SWEEP) { ex = (nx + 1) / 2; ey = ny; ez = (nz + zc - 1) / zc; }
+    else if (kind == TK_COLZ) { ex = nx; ey = ny; ez = (nz + kColZ - 1) / kColZ; }
     else { ex = nx; ey = ny; ez = nz; }
 }
 
-inline __host__ __device__ int tiles_of(int kind, int nx, int ny, int nz)
+inline __host__ __device__ int tiles_of(int kind, int nx, int ny, int nz, int zc = kSweepZ)
 {
     int ex, ey, ez;
-    tile_extent(kind, nx, ny, nz, ex, ey, ez);
+    tile_extent(kind, nx, ny, nz, ex, ey, ez, zc);
     return ((ex + kTX - 1) / kTX) * ((ey + kTY - 1) / kTY) * ez;
 }
 
@@ -83,6 +89,16 @@ struct BoxSet {
     const int *tstart[TK_NKIND];
     int ntiles[TK_NKIND];
     int nbox;
+};
+
+// The coarse end of one box's V-cycle, run by a single CTA: levels
+// lv[0] (the first level small enough) down to lv[nlev-1] (the coarsest).
+constexpr int kMaxCoarse = 10;
+template <class T>
+struct CoarseJob {
+    int nlev;
+    int box;
+    Box<T> lv[kMaxCoarse];
 };
 
 // Last box b with tstart[b] <= t (tstart ascending, tstart[0] = 0).
@@ -101,10 +117,11 @@ __device__ __forceinline__ int find_box(const int *__restrict__ tstart, int nbox
 struct TilePos {
     int x, y, z;
 };
-__device__ __forceinline__ TilePos tile_pos(int kind, int nx, int ny, int nz, int local)
+__device__ __forceinline__ TilePos tile_pos(int kind, int nx, int ny, int nz, int local,
+                                            int zc = kSweepZ)
 {
     int ex, ey, ez;
-    tile_extent(kind, nx, ny, nz, ex, ey, ez);
+    tile_extent(kind, nx, ny, nz, ex, ey, ez, zc);
     int ntx = (ex + kTX - 1) / kTX, nty = (ey + kTY - 1) / kTY;
     int tx = local % ntx;
     local /= ntx;

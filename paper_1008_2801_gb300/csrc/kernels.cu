@@ -49,12 +49,14 @@ __device__ __forceinline__ T gs_value(const T *__restrict__ src, const T *__rest
     return (s - f[c]) * invD[c];
 }
 
-// f_c - (A phi)_c, with the diagonal summed from the six weights.
+// f_c - (A phi)_c.  The diagonal comes from the stored D when given (FP64
+// levels: saves five FP64 adds on GB300's narrow FP64 pipe), else it is
+// summed from the six weights.
 template <class T>
 __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__restrict__ f,
                                          const T *__restrict__ wx, const T *__restrict__ wy,
-                                         const T *__restrict__ wz, long long c, int P,
-                                         long long Q)
+                                         const T *__restrict__ wz, const T *__restrict__ Dg,
+                                         long long c, int P, long long Q)
 {
     T a = wx[c], b = wx[c + 1], d = wy[c], e = wy[c + P], g = wz[c], h = wz[c + Q];
     T s = a * phi[c - 1];
@@ -63,8 +65,8 @@ __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__r
     s = fmadd(e, phi[c + P], s);
     s = fmadd(g, phi[c - Q], s);
     s = fmadd(h, phi[c + Q], s);
-    T D = ((a + b) + (d + e)) + (g + h);
-    return f[c] - (s - D * phi[c]);
+    const T D = Dg ? Dg[c] : ((a + b) + (d + e)) + (g + h);
+    return f[c] - fmadd(-D, phi[c], s);
 }
 
 template <class T>
@@ -127,14 +129,15 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_sweep(BoxSet<T> S, const int 
     const T *__restrict__ wy = B.wy;
     const T *__restrict__ wz = B.wz;
 
-    const TilePos tp = tile_pos(TK_SWEEP, nx, ny, nz, t - ts[b]);
+    const int zc = B.zc;
+    const TilePos tp = tile_pos(TK_SWEEP, nx, ny, nz, t - ts[b], zc);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = 2 * (tp.x - tx);
     const int y0 = tp.y - ty;
     const int xa = x0 + 2 * tx;
     const int y = y0 + ty;
-    const int z0 = tp.z * kSweepZ;
-    const int z1 = min(z0 + kSweepZ, nz);
+    const int z0 = tp.z * zc;
+    const int z1 = min(z0 + zc, nz);
     const bool rowin = y < ny;
 
     for (int k = z0 - 1; k <= z1; ++k) {
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const long long q = (long long)(2 * K + c) * Q + (long long)(2 * J + bb) * P + 2 * I + a;
-                sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, q, P, Q);
+                sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, q, P, Q);
             }
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
     B.fc[cc] = sum * T(0.125);
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_field(BoxSet<T> S)
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
     const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    B.phi2[c] = residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, c, B.P, B.Q);
+    B.phi2[c] = residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
 }
 
 // ------------------------------------------------------------- norms ----
@@ -276,16 +279,19 @@ __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const i
                                                             int mode, double *__restrict__ partials)
 {
     const int t = blockIdx.x;
-    const int *ts = S.tstart[TK_CELL];
+    const int *ts = S.tstart[TK_COLZ];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
     double v = 0.0;
     if (p.x < B.nx && p.y < B.ny) {
-        const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-        T r = mode ? B.f[c] : residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, c, B.P, B.Q);
-        v = (double)r * (double)r;
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+        for (int k = z0; k < z1; ++k) {
+            const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
+            const T r = mode ? B.f[c] : residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+            v = fma((double)r, (double)r, v);
+        }
     }
     double s = block_sum(v);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
@@ -298,13 +304,14 @@ __global__ void __launch_bounds__(1024) k_norm_finish(BoxSet<T> S, const int *__
                                                       const double *__restrict__ partials,
                                                       double *__restrict__ out,
                                                       double *__restrict__ copy,
-                                                      double *__restrict__ inv)
+                                                      double *__restrict__ inv,
+                                                      const double *__restrict__ mult)
 {
     __shared__ double wsum[32];
     const int b = blockIdx.x;
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    const int *ts = S.tstart[TK_CELL];
+    const int *ts = S.tstart[TK_COLZ];
     const int lo = ts[b], hi = ts[b + 1];
     double s = 0.0;
     for (int q = lo + (int)threadIdx.x; q < hi; q += 1024) s += partials[q];
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(1024) k_norm_finish(BoxSet<T> S, const int *__
     if (threadIdx.x == 0) {
         double tot = 0.0;
         for (int w = 0; w < 32; ++w) tot += wsum[w];
-        const double nrm = sqrt(tot);
+        const double nrm = mult ? sqrt(tot) * mult[B.box] : sqrt(tot);
         out[B.box] = nrm;
         if (copy) copy[B.box] = nrm;
         if (inv) inv[B.box] = nrm > 0.0 ? 1.0 / nrm : 0.0;
@@ -353,13 +360,144 @@ __global__ void __launch_bounds__(kThreads) k_bottom(BoxSet<T> S, const int *__r
     }
 }
 
-// ------------------------------------------------ mixed refinement step ----
+// --------------------------------------------- coarse V-cycle in one CTA ----
+//
+// Levels of a few thousand cells take microseconds of work but a kernel
+// launch each; the coarse end of every box's V-cycle therefore runs inside
+// one CTA per box, with block barriers between stages: nu1 red/black passes
+// and residual + restriction going down, the dense coarsest solve, then
+// prolongation and nu2 passes going up.  Same stage definitions as the
+// per-level kernels; data stay in global memory (L1/L2 resident).
 
-__global__ void __launch_bounds__(kThreads) k_refine(BoxSet<double> S64, BoxSet<float> S32,
-                                                     const int *__restrict__ active, int x_in_is_phi2,
-                                                     const double *__restrict__ c_e,
-                                                     const double *__restrict__ c_r_inv,
-                                                     double *__restrict__ partials)
+// FP32: 1024 threads; FP64: 512 (its register footprint is larger)
+template <class T>
+struct CoarseThreads { static constexpr int value = sizeof(T) == 8 ? 512 : 1024; };
+
+template <class T>
+__device__ __forceinline__ void cta_pass(const Box<T> &B, int color)
+{
+    const int npx = (B.nx + 1) >> 1;
+    const int tot = npx * B.ny * B.nz;
+    for (int q = threadIdx.x; q < tot; q += CoarseThreads<T>::value) {
+        const int p = q % npx;
+        const int r = q / npx;
+        const int j = r % B.ny, k = r / B.ny;
+        const int i = 2 * p + ((j + k + color) & 1);
+        if (i >= B.nx) continue;
+        const long long c = (long long)k * B.Q + (long long)j * B.P + i;
+        B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, B.P, B.Q);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void cta_resid_restrict(const Box<T> &B)
+{
+    const int cx = B.nx / 2, cy = B.ny / 2, cz = B.nz / 2;
+    const int tot = cx * cy * cz;
+    for (int q = threadIdx.x; q < tot; q += CoarseThreads<T>::value) {
+        const int I = q % cx, r = q / cx;
+        const int J = r % cy, K = r / cy;
+        T sum = T(0);
+        for (int c = 0; c < 2; ++c)
+            for (int bb = 0; bb < 2; ++bb)
+                for (int a = 0; a < 2; ++a) {
+                    const long long g =
+                        (long long)(2 * K + c) * B.Q + (long long)(2 * J + bb) * B.P + 2 * I + a;
+                    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, g, B.P, B.Q);
+                }
+        const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
+        B.fc[cc] = sum * T(0.125);
+        B.phic[cc] = T(0);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void cta_prolong(const Box<T> &B)
+{
+    const int tot = B.nx * B.ny * B.nz;
+    for (int q = threadIdx.x; q < tot; q += CoarseThreads<T>::value) {
+        const int i = q % B.nx, r = q / B.nx;
+        const int j = r % B.ny, k = r / B.ny;
+        const long long c = (long long)k * B.Q + (long long)j * B.P + i;
+        B.phi[c] += B.phic[(long long)(k >> 1) * B.cQ + (long long)(j >> 1) * B.cP + (i >> 1)];
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void cta_bottom(const Box<T> &B, T *fs)
+{
+    const int nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
+    for (int q = threadIdx.x; q < n; q += CoarseThreads<T>::value) {
+        const int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
+        fs[q] = B.f[(long long)k * B.Q + (long long)j * B.P + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < n; r += CoarseThreads<T>::value / 32) {
+        const T *row = B.ainv + (long long)r * n;
+        T acc = T(0);
+        for (int q = lane; q < n; q += 32) acc = fmadd(row[q], fs[q], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const int i = r % nx, j = (r / nx) % ny, k = r / (nx * ny);
+            B.phi[(long long)k * B.Q + (long long)j * B.P + i] = acc;
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const CoarseJob<T> *__restrict__ jobs,
+                                                                  const int *__restrict__ active,
+                                                                  int nu1, int nu2)
+{
+    __shared__ CoarseJob<T> J;
+    __shared__ T fs[MG_BOTTOM_CELLS];
+    {
+        const int words = (int)(sizeof(CoarseJob<T>) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(jobs + blockIdx.x);
+        int *dst = reinterpret_cast<int *>(&J);
+        for (int w = threadIdx.x; w < words; w += CoarseThreads<T>::value) dst[w] = src[w];
+    }
+    __syncthreads();
+    if (active && !active[J.box]) return;  // uniform over the CTA
+    const int nl = J.nlev;
+    for (int l = 0; l + 1 < nl; ++l) {
+        for (int s = 0; s < nu1; ++s) {
+            cta_pass<T>(J.lv[l], 0);
+            __syncthreads();
+            cta_pass<T>(J.lv[l], 1);
+            __syncthreads();
+        }
+        cta_resid_restrict<T>(J.lv[l]);
+        __syncthreads();
+    }
+    cta_bottom<T>(J.lv[nl - 1], fs);
+    __syncthreads();
+    for (int l = nl - 2; l >= 0; --l) {
+        cta_prolong<T>(J.lv[l]);
+        __syncthreads();
+        for (int s = 0; s < nu2; ++s) {
+            cta_pass<T>(J.lv[l], 0);
+            __syncthreads();
+            cta_pass<T>(J.lv[l], 1);
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------ mixed refinement step ----
+//
+// FP64 iterative refinement around FP32 V-cycles, in two passes per step:
+//   k_refine_update:   x += c_e e               (in place, pointwise)
+//   k_refine_residual: r = f - A64 x;  r32 = float(r) * float(1 / c_r);
+//                      partial sums of r32^2 (FP32 per column, FP64 per CTA)
+// so ||r|| = c_r * sqrt(sum r32^2).  Only the update, the residual and their
+// conversions use the FP64 pipe (GB300 issues 2 FP64 FMA per SM per clock
+// against 128 FP32): 11 FP64-pipe operations per cell.
+
+__global__ void __launch_bounds__(kThreads) k_refine_update(BoxSet<double> S64, BoxSet<float> S32,
+                                                            const int *__restrict__ active,
+                                                            const double *__restrict__ c_e)
 {
     const int t = blockIdx.x;
     const int *ts = S64.tstart[TK_CELL];
@@ -368,38 +506,36 @@ __global__ void __launch_bounds__(kThreads) k_refine(BoxSet<double> S64, BoxSet<
     const Box<float> &E = S32.boxes[b];
     if (active && !active[B.box]) return;
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
-    double r2 = 0.0;
+    if (p.x >= B.nx || p.y >= B.ny) return;
+    const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
+    B.phi[c] = fma(c_e[B.box], (double)E.phi[c], B.phi[c]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64, BoxSet<float> S32,
+                                                              const int *__restrict__ active,
+                                                              const double *__restrict__ c_r_inv,
+                                                              double *__restrict__ partials)
+{
+    const int t = blockIdx.x;
+    const int *ts = S64.tstart[TK_COLZ];
+    const int b = find_box(ts, S64.nbox, t);
+    const Box<double> &B = S64.boxes[b];
+    const Box<float> &E = S32.boxes[b];
+    if (active && !active[B.box]) return;
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
+    float acc = 0.f;
     if (p.x < B.nx && p.y < B.ny) {
-        const int P = B.P;
-        const long long Q = B.Q;
-        const long long c = (long long)p.z * Q + (long long)p.y * P + p.x;
-        const double *__restrict__ xi = x_in_is_phi2 ? B.phi2 : B.phi;
-        double *__restrict__ xo = x_in_is_phi2 ? B.phi : B.phi2;
-        const float *__restrict__ e = E.phi;
-        const double ce = c_e[B.box];
-        const double cri = c_r_inv[B.box];
-        const double xc = fma(ce, (double)e[c], xi[c]);
-        const double xw = fma(ce, (double)e[c - 1], xi[c - 1]);
-        const double xe = fma(ce, (double)e[c + 1], xi[c + 1]);
-        const double xs = fma(ce, (double)e[c - P], xi[c - P]);
-        const double xn = fma(ce, (double)e[c + P], xi[c + P]);
-        const double xd = fma(ce, (double)e[c - Q], xi[c - Q]);
-        const double xu = fma(ce, (double)e[c + Q], xi[c + Q]);
-        const double a = B.wx[c], bb = B.wx[c + 1], d = B.wy[c], ee = B.wy[c + P], g = B.wz[c],
-                     h = B.wz[c + Q];
-        double s = a * xw;
-        s = fma(bb, xe, s);
-        s = fma(d, xs, s);
-        s = fma(ee, xn, s);
-        s = fma(g, xd, s);
-        s = fma(h, xu, s);
-        const double D = ((a + bb) + (d + ee)) + (g + h);
-        const double r = B.f[c] - (s - D * xc);
-        xo[c] = xc;
-        E.f[c] = (float)(r * cri);
-        r2 = r * r;
+        const float cri = (float)c_r_inv[B.box];
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+        for (int k = z0; k < z1; ++k) {
+            const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
+            const double r = residual_at<double>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+            const float r32 = (float)r * cri;
+            E.f[c] = r32;
+            acc = fmaf(r32, r32, acc);
+        }
     }
-    double s = block_sum(r2);
+    double s = block_sum((double)acc);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
 }
 
@@ -526,14 +662,16 @@ __global__ void k_coarsen(int nx, int ny, int nz, int P, long long Q, const doub
 
 __global__ void k_inv_diag(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
                            const double *__restrict__ wy, const double *__restrict__ wz,
-                           double *__restrict__ invD)
+                           double *__restrict__ invD, double *__restrict__ Dout)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= nx || j >= ny || k >= nz) return;
     const long long c = (long long)k * Q + (long long)j * P + i;
-    invD[c] = 1.0 / (((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]));
+    const double D = ((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]);
+    invD[c] = 1.0 / D;
+    if (Dout) Dout[c] = D;
 }
 
 // Positions (i, j, k) in [0, nx] x [0, ny] x [0, nz]: every stored weight.
@@ -657,6 +795,20 @@ cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, c
 }
 
 template <class T>
+int sweep_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep<T>, kThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 4;
+    }
+    return n > 0 ? n : 1;
+}
+template int sweep_ctas_per_sm<double>();
+template int sweep_ctas_per_sm<float>();
+
+template <class T>
 cudaError_t launch_rbgs_sweep(const BoxSet<T> &S, const int *active, int src_is_phi2,
                               cudaStream_t st)
 {
@@ -693,17 +845,18 @@ template <class T>
 cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode, double *partials,
                                  cudaStream_t st)
 {
-    if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_norm_partials<T><<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, active, mode, partials);
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    k_norm_partials<T><<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, active, mode, partials);
     return counted(cudaGetLastError());
 }
 
 template <class T>
 cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const double *partials,
-                               double *out, double *copy, double *inv, cudaStream_t st)
+                               double *out, double *copy, double *inv, cudaStream_t st,
+                               const double *mult)
 {
     if (S.nbox == 0) return cudaSuccess;
-    k_norm_finish<T><<<S.nbox, 1024, 0, st>>>(S, active, partials, out, copy, inv);
+    k_norm_finish<T><<<S.nbox, 1024, 0, st>>>(S, active, partials, out, copy, inv, mult);
     return counted(cudaGetLastError());
 }
 
@@ -716,13 +869,30 @@ cudaError_t launch_bottom(const BoxSet<T> &S, const int *active, int max_cells, 
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_refine(const BoxSet<double> &S64, const BoxSet<float> &S32, const int *active,
-                          int x_in_is_phi2, const double *c_e, const double *c_r_inv,
-                          double *partials, cudaStream_t st)
+template <class T>
+cudaError_t launch_coarse_vcycle(const CoarseJob<T> *jobs, int njobs, const int *active, int nu1,
+                                 int nu2, cudaStream_t st)
+{
+    if (njobs == 0) return cudaSuccess;
+    k_coarse_vcycle<T><<<njobs, CoarseThreads<T>::value, 0, st>>>(jobs, active, nu1, nu2);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_refine_update(const BoxSet<double> &S64, const BoxSet<float> &S32,
+                                 const int *active, const double *c_e, cudaStream_t st)
 {
     if (S64.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_refine<<<S64.ntiles[TK_CELL], block2d(), 0, st>>>(S64, S32, active, x_in_is_phi2, c_e,
-                                                         c_r_inv, partials);
+    k_refine_update<<<S64.ntiles[TK_CELL], block2d(), 0, st>>>(S64, S32, active, c_e);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float> &S32,
+                                   const int *active, const double *c_r_inv, double *partials,
+                                   cudaStream_t st)
+{
+    if (S64.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    k_refine_residual<<<S64.ntiles[TK_COLZ], block2d(), 0, st>>>(S64, S32, active, c_r_inv,
+                                                                  partials);
     return counted(cudaGetLastError());
 }
 
@@ -782,10 +952,10 @@ cudaError_t launch_coarsen(int nx, int ny, int nz, const double *wx, const doubl
 }
 
 cudaError_t launch_inv_diag(int nx, int ny, int nz, const double *wx, const double *wy,
-                            const double *wz, double *invD, cudaStream_t st)
+                            const double *wz, double *invD, double *D, cudaStream_t st)
 {
     k_inv_diag<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, (int)pitch_row(nx),
-                                                        pitch_plane(nx, ny), wx, wy, wz, invD);
+                                                        pitch_plane(nx, ny), wx, wy, wz, invD, D);
     return counted(cudaGetLastError());
 }
 
@@ -825,9 +995,12 @@ cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double
     template cudaError_t launch_norm_partials<T>(const BoxSet<T> &, const int *, int, double *,   \
                                                  cudaStream_t);                                   \
     template cudaError_t launch_norm_finish<T>(const BoxSet<T> &, const int *, const double *,    \
-                                               double *, double *, double *, cudaStream_t);       \
+                                               double *, double *, double *, cudaStream_t,        \
+                                               const double *);                                   \
     template cudaError_t launch_bottom<T>(const BoxSet<T> &, const int *, int, cudaStream_t);   \
-    template cudaError_t launch_zero<T>(const BoxSet<T> &, const int *, cudaStream_t);
+    template cudaError_t launch_zero<T>(const BoxSet<T> &, const int *, cudaStream_t);          \
+    template cudaError_t launch_coarse_vcycle<T>(const CoarseJob<T> *, int, const int *, int, int, \
+                                                 cudaStream_t);
 
 MG_INSTANTIATE(double)
 MG_INSTANTIATE(float)

@@ -15,6 +15,10 @@ long long launch_counter();
 template <class T>
 cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, cudaStream_t st);
 
+// Resident CTAs per SM of the fused sweep kernel (occupancy query).
+template <class T>
+int sweep_ctas_per_sm();
+
 // Fused red+black sweep, out of place: Box::phi -> Box::phi2 (src_is_phi2
 // swaps the roles).
 template <class T>
@@ -43,21 +47,30 @@ cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode
 // out[Box::box] = sqrt(sum of the box's partials), fixed order; inactive
 // boxes keep their old value.  copy and inv (nullable) receive the same value
 // and its reciprocal (0 for a zero norm).
+// mult (nullable, per box) scales the norm before it is stored.
 template <class T>
 cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const double *partials,
-                               double *out, double *copy, double *inv, cudaStream_t st);
+                               double *out, double *copy, double *inv, cudaStream_t st,
+                               const double *mult = nullptr);
 
 // Coarsest level: phi = Ainv f (dense, one warp per row).
 template <class T>
 cudaError_t launch_bottom(const BoxSet<T> &S, const int *active, int max_cells, cudaStream_t st);
 
-// Mixed-precision refinement on the finest level of every box:
-// x_out = x_in + c_e[b] e; r = f - A x_out; r32 = r * c_r_inv[b]; partial sums
-// of r^2.  S64: phi/phi2 = x_in/x_out (swapped by x_in_is_phi2), f, weights.
-// S32: phi = e, f = r32.
-cudaError_t launch_refine(const BoxSet<double> &S64, const BoxSet<float> &S32, const int *active,
-                          int x_in_is_phi2, const double *c_e, const double *c_r_inv,
-                          double *partials, cudaStream_t st);
+// The coarse end of the V-cycle of each job's box in one CTA per job.
+template <class T>
+cudaError_t launch_coarse_vcycle(const CoarseJob<T> *jobs, int njobs, const int *active, int nu1,
+                                 int nu2, cudaStream_t st);
+
+// Mixed-precision refinement on the finest level of every box (FP64 phi = x,
+// f, weights, D in S64; FP32 phi = e, f = r32 in S32):
+//   update:   x += c_e[b] e
+//   residual: r = f - A x; r32 = r * c_r_inv[b]; partial sums of r32^2
+cudaError_t launch_refine_update(const BoxSet<double> &S64, const BoxSet<float> &S32,
+                                 const int *active, const double *c_e, cudaStream_t st);
+cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float> &S32,
+                                   const int *active, const double *c_r_inv, double *partials,
+                                   cudaStream_t st);
 
 // ---- moving data between packed user arrays and the level layout --------
 // user[off[b] + (k*ny + j)*nx + i] -> level 0 f (to_f) or phi of box b.
@@ -81,8 +94,9 @@ cudaError_t launch_face_weights(int nx, int ny, int nz, double inv_h2, const dou
 cudaError_t launch_coarsen(int nx, int ny, int nz, const double *wx, const double *wy,
                            const double *wz, double *cwx, double *cwy, double *cwz,
                            cudaStream_t st);
+// invD = 1 / D and (D nullable) D = sum of the six weights.
 cudaError_t launch_inv_diag(int nx, int ny, int nz, const double *wx, const double *wy,
-                            const double *wz, double *invD, cudaStream_t st);
+                            const double *wz, double *invD, double *D, cudaStream_t st);
 cudaError_t launch_round_f32(int nx, int ny, int nz, const double *wx, const double *wy,
                              const double *wz, const double *invD, float *wx32, float *wy32,
                              float *wz32, float *invD32, cudaStream_t st);

@@ -48,7 +48,7 @@ struct TempSet {
         S.nbox = 1;
         for (int k = 0; k < TK_NKIND; ++k) {
             h.ts[k][0] = 0;
-            h.ts[k][1] = tiles_of(k, B.nx, B.ny, B.nz);
+            h.ts[k][1] = tiles_of(k, B.nx, B.ny, B.nz, B.zc);
             S.ntiles[k] = h.ts[k][1];
         }
         CKO(cudaMallocAsync(&mem, sizeof h, st));
@@ -81,6 +81,7 @@ Box<T> level_box(const int n[3], const void *wx, const void *wy, const void *wz,
     B.f = logical<T>(f, n);
     B.phi = logical<T>(phi, n);
     B.phi2 = logical<T>(phi2, n);
+    B.zc = kSweepZ;
     return B;
 }
 
@@ -131,12 +132,13 @@ int mg_op_coarsen_weights(const int n[3], const double *wx, const double *wy, co
 }
 
 int mg_op_inv_diag(const int n[3], const double *wx, const double *wy, const double *wz,
-                   double *invD, void *stream)
+                   double *invD, double *D, void *stream)
 {
     if (bad_dims(n) || !wx || !wy || !wz || !invD)
         return set_error(MG_ERR_INVALID_ARG, "bad argument");
     CKO(launch_inv_diag(n[0], n[1], n[2], logical<double>(wx, n), logical<double>(wy, n),
-                        logical<double>(wz, n), logical<double>(invD, n), (cudaStream_t)stream));
+                        logical<double>(wz, n), logical<double>(invD, n), logical<double>(D, n),
+                        (cudaStream_t)stream));
     return MG_OK;
 }
 
@@ -180,7 +182,7 @@ int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, co
 }
 
 int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                     const void *invD, const void *f, const void *phi_in, void *phi_out,
+                     const void *invD, const void *f, const void *phi_in, void *phi_out, int zc,
                      void *stream)
 {
     if (bad_dims(n) || !wx || !wy || !wz || !invD || !f || !phi_in || !phi_out ||
@@ -188,6 +190,7 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
         return set_error(MG_ERR_INVALID_ARG, "bad argument (phi_in and phi_out must differ)");
     DISPATCH(prec, {
         Box<T> B = level_box<T>(n, wx, wy, wz, invD, f, phi_in, phi_out);
+        B.zc = zc > 0 ? zc : kSweepZ;
         return with_set(B, (cudaStream_t)stream, [&](const BoxSet<T> &S) {
             return launch_rbgs_sweep(S, nullptr, 0, (cudaStream_t)stream);
         });
@@ -195,12 +198,13 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
 }
 
 int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                   const void *f, const void *phi, void *r, void *stream)
+                   const void *D, const void *f, const void *phi, void *r, void *stream)
 {
     if (bad_dims(n) || !wx || !wy || !wz || !f || !phi || !r)
         return set_error(MG_ERR_INVALID_ARG, "bad argument");
     DISPATCH(prec, {
         Box<T> B = level_box<T>(n, wx, wy, wz, nullptr, f, phi, r);
+        B.D = logical<T>(D, n);
         return with_set(B, (cudaStream_t)stream, [&](const BoxSet<T> &S) {
             return launch_residual_field(S, (cudaStream_t)stream);
         });
@@ -208,14 +212,15 @@ int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, con
 }
 
 int mg_op_residual_restrict(int prec, const int n[3], const void *wx, const void *wy,
-                            const void *wz, const void *f, const void *phi, void *fc, void *phic,
-                            void *stream)
+                            const void *wz, const void *D, const void *f, const void *phi,
+                            void *fc, void *phic, void *stream)
 {
     if (bad_dims(n) || !all_even(n) || !wx || !wy || !wz || !f || !phi || !fc || !phic)
         return set_error(MG_ERR_INVALID_ARG, "bad argument (fine dims must be even)");
     const int c[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
     DISPATCH(prec, {
         Box<T> B = level_box<T>(n, wx, wy, wz, nullptr, f, phi, nullptr);
+        B.D = logical<T>(D, n);
         B.fc = logical<T>(fc, c);
         B.phic = logical<T>(phic, c);
         B.cP = (int)pitch_row(c[0]);
@@ -275,13 +280,14 @@ long long mg_op_norm_scratch(const int n[3])
 }
 
 int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                        const void *f, const void *phi, double *partials, double *out,
-                        void *stream)
+                        const void *D, const void *f, const void *phi, double *partials,
+                        double *out, void *stream)
 {
     if (bad_dims(n) || !wx || !wy || !wz || !f || !phi || !partials || !out)
         return set_error(MG_ERR_INVALID_ARG, "bad argument");
     DISPATCH(prec, {
         Box<T> B = level_box<T>(n, wx, wy, wz, nullptr, f, phi, nullptr);
+        B.D = logical<T>(D, n);
         return with_set(B, (cudaStream_t)stream, [&](const BoxSet<T> &S) {
             cudaError_t e = launch_norm_partials(S, nullptr, 0, partials, (cudaStream_t)stream);
             if (e != cudaSuccess) return e;
@@ -292,15 +298,17 @@ int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy
 }
 
 int mg_op_refine(const int n[3], const double *wx, const double *wy, const double *wz,
-                 const double *f, const double *x_in, double *x_out, const float *e, float *r32,
+                 const double *D, const double *f, double *x, const float *e, float *r32,
                  const double *c_e, const double *c_r, double *partials, double *out,
                  void *stream)
 {
-    if (bad_dims(n) || !wx || !wy || !wz || !f || !x_in || !x_out || !e || !r32 || !c_e || !c_r ||
-        !partials || !out || x_in == x_out)
-        return set_error(MG_ERR_INVALID_ARG, "bad argument (x_in and x_out must differ)");
+    if (bad_dims(n) || !wx || !wy || !wz || !f || !x || !e || !r32 || !c_e || !c_r ||
+        !partials || !out)
+        return set_error(MG_ERR_INVALID_ARG, "bad argument");
+    cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
-    Box<double> B = level_box<double>(n, wx, wy, wz, nullptr, f, x_in, x_out);
+    Box<double> B = level_box<double>(n, wx, wy, wz, nullptr, f, x, nullptr);
+    B.D = logical<double>(D, n);
     Box<float> E = level_box<float>(n, nullptr, nullptr, nullptr, nullptr, r32, e, nullptr);
     TempSet<double> s64;
     TempSet<float> s32;
@@ -308,12 +316,12 @@ int mg_op_refine(const int n[3], const double *wx, const double *wy, const doubl
     if (rc != MG_OK) return rc;
     rc = s32.make(E, st);
     if (rc != MG_OK) return rc;
-    // the kernel takes the reciprocal of the residual scale
     double *sc = nullptr;  // se, sr, sr_inv
     CKO(cudaMallocAsync(&sc, 3 * sizeof(double), st));
     CKO(launch_scales(1, nullptr, 1, nullptr, c_r, sc, sc + 1, sc + 2, st));
-    CKO(launch_refine(s64.S, s32.S, nullptr, 0, c_e, sc + 2, partials, st));
-    CKO(launch_norm_finish(s64.S, nullptr, partials, out, nullptr, nullptr, st));
+    CKO(launch_refine_update(s64.S, s32.S, nullptr, c_e, st));
+    CKO(launch_refine_residual(s64.S, s32.S, nullptr, sc + 2, partials, st));
+    CKO(launch_norm_finish(s64.S, nullptr, partials, out, nullptr, nullptr, st, sc + 1));
     CKO(cudaFreeAsync(sc, st));
     return MG_OK;
 }

@@ -122,6 +122,7 @@ static void carve(Solver *s, Hier<T> &H, Bump &bump, bool full)
             L.wy = arr();
             L.wz = arr();
             L.invD = arr();
+            if (sizeof(T) == sizeof(double)) L.D = arr();
             if (full || l == 0) {
                 L.phi = arr();
                 L.phi2 = arr();
@@ -147,6 +148,7 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
     B.wy = L.wy;
     B.wz = L.wz;
     B.invD = L.invD;
+    B.D = L.D;
     B.nx = d[0];
     B.ny = d[1];
     B.nz = d[2];
@@ -162,6 +164,7 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
     }
     if (l == s->nlev[b] - 1) B.ainv = H.ainv[b];
     B.box = b;
+    B.zc = kSweepZ;
     return B;
 }
 
@@ -196,7 +199,8 @@ static SetPlan<T> plan_set(DescBlob &blob, BoxSet<T> *target, const std::vector<
     for (int k = 0; k < TK_NKIND; ++k) {
         std::vector<int> ts(boxes.size() + 1, 0);
         for (size_t i = 0; i < boxes.size(); ++i)
-            ts[i + 1] = ts[i] + tiles_of(k, boxes[i].nx, boxes[i].ny, boxes[i].nz);
+            ts[i + 1] = ts[i] + tiles_of(k, boxes[i].nx, boxes[i].ny, boxes[i].nz,
+                                         boxes[i].zc > 0 ? boxes[i].zc : kSweepZ);
         target->ntiles[k] = ts.back();
         p.ts_off[k] = blob.put(ts.data(), ts.size() * sizeof(int));
     }
@@ -211,23 +215,94 @@ static void patch_set(const SetPlan<T> &p, char *dev)
         p.target->tstart[k] = reinterpret_cast<const int *>(dev + p.ts_off[k]);
 }
 
+// Planes per CTA of the fused sweep for a set of boxes: the grid should fill
+// whole waves of resident CTAs (a second, nearly empty wave doubles the time
+// of a z-marching kernel), while short chunks pay one extra red half-plane
+// per chunk boundary.  Returns the chunk length and its score (fraction of
+// useful work, 1 = perfect).
 template <class T>
-static void plan_hier(const Solver *s, Hier<T> &H, DescBlob &blob, std::vector<SetPlan<T>> &plans)
+static int choose_zc(const std::vector<Box<T>> &boxes, long long slots, double *score)
+{
+    int maxnz = 1;
+    for (const auto &B : boxes) maxnz = std::max(maxnz, B.nz);
+    int best = std::min(kSweepZ, maxnz);
+    double best_s = -1.0;
+    for (int Z = 2; Z <= maxnz; ++Z) {
+        long long ctas = 0;
+        for (const auto &B : boxes) ctas += tiles_of(TK_SWEEP, B.nx, B.ny, B.nz, Z);
+        const long long waves = (ctas + slots - 1) / slots;
+        const double fill = (double)ctas / (double)(waves * slots);
+        const double sc = fill * (double)Z / (Z + 1.0);
+        if (sc > best_s + 1e-9) {
+            best_s = sc;
+            best = Z;
+        }
+    }
+    *score = best_s;
+    return best;
+}
+
+// Cell limit of the levels run by the one-CTA coarse kernel.
+template <class T>
+static long long coarse_limit(const mg_opts &o)
+{
+    if (o.coarse_cells < 0) return -1;
+    if (o.coarse_cells > 0) return o.coarse_cells;
+    return sizeof(T) == sizeof(double) ? 1024 : 4096;
+}
+
+template <class T>
+static void plan_hier(const Solver *s, Hier<T> &H, DescBlob &blob, std::vector<SetPlan<T>> &plans,
+                      size_t *jobs_off)
 {
     H.smooth.assign(std::max(s->maxlev - 1, 0), BoxSet<T>{});
     std::vector<Box<T>> fine, bottom;
+    std::vector<CoarseJob<T>> jobs;
+    const long long lim = coarse_limit<T>(s->opts);
+    H.lc.assign(s->nbox, 0);
     for (int b = 0; b < s->nbox; ++b) {
         fine.push_back(make_box(s, H, b, 0));
         bottom.push_back(make_box(s, H, b, s->nlev[b] - 1));
+        // first level small enough for the coarse kernel (the coarsest level
+        // always is: it is solved there when the kernel is off)
+        int lc = s->nlev[b] - 1;
+        if (lim > 0) {
+            for (int l = 0; l < s->nlev[b]; ++l) {
+                const auto &d = s->dims[b][l];
+                if ((long long)d[0] * d[1] * d[2] <= lim && s->nlev[b] - l <= kMaxCoarse) {
+                    lc = l;
+                    break;
+                }
+            }
+        }
+        H.lc[b] = lc;
+        CoarseJob<T> J;
+        memset(&J, 0, sizeof J);
+        J.nlev = s->nlev[b] - lc;
+        J.box = b;
+        for (int l = lc; l < s->nlev[b]; ++l) J.lv[l - lc] = make_box(s, H, b, l);
+        jobs.push_back(J);
     }
     plans.push_back(plan_set(blob, &H.fine, fine));
     plans.push_back(plan_set(blob, &H.bottom, bottom));
+    H.fused.assign(H.smooth.size(), 0);
+    const long long slots = (long long)s->sms * sweep_ctas_per_sm<T>();
     for (int l = 0; l + 1 < s->maxlev; ++l) {
         std::vector<Box<T>> set;
         for (int b = 0; b < s->nbox; ++b)
-            if (l < s->nlev[b] - 1) set.push_back(make_box(s, H, b, l));
+            if (l < H.lc[b]) set.push_back(make_box(s, H, b, l));
+        if (!set.empty()) {
+            double score = 0.0;
+            const int zc = choose_zc(set, slots, &score);
+            for (auto &B : set) B.zc = zc;
+            // fused sweeps when the grid can keep the GPU busy
+            const bool ok = score >= 0.7;
+            H.fused[l] = s->opts.smoother == 2 || (s->opts.smoother == 0 && ok);
+        }
         plans.push_back(plan_set(blob, &H.smooth[l], set));
     }
+    H.njobs = (int)jobs.size();
+    *jobs_off = blob.put(jobs.data(), jobs.size() * sizeof(CoarseJob<T>));
 }
 
 static int validate_opts(const mg_opts *o)
@@ -256,10 +331,12 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (opts) o = *opts;
     CKS(validate_opts(&o));
 
-    int dev = 0;
+    int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     Solver *s = new Solver();
     s->dev = dev;
+    s->sms = sms;
     s->nbox = nbox;
     s->opts = o;
     s->has32 = o.precision == MG_MIXED;
@@ -340,8 +417,9 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     DescBlob blob;
     std::vector<SetPlan<double>> p64;
     std::vector<SetPlan<float>> p32;
-    plan_hier(s, s->h64, blob, p64);
-    if (s->has32) plan_hier(s, s->h32, blob, p32);
+    size_t jobs64 = 0, jobs32 = 0;
+    plan_hier(s, s->h64, blob, p64, &jobs64);
+    if (s->has32) plan_hier(s, s->h32, blob, p32, &jobs32);
     const size_t off_at = blob.put(s->off.data(), s->off.size() * sizeof(long long));
     std::vector<int> zeros(nbox, 0);
     const size_t side_at = blob.put(zeros.data(), zeros.size() * sizeof(int));
@@ -357,6 +435,8 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     }
     for (auto &p : p64) patch_set(p, s->desc);
     for (auto &p : p32) patch_set(p, s->desc);
+    s->h64.jobs = reinterpret_cast<const CoarseJob<double> *>(s->desc + jobs64);
+    if (s->has32) s->h32.jobs = reinterpret_cast<const CoarseJob<float> *>(s->desc + jobs32);
     s->doff = reinterpret_cast<const long long *>(s->desc + off_at);
     s->dside = reinterpret_cast<int *>(s->desc + side_at);
 
@@ -472,7 +552,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         }
         for (int l = 0; l < s->nlev[b]; ++l) {
             const auto &d = s->dims[b][l];
-            CK(launch_inv_diag(d[0], d[1], d[2], L[l].wx, L[l].wy, L[l].wz, L[l].invD, st));
+            CK(launch_inv_diag(d[0], d[1], d[2], L[l].wx, L[l].wy, L[l].wz, L[l].invD, L[l].D, st));
             if (s->has32) {
                 auto &M = s->h32.lv[b][l];
                 CK(launch_round_f32(d[0], d[1], d[2], L[l].wx, L[l].wy, L[l].wz, L[l].invD,
@@ -553,16 +633,12 @@ static void prof_collect(Solver *s)
 
 // ------------------------------------------------------------ the cycle ----
 
-// Fused sweeps need enough CTAs to fill the GPU; small levels use passes.
-constexpr int kMinSweepTiles = 600;
-
 template <class T>
-static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, cudaStream_t st)
+static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool fused,
+                          cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
     int left = nu;
-    const bool fused = s->opts.smoother == 2 ||
-                       (s->opts.smoother == 0 && S.ntiles[TK_SWEEP] >= kMinSweepTiles);
     if (fused) {
         for (; left >= 2; left -= 2) {
             for (int src = 0; src < 2; ++src) {
@@ -591,14 +667,16 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st)
     for (int l = 0; l < nl; ++l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
-        if ((e = smooth(s, S, s->opts.nu1, l == 0, st)) != cudaSuccess) return e;
+        if ((e = smooth(s, S, s->opts.nu1, l == 0, H.fused[l] != 0, st)) != cudaSuccess) return e;
         int sl = l == 0 ? prof_begin(s, MG_PROF_RESTRICT, st) : -1;
         if ((e = launch_resid_restrict(S, s->active, st)) != cudaSuccess) return e;
         prof_end(s, sl, st);
         if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     }
-    if (nl == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
-    if ((e = launch_bottom(H.bottom, s->active, s->max_bottom, st)) != cudaSuccess) return e;
+    if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
+    if ((e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st)) !=
+        cudaSuccess)
+        return e;
     for (int l = nl - 1; l >= 0; --l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
@@ -609,7 +687,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st)
         int sl = l == 0 ? prof_begin(s, MG_PROF_PROLONG, st) : -1;
         if ((e = launch_prolong(S, s->active, st)) != cudaSuccess) return e;
         prof_end(s, sl, st);
-        if ((e = smooth(s, S, s->opts.nu2, l == 0, st)) != cudaSuccess) return e;
+        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, st)) != cudaSuccess) return e;
     }
     prof_end(s, coarse, st);
     return cudaSuccess;
@@ -820,31 +898,30 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
         }
     } else {
         // FP64 iterative refinement around FP32 V-cycles: step k forms
-        // x_k = x_{k-1} + se e (e from the last FP32 cycle), the FP64 residual
-        // r_k = f - A x_k, its norm, and r32 = r_k / sr for the next cycle.
+        // x_k = x_{k-1} + se e (e from the last FP32 cycle; nothing at k = 0),
+        // the FP64 residual r_k = f - A x_k, r32 = r_k / sr for the next
+        // cycle and ||r_k|| = sr ||r32||.
         CK(launch_zero(s->h32.fine, nullptr, stream));
         CK(launch_scales(nbox, s->active, 1, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv, stream));
-        int flag = 0;  // 1: current x is in phi2
         for (int k = 0; any; ++k) {
             s->rec = &s->direct;
             const int sl = prof_begin(s, MG_PROF_REFINE, stream);
-            CK(launch_refine(H.fine, s->h32.fine, s->active, flag, s->se, s->sr_inv, s->partials,
-                             stream));
+            if (k > 0) CK(launch_refine_update(H.fine, s->h32.fine, s->active, s->se, stream));
+            CK(launch_refine_residual(H.fine, s->h32.fine, s->active, s->sr_inv, s->partials,
+                                      stream));
             CK(launch_norm_finish(H.fine, s->active, s->partials, s->dnorm, nullptr, nullptr,
-                                  stream));
+                                  stream, s->sr));
             prof_end(s, sl, stream);
             s->rec = nullptr;
             CK(launch_scales(nbox, s->active, 0, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv,
                              stream));
-            flag ^= 1;
             CKS(read_norms(s, s->dnorm, s->hnorm, stream));
             if (s->prof) prof_collect(s);
             bool changed = false;
             any = false;
             for (int b = 0; b < nbox; ++b) {
                 if (bs[b].done) continue;
-                side[b] = flag;
-                // step 0 only re-forms the starting residual
+                // step 0 only forms the starting residual
                 if (k == 0) {
                     any = true;
                     continue;

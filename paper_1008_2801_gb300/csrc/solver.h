@@ -18,6 +18,7 @@ template <class T>
 struct LevelBufs {
     T *phi = nullptr, *phi2 = nullptr, *f = nullptr;
     T *wx = nullptr, *wy = nullptr, *wz = nullptr, *invD = nullptr;
+    T *D = nullptr;  // FP64 levels only: sum of the six weights
 };
 
 // All levels of all boxes in one precision, plus the launch sets.
@@ -26,8 +27,12 @@ struct Hier {
     std::vector<std::vector<LevelBufs<T>>> lv;  // [box][level]
     std::vector<T *> ainv;                      // [box] dense coarsest-level inverse
     std::vector<BoxSet<T>> smooth;              // [level]: boxes not yet at their bottom
+    std::vector<char> fused;                    // [level]: smooth with fused sweeps
     BoxSet<T> fine{};                           // level 0 of every box
     BoxSet<T> bottom{};                         // coarsest level of every box
+    std::vector<int> lc;                        // [box] first level run by the coarse kernel
+    const CoarseJob<T> *jobs = nullptr;         // [box] device
+    int njobs = 0;
     cudaGraphExec_t graph = nullptr;            // captured V-cycle (+ fine norm for FP64)
 };
 
@@ -47,6 +52,7 @@ struct Solver {
     std::vector<int> nlev;                           // [box]
     int maxlev = 0;
     int max_bottom = 0;                              // most cells on a coarsest level
+    int sms = 0;                                     // multiprocessors of the device
     std::vector<long long> off;                      // [box+1] packed cell offsets
     long long total = 0;                             // packed cells
 

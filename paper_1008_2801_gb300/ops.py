@@ -84,10 +84,12 @@ def coarsen_weights(w, shape):
     return cw
 
 
-def inv_diag(w, shape):
+def inv_diag(w, shape, with_diag=False):
     d = level(shape, device=w[0].device)
-    check(_lib.load().mg_op_inv_diag(_n(shape), *map(_p, w), _p(d), _s(d)), "mg_op_inv_diag")
-    return d
+    D = level(shape, device=w[0].device) if with_diag else None
+    check(_lib.load().mg_op_inv_diag(_n(shape), *map(_p, w), _p(d), _p(D), _s(d)),
+          "mg_op_inv_diag")
+    return (d, D) if with_diag else d
 
 
 def round_f32(w, invD, shape):
@@ -103,30 +105,30 @@ def rbgs_pass(w, invD, f, phi, shape, color):
     return phi
 
 
-def rbgs_sweep(w, invD, f, phi_in, shape, phi_out=None):
+def rbgs_sweep(w, invD, f, phi_in, shape, phi_out=None, zc=0):
     if phi_out is None:
         phi_out = torch.zeros_like(phi_in)
     check(_lib.load().mg_op_rbgs_sweep(_PREC[phi_in.dtype], _n(shape), *map(_p, w), _p(invD),
-                                       _p(f), _p(phi_in), _p(phi_out), _s(phi_in)),
+                                       _p(f), _p(phi_in), _p(phi_out), int(zc), _s(phi_in)),
           "mg_op_rbgs_sweep")
     return phi_out
 
 
-def residual(w, f, phi, shape):
+def residual(w, f, phi, shape, D=None):
     r = torch.zeros_like(phi)
-    check(_lib.load().mg_op_residual(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(f), _p(phi),
-                                     _p(r), _s(phi)), "mg_op_residual")
+    check(_lib.load().mg_op_residual(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D), _p(f),
+                                     _p(phi), _p(r), _s(phi)), "mg_op_residual")
     return r
 
 
-def residual_restrict(w, f, phi, shape):
+def residual_restrict(w, f, phi, shape, D=None):
     nz, ny, nx = shape
     c = (nz // 2, ny // 2, nx // 2)
     fc = level(c, phi.dtype, phi.device)
     phic = level(c, phi.dtype, phi.device)
     phic.fill_(7.0)  # must come back zero inside the box
-    check(_lib.load().mg_op_residual_restrict(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(f),
-                                              _p(phi), _p(fc), _p(phic), _s(phi)),
+    check(_lib.load().mg_op_residual_restrict(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D),
+                                              _p(f), _p(phi), _p(fc), _p(phic), _s(phi)),
           "mg_op_residual_restrict")
     return fc, phic
 
@@ -154,28 +156,28 @@ def bottom_solve(ainv, f, shape):
     return phi
 
 
-def residual_norm(w, f, phi, shape):
+def residual_norm(w, f, phi, shape, D=None):
     L = _lib.load()
     m = L.mg_op_norm_scratch(_n(shape))
     part = torch.empty(max(int(m), 1), dtype=torch.float64, device=phi.device)
     out = torch.zeros(1, dtype=torch.float64, device=phi.device)
-    check(L.mg_op_residual_norm(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(f), _p(phi),
+    check(L.mg_op_residual_norm(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D), _p(f), _p(phi),
                                 _p(part), _p(out), _s(phi)), "mg_op_residual_norm")
     return out
 
 
-def refine(w, f, x_in, e32, c_e, c_r, shape):
+def refine(w, D, f, x, e32, c_e, c_r, shape):
+    """x += c_e e in place; returns (x, r32 = (f - A x) / c_r, ||f - A x||)."""
     L = _lib.load()
-    x_out = torch.zeros_like(x_in)
     r32 = torch.zeros_like(e32)
     m = L.mg_op_norm_scratch(_n(shape))
-    part = torch.empty(max(int(m), 1), dtype=torch.float64, device=x_in.device)
-    out = torch.zeros(1, dtype=torch.float64, device=x_in.device)
-    ce = torch.tensor([c_e], dtype=torch.float64, device=x_in.device)
-    cr = torch.tensor([c_r], dtype=torch.float64, device=x_in.device)
-    check(L.mg_op_refine(_n(shape), *map(_p, w), _p(f), _p(x_in), _p(x_out), _p(e32), _p(r32),
-                         _p(ce), _p(cr), _p(part), _p(out), _s(x_in)), "mg_op_refine")
-    return x_out, r32, out
+    part = torch.empty(max(int(m), 1), dtype=torch.float64, device=x.device)
+    out = torch.zeros(1, dtype=torch.float64, device=x.device)
+    ce = torch.tensor([c_e], dtype=torch.float64, device=x.device)
+    cr = torch.tensor([c_r], dtype=torch.float64, device=x.device)
+    check(L.mg_op_refine(_n(shape), *map(_p, w), _p(D), _p(f), _p(x), _p(e32), _p(r32),
+                         _p(ce), _p(cr), _p(part), _p(out), _s(x)), "mg_op_refine")
+    return x, r32, out
 
 
 def beta_grad(beta, phi, lam, h, dbeta=None):

@@ -44,13 +44,14 @@ def _check_tensor(t, name, numel=None, device=None):
         raise ValueError(f"{name} is on {t.device}, solver on {device}")
 
 
-def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother):
+def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
     o.nu1, o.nu2, o.max_cycles = nu1, nu2, max_cycles
     o.use_graph = 1 if use_graph else 0
     o.smoother = SMOOTHERS[smoother]
+    o.coarse_cells = int(coarse_cells)
     return o
 
 
@@ -79,7 +80,7 @@ class Solver:
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
-                 use_graph=True, smoother="auto", device=None):
+                 use_graph=True, smoother="auto", device=None, coarse_cells=0):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -88,7 +89,7 @@ class Solver:
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
-        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother)
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, 0,
                               ctypes.byref(o)), "mg_create")
@@ -189,7 +190,7 @@ class BatchSolver:
     are packed back to back in box order (see ``pack``/``unpack``)."""
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
-                 use_graph=True, smoother="auto", device=None):
+                 use_graph=True, smoother="auto", device=None, coarse_cells=0):
         L = _lib.load()
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         nb = len(self.shapes)
@@ -199,7 +200,7 @@ class BatchSolver:
         n = (ctypes.c_int * (3 * nb))(*[v for s in self.shapes for v in (s[2], s[1], s[0])])
         d = (ctypes.c_double * nb)(*dxs)
         self._h = ctypes.c_void_p()
-        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother)
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, 0, ctypes.byref(o)),
                   "mg_batch_create")

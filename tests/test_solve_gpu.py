@@ -126,6 +126,19 @@ def test_graph_and_smoother_options_agree(cuda_device):
     assert np.linalg.norm(odd - base) <= 1e-9 * np.linalg.norm(base)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_coarse_kernel_matches_per_level_launches(cuda_device, precision):
+    # the one-CTA coarse V-cycle runs the same stage arithmetic in the same
+    # order as the per-level kernels, so the solutions agree to rounding
+    d = inputs.stellar((64, 32, 48), 9)
+    shape = d["f"].shape
+    base, st0 = _solve(d["beta"], d["f"], d["dx"], cuda_device, precision, coarse_cells=-1)
+    for cells in (0, 64, 4096, 10 ** 6):
+        got, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, precision, coarse_cells=cells)
+        assert st["status"] == "ok" and st["cycles"] == st0["cycles"]
+        assert np.linalg.norm(got - base) <= 1e-12 * np.linalg.norm(base), cells
+
+
 def test_deterministic_run_to_run(cuda_device):
     d = inputs.stellar(48, 6)
     a, _ = _solve(d["beta"], d["f"], d["dx"], cuda_device)
