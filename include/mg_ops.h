@@ -109,6 +109,27 @@ int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy
                         const void *wz, const void *D, const void *f, const void *phi,
                         double *partials, double *out, void *stream);
 
+/* Residual norm that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory, such as
+ * an application whose device memory all belongs to its own pool allocator
+ * (nothing may call cudaMalloc beside it) or a time-critical loop that cannot
+ * take the implicit synchronisation of cudaMalloc/cudaFree.  It computes the
+ * same *out = ||f - A phi||_2 as mg_op_residual_norm, but its per-tile partial
+ * sums live in a file-scope device array of 65536 doubles (512 KiB, held on
+ * every GPU that loads the library until the process exits) instead of
+ * caller scratch; it calls no cudaMalloc, cudaFree or allocating routine.
+ * Limit: ceil(nx/32) * ceil(ny/8) * ceil(nz/16) <= 65536 (e.g. 512^3 uses
+ * 32768); larger boxes return MG_ERR_INVALID_ARG before anything runs.
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call reuses the array and overwrites the slots it
+ * reads, so nothing needs clearing, but calls that overlap on the GPU race on
+ * it: order them (same stream, or synchronise).  Arguments as
+ * mg_op_residual_norm without `partials`. */
+int mg_op_residual_norm_noalloc(int prec, const int n[3], const void *wx, const void *wy,
+                                const void *wz, const void *D, const void *f, const void *phi,
+                                double *out, void *stream);
+
 /* Mixed-precision refinement step on the finest level (FP64 x, f, weights,
  * D; FP32 correction e and scaled residual r32):
  *   x += (*c_e) e  (in place);  r = f - A64 x;  r32 = float(r) * float(1/(*c_r));

@@ -100,6 +100,7 @@ _SIGS = {
     "mg_op_bottom_solve": (c_int, [c_int, c_int3] + [c_void_p] * 4),
     "mg_op_norm_scratch": (c_ll, [c_int3]),
     "mg_op_residual_norm": (c_int, [c_int, c_int3] + [c_void_p] * 9),
+    "mg_op_residual_norm_noalloc": (c_int, [c_int, c_int3] + [c_void_p] * 8),
     "mg_op_refine": (c_int, [c_int3] + [c_void_p] * 13),
     "mg_op_beta_grad": (c_int, [c_int3, c_double] + [c_void_p] * 5),
 }
