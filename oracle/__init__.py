@@ -77,6 +77,9 @@ def lib():
             L.oracle_adjoint.argtypes = [_I, _I, _I, _F, _D, _D, _D, _D, _D, _F, _I,
                                          ctypes.POINTER(_I)]
             L.oracle_adjoint.restype = _I
+            DN = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+            L.oracle_divergence.argtypes = [_I, _I, _I, _F, _D, _D, _D, ctypes.c_void_p, _D]
+            L.oracle_correct.argtypes = [_I, _I, _I, _F, _D, _D, DN, DN, DN]
             _lib = L
     return _lib
 
@@ -224,6 +227,29 @@ def adjoint(beta, h, phi, g, tol=1e-13, max_cycles=200):
         lam[b] = lb
         infos.append({"status": STATUS[s], "cycles": cyc.value})
     return (lam[0] if single else lam), dbeta, infos
+
+
+def divergence(u, v, w, h, S=None):
+    """f = div(u, v, w) - S on the cells (face arrays in their natural layouts)."""
+    u, v, w = _c(u), _c(v), _c(w)
+    nz, ny, nx1 = u.shape
+    nx = nx1 - 1
+    f = np.empty((nz, ny, nx))
+    Sp = None
+    if S is not None:
+        S = _c(S)
+        Sp = S.ctypes.data_as(ctypes.c_void_p)
+    lib().oracle_divergence(nx, ny, nz, float(h), u, v, w, Sp, f)
+    return f
+
+
+def correct(beta, h, phi, u, v, w):
+    """Returns the face velocities minus beta_face grad(phi) (copies)."""
+    beta, phi = _c(beta), _c(phi)
+    u, v, w = _c(u).copy(), _c(v).copy(), _c(w).copy()
+    nx, ny, nz = _dims(beta)
+    lib().oracle_correct(nx, ny, nz, float(h), beta, phi, u, v, w)
+    return u, v, w
 
 
 def dense_matrix(faces, h, shape):

@@ -33,7 +33,10 @@
  *   adjoint      for L with dL/dphi = g: A lambda = g (A is symmetric),
  *                dL/df = lambda, dL/dbeta_face = (lambda_n - lambda_c)
  *                (phi_n - phi_c)/h^2 (wall face: lambda_c phi_c / h^2), chained
- *                to cell beta through the harmonic mean.
+ *                to cell beta through the harmonic mean;
+ *   projection   f = div(u) - S from face velocities; after the solve each
+ *                face velocity loses beta_face (phi_high - phi_low) / h, so
+ *                the corrected field has div = S.
  *
  * Loops over cells run under OpenMP where each iteration is independent; all
  * reductions are serial, so results do not depend on the thread count.
@@ -565,4 +568,63 @@ int oracle_adjoint(int nx, int ny, int nz, double h, const double *beta,
     if (s == OR_NONFINITE || s == OR_BAD) return s;
     oracle_beta_grad(nx, ny, nz, h, beta, phi, lam, dbeta);
     return s;
+}
+
+/* ------------------------------------------------------------ projection */
+
+/* The velocity constraint around the solve (paper Sec. 1): with face
+ * velocities u (x faces, (nz, ny, nx+1)), v (y faces), w (z faces) and a cell
+ * source S (nullable = 0), the right-hand side is the discrete divergence
+ * minus the source,
+ *     f_c = (u_{i+1} - u_i + v_{j+1} - v_j + w_{k+1} - w_k) / h - S_c. */
+void oracle_divergence(int nx, int ny, int nz, double h, const double *u, const double *v,
+                       const double *w, const double *S, double *f)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double d = (u[xface(i + 1, j, k, nx, ny)] - u[xface(i, j, k, nx, ny)]) +
+                           (v[yface(i, j + 1, k, nx, ny)] - v[yface(i, j, k, nx, ny)]) +
+                           (w[zface(i, j, k + 1, nx, ny)] - w[zface(i, j, k, nx, ny)]);
+                size_t c = cell(i, j, k, nx, ny);
+                f[c] = d / h - (S ? S[c] : 0.0);
+            }
+}
+
+/* Velocity correction after the solve: every face velocity loses the face
+ * flux beta_face (phi_high - phi_low) / h, with phi = 0 outside the box and
+ * the wall faces' doubled beta, so that div(u') = div(u) - A phi. */
+void oracle_correct(int nx, int ny, int nz, double h, const double *beta, const double *phi,
+                    double *u, double *v, double *w)
+{
+    size_t nfx = (size_t)nz * ny * (nx + 1), nfy = (size_t)nz * (ny + 1) * nx,
+           nfz = (size_t)(nz + 1) * ny * nx;
+    double *bx = (double *)malloc(sizeof(double) * nfx);
+    double *by = (double *)malloc(sizeof(double) * nfy);
+    double *bz = (double *)malloc(sizeof(double) * nfz);
+    oracle_face_beta(nx, ny, nz, beta, bx, by, bz);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                size_t q = xface(i, j, k, nx, ny);
+                u[q] -= bx[q] * (value_at(phi, i, j, k, nx, ny, nz) -
+                                 value_at(phi, i - 1, j, k, nx, ny, nz)) / h;
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t q = yface(i, j, k, nx, ny);
+                v[q] -= by[q] * (value_at(phi, i, j, k, nx, ny, nz) -
+                                 value_at(phi, i, j - 1, k, nx, ny, nz)) / h;
+            }
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t q = zface(i, j, k, nx, ny);
+                w[q] -= bz[q] * (value_at(phi, i, j, k, nx, ny, nz) -
+                                 value_at(phi, i, j, k - 1, nx, ny, nz)) / h;
+            }
+    free(bx);
+    free(by);
+    free(bz);
 }

@@ -296,3 +296,54 @@ def test_not_converged_reports_history():
     phi, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-14, max_cycles=2)
     assert info["status"] == "not_converged" and info["cycles"] == 2
     assert info["hist"][2] < info["hist"][1] < info["hist"][0] == 1.0
+
+
+# ---- projection steps around the solve (velocity constraint, paper Sec. 1)
+
+def _faces_random(shape, seed):
+    nz, ny, nx = shape
+    r = _rng(seed)
+    return (r.standard_normal((nz, ny, nx + 1)), r.standard_normal((nz, ny + 1, nx)),
+            r.standard_normal((nz + 1, ny, nx)))
+
+
+def test_divergence_of_a_linear_field_is_its_trace():
+    nz, ny, nx = 6, 5, 7
+    h = 0.1
+    a, b, c = 1.3, -0.4, 2.2
+    u = a * h * np.arange(nx + 1)[None, None, :] * np.ones((nz, ny, 1))
+    v = b * h * np.arange(ny + 1)[None, :, None] * np.ones((nz, 1, nx))
+    w = c * h * np.arange(nz + 1)[:, None, None] * np.ones((1, ny, nx))
+    f = O.divergence(u, v, w, h)
+    assert np.max(np.abs(f - (a + b + c))) <= 1e-13
+    S = np.full((nz, ny, nx), 0.7)
+    assert np.max(np.abs(O.divergence(u, v, w, h, S) - (a + b + c - 0.7))) <= 1e-13
+
+
+def test_correction_removes_the_operator_from_the_divergence():
+    # div(u - beta_face grad phi) = div(u) - A phi, on every cell including
+    # those next to the walls (ties signs and wall faces to A)
+    shape = (6, 7, 9)
+    h = 0.15
+    beta = _rough_beta(shape, 30)
+    phi = _rng(31).standard_normal(shape)
+    u, v, w = _faces_random(shape, 32)
+    u2, v2, w2 = O.correct(beta, h, phi, u, v, w)
+    lhs = O.divergence(u2, v2, w2, h)
+    rhs = O.divergence(u, v, w, h) - O.apply(O.face_beta(beta), h, phi)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+
+
+def test_projection_enforces_the_constraint():
+    shape = (12, 16, 20)
+    nz, ny, nx = shape
+    d = inputs.stellar((nx, ny, nz), 33)
+    h = d["dx"]
+    u, v, w = _faces_random(shape, 34)
+    S = _rng(35).standard_normal(shape)
+    f = O.divergence(u, v, w, h, S)
+    phi, info = O.solve(d["beta"], f, h, tol=1e-14)
+    assert info["status"] == "ok"
+    u2, v2, w2 = O.correct(d["beta"], h, phi, u, v, w)
+    div = O.divergence(u2, v2, w2, h)
+    assert np.linalg.norm(div - S) <= 1e-12 * np.linalg.norm(f)
