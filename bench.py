@@ -207,11 +207,12 @@ def run_gpu(args):
     phi = torch.zeros_like(f)
     stream = torch.cuda.current_stream(dev)
 
-    def timed(solver, steps, warm):
+    def timed(solver, steps, warm, prof):
         def step():
             phi.zero_()
             solver.set_beta(beta)
             return solver.solve(f, phi=phi, tol=TOL)[1]
+        solver.profile(prof)
         for _ in range(warm):
             st = step()
         solver.read_profile(reset=True)
@@ -230,12 +231,16 @@ def run_gpu(args):
         ms = e0.elapsed_time(e1) / steps
         return ms, st, solver.read_profile(reset=True), clocks
 
+    # value: the solver as a user runs it (the cycle loop is one conditional
+    # graph, judged on the device).  Then the same steps again with CUDA
+    # events around each stage (host-judged loop, since event nodes cannot sit
+    # in a conditional graph body): stage split and the roofline kernel time.
     s64 = Solver((n, n, n), d["dx"], precision="fp64", device=dev)
-    s64.profile(True)
-    ms, st64, prof, clocks = timed(s64, args.steps, max(args.warmup, 3))
+    ms, st64, prof0, clocks = timed(s64, args.steps, max(args.warmup, 3), False)
     ms_max = max_over_ranks(ms, dev)
     value = world * N / (ms_max / 1e3)
     phi64 = phi.cpu().numpy()
+    ms_prof, _, prof, _ = timed(s64, args.steps, 1, True)
 
     # dominant level-0 kernel of the FP64 step and its roofline
     fine = {k: v for k, v in prof.items() if k != "kernels" and v["launches"]}
@@ -278,18 +283,21 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (working set ~1 GB > 129 MB)",
                       "parallelism": f"independent box per GPU x {world}"},
            "roofline": roof, "stage_ms_per_step": stage_ms,
-           "gpu_launches": prof["kernels"], "clocks": clocks}
+           "stage_timing": f"CUDA events around each stage in a second timed pass of the same "
+                           f"{args.steps} steps ({ms_prof:.3f} ms/step with events, host-judged loop)",
+           "gpu_launches": prof0["kernels"], "clocks": clocks}
     s64.close()
 
     # mixed precision on the same input
     smx = Solver((n, n, n), d["dx"], precision="mixed", device=dev)
-    smx.profile(True)
-    msm, stm, profm, _ = timed(smx, args.steps, max(args.warmup, 3))
+    msm, stm, _, _ = timed(smx, args.steps, max(args.warmup, 3), False)
     msm = max_over_ranks(msm, dev)
     phimx = phi.cpu().numpy()
+    _, _, profm, _ = timed(smx, args.steps, 1, True)
     finem = {k: v for k, v in profm.items() if k != "kernels" and v["launches"]}
     mixed = {"value": world * N / (msm / 1e3), "unit": "cells/s", "ms_per_step": msm,
-             "steps": stm["cycles"], "rel_resid": stm["rel_resid"],
+             "refinement_steps": stm["cycles"], "fp32_vcycles_per_step": 2,
+             "rel_resid": stm["rel_resid"],
              "speedup_vs_fp64": ms_max / msm,
              "stage_ms_per_step": {k: round(v["ms"] / max(args.steps, 1), 4)
                                    for k, v in finem.items()}}
@@ -426,6 +434,49 @@ def run_extra(dev, args):
         s.close()
     ex["batched_64"] = res
     del bp, fp
+
+    # projection steps around a 256^3 solve: f = div(u) - S, solve, u -= beta grad(phi)
+    d = inputs.config(2)
+    n = d["f"].shape[0]
+    g = torch.Generator(device=dev)
+    g.manual_seed(6)
+    u = torch.randn((n, n, n + 1), dtype=torch.float64, device=dev, generator=g)
+    v = torch.randn((n, n + 1, n), dtype=torch.float64, device=dev, generator=g)
+    w = torch.randn((n + 1, n, n), dtype=torch.float64, device=dev, generator=g)
+    S = torch.randn((n, n, n), dtype=torch.float64, device=dev, generator=g)
+    beta = torch.from_numpy(d["beta"]).to(dev)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        s = Solver((n, n, n), d["dx"], precision=prec, device=dev)
+        s.set_beta(beta)
+        u0, v0, w0 = u.clone(), v.clone(), w.clone()
+
+        def proj():
+            u0.copy_(u)
+            v0.copy_(v)
+            w0.copy_(w)
+            t = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            t[0].record()
+            f = s.project_rhs(u0, v0, w0, S)
+            t[1].record()
+            phi, st = s.solve(f, tol=TOL)
+            t[2].record()
+            s.project_correct(phi, u0, v0, w0)
+            t[3].record()
+            return t, st
+        proj()
+        torch.cuda.synchronize(dev)
+        t, st = proj()
+        torch.cuda.synchronize(dev)
+        rhs_ms, sol_ms, cor_ms = (t[0].elapsed_time(t[1]), t[1].elapsed_time(t[2]),
+                                  t[2].elapsed_time(t[3]))
+        res[prec] = {"rhs_ms": rhs_ms, "solve_ms": sol_ms, "correct_ms": cor_ms,
+                     "rhs_gbs": 40 * n ** 3 / (rhs_ms / 1e3) / 1e9,
+                     "correct_gbs": 80 * n ** 3 / (cor_ms / 1e3) / 1e9,
+                     "cycles": st["cycles"]}
+        s.close()
+    ex["projection_256^3"] = res
+    del u, v, w, S
 
     # adjoint, 128^3 x 8 right-hand sides
     d = inputs.config(5)

@@ -86,7 +86,18 @@ typedef struct {
                          per box (the coarse end of the V-cycle as a single
                          launch); 0 default (4096 in FP32 V-cycles, 1024 in
                          FP64 ones, whose FP64 rate per SM is low), -1 off */
-    int reserved[9];
+    int inner_cycles; /* MG_MIXED: FP32 V-cycles per FP64 refinement step
+                         (0 default = 2; 1..8) */
+    int full_residual;/* 0 (default): right after a red-black sweep the black
+                         cells satisfy their equations, so the restricted
+                         residual and the cycle's residual norm are formed
+                         from the red cells only; 1: always every cell */
+    int tma;          /* 0 (default): FP32 fused sweeps read their operands
+                         with plain loads and a one-plane register prefetch;
+                         1: they stage their tiles in a shared-memory ring
+                         filled by the Tensor Memory Accelerator (when the
+                         driver can encode tensor maps) */
+    int reserved[6];
 } mg_opts;
 
 typedef struct {
@@ -143,6 +154,23 @@ int mg_solve_multi(mg_ctx *ctx, int nrhs, const double *f, double *phi, double t
  * The forward beta must still be the one set.  Returns as mg_solve_multi. */
 int mg_adjoint(mg_ctx *ctx, int nrhs, const double *phi, const double *g, double *dLdf,
                double *dLdbeta, double tol, mg_stats *st, void *stream);
+
+/* ---- projection steps around the solve: the velocity constraint the
+ * solve enforces (paper Sec. 1).  Face velocities in natural C layouts:
+ * u (nz, ny, nx+1) on x faces, v (nz, ny+1, nx), w (nz+1, ny, nx); cell
+ * arrays (nz, ny, nx).  Device pointers on the context's device; async.
+ *   mg_project_rhs:     f = div(u, v, w) - S, div = sum of the face
+ *                       differences / dx (S may be NULL for 0);
+ *   mg_project_correct: u, v, w -= beta_face * (phi_high - phi_low) / dx on
+ *                       every face, phi = 0 outside and wall faces with
+ *                       2 beta (the operator's own faces), using the beta of
+ *                       the last mg_set_beta; then div(u, v, w) = S up to the
+ *                       solve's residual.
+ * Errors: INVALID_ARG (NULL, no beta set), CUDA. */
+int mg_project_rhs(mg_ctx *ctx, const double *u, const double *v, const double *w,
+                   const double *S, double *f, void *stream);
+int mg_project_correct(mg_ctx *ctx, const double *phi, double *u, double *v, double *w,
+                       void *stream);
 
 /* Level list of a context: *nlev levels, dims[3*l .. 3*l+2] = (nx, ny, nz)
  * of level l (dims may be NULL; room for 32 levels). */

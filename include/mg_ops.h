@@ -72,6 +72,17 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
                      const void *invD, const void *f, const void *phi_in, void *phi_out, int zc,
                      void *stream);
 
+/* The same sweep in FP32 with its operand tiles staged by the Tensor Memory
+ * Accelerator (bulk tensor copies into shared memory, completion counted by
+ * mbarriers).  Bitwise equal to mg_op_rbgs_sweep with MG_OPS_F32.  Waits on
+ * the copies are bounded: MG_ERR_TIMEOUT if one gave up.  Synchronises the
+ * stream (to read the error word); MG_ERR_UNSUPPORTED if the driver cannot
+ * encode tensor maps or the level is too small for one copy box (needs
+ * nx >= 64 and ny >= 11). */
+int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const float *wz,
+                         const float *invD, const float *f, const float *phi_in, float *phi_out,
+                         int zc, void *stream);
+
 /* In the residual stages below, D (nullable) is the stored diagonal of
  * mg_op_inv_diag in the stage precision; when NULL it is summed from the six
  * weights of each cell. */
@@ -85,6 +96,14 @@ int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, con
 int mg_op_residual_restrict(int prec, const int n_fine[3], const void *wx, const void *wy,
                             const void *wz, const void *D, const void *f, const void *phi,
                             void *fc, void *phic, void *stream);
+
+/* The same right after a red-black sweep (the last operation on phi was a
+ * black pass): the black cells then satisfy their own equations, so only the
+ * 4 red children of each coarse cell are evaluated and the black ones count
+ * as zero.  Equal to mg_op_residual_restrict to rounding in that state. */
+int mg_op_residual_restrict_red(int prec, const int n_fine[3], const void *wx, const void *wy,
+                                const void *wz, const void *D, const void *f, const void *phi,
+                                void *fc, void *phic, void *stream);
 
 /* phi += coarse value of each cell's parent (piecewise-constant
  * prolongation) for an all-even fine level n. */

@@ -39,7 +39,8 @@ STATUS_NAMES = {
 class mg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("max_cycles", c_int),
                 ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
-                ("reserved", c_int * 9)]
+                ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
+                ("reserved", c_int * 6)]
 
 
 class mg_stats(ctypes.Structure):
@@ -71,6 +72,8 @@ _SIGS = {
     "mg_adjoint": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
                            ctypes.POINTER(mg_stats), c_void_p]),
     "mg_levels": (c_int, [c_void_p, c_int_p, c_int_p]),
+    "mg_project_rhs": (c_int, [c_void_p] * 7),
+    "mg_project_correct": (c_int, [c_void_p] * 6),
     "mg_destroy": (None, [c_void_p]),
     "mg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int_p,
                                 ctypes.POINTER(c_double), c_int, ctypes.POINTER(mg_opts)]),
@@ -93,8 +96,10 @@ _SIGS = {
     "mg_op_round_f32": (c_int, [c_int3] + [c_void_p] * 9),
     "mg_op_rbgs_pass": (c_int, [c_int, c_int3] + [c_void_p] * 6 + [c_int, c_void_p]),
     "mg_op_rbgs_sweep": (c_int, [c_int, c_int3] + [c_void_p] * 7 + [c_int, c_void_p]),
+    "mg_op_rbgs_sweep_tma": (c_int, [c_int3] + [c_void_p] * 7 + [c_int, c_void_p]),
     "mg_op_residual": (c_int, [c_int, c_int3] + [c_void_p] * 8),
     "mg_op_residual_restrict": (c_int, [c_int, c_int3] + [c_void_p] * 9),
+    "mg_op_residual_restrict_red": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_prolong_add": (c_int, [c_int, c_int3, c_void_p, c_void_p, c_void_p]),
     "mg_op_bottom_inverse": (c_int, [c_int3] + [c_void_p] * 6),
     "mg_op_bottom_solve": (c_int, [c_int, c_int3] + [c_void_p] * 4),

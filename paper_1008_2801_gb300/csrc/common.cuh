@@ -25,6 +25,7 @@ constexpr int kTX = 32;   // tile width  (threads along x)
 constexpr int kTY = 8;    // tile height (threads along y)
 constexpr int kThreads = kTX * kTY;
 constexpr int kSweepZ = 32;   // default planes per CTA of the fused red-black sweep
+constexpr int kSweepTY = 8;   // tile height (rows) of the fused sweep: 64 x 8 cells
 constexpr int kColZ = 16;     // planes per thread of the column kernels (norms)
 
 inline __host__ __device__ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -60,7 +61,17 @@ struct Box {
 // (ceil(nx/2) per row), the cells of the next-coarser level, pairs along x
 // with z cut into chunks of kSweepZ planes (the fused sweep marches in z), or
 // cells with z cut into chunks of kColZ planes (one thread per column chunk).
-enum TileKind { TK_CELL = 0, TK_PAIR = 1, TK_COARSE = 2, TK_SWEEP = 3, TK_COLZ = 4, TK_NKIND = 5 };
+enum TileKind {
+    TK_CELL = 0,
+    TK_PAIR = 1,
+    TK_COARSE = 2,
+    TK_SWEEP = 3,
+    TK_COLZ = 4,
+    TK_FACE = 5,   // positions [0, nx] x [0, ny] x [0, nz] (every stored face)
+    TK_CFACE = 6,  // positions of the next-coarser level's faces
+    TK_PCOLZ = 7,  // red-black pairs along x, z in chunks of kColZ planes
+    TK_NKIND = 8
+};
 
 // zc: planes per CTA of the fused sweep (TK_SWEEP only).
 inline __host__ __device__ void tile_extent(int kind, int nx, int ny, int nz, int &ex, int &ey,
@@ -70,26 +81,53 @@ inline __host__ __device__ void tile_extent(int kind, int nx, int ny, int nz, in
     else if (kind == TK_COARSE) { ex = nx / 2; ey = ny / 2; ez = nz / 2; }
     else if (kind == TK_SWEEP) { ex = (nx + 1) / 2; ey = ny; ez = (nz + zc - 1) / zc; }
     else if (kind == TK_COLZ) { ex = nx; ey = ny; ez = (nz + kColZ - 1) / kColZ; }
+    else if (kind == TK_FACE) { ex = nx + 1; ey = ny + 1; ez = nz + 1; }
+    else if (kind == TK_CFACE) { ex = nx / 2 + 1; ey = ny / 2 + 1; ez = nz / 2 + 1; }
+    else if (kind == TK_PCOLZ) { ex = (nx + 1) / 2; ey = ny; ez = (nz + kColZ - 1) / kColZ; }
     else { ex = nx; ey = ny; ez = nz; }
 }
+
+inline __host__ __device__ int tile_rows(int kind) { return kind == TK_SWEEP ? kSweepTY : kTY; }
 
 inline __host__ __device__ int tiles_of(int kind, int nx, int ny, int nz, int zc = kSweepZ)
 {
     int ex, ey, ez;
     tile_extent(kind, nx, ny, nz, ex, ey, ez, zc);
-    return ((ex + kTX - 1) / kTX) * ((ey + kTY - 1) / kTY) * ez;
+    const int ty = tile_rows(kind);
+    return ((ex + kTX - 1) / kTX) * ((ey + ty - 1) / ty) * ez;
 }
 
 // A set of boxes launched together (one box, or every box of a batch that is
 // active at a level).  tstart[kind] is a device prefix array of nbox + 1 tile
 // offsets for each tile kind; one CTA handles one tile.
-template <class T>
-struct BoxSet {
-    const Box<T> *boxes;
+template <class D>
+struct DescSet {
+    const D *boxes;
     const int *tstart[TK_NKIND];
     int ntiles[TK_NKIND];
     int nbox;
 };
+template <class T>
+using BoxSet = DescSet<Box<T>>;
+
+// One box at one level as the set-up kernels see it (FP64 weights written
+// from cell beta or from the finer level; FP32 copies for mixed precision;
+// the dense inverse on the coarsest level).
+struct SetupBox {
+    double *wx, *wy, *wz, *invD, *D;
+    double *cwx, *cwy, *cwz;           // next-coarser level's weights (coarsening)
+    float *wx32, *wy32, *wz32, *invD32;  // NULL unless mixed precision
+    const double *beta;                 // finest level: the box's cell beta
+    double inv_h2;
+    double *work, *inv64;               // coarsest level: scratch and A^{-1}
+    float *inv32;
+    int nx, ny, nz, P;
+    long long Q;
+    int cP;
+    long long cQ;
+    int zc;                             // unused (tile bookkeeping)
+};
+typedef DescSet<SetupBox> SetupSet;
 
 // The coarse end of one box's V-cycle, run by a single CTA: levels
 // lv[0] (the first level small enough) down to lv[nlev-1] (the coarsest).
@@ -99,6 +137,20 @@ struct CoarseJob {
     int nlev;
     int box;
     Box<T> lv[kMaxCoarse];
+};
+
+// Per-box convergence state of a solve, kept on the device so that the
+// V-cycle loop can run as a conditional CUDA graph with no host round trip.
+struct JudgeState {
+    int *status;      // [nbox] mg_status (NOT_CONVERGED while running)
+    int *cycles;      // [nbox] cycles (or refinement steps) done
+    int *stall;       // [nbox] consecutive cycles without a 10% gain
+    double *rel0;     // [nbox] starting relative residual
+    double *best;     // [nbox] best relative residual so far
+    double *hist;     // [nbox * MG_MAX_HIST] relative residual after each cycle
+    int *step;        // [1] cycles run by the loop
+    double *tol;      // [1] relative residual target
+    int max_cycles;
 };
 
 // Last box b with tstart[b] <= t (tstart ascending, tstart[0] = 0).
@@ -122,14 +174,15 @@ __device__ __forceinline__ TilePos tile_pos(int kind, int nx, int ny, int nz, in
 {
     int ex, ey, ez;
     tile_extent(kind, nx, ny, nz, ex, ey, ez, zc);
-    int ntx = (ex + kTX - 1) / kTX, nty = (ey + kTY - 1) / kTY;
+    const int rows = tile_rows(kind);
+    int ntx = (ex + kTX - 1) / kTX, nty = (ey + rows - 1) / rows;
     int tx = local % ntx;
     local /= ntx;
     int ty = local % nty;
     int tz = local / nty;
     TilePos p;
     p.x = tx * kTX + (int)threadIdx.x;
-    p.y = ty * kTY + (int)threadIdx.y;
+    p.y = ty * rows + (int)threadIdx.y;
     p.z = tz;
     return p;
 }

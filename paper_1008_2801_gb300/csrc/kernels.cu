@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass(BoxSet<T> S, const int *
 // -------------------------------------- fused red+black sweep (z-march) ----
 //
 // dst = black pass of (red pass of src), out of place.  The CTA owns a tile
-// of 64 x kTY columns and a chunk of kSweepZ planes; thread (tx, ty) owns the
+// of 64 x kSweepTY columns and a chunk of zc planes; thread (tx, ty) owns the
 // cell pair (x0 + 2tx, x0 + 2tx + 1) of row y0 + ty, which holds exactly one
 // red and one black cell on every plane.  Marching k upward, step k computes
 // the new red values of plane k (own column plus the red cells of a one-cell
@@ -109,11 +109,89 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass(BoxSet<T> S, const int *
 // values of plane k-1 from the red values of planes k-2, k-1, k, and stores
 // both cells of the pair for plane k-1.  Reading src and writing dst keeps
 // every CTA's inputs unchanged while other CTAs run.
-template <class T>
-__global__ void __launch_bounds__(kThreads) k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active,
-                                                         int src_is_phi2)
+//
+// The global operands of step k+1 (own red cell, ring cell, and the black
+// cell updated at step k+1) are loaded into registers during step k, before
+// its barriers, so DRAM latency overlaps the barrier waits and arithmetic.
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
 {
-    __shared__ T red[3][kTY + 2][2 * kTX + 2];
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <class T>
+struct RedIn {  // a Gauss-Seidel update's 14 operands
+    T sw, se, ss, sn, sd, su, wxa, wxb, wya, wyb, wza, wzb, f, id;
+};
+template <class T>
+struct BlackIn {  // a black update's global operands (red neighbours come from smem)
+    T wxa, wxb, wya, wyb, wza, wzb, f, id;
+};
+
+template <class T>
+__device__ __forceinline__ void load_red(RedIn<T> &r, bool ok, const T *__restrict__ src,
+                                         const T *__restrict__ f, const T *__restrict__ invD,
+                                         const T *__restrict__ wx, const T *__restrict__ wy,
+                                         const T *__restrict__ wz, long long c, int P, long long Q)
+{
+    if (ok) {
+        r.sw = src[c - 1];
+        r.se = src[c + 1];
+        r.ss = src[c - P];
+        r.sn = src[c + P];
+        r.sd = src[c - Q];
+        r.su = src[c + Q];
+        r.wxa = wx[c];
+        r.wxb = wx[c + 1];
+        r.wya = wy[c];
+        r.wyb = wy[c + P];
+        r.wza = wz[c];
+        r.wzb = wz[c + Q];
+        r.f = f[c];
+        r.id = invD[c];
+    } else {
+        r.sw = r.se = r.ss = r.sn = r.sd = r.su = T(0);
+        r.wxa = r.wxb = r.wya = r.wyb = r.wza = r.wzb = r.f = r.id = T(0);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T eval_red(const RedIn<T> &r)
+{
+    T s = r.wxa * r.sw;
+    s = fmadd(r.wxb, r.se, s);
+    s = fmadd(r.wya, r.ss, s);
+    s = fmadd(r.wyb, r.sn, s);
+    s = fmadd(r.wza, r.sd, s);
+    s = fmadd(r.wzb, r.su, s);
+    return (s - r.f) * r.id;
+}
+
+template <class T>
+__device__ __forceinline__ void load_black(BlackIn<T> &b, bool ok, const T *__restrict__ f,
+                                           const T *__restrict__ invD, const T *__restrict__ wx,
+                                           const T *__restrict__ wy, const T *__restrict__ wz,
+                                           long long c, int P, long long Q)
+{
+    if (ok) {
+        b.wxa = wx[c];
+        b.wxb = wx[c + 1];
+        b.wya = wy[c];
+        b.wyb = wy[c + P];
+        b.wza = wz[c];
+        b.wzb = wz[c + Q];
+        b.f = f[c];
+        b.id = invD[c];
+    } else {
+        b.wxa = b.wxb = b.wya = b.wyb = b.wza = b.wzb = b.f = b.id = T(0);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTX * kSweepTY, sizeof(T) == 4 ? 4 : 2) k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active,
+                                                               int src_is_phi2)
+{
+    __shared__ T red[3][kSweepTY + 2][2 * kTX + 2];
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_SWEEP];
     const int b = find_box(ts, S.nbox, t);
@@ -140,38 +218,84 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_sweep(BoxSet<T> S, const int 
     const int z1 = min(z0 + zc, nz);
     const bool rowin = y < ny;
 
+    // ring role of this thread: a red cell of the row below / above the tile
+    // (ty 0 / 1), of the column left / right of it (ty 2, tx < kSweepTY), or none
+    const bool ring_row = ty < 2;
+    const bool ring_col = ty == 2 && tx < kSweepTY;
+    const int ring_y = ty == 0 ? y0 - 1 : y0 + kSweepTY;           // ring_row
+    const int ring_x = tx < kSweepTY / 2 ? x0 - 1 : x0 + 2 * kTX;   // ring_col
+    const int ring_m = tx % (kSweepTY / 2);
+    // position (x, yy) of the ring cell at plane k, and whether it is inside
+    auto ring_at = [&](int k, int &xx, int &yy) -> bool {
+        if (ring_row) {
+            yy = ring_y;
+            xx = x0 + 2 * tx + ((yy + k) & 1);
+            return yy >= 0 && yy < ny && xx < nx;
+        }
+        xx = ring_x;
+        yy = y0 + 2 * ring_m + ((xx + y0 + k) & 1);
+        return xx >= 0 && xx < nx && yy < ny;
+    };
+    auto own_ok = [&](int k, int &xr) -> bool {
+        xr = xa + ((y + k) & 1);
+        return k >= 0 && k < nz && rowin && xr < nx;
+    };
+    auto cidx = [&](int k, int yy, int xx) { return (long long)k * Q + (long long)yy * P + xx; };
+
+    RedIn<T> R, G;
+    BlackIn<T> Bk;
+    {
+        const int k = z0 - 1;
+        int xr, xx, yy;
+        const bool ok = own_ok(k, xr);
+        load_red(R, ok, src, f, invD, wx, wy, wz, ok ? cidx(k, y, xr) : 0, P, Q);
+        load_red(G, false, src, f, invD, wx, wy, wz, 0, P, Q);
+        load_black(Bk, false, f, invD, wx, wy, wz, 0, P, Q);
+        (void)xx;
+        (void)yy;
+    }
+
     for (int k = z0 - 1; k <= z1; ++k) {
         const int s0 = (k - z0 + 3) % 3;
-        const bool plane_in = k >= 0 && k < nz;
-        // (1) red values of plane k: own column
-        {
-            const int xr = xa + ((y + k) & 1);
-            T v = T(0);
-            if (plane_in && rowin && xr < nx)
-                v = gs_value<T>(src, f, invD, wx, wy, wz, (long long)k * Q + (long long)y * P + xr,
-                                P, Q);
-            red[s0][ty + 1][xr - x0 + 1] = v;
+        // (1) red values of plane k from the prefetched operands
+        int xr;
+        const bool own = own_ok(k, xr);
+        const T v_own = own ? eval_red(R) : T(0);
+        int rx = 0, ry = 0;
+        const bool ring_here = (ring_row || ring_col) && k >= z0 && k < z1;
+        const bool ring_in = ring_here && ring_at(k, rx, ry);
+        const T v_ring = ring_in ? eval_red(G) : T(0);
+        // ask L2 for the own column two planes ahead (more bytes in flight
+        // than the registers alone can hold)
+        if (k + 2 <= z1 && k + 2 < nz && rowin) {
+            const long long c2 = cidx(k + 2, y, xa);
+            prefetch_l2(src + c2 + Q);
+            prefetch_l2(f + c2);
+            prefetch_l2(invD + c2);
+            prefetch_l2(wx + c2);
+            prefetch_l2(wy + c2);
+            prefetch_l2(wz + c2 + Q);
         }
-        // ... and the red cells of the ring, needed by this plane's black cells
-        if (k >= z0 && k < z1) {
-            if (ty < 2) {
-                const int yy = (ty == 0) ? y0 - 1 : y0 + kTY;
-                const int xr = x0 + 2 * tx + ((yy + k) & 1);
-                T v = T(0);
-                if (yy >= 0 && yy < ny && xr < nx)
-                    v = gs_value<T>(src, f, invD, wx, wy, wz,
-                                    (long long)k * Q + (long long)yy * P + xr, P, Q);
-                red[s0][ty == 0 ? 0 : kTY + 1][xr - x0 + 1] = v;
-            } else if (ty == 2 && tx < kTY) {
-                const int xx = (tx < kTY / 2) ? x0 - 1 : x0 + 2 * kTX;
-                const int m = tx % (kTY / 2);
-                const int yy = y0 + 2 * m + ((xx + y0 + k) & 1);
-                T v = T(0);
-                if (xx >= 0 && xx < nx && yy < ny)
-                    v = gs_value<T>(src, f, invD, wx, wy, wz,
-                                    (long long)k * Q + (long long)yy * P + xx, P, Q);
-                red[s0][yy - y0 + 1][xx - x0 + 1] = v;
-            }
+        // prefetch step k+1: own red at k+1, ring at k+1, black at plane k
+        RedIn<T> Rn, Gn;
+        BlackIn<T> Bn;
+        {
+            int xr1;
+            const bool ok = k + 1 <= z1 && own_ok(k + 1, xr1);
+            load_red(Rn, ok, src, f, invD, wx, wy, wz, ok ? cidx(k + 1, y, xr1) : 0, P, Q);
+            int gx = 0, gy = 0;
+            const bool gok = (ring_row || ring_col) && k + 1 >= z0 && k + 1 < z1 &&
+                             ring_at(k + 1, gx, gy);
+            load_red(Gn, gok, src, f, invD, wx, wy, wz, gok ? cidx(k + 1, gy, gx) : 0, P, Q);
+            const int xb = xa + (((y + k) & 1) ^ 1);
+            const bool bok = k >= z0 && k < z1 && rowin && xb < nx;
+            load_black(Bn, bok, f, invD, wx, wy, wz, bok ? cidx(k, y, xb) : 0, P, Q);
+        }
+        red[s0][ty + 1][xr - x0 + 1] = v_own;
+        if (ring_here) {
+            int gx, gy;
+            ring_at(k, gx, gy);
+            red[s0][gy - y0 + 1][gx - x0 + 1] = v_ring;
         }
         __syncthreads();
         // (2) black values of plane k-1, then store the pair of plane k-1
@@ -185,14 +309,13 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_sweep(BoxSet<T> S, const int 
             const T rv = red[sm][ty + 1][xa + parm - x0 + 1];
             T bv = T(0);
             if (xb < nx) {
-                const long long c = (long long)km * Q + (long long)y * P + xb;
-                T s = wx[c] * red[sm][ty + 1][lb - 1];
-                s = fmadd(wx[c + 1], red[sm][ty + 1][lb + 1], s);
-                s = fmadd(wy[c], red[sm][ty][lb], s);
-                s = fmadd(wy[c + P], red[sm][ty + 2][lb], s);
-                s = fmadd(wz[c], red[smm][ty + 1][lb], s);
-                s = fmadd(wz[c + Q], red[s0][ty + 1][lb], s);
-                bv = (s - f[c]) * invD[c];
+                T s = Bk.wxa * red[sm][ty + 1][lb - 1];
+                s = fmadd(Bk.wxb, red[sm][ty + 1][lb + 1], s);
+                s = fmadd(Bk.wya, red[sm][ty][lb], s);
+                s = fmadd(Bk.wyb, red[sm][ty + 2][lb], s);
+                s = fmadd(Bk.wza, red[smm][ty + 1][lb], s);
+                s = fmadd(Bk.wzb, red[s0][ty + 1][lb], s);
+                bv = (s - Bk.f) * Bk.id;
             }
             const long long c0 = (long long)km * Q + (long long)y * P + xa;
             const T va = parm ? bv : rv;
@@ -207,6 +330,9 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_sweep(BoxSet<T> S, const int 
             }
         }
         __syncthreads();
+        R = Rn;
+        G = Gn;
+        Bk = Bn;
     }
 }
 
@@ -240,21 +366,65 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
     B.phic[cc] = T(0);
 }
 
+// After a red-black sweep every black cell satisfies its own equation (its
+// residual is rounding-level), so right after smoothing the residual is
+// carried by the red cells alone.  This variant restricts the residual of the
+// 4 red children of each coarse cell (the black 4 count as zero): half the
+// stencil work of k_resid_restrict, the same coarse right-hand side to
+// rounding.  Valid only when the last operation on phi was a black pass.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
+                                                                 const int *__restrict__ active)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_COARSE];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<T> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    const int nx = B.nx, ny = B.ny, nz = B.nz, P = B.P;
+    const long long Q = B.Q;
+    TilePos p = tile_pos(TK_COARSE, nx, ny, nz, t - ts[b]);
+    const int I = p.x, J = p.y, K = p.z;
+    if (I >= nx / 2 || J >= ny / 2) return;
+    // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c) even
+    const long long o = (long long)(2 * K) * Q + (long long)(2 * J) * P + 2 * I;
+    T sum = residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o, P, Q);
+    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + P + 1, P, Q);
+    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + 1, P, Q);
+    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + P, P, Q);
+    const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
+    B.fc[cc] = sum * T(0.125);
+    B.phic[cc] = T(0);
+}
+
 // --------------------------------------------------------- prolongation ----
 
+// One thread per coarse cell: its correction is added to the 8 children (two
+// rows of two planes, each child pair one vector store when nx allows).
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__restrict__ active)
 {
     const int t = blockIdx.x;
-    const int *ts = S.tstart[TK_CELL];
+    const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
-    if (p.x >= B.nx || p.y >= B.ny) return;
-    const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    const long long cc = (long long)(p.z >> 1) * B.cQ + (long long)(p.y >> 1) * B.cP + (p.x >> 1);
-    B.phi[c] += B.phic[cc];
+    TilePos p = tile_pos(TK_COARSE, B.nx, B.ny, B.nz, t - ts[b]);
+    const int I = p.x, J = p.y, K = p.z;
+    if (I >= B.nx / 2 || J >= B.ny / 2) return;
+    const T e = B.phic[(long long)K * B.cQ + (long long)J * B.cP + I];
+    const long long o = (long long)(2 * K) * B.Q + (long long)(2 * J) * B.P + 2 * I;
+    typedef typename Vec2<T>::type V2;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            V2 *q = reinterpret_cast<V2 *>(B.phi + o + c * B.Q + r * B.P);
+            V2 v = *q;
+            v.x += e;
+            v.y += e;
+            *q = v;
+        }
 }
 
 // -------------------------------------------------------- residual field ----
@@ -274,22 +444,30 @@ __global__ void __launch_bounds__(kThreads) k_residual_field(BoxSet<T> S)
 
 // ------------------------------------------------------------- norms ----
 
+// mode 0: residual of every cell; 1: f; 2: residual of the red cells only
+// (right after a red-black sweep), one thread per red-black pair so that no
+// lane idles.  Each thread adds a column of kColZ planes.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const int *__restrict__ active,
                                                             int mode, double *__restrict__ partials)
 {
+    const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
     const int t = blockIdx.x;
-    const int *ts = S.tstart[TK_COLZ];
+    const int *ts = S.tstart[kind];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
+    TilePos p = tile_pos(kind, B.nx, B.ny, B.nz, t - ts[b]);
     double v = 0.0;
-    if (p.x < B.nx && p.y < B.ny) {
+    const int ex = mode == 2 ? (B.nx + 1) / 2 : B.nx;
+    if (p.x < ex && p.y < B.ny) {
         const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
         for (int k = z0; k < z1; ++k) {
-            const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
-            const T r = mode ? B.f[c] : residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+            const int x = mode == 2 ? 2 * p.x + ((p.y + k) & 1) : p.x;
+            if (x >= B.nx) continue;
+            const long long c = (long long)k * B.Q + (long long)p.y * B.P + x;
+            const T r = mode == 1 ? B.f[c]
+                                  : residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
             v = fma((double)r, (double)r, v);
         }
     }
@@ -305,13 +483,13 @@ __global__ void __launch_bounds__(1024) k_norm_finish(BoxSet<T> S, const int *__
                                                       double *__restrict__ out,
                                                       double *__restrict__ copy,
                                                       double *__restrict__ inv,
-                                                      const double *__restrict__ mult)
+                                                      const double *__restrict__ mult, int kind)
 {
     __shared__ double wsum[32];
     const int b = blockIdx.x;
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    const int *ts = S.tstart[TK_COLZ];
+    const int *ts = S.tstart[kind];
     const int lo = ts[b], hi = ts[b + 1];
     double s = 0.0;
     for (int q = lo + (int)threadIdx.x; q < hi; q += 1024) s += partials[q];
@@ -539,6 +717,49 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
 }
 
+// ----------------------------------------------- on-device convergence ----
+//
+// The same decision as the host loop, per active box, after each cycle:
+// non-finite -> MG_ERR_NONFINITE; rel <= tol -> MG_OK; rel > 1e3 max(rel0,
+// tol) -> MG_ERR_DIVERGED; five cycles in a row without a 10% gain over the
+// best, or max_cycles reached -> MG_ERR_NOT_CONVERGED.  A decided box is made
+// inactive; the loop continues (graph condition 1) while any box is active.
+__global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restrict__ norm,
+                                                const double *__restrict__ normf,
+                                                int *__restrict__ active, JudgeState J,
+                                                cudaGraphConditionalHandle handle, int use_handle)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const int c = *J.step + 1;
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
+        if (!active[b]) continue;
+        const double rel = norm[b] / normf[b];
+        if (c < MG_MAX_HIST) J.hist[(long long)b * MG_MAX_HIST + c] = rel;
+        J.cycles[b] = c;
+        int st = MG_ERR_NOT_CONVERGED;
+        bool done = true;
+        if (!isfinite(rel)) st = MG_ERR_NONFINITE;
+        else if (rel <= *J.tol) st = MG_OK;
+        else if (rel > 1e3 * fmax(J.rel0[b], *J.tol)) st = MG_ERR_DIVERGED;
+        else {
+            int stall = rel > 0.9 * J.best[b] ? J.stall[b] + 1 : 0;
+            J.stall[b] = stall;
+            J.best[b] = fmin(J.best[b], rel);
+            done = stall >= 5 || c >= J.max_cycles;
+        }
+        J.status[b] = st;
+        if (done) active[b] = 0;
+        else any = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *J.step = c;
+        if (use_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+    }
+}
+
 // ------------------------------------------------- packing and helpers ----
 
 __global__ void __launch_bounds__(kThreads) k_pack(BoxSet<double> S, const long long *__restrict__ off,
@@ -604,18 +825,20 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 }
 
 // ------------------------------------------------------------- set-up ----
+//
+// Each set-up step is a per-position device function, called by a one-box
+// kernel (the single-stage entry points) and by a set kernel that covers
+// every box of a level in one launch (the solver).
 
 __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
-// Thread per position (i, j, k) in [0, nx] x [0, ny] x [0, nz].
-__global__ void k_face_weights(int nx, int ny, int nz, int P, long long Q, double inv_h2,
-                               const double *__restrict__ beta, double *__restrict__ wx,
-                               double *__restrict__ wy, double *__restrict__ wz)
+// Face weights at position (i, j, k) in [0, nx] x [0, ny] x [0, nz]: harmonic
+// mean of the two cells' beta (2 beta on a wall face) over h^2.
+__device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, long long Q,
+                                                double inv_h2, const double *__restrict__ beta,
+                                                double *wx, double *wy, double *wz, int i, int j,
+                                                int k)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i > nx || j > ny || k > nz) return;
     auto bc = [&](int a, int bb, int c) { return beta[((long long)c * ny + bb) * nx + a]; };
     const long long q = (long long)k * Q + (long long)j * P + i;
     if (j < ny && k < nz) {
@@ -637,16 +860,14 @@ __global__ void k_face_weights(int nx, int ny, int nz, int P, long long Q, doubl
 
 // Coarse position (I, J, K) in [0, cx] x [0, cy] x [0, cz]; coarse face
 // beta = mean of the 4 fine faces, coarse h = 2h: w_c = (sum of 4 w) / 16.
-__global__ void k_coarsen(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
-                          const double *__restrict__ wy, const double *__restrict__ wz, int cP,
-                          long long cQ, double *__restrict__ cwx, double *__restrict__ cwy,
-                          double *__restrict__ cwz)
+__device__ __forceinline__ void coarsen_at(int nx, int ny, int nz, int P, long long Q,
+                                           const double *__restrict__ wx,
+                                           const double *__restrict__ wy,
+                                           const double *__restrict__ wz, int cP, long long cQ,
+                                           double *cwx, double *cwy, double *cwz, int I, int J,
+                                           int K)
 {
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int K = blockIdx.z;
-    if (I > cx || J > cy || K > cz) return;
     auto at = [&](int i, int j, int k) { return (long long)k * Q + (long long)j * P + i; };
     const long long cq = (long long)K * cQ + (long long)J * cP + I;
     if (J < cy && K < cz)
@@ -660,31 +881,26 @@ __global__ void k_coarsen(int nx, int ny, int nz, int P, long long Q, const doub
                    wz[at(2 * I, 2 * J + 1, 2 * K)] + wz[at(2 * I + 1, 2 * J + 1, 2 * K)]) * 0.0625;
 }
 
-__global__ void k_inv_diag(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
-                           const double *__restrict__ wy, const double *__restrict__ wz,
-                           double *__restrict__ invD, double *__restrict__ Dout)
+__device__ __forceinline__ void inv_diag_at(int P, long long Q, const double *__restrict__ wx,
+                                            const double *__restrict__ wy,
+                                            const double *__restrict__ wz, double *invD,
+                                            double *Dout, long long c)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= nx || j >= ny || k >= nz) return;
-    const long long c = (long long)k * Q + (long long)j * P + i;
     const double D = ((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]);
     invD[c] = 1.0 / D;
     if (Dout) Dout[c] = D;
 }
 
-// Positions (i, j, k) in [0, nx] x [0, ny] x [0, nz]: every stored weight.
-__global__ void k_round_f32(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
-                            const double *__restrict__ wy, const double *__restrict__ wz,
-                            const double *__restrict__ invD, float *__restrict__ wx32,
-                            float *__restrict__ wy32, float *__restrict__ wz32,
-                            float *__restrict__ invD32)
+// Every stored weight (and the inverse diagonal) at position (i, j, k) in
+// [0, nx] x [0, ny] x [0, nz], rounded to FP32.
+__device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long long Q,
+                                         const double *__restrict__ wx,
+                                         const double *__restrict__ wy,
+                                         const double *__restrict__ wz,
+                                         const double *__restrict__ invD, float *wx32,
+                                         float *wy32, float *wz32, float *invD32, int i, int j,
+                                         int k)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i > nx || j > ny || k > nz) return;
     const long long q = (long long)k * Q + (long long)j * P + i;
     if (j < ny && k < nz) wx32[q] = (float)wx[q];
     if (i < nx && k < nz) wy32[q] = (float)wy[q];
@@ -692,18 +908,15 @@ __global__ void k_round_f32(int nx, int ny, int nz, int P, long long Q, const do
     if (i < nx && j < ny && k < nz) invD32[q] = (float)invD[q];
 }
 
-// One CTA: assemble M = -A (symmetric positive definite) densely in work,
-// invert it by Gauss-Jordan elimination without pivoting (M is diagonally
-// dominant), and write A^{-1} = -M^{-1}.
-__global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz, int P, long long Q,
-                                                         const double *__restrict__ wx,
-                                                         const double *__restrict__ wy,
-                                                         const double *__restrict__ wz,
-                                                         double *__restrict__ a,
-                                                         double *__restrict__ inv64,
-                                                         float *__restrict__ inv32)
+// The calling CTA assembles M = -A (symmetric positive definite) densely in
+// `a`, inverts it by Gauss-Jordan elimination without pivoting (M is
+// diagonally dominant) and writes A^{-1} = -M^{-1} (FP64, and FP32 if inv32).
+__device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P, long long Q,
+                                                   const double *__restrict__ wx,
+                                                   const double *__restrict__ wy,
+                                                   const double *__restrict__ wz, double *a,
+                                                   double *inv64, float *inv32, double *col)
 {
-    __shared__ double col[MG_BOTTOM_CELLS];
     const int n = nx * ny * nz;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -747,6 +960,153 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
         inv64[e] = v;
         if (inv32) inv32[e] = (float)v;
     }
+}
+
+// ---- one box (single-stage entry points): grid over positions
+
+__global__ void k_face_weights(int nx, int ny, int nz, int P, long long Q, double inv_h2,
+                               const double *__restrict__ beta, double *__restrict__ wx,
+                               double *__restrict__ wy, double *__restrict__ wz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i > nx || j > ny || k > nz) return;
+    face_weights_at(nx, ny, nz, P, Q, inv_h2, beta, wx, wy, wz, i, j, k);
+}
+
+__global__ void k_coarsen(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
+                          const double *__restrict__ wy, const double *__restrict__ wz, int cP,
+                          long long cQ, double *__restrict__ cwx, double *__restrict__ cwy,
+                          double *__restrict__ cwz)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I > nx / 2 || J > ny / 2 || K > nz / 2) return;
+    coarsen_at(nx, ny, nz, P, Q, wx, wy, wz, cP, cQ, cwx, cwy, cwz, I, J, K);
+}
+
+__global__ void k_inv_diag(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
+                           const double *__restrict__ wy, const double *__restrict__ wz,
+                           double *__restrict__ invD, double *__restrict__ Dout)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny || k >= nz) return;
+    inv_diag_at(P, Q, wx, wy, wz, invD, Dout, (long long)k * Q + (long long)j * P + i);
+}
+
+__global__ void k_round_f32(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
+                            const double *__restrict__ wy, const double *__restrict__ wz,
+                            const double *__restrict__ invD, float *__restrict__ wx32,
+                            float *__restrict__ wy32, float *__restrict__ wz32,
+                            float *__restrict__ invD32)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i > nx || j > ny || k > nz) return;
+    round_at(nx, ny, nz, P, Q, wx, wy, wz, invD, wx32, wy32, wz32, invD32, i, j, k);
+}
+
+__global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz, int P, long long Q,
+                                                         const double *__restrict__ wx,
+                                                         const double *__restrict__ wy,
+                                                         const double *__restrict__ wz,
+                                                         double *__restrict__ a,
+                                                         double *__restrict__ inv64,
+                                                         float *__restrict__ inv32)
+{
+    __shared__ double col[MG_BOTTOM_CELLS];
+    bottom_inverse_cta(nx, ny, nz, P, Q, wx, wy, wz, a, inv64, inv32, col);
+}
+
+// ---- every box of a level in one launch (the solver's set-up)
+
+// step 0 faces (TK_FACE), 1 coarsen (TK_CFACE), 2 diagonal (TK_CELL),
+// 3 FP32 copies (TK_FACE)
+__global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
+{
+    const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[kind];
+    const int b = find_box(ts, S.nbox, t);
+    const SetupBox &B = S.boxes[b];
+    const TilePos p = tile_pos(kind, B.nx, B.ny, B.nz, t - ts[b]);
+    int ex, ey, ez;
+    tile_extent(kind, B.nx, B.ny, B.nz, ex, ey, ez);
+    if (p.x >= ex || p.y >= ey) return;
+    if (step == 0)
+        face_weights_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.beta, B.wx, B.wy, B.wz, p.x, p.y,
+                        p.z);
+    else if (step == 1)
+        coarsen_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.cP, B.cQ, B.cwx, B.cwy, B.cwz,
+                   p.x, p.y, p.z);
+    else if (step == 2)
+        inv_diag_at(B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.D,
+                    (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
+    else
+        round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
+                 B.invD32, p.x, p.y, p.z);
+}
+
+// One CTA per box: the coarsest level's dense inverse.
+__global__ void __launch_bounds__(1024) k_setup_bottom(SetupSet S)
+{
+    __shared__ double col[MG_BOTTOM_CELLS];
+    const SetupBox &B = S.boxes[blockIdx.x];
+    bottom_inverse_cta(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.work, B.inv64, B.inv32,
+                       col);
+}
+
+// ----------------------------------------------------- projection steps ----
+//
+// The velocity constraint around the solve (the equation of a MAESTRO step
+// enforces it): f = div(u) - S from face velocities, and after the solve
+// u -= beta_face grad(phi) on every face (phi = 0 outside, wall faces with
+// doubled beta), so that div(u) = S.  beta_face / h = w h with the stored
+// level weights w = beta_face / h^2.  Velocity and cell arrays are in their
+// natural C layouts: u (nz, ny, nx+1), v (nz, ny+1, nx), w (nz+1, ny, nx).
+
+__global__ void k_project_rhs(int nx, int ny, int nz, double inv_h, const double *__restrict__ u,
+                              const double *__restrict__ v, const double *__restrict__ w,
+                              const double *__restrict__ S, double *__restrict__ f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny || k >= nz) return;
+    const long long ux = ((long long)k * ny + j) * (nx + 1) + i;
+    const long long vy = ((long long)k * (ny + 1) + j) * nx + i;
+    const long long wz = ((long long)k * ny + j) * nx + i;
+    const long long c = wz;
+    const double d = (u[ux + 1] - u[ux]) + (v[vy + nx] - v[vy]) + (w[wz + (long long)nx * ny] - w[wz]);
+    f[c] = d * inv_h - (S ? S[c] : 0.0);
+}
+
+__global__ void k_project_correct(int nx, int ny, int nz, int P, long long Q, double h,
+                                  const double *__restrict__ wx, const double *__restrict__ wy,
+                                  const double *__restrict__ wzf, const double *__restrict__ phi,
+                                  double *__restrict__ u, double *__restrict__ v,
+                                  double *__restrict__ w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i > nx || j > ny || k > nz) return;
+    auto ph = [&](int a, int b, int c) -> double {
+        if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) return 0.0;
+        return phi[((long long)c * ny + b) * nx + a];
+    };
+    const long long q = (long long)k * Q + (long long)j * P + i;
+    if (j < ny && k < nz)
+        u[((long long)k * ny + j) * (nx + 1) + i] -= wx[q] * h * (ph(i, j, k) - ph(i - 1, j, k));
+    if (i < nx && k < nz)
+        v[((long long)k * (ny + 1) + j) * nx + i] -= wy[q] * h * (ph(i, j, k) - ph(i, j - 1, k));
+    if (i < nx && j < ny)
+        w[((long long)k * ny + j) * nx + i] -= wzf[q] * h * (ph(i, j, k) - ph(i, j, k - 1));
 }
 
 // dbeta += chain of dL/dbeta_face through the harmonic mean (see mg.h).
@@ -798,7 +1158,7 @@ template <class T>
 int sweep_ctas_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep<T>, kThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep<T>, kTX * kSweepTY, 0) !=
         cudaSuccess) {
         cudaGetLastError();
         return 4;
@@ -813,7 +1173,7 @@ cudaError_t launch_rbgs_sweep(const BoxSet<T> &S, const int *active, int src_is_
                               cudaStream_t st)
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
-    k_rbgs_sweep<T><<<S.ntiles[TK_SWEEP], block2d(), 0, st>>>(S, active, src_is_phi2);
+    k_rbgs_sweep<T><<<S.ntiles[TK_SWEEP], dim3(kTX, kSweepTY), 0, st>>>(S, active, src_is_phi2);
     return counted(cudaGetLastError());
 }
 
@@ -826,10 +1186,18 @@ cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStr
 }
 
 template <class T>
+cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st)
+{
+    if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
+    k_resid_restrict_red<T><<<S.ntiles[TK_COARSE], block2d(), 0, st>>>(S, active);
+    return counted(cudaGetLastError());
+}
+
+template <class T>
 cudaError_t launch_prolong(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
-    if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_prolong<T><<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, active);
+    if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
+    k_prolong<T><<<S.ntiles[TK_COARSE], block2d(), 0, st>>>(S, active);
     return counted(cudaGetLastError());
 }
 
@@ -845,18 +1213,20 @@ template <class T>
 cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode, double *partials,
                                  cudaStream_t st)
 {
-    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
-    k_norm_partials<T><<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, active, mode, partials);
+    const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
+    if (S.ntiles[kind] == 0) return cudaSuccess;
+    k_norm_partials<T><<<S.ntiles[kind], block2d(), 0, st>>>(S, active, mode, partials);
     return counted(cudaGetLastError());
 }
 
 template <class T>
 cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const double *partials,
                                double *out, double *copy, double *inv, cudaStream_t st,
-                               const double *mult)
+                               const double *mult, int mode)
 {
     if (S.nbox == 0) return cudaSuccess;
-    k_norm_finish<T><<<S.nbox, 1024, 0, st>>>(S, active, partials, out, copy, inv, mult);
+    const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
+    k_norm_finish<T><<<S.nbox, 1024, 0, st>>>(S, active, partials, out, copy, inv, mult, kind);
     return counted(cudaGetLastError());
 }
 
@@ -893,6 +1263,15 @@ cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float
     if (S64.ntiles[TK_COLZ] == 0) return cudaSuccess;
     k_refine_residual<<<S64.ntiles[TK_COLZ], block2d(), 0, st>>>(S64, S32, active, c_r_inv,
                                                                   partials);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int *active,
+                         const JudgeState &J, cudaGraphConditionalHandle handle, int use_handle,
+                         cudaStream_t st)
+{
+    k_judge<<<1, nbox < 1024 ? ((nbox + 31) / 32) * 32 : 1024, 0, st>>>(nbox, norm, normf, active,
+                                                                        J, handle, use_handle);
     return counted(cudaGetLastError());
 }
 
@@ -978,6 +1357,37 @@ cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, cons
     return counted(cudaGetLastError());
 }
 
+cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st)
+{
+    const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
+    if (S.ntiles[kind] == 0) return cudaSuccess;
+    k_setup<<<S.ntiles[kind], block2d(), 0, st>>>(S, step);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_setup_bottom(const SetupSet &S, cudaStream_t st)
+{
+    if (S.nbox == 0) return cudaSuccess;
+    k_setup_bottom<<<S.nbox, 1024, 0, st>>>(S);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_project_rhs(int nx, int ny, int nz, double h, const double *u, const double *v,
+                               const double *w, const double *S, double *f, cudaStream_t st)
+{
+    k_project_rhs<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, 1.0 / h, u, v, w, S, f);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_project_correct(int nx, int ny, int nz, double h, const double *wx,
+                                   const double *wy, const double *wz, const double *phi,
+                                   double *u, double *v, double *w, cudaStream_t st)
+{
+    k_project_correct<<<grid3(nx + 1, ny + 1, nz + 1), block2d(), 0, st>>>(
+        nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny), h, wx, wy, wz, phi, u, v, w);
+    return counted(cudaGetLastError());
+}
+
 cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double *beta,
                              const double *phi, const double *lam, double *dbeta, cudaStream_t st)
 {
@@ -990,13 +1400,15 @@ cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double
     template cudaError_t launch_rbgs_pass<T>(const BoxSet<T> &, const int *, int, cudaStream_t);  \
     template cudaError_t launch_rbgs_sweep<T>(const BoxSet<T> &, const int *, int, cudaStream_t); \
     template cudaError_t launch_resid_restrict<T>(const BoxSet<T> &, const int *, cudaStream_t);  \
+    template cudaError_t launch_resid_restrict_red<T>(const BoxSet<T> &, const int *,             \
+                                                      cudaStream_t);                              \
     template cudaError_t launch_prolong<T>(const BoxSet<T> &, const int *, cudaStream_t);         \
     template cudaError_t launch_residual_field<T>(const BoxSet<T> &, cudaStream_t);               \
     template cudaError_t launch_norm_partials<T>(const BoxSet<T> &, const int *, int, double *,   \
                                                  cudaStream_t);                                   \
     template cudaError_t launch_norm_finish<T>(const BoxSet<T> &, const int *, const double *,    \
                                                double *, double *, double *, cudaStream_t,        \
-                                               const double *);                                   \
+                                               const double *, int);                              \
     template cudaError_t launch_bottom<T>(const BoxSet<T> &, const int *, int, cudaStream_t);   \
     template cudaError_t launch_zero<T>(const BoxSet<T> &, const int *, cudaStream_t);          \
     template cudaError_t launch_coarse_vcycle<T>(const CoarseJob<T> *, int, const int *, int, int, \

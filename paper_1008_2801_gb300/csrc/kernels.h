@@ -15,6 +15,22 @@ long long launch_counter();
 template <class T>
 cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, cudaStream_t st);
 
+// ---- FP32 fused sweep fed by the Tensor Memory Accelerator (sweep_tma.cu)
+struct SweepMaps;  // seven tensor maps of one box level (device memory, 64-B aligned)
+size_t sweep_maps_size();
+// The TMA sweep serves levels whose rows and planes hold a whole copy box.
+bool sweep_tma_fits(int nx, int ny);
+// Encode the maps from the arrays' allocation bases (logical (0, 0, -1));
+// false if the driver offers no encoder.
+bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_base,
+                       const float *phi2_base, const float *f_base, const float *invD_base,
+                       const float *wx_base, const float *wy_base, const float *wz_base);
+int sweep_tma_ctas_per_sm();
+// Same result as launch_rbgs_sweep<float>; *err is set to 1 if a bounded
+// wait on a tile copy gave up (the CTA then stops).
+cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps,
+                                  const int *active, int src_is_phi2, int *err, cudaStream_t st);
+
 // Resident CTAs per SM of the fused sweep kernel (occupancy query).
 template <class T>
 int sweep_ctas_per_sm();
@@ -29,6 +45,11 @@ cudaError_t launch_rbgs_sweep(const BoxSet<T> &S, const int *active, int src_is_
 template <class T>
 cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStream_t st);
 
+// Same, right after a red-black sweep: only the 4 red children carry a
+// residual (black cells satisfy their equations), half the stencil work.
+template <class T>
+cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st);
+
 // phi += phic[parent].
 template <class T>
 cudaError_t launch_prolong(const BoxSet<T> &S, const int *active, cudaStream_t st);
@@ -39,7 +60,8 @@ cudaError_t launch_residual_field(const BoxSet<T> &S, cudaStream_t st);
 
 // Residual norm of level 0: partial sums, then out[Box::box] (see below).
 
-// Per-tile partial sums of squares: mode 0 = residual f - A phi, mode 1 = f.
+// Per-tile partial sums of squares: mode 0 = residual f - A phi, mode 1 = f,
+// mode 2 = residual at red cells only (right after a red-black sweep).
 template <class T>
 cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode,
                                  double *partials, cudaStream_t st);
@@ -47,11 +69,12 @@ cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode
 // out[Box::box] = sqrt(sum of the box's partials), fixed order; inactive
 // boxes keep their old value.  copy and inv (nullable) receive the same value
 // and its reciprocal (0 for a zero norm).
-// mult (nullable, per box) scales the norm before it is stored.
+// mult (nullable, per box) scales the norm before it is stored; mode is the
+// partials' mode (their tile kind).
 template <class T>
 cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const double *partials,
                                double *out, double *copy, double *inv, cudaStream_t st,
-                               const double *mult = nullptr);
+                               const double *mult = nullptr, int mode = 0);
 
 // Coarsest level: phi = Ainv f (dense, one warp per row).
 template <class T>
@@ -71,6 +94,12 @@ cudaError_t launch_refine_update(const BoxSet<double> &S64, const BoxSet<float> 
 cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float> &S32,
                                    const int *active, const double *c_r_inv, double *partials,
                                    cudaStream_t st);
+
+// One convergence decision per active box after a cycle (see k_judge); sets
+// the graph condition to "any box still active" when use_handle is 1.
+cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int *active,
+                         const JudgeState &J, cudaGraphConditionalHandle handle, int use_handle,
+                         cudaStream_t st);
 
 // ---- moving data between packed user arrays and the level layout --------
 // user[off[b] + (k*ny + j)*nx + i] -> level 0 f (to_f) or phi of box b.
@@ -103,6 +132,21 @@ cudaError_t launch_round_f32(int nx, int ny, int nz, const double *wx, const dou
 cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, const double *wy,
                                   const double *wz, double *work, double *inv64, float *inv32,
                                   cudaStream_t st);
+// ---- set-up of every box of a level in one launch ------------------------
+// step 0: face weights from beta; 1: coarse weights; 2: D and 1/D; 3: FP32
+// copies.
+cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st);
+// The coarsest level's dense inverse, one CTA per box.
+cudaError_t launch_setup_bottom(const SetupSet &S, cudaStream_t st);
+
+// Projection steps (natural layouts): f = div(u, v, w) - S (S nullable), and
+// u, v, w -= beta_face grad(phi) using the level-0 weights.
+cudaError_t launch_project_rhs(int nx, int ny, int nz, double h, const double *u, const double *v,
+                               const double *w, const double *S, double *f, cudaStream_t st);
+cudaError_t launch_project_correct(int nx, int ny, int nz, double h, const double *wx,
+                                   const double *wy, const double *wz, const double *phi,
+                                   double *u, double *v, double *w, cudaStream_t st);
+
 cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double *beta,
                              const double *phi, const double *lam, double *dbeta,
                              cudaStream_t st);

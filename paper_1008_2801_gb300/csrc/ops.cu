@@ -1,7 +1,9 @@
 // ops.cu -- single-stage entry points (mg_ops.h): one box, caller-owned
 // arrays in the level layout, one kernel (or a short fixed sequence) each.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "kernels.h"
 #include "mg_ops.h"
@@ -197,6 +199,40 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
     });
 }
 
+int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const float *wz,
+                         const float *invD, const float *f, const float *phi_in, float *phi_out,
+                         int zc, void *stream)
+{
+    if (bad_dims(n) || !wx || !wy || !wz || !invD || !f || !phi_in || !phi_out ||
+        phi_in == phi_out)
+        return set_error(MG_ERR_INVALID_ARG, "bad argument (phi_in and phi_out must differ)");
+    cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    Box<float> B = level_box<float>(n, wx, wy, wz, invD, f, phi_in, phi_out);
+    B.zc = zc > 0 ? zc : kSweepZ;
+    std::vector<char> host(sweep_maps_size() + 64);
+    SweepMaps *m = reinterpret_cast<SweepMaps *>(round_up((long long)(uintptr_t)host.data(), 64));
+    if (!sweep_tma_fits(n[0], n[1]))
+        return set_error(MG_ERR_UNSUPPORTED, "level too small for the TMA sweep (nx >= 64, ny >= 11)");
+    if (!encode_sweep_maps(m, n[0], n[1], n[2], phi_in, phi_out, f, invD, wx, wy, wz))
+        return set_error(MG_ERR_UNSUPPORTED, "tensor maps cannot be encoded on this driver");
+    TempSet<float> ts;
+    int rc = ts.make(B, st);
+    if (rc != MG_OK) return rc;
+    char *dev = nullptr;
+    CKO(cudaMallocAsync(&dev, sweep_maps_size() + 64, st));
+    int *err = reinterpret_cast<int *>(dev + sweep_maps_size());
+    CKO(cudaMemcpyAsync(dev, m, sweep_maps_size(), cudaMemcpyHostToDevice, st));
+    CKO(cudaMemsetAsync(err, 0, sizeof(int), st));
+    CKO(launch_rbgs_sweep_tma(ts.S, reinterpret_cast<const SweepMaps *>(dev), nullptr, 0, err, st));
+    int herr = 0;
+    CKO(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKO(cudaStreamSynchronize(st));
+    CKO(cudaFreeAsync(dev, st));
+    if (herr) return set_error(MG_ERR_TIMEOUT, "a tile-copy wait gave up");
+    return MG_OK;
+}
+
 int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
                    const void *D, const void *f, const void *phi, void *r, void *stream)
 {
@@ -227,6 +263,26 @@ int mg_op_residual_restrict(int prec, const int n[3], const void *wx, const void
         B.cQ = pitch_plane(c[0], c[1]);
         return with_set(B, (cudaStream_t)stream, [&](const BoxSet<T> &S) {
             return launch_resid_restrict(S, nullptr, (cudaStream_t)stream);
+        });
+    });
+}
+
+int mg_op_residual_restrict_red(int prec, const int n[3], const void *wx, const void *wy,
+                                const void *wz, const void *D, const void *f, const void *phi,
+                                void *fc, void *phic, void *stream)
+{
+    if (bad_dims(n) || !all_even(n) || !wx || !wy || !wz || !f || !phi || !fc || !phic)
+        return set_error(MG_ERR_INVALID_ARG, "bad argument (fine dims must be even)");
+    const int c[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
+    DISPATCH(prec, {
+        Box<T> B = level_box<T>(n, wx, wy, wz, nullptr, f, phi, nullptr);
+        B.D = logical<T>(D, n);
+        B.fc = logical<T>(fc, c);
+        B.phic = logical<T>(phic, c);
+        B.cP = (int)pitch_row(c[0]);
+        B.cQ = pitch_plane(c[0], c[1]);
+        return with_set(B, (cudaStream_t)stream, [&](const BoxSet<T> &S) {
+            return launch_resid_restrict_red(S, nullptr, (cudaStream_t)stream);
         });
     });
 }

@@ -28,6 +28,7 @@ struct Hier {
     std::vector<T *> ainv;                      // [box] dense coarsest-level inverse
     std::vector<BoxSet<T>> smooth;              // [level]: boxes not yet at their bottom
     std::vector<char> fused;                    // [level]: smooth with fused sweeps
+    std::vector<const SweepMaps *> maps;        // [level]: TMA maps of the level's boxes (or null)
     BoxSet<T> fine{};                           // level 0 of every box
     BoxSet<T> bottom{};                         // coarsest level of every box
     std::vector<int> lc;                        // [box] first level run by the coarse kernel
@@ -45,6 +46,7 @@ struct ProfSlot {
 struct Solver {
     int dev = 0;
     int nbox = 0;
+    bool shared = false;  // all boxes are one box's right-hand sides: one weight set
     mg_opts opts{};
     std::vector<std::array<int, 3>> n;              // [box] fine dims (nx, ny, nz)
     std::vector<double> dx;                          // [box]
@@ -74,7 +76,7 @@ struct Solver {
     int *dside = nullptr;          // [nbox] device: 1 if the solution ended in phi2
     double *hnorm = nullptr;       // pinned [2 * nbox]
     int *hactive = nullptr;        // pinned [nbox]
-    int *hside = nullptr;          // pinned [nbox]
+    int *hside = nullptr;          // pinned [nbox + 1]; the last is the error word's copy
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;  // packed staging
     cudaStream_t cap = nullptr;    // capture stream
     cudaEvent_t ev_setup0 = nullptr, ev_setup1 = nullptr;
@@ -96,10 +98,28 @@ struct Solver {
     long long kernels = 0;                // kernels launched by this solver
     long long cap_kernels = 0;            // kernels enqueued into graph captures
     long long graph_kernels64 = 0, graph_kernels32 = 0;
+
+    // set-up launch sets
+    std::vector<SetupSet> setup_lv;       // [level] every box that has the level
+    std::vector<SetupSet> setup_coarsen;  // [level] boxes that have level + 1
+    SetupSet setup_bottom{};              // coarsest level of every box
+
+    int *derr = nullptr;                  // device error word (bounded waits that gave up)
+    bool tma = false;                     // FP32 fused sweeps use the TMA kernel
+
+    // on-device convergence loop (conditional CUDA graph)
+    char *jblock = nullptr;               // device: judge state block
+    char *hjblock = nullptr;              // pinned host mirror
+    size_t jbytes = 0;
+    JudgeState J{};
+    cudaGraphExec_t loop64 = nullptr, loop32 = nullptr;
+    long long loop_kernels64 = 0, loop_kernels32 = 0;  // kernels per loop iteration
 };
 
+// shared_weights: the nbox boxes are right-hand sides of one box (same dims,
+// dx and beta); weights, diagonals and the coarsest inverse exist once.
 int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
-                  const mg_opts *opts);
+                  const mg_opts *opts, bool shared_weights = false);
 void solver_destroy(Solver *s);
 int solver_set_beta(Solver *s, const double *beta_packed, cudaStream_t st);
 // Solve every box; f/phi packed.  zero_guess ignores phi's input.

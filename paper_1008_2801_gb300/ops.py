@@ -114,6 +114,16 @@ def rbgs_sweep(w, invD, f, phi_in, shape, phi_out=None, zc=0):
     return phi_out
 
 
+def rbgs_sweep_tma(w, invD, f, phi_in, shape, phi_out=None, zc=0):
+    """FP32 fused sweep with TMA-staged tiles (bitwise equal to rbgs_sweep)."""
+    if phi_out is None:
+        phi_out = torch.zeros_like(phi_in)
+    check(_lib.load().mg_op_rbgs_sweep_tma(_n(shape), *map(_p, w), _p(invD), _p(f), _p(phi_in),
+                                           _p(phi_out), int(zc), _s(phi_in)),
+          "mg_op_rbgs_sweep_tma")
+    return phi_out
+
+
 def residual(w, f, phi, shape, D=None):
     r = torch.zeros_like(phi)
     check(_lib.load().mg_op_residual(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D), _p(f),
@@ -121,15 +131,16 @@ def residual(w, f, phi, shape, D=None):
     return r
 
 
-def residual_restrict(w, f, phi, shape, D=None):
+def residual_restrict(w, f, phi, shape, D=None, red_only=False):
     nz, ny, nx = shape
     c = (nz // 2, ny // 2, nx // 2)
     fc = level(c, phi.dtype, phi.device)
     phic = level(c, phi.dtype, phi.device)
     phic.fill_(7.0)  # must come back zero inside the box
-    check(_lib.load().mg_op_residual_restrict(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D),
-                                              _p(f), _p(phi), _p(fc), _p(phic), _s(phi)),
-          "mg_op_residual_restrict")
+    L = _lib.load()
+    fn = L.mg_op_residual_restrict_red if red_only else L.mg_op_residual_restrict
+    check(fn(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D), _p(f), _p(phi), _p(fc), _p(phic),
+             _s(phi)), "mg_op_residual_restrict")
     return fc, phic
 
 

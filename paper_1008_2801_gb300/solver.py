@@ -44,7 +44,8 @@ def _check_tensor(t, name, numel=None, device=None):
         raise ValueError(f"{name} is on {t.device}, solver on {device}")
 
 
-def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0):
+def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
+          full_residual=False, tma=False):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -52,6 +53,9 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0):
     o.use_graph = 1 if use_graph else 0
     o.smoother = SMOOTHERS[smoother]
     o.coarse_cells = int(coarse_cells)
+    o.inner_cycles = int(inner_cycles)
+    o.full_residual = 1 if full_residual else 0
+    o.tma = 1 if tma else 0
     return o
 
 
@@ -80,7 +84,8 @@ class Solver:
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
-                 use_graph=True, smoother="auto", device=None, coarse_cells=0):
+                 use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
+                 full_residual=False, tma=False):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -89,7 +94,8 @@ class Solver:
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
-        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells)
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
+                  full_residual, tma)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, 0,
                               ctypes.byref(o)), "mg_create")
@@ -156,6 +162,45 @@ class Solver:
             raise MGError(rc, "mg_adjoint")
         return lam, dbeta
 
+    # ---- projection steps around the solve (the velocity constraint)
+
+    def _vel_check(self, u, v, w):
+        nz, ny, nx = self.shape
+        for t, nm, shp in ((u, "u", (nz, ny, nx + 1)), (v, "v", (nz, ny + 1, nx)),
+                           (w, "w", (nz + 1, ny, nx))):
+            _check_tensor(t, nm, shp[0] * shp[1] * shp[2], self.device)
+            if not t.is_cuda:
+                raise ValueError(f"{nm} must be on the solver's device")
+
+    def project_rhs(self, u, v, w, S=None):
+        """f = div(u, v, w) - S (face velocities in natural layouts)."""
+        self._vel_check(u, v, w)
+        f = torch.empty(self.shape, dtype=torch.float64, device=u.device)
+        if S is not None:
+            _check_tensor(S, "S", self.numel, self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().mg_project_rhs(self._h, _ptr(u), _ptr(v), _ptr(w),
+                                             _ptr(S) if S is not None else None, _ptr(f),
+                                             _stream_of(u)), "mg_project_rhs")
+        return f
+
+    def project_correct(self, phi, u, v, w):
+        """u, v, w -= beta_face grad(phi), in place."""
+        self._vel_check(u, v, w)
+        _check_tensor(phi, "phi", self.numel, self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().mg_project_correct(self._h, _ptr(phi), _ptr(u), _ptr(v), _ptr(w),
+                                                 _stream_of(u)), "mg_project_correct")
+        return u, v, w
+
+    def project(self, u, v, w, S=None, tol=1e-10):
+        """Make div(u, v, w) = S: form f, solve div(beta grad phi) = f, correct
+        the face velocities in place.  Returns (phi, stats)."""
+        f = self.project_rhs(u, v, w, S)
+        phi, st = self.solve(f, tol=tol)
+        self.project_correct(phi, u, v, w)
+        return phi, st
+
     def profile(self, on: bool = True):
         """Record per-stage device times (CUDA events inside the V-cycle graph)."""
         check(_lib.load().mg_profile_enable(self._h, 1 if on else 0), "mg_profile_enable")
@@ -190,7 +235,8 @@ class BatchSolver:
     are packed back to back in box order (see ``pack``/``unpack``)."""
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
-                 use_graph=True, smoother="auto", device=None, coarse_cells=0):
+                 use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
+                 full_residual=False, tma=False):
         L = _lib.load()
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         nb = len(self.shapes)
@@ -200,7 +246,8 @@ class BatchSolver:
         n = (ctypes.c_int * (3 * nb))(*[v for s in self.shapes for v in (s[2], s[1], s[0])])
         d = (ctypes.c_double * nb)(*dxs)
         self._h = ctypes.c_void_p()
-        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells)
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
+                  full_residual, tma)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, 0, ctypes.byref(o)),
                   "mg_batch_create")

@@ -1,0 +1,25 @@
+"""Cache logic of the autotuner (no GPU): keys, round trip, candidate sets."""
+import json
+
+from paper_1008_2801_gb300 import autotune
+
+
+def test_cache_round_trip(tmp_path, monkeypatch):
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("MG_TUNE_CACHE", str(path))
+    assert autotune.lookup("GPU", [(8, 8, 8)], "fp64") is None
+    autotune.record("GPU", [(8, 8, 8)], "fp64", {"smoother": "passes"}, 1.5)
+    autotune.record("GPU", [(8, 8, 8)], "mixed", {"smoother": "fused"}, 1.0)
+    assert autotune.lookup("GPU", [(8, 8, 8)], "fp64")["opts"] == {"smoother": "passes"}
+    assert autotune.lookup("GPU", [(8, 8, 8)], "mixed")["ms"] == 1.0
+    assert autotune.lookup("GPU", [(8, 8, 16)], "fp64") is None
+    assert len(json.loads(path.read_text())) == 2
+
+
+def test_candidates_cover_the_options():
+    c64 = list(autotune.candidates("fp64"))
+    cmx = list(autotune.candidates("mixed"))
+    assert len(cmx) == 3 * len(c64)
+    assert {c["smoother"] for c in c64} == {"auto", "passes", "fused"}
+    assert {c["inner_cycles"] for c in cmx} == {1, 2, 3}
+    assert autotune.key("G", [(2, 3, 4), (5, 6, 7)], "fp64") == "G|fp64|2x3x4;5x6x7"

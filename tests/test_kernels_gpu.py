@@ -129,6 +129,23 @@ def test_fused_sweep_equals_red_then_black(cuda_device, shape, dtype, zc):
     assert not full[0].any() and not full[-1].any() and not full[:, :, shape[2]:].any()
 
 
+@pytest.mark.parametrize("zc", [0, 1, 3, 8])
+@pytest.mark.parametrize("shape", [(12, 11, 64), (70, 20, 130), (33, 40, 136)])
+def test_tma_sweep_is_bitwise_the_plain_sweep(cuda_device, shape, zc):
+    # same arithmetic in the same order; only the operand staging differs
+    beta, f, phi, h = _case(shape, 14)
+    w, invD = _weights(beta, h, shape, cuda_device, torch.float32)
+    ft = _level(shape, f, cuda_device, torch.float32)
+    pin = _level(shape, phi, cuda_device, torch.float32)
+    before = pin.clone()
+    a = K.rbgs_sweep(w, invD, ft, pin, shape, zc=zc)
+    b = K.rbgs_sweep_tma(w, invD, ft, pin, shape, zc=zc)
+    assert torch.equal(pin, before)
+    assert torch.equal(a, b)
+    full = b.cpu()
+    assert not full[0].any() and not full[-1].any() and not full[:, :, shape[2]:].any()
+
+
 @pytest.mark.parametrize("stored_diag", [False, True])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("shape", SHAPES)
@@ -176,6 +193,26 @@ def test_residual_restrict_and_prolong(cuda_device, shape, dtype, stored_diag):
     want = O.prolong_add(e, phi)
     got = K.get(pt, shape).cpu().double().numpy()
     assert np.max(np.abs(got - want)) <= _tol(dtype) * 2
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", EVEN)
+def test_red_children_restriction_after_a_sweep(cuda_device, shape, dtype):
+    # right after a red then black pass the black residuals vanish (to
+    # rounding), so restricting the red children alone equals the oracle's
+    # residual + restriction of the same state
+    beta, f, phi, h = _case(shape, 13)
+    faces = O.face_beta(beta)
+    phi = O.rbgs_pass(faces, h, f, O.rbgs_pass(faces, h, f, phi, 0), 1)
+    w, _ = _weights(beta, h, shape, cuda_device, dtype)
+    D = K.inv_diag(w, shape, with_diag=True)[1] if dtype == torch.float64 else None
+    fc, phic = K.residual_restrict(w, _level(shape, f, cuda_device, dtype),
+                                   _level(shape, phi, cuda_device, dtype), shape, D, red_only=True)
+    c = tuple(s // 2 for s in shape)
+    ref = O.restrict(O.residual(faces, h, f, phi))
+    scale = np.max(np.abs(f)) + 2 * 6 * np.max(faces[0]) / h ** 2 * np.max(np.abs(phi))
+    assert np.max(np.abs(K.get(fc, c).cpu().double().numpy() - ref)) <= _tol(dtype) * scale
+    assert not K.get(phic, c).any()
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (3, 8, 8), (7, 3, 5), (4, 16, 16)])
