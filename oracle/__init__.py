@@ -9,6 +9,11 @@ function, each stated in that file's header); this wrapper only marshals
 numpy arrays.  Arrays are float64 in C order: cells (nz, ny, nx), x faces
 (nz, ny, nx+1), y faces (nz, ny+1, nx), z faces (nz+1, ny, nx).
 
+Walls: every function that builds face coefficients takes ``bc``, a mask
+with bit w set when wall w (x-, x+, y-, y+, z-, z+) is Neumann; 0 means every
+wall Dirichlet.  ``bc_lift`` moves non-zero wall values to the right-hand side;
+``wall_values`` gives the packed layout of those values.
+
 Parity status: every function here is pinned by the CPU tests in
 ``tests/test_oracle.py`` (closed forms, invariants, dense direct solves and
 finite differences); none is "parity unpinned".
@@ -60,6 +65,8 @@ def lib():
             L.oracle_num_threads.restype = _I
             L.oracle_set_threads.argtypes = [_I]
             L.oracle_face_beta.argtypes = [_I, _I, _I, _D, _D, _D, _D]
+            L.oracle_face_beta_bc.argtypes = [_I, _I, _I, _D, _I, _D, _D, _D]
+            L.oracle_bc_lift.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D]
             L.oracle_coarsen_faces.argtypes = [_I, _I, _I, _D, _D, _D, _D, _D, _D]
             L.oracle_apply.argtypes = [_I, _I, _I, _F, _D, _D, _D, _D, _D]
             L.oracle_residual.argtypes = [_I, _I, _I, _F, _D, _D, _D, _D, _D, _D]
@@ -73,6 +80,13 @@ def lib():
             L.oracle_solve.argtypes = [_I, _I, _I, _F, _D, _D, _D, _F, _I, _I, _I, _D,
                                        ctypes.POINTER(_I)]
             L.oracle_solve.restype = _I
+            L.oracle_solve_bc.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D, _F, _I, _I, _I, _D,
+                                          ctypes.POINTER(_I)]
+            L.oracle_solve_bc.restype = _I
+            L.oracle_beta_grad_bc.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D, _D]
+            L.oracle_adjoint_bc.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D, _D, _D, _F, _I,
+                                            ctypes.POINTER(_I)]
+            L.oracle_adjoint_bc.restype = _I
             L.oracle_beta_grad.argtypes = [_I, _I, _I, _F, _D, _D, _D, _D]
             L.oracle_adjoint.argtypes = [_I, _I, _I, _F, _D, _D, _D, _D, _D, _F, _I,
                                          ctypes.POINTER(_I)]
@@ -80,6 +94,7 @@ def lib():
             DN = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
             L.oracle_divergence.argtypes = [_I, _I, _I, _F, _D, _D, _D, ctypes.c_void_p, _D]
             L.oracle_correct.argtypes = [_I, _I, _I, _F, _D, _D, DN, DN, DN]
+            L.oracle_correct_bc.argtypes = [_I, _I, _I, _F, _D, _I, _D, DN, DN, DN]
             _lib = L
     return _lib
 
@@ -101,15 +116,40 @@ def set_threads(n: int) -> None:
     lib().oracle_set_threads(int(n))
 
 
-def face_beta(beta):
-    """Face coefficients (bx, by, bz) from cell beta (harmonic mean, 2 beta on walls)."""
+def face_beta(beta, bc=0):
+    """Face coefficients (bx, by, bz) from cell beta: harmonic mean inside;
+    2 beta on Dirichlet walls, 0 on the Neumann walls of the mask ``bc``."""
     beta = _c(beta)
     nx, ny, nz = _dims(beta)
     bx = np.empty((nz, ny, nx + 1))
     by = np.empty((nz, ny + 1, nx))
     bz = np.empty((nz + 1, ny, nx))
-    lib().oracle_face_beta(nx, ny, nz, beta, bx, by, bz)
+    lib().oracle_face_beta_bc(nx, ny, nz, beta, int(bc), bx, by, bz)
     return bx, by, bz
+
+
+def wall_shapes(shape):
+    """Shapes of the six packed wall arrays (x-, x+, y-, y+, z-, z+) of an
+    (nz, ny, nx) box: x walls (nz, ny), y walls (nz, nx), z walls (ny, nx)."""
+    nz, ny, nx = shape
+    return [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+
+
+def wall_values(walls):
+    """Packs six wall arrays (x-, x+, y-, y+, z-, z+) into one flat array."""
+    return np.concatenate([_c(w).ravel() for w in walls])
+
+
+def bc_lift(beta, h, f, vals, bc=0):
+    """f minus the lift of the packed wall values ``vals`` (Dirichlet: phi on
+    the wall; Neumann: outward flux beta dphi/dn), for walls of mask ``bc``."""
+    beta = _c(beta)
+    f = _c(f).copy()
+    vals = _c(vals).ravel()
+    nx, ny, nz = _dims(beta)
+    assert vals.size == 2 * (ny * nz + nz * nx + ny * nx)
+    lib().oracle_bc_lift(nx, ny, nz, float(h), beta, int(bc), vals, f)
+    return f
 
 
 def coarsen_faces(bx, by, bz):
@@ -183,28 +223,30 @@ def levels(n):
     return [tuple(int(v) for v in d[3 * i:3 * i + 3]) for i in range(k)]
 
 
-def solve(beta, f, h, tol=1e-13, max_cycles=200, phi0=None, nu1=2, nu2=2):
-    """Solve div(beta grad phi) = f; returns (phi, info dict)."""
+def solve(beta, f, h, tol=1e-13, max_cycles=200, phi0=None, nu1=2, nu2=2, bc=0):
+    """Solve div(beta grad phi) = f with homogeneous walls of mask ``bc``;
+    returns (phi, info dict).  With every wall Neumann (bc = 63) f loses its
+    mean and phi has zero mean."""
     beta, f = _c(beta), _c(f)
     nx, ny, nz = _dims(f)
     phi = np.zeros_like(f) if phi0 is None else _c(phi0).copy()
     hist = np.zeros(max_cycles + 1)
     cyc = _I(0)
-    s = lib().oracle_solve(nx, ny, nz, float(h), beta, f, phi, float(tol), int(max_cycles),
-                           int(nu1), int(nu2), hist, ctypes.byref(cyc))
+    s = lib().oracle_solve_bc(nx, ny, nz, float(h), beta, int(bc), f, phi, float(tol),
+                              int(max_cycles), int(nu1), int(nu2), hist, ctypes.byref(cyc))
     return phi, {"status": STATUS[s], "cycles": cyc.value, "hist": hist[:cyc.value + 1].copy()}
 
 
-def beta_grad(beta, h, phi, lam):
+def beta_grad(beta, h, phi, lam, bc=0):
     """dL/dbeta_cell from one (phi, lambda) pair."""
     beta, phi, lam = _c(beta), _c(phi), _c(lam)
     nx, ny, nz = _dims(beta)
     out = np.zeros_like(beta)
-    lib().oracle_beta_grad(nx, ny, nz, float(h), beta, phi, lam, out)
+    lib().oracle_beta_grad_bc(nx, ny, nz, float(h), beta, int(bc), phi, lam, out)
     return out
 
 
-def adjoint(beta, h, phi, g, tol=1e-13, max_cycles=200):
+def adjoint(beta, h, phi, g, tol=1e-13, max_cycles=200, bc=0):
     """Returns (lambda = dL/df, dL/dbeta_cell, info) for dL/dphi = g.
 
     ``phi`` and ``g`` may carry a leading right-hand-side dimension; the beta
@@ -222,8 +264,8 @@ def adjoint(beta, h, phi, g, tol=1e-13, max_cycles=200):
     for b in range(phi.shape[0]):
         lb = np.zeros_like(beta)
         cyc = _I(0)
-        s = lib().oracle_adjoint(nx, ny, nz, float(h), beta, _c(phi[b]), _c(g[b]), lb, dbeta,
-                                 float(tol), int(max_cycles), ctypes.byref(cyc))
+        s = lib().oracle_adjoint_bc(nx, ny, nz, float(h), beta, int(bc), _c(phi[b]), _c(g[b]),
+                                    lb, dbeta, float(tol), int(max_cycles), ctypes.byref(cyc))
         lam[b] = lb
         infos.append({"status": STATUS[s], "cycles": cyc.value})
     return (lam[0] if single else lam), dbeta, infos
@@ -243,12 +285,12 @@ def divergence(u, v, w, h, S=None):
     return f
 
 
-def correct(beta, h, phi, u, v, w):
+def correct(beta, h, phi, u, v, w, bc=0):
     """Returns the face velocities minus beta_face grad(phi) (copies)."""
     beta, phi = _c(beta), _c(phi)
     u, v, w = _c(u).copy(), _c(v).copy(), _c(w).copy()
     nx, ny, nz = _dims(beta)
-    lib().oracle_correct(nx, ny, nz, float(h), beta, phi, u, v, w)
+    lib().oracle_correct_bc(nx, ny, nz, float(h), beta, int(bc), phi, u, v, w)
     return u, v, w
 
 

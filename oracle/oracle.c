@@ -36,7 +36,20 @@
  *                to cell beta through the harmonic mean;
  *   projection   f = div(u) - S from face velocities; after the solve each
  *                face velocity loses beta_face (phi_high - phi_low) / h, so
- *                the corrected field has div = S.
+ *                the corrected field has div = S;
+ *   walls        a mask bc selects each wall's condition, bit w for wall w in
+ *                the order x-, x+, y-, y+, z-, z+: bit clear = Dirichlet (the
+ *                wall face carries 2 beta, as above), bit set = Neumann (no
+ *                flux through the wall: the wall face carries 0).  Non-zero
+ *                wall values move to the right-hand side (a lift): a
+ *                Dirichlet value g adds 2 beta (g - phi_c)/h^2 to row c, a
+ *                Neumann outward flux q (beta dphi/dn) adds q/h, so the solve
+ *                runs on f - 2 beta g/h^2 - q/h with homogeneous walls.  With
+ *                every wall Neumann, A is singular (constants): the solve
+ *                removes the mean of f (the compatibility condition) and
+ *                returns the zero-mean solution; its coarsest level is solved
+ *                with M + c 1 1^T, which is positive definite and exact on
+ *                zero-mean right-hand sides.
  *
  * Loops over cells run under OpenMP where each iteration is independent; all
  * reductions are serial, so results do not depend on the thread count.
@@ -98,16 +111,23 @@ void oracle_set_threads(int n)
 
 static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
-/* Face coefficients from cell beta: harmonic mean inside, 2 beta on walls. */
-void oracle_face_beta(int nx, int ny, int nz, const double *beta,
-                      double *bx, double *by, double *bz)
+/* Wall w (0..5 = x-, x+, y-, y+, z-, z+) is Neumann when bit w of bc is set. */
+static int neumann(int bc, int w) { return (bc >> w) & 1; }
+
+/* The coefficient of a wall face next to a cell of coefficient b. */
+static double wall_face(int bc, int w, double b) { return neumann(bc, w) ? 0.0 : 2.0 * b; }
+
+/* Face coefficients from cell beta: harmonic mean inside; on walls 2 beta
+ * (Dirichlet) or 0 (Neumann) as the mask bc says. */
+void oracle_face_beta_bc(int nx, int ny, int nz, const double *beta, int bc,
+                         double *bx, double *by, double *bz)
 {
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i <= nx; ++i) {
                 double v;
-                if (i == 0) v = 2.0 * beta[cell(0, j, k, nx, ny)];
-                else if (i == nx) v = 2.0 * beta[cell(nx - 1, j, k, nx, ny)];
+                if (i == 0) v = wall_face(bc, 0, beta[cell(0, j, k, nx, ny)]);
+                else if (i == nx) v = wall_face(bc, 1, beta[cell(nx - 1, j, k, nx, ny)]);
                 else v = harmonic(beta[cell(i - 1, j, k, nx, ny)], beta[cell(i, j, k, nx, ny)]);
                 bx[xface(i, j, k, nx, ny)] = v;
             }
@@ -115,8 +135,8 @@ void oracle_face_beta(int nx, int ny, int nz, const double *beta,
         for (int j = 0; j <= ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 double v;
-                if (j == 0) v = 2.0 * beta[cell(i, 0, k, nx, ny)];
-                else if (j == ny) v = 2.0 * beta[cell(i, ny - 1, k, nx, ny)];
+                if (j == 0) v = wall_face(bc, 2, beta[cell(i, 0, k, nx, ny)]);
+                else if (j == ny) v = wall_face(bc, 3, beta[cell(i, ny - 1, k, nx, ny)]);
                 else v = harmonic(beta[cell(i, j - 1, k, nx, ny)], beta[cell(i, j, k, nx, ny)]);
                 by[yface(i, j, k, nx, ny)] = v;
             }
@@ -124,11 +144,49 @@ void oracle_face_beta(int nx, int ny, int nz, const double *beta,
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 double v;
-                if (k == 0) v = 2.0 * beta[cell(i, j, 0, nx, ny)];
-                else if (k == nz) v = 2.0 * beta[cell(i, j, nz - 1, nx, ny)];
+                if (k == 0) v = wall_face(bc, 4, beta[cell(i, j, 0, nx, ny)]);
+                else if (k == nz) v = wall_face(bc, 5, beta[cell(i, j, nz - 1, nx, ny)]);
                 else v = harmonic(beta[cell(i, j, k - 1, nx, ny)], beta[cell(i, j, k, nx, ny)]);
                 bz[zface(i, j, k, nx, ny)] = v;
             }
+}
+
+/* Face coefficients with every wall Dirichlet. */
+void oracle_face_beta(int nx, int ny, int nz, const double *beta,
+                      double *bx, double *by, double *bz)
+{
+    oracle_face_beta_bc(nx, ny, nz, beta, 0, bx, by, bz);
+}
+
+/* Right-hand-side lift of non-zero wall values.  vals holds one value per
+ * wall face, walls in the order x-, x+, y-, y+, z-, z+; an x wall is an
+ * (nz, ny) array, a y wall (nz, nx), a z wall (ny, nx), C order.  For a
+ * Dirichlet wall the value is phi on the wall and the adjacent cell's row
+ * gains 2 beta_c (g - phi_c)/h^2, of which the known part 2 beta_c g/h^2 is
+ * subtracted from f; for a Neumann wall it is the outward flux beta dphi/dn
+ * and q/h is subtracted from f. */
+void oracle_bc_lift(int nx, int ny, int nz, double h, const double *beta, int bc,
+                    const double *vals, double *f)
+{
+    double ih = 1.0 / h, ih2 = 1.0 / (h * h);
+    size_t off = 0;
+    for (int w = 0; w < 6; ++w) {
+        int axis = w / 2, hi = w & 1;
+        int na = axis == 0 ? ny : nx;                 /* fastest wall index */
+        int nb = axis == 2 ? ny : nz;                 /* slowest wall index */
+        for (int b = 0; b < nb; ++b)
+            for (int a = 0; a < na; ++a) {
+                int i, j, k;
+                if (axis == 0) { i = hi ? nx - 1 : 0; j = a; k = b; }
+                else if (axis == 1) { i = a; j = hi ? ny - 1 : 0; k = b; }
+                else { i = a; j = b; k = hi ? nz - 1 : 0; }
+                size_t c = cell(i, j, k, nx, ny);
+                double v = vals[off + (size_t)b * na + a];
+                if (neumann(bc, w)) f[c] -= v * ih;
+                else f[c] -= 2.0 * beta[c] * v * ih2;
+            }
+        off += (size_t)na * nb;
+    }
 }
 
 /* Coarse face beta = mean of the 4 fine faces that make up the coarse face.
@@ -302,8 +360,10 @@ typedef struct {
 
 typedef struct {
     int nlev, nu1, nu2;
+    int singular;            /* every wall Neumann: A has the constants as null space */
     level_t L[MAXLEV];
-    /* coarsest level: dense Cholesky factor of M = -h^2 A (SPD) */
+    /* coarsest level: dense Cholesky factor of M = -h^2 A (SPD), plus
+     * c 1 1^T when A is singular */
     int dense_n;
     double *chol;
 } hier_t;
@@ -323,7 +383,10 @@ static void free_hier(hier_t *H)
 
 /* Dense M = -h^2 A on the coarsest level, built column by column from the
  * operator applied to unit vectors, then factored M = L L^T in place
- * (lower triangle).  Returns 0, or -1 if M is not positive definite. */
+ * (lower triangle).  When A is singular, c 1 1^T with c = trace(M)/n^2 is
+ * added first: M + c 1 1^T is positive definite, and for a right-hand side
+ * of zero sum its solution is the zero-mean solution of M x = rhs.
+ * Returns 0, or -1 if the matrix is not positive definite. */
 static int factor_bottom(hier_t *H)
 {
     level_t *b = &H->L[H->nlev - 1];
@@ -341,6 +404,12 @@ static int factor_bottom(hier_t *H)
     free(e);
     free(col);
     double *a = H->chol;
+    if (H->singular) {
+        double tr = 0.0;
+        for (int c = 0; c < n; ++c) tr += a[(size_t)c * n + c];
+        double shift = tr / ((double)n * n);
+        for (size_t q = 0; q < (size_t)n * n; ++q) a[q] += shift;
+    }
     for (int j = 0; j < n; ++j) {
         double d = a[(size_t)j * n + j];
         for (int p = 0; p < j; ++p) d -= a[(size_t)j * n + p] * a[(size_t)j * n + p];
@@ -356,13 +425,28 @@ static int factor_bottom(hier_t *H)
     return 0;
 }
 
+static double mean(size_t n, const double *x)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) s += x[i];
+    return s / (double)n;
+}
+
+static void remove_mean(size_t n, double *x)
+{
+    double m = mean(n, x);
+    for (size_t i = 0; i < n; ++i) x[i] -= m;
+}
+
 /* Conjugate gradients on M x = rhs with M = -h^2 A, for coarsest levels too
- * large for a dense factor.  Iterates until ||rhs - M x|| <= 1e-15 ||rhs||
- * or the residual stops falling. */
-static void cg_bottom(level_t *b)
+ * large for a dense factor.  Iterates until ||rhs - M x|| <= 1e-15 ||rhs||.
+ * When A is singular the right-hand side loses its mean first (CG then stays
+ * in the zero-mean subspace, where M is positive definite). */
+static void cg_bottom(level_t *b, int singular)
 {
     size_t n = ncell(b);
     double *x = b->phi, *rhs = b->r;
+    if (singular) remove_mean(n, rhs);
     double *res = (double *)malloc(sizeof(double) * n);
     double *p = (double *)malloc(sizeof(double) * n);
     double *q = (double *)malloc(sizeof(double) * n);
@@ -410,19 +494,21 @@ static void bottom_solve(hier_t *H)
         }
     } else {
         for (size_t i = 0; i < n; ++i) b->r[i] = -h2 * b->f[i];
-        cg_bottom(b);
+        cg_bottom(b, H->singular);
     }
 }
 
-/* Build the hierarchy (faces on every level) from cell beta. */
+/* Build the hierarchy (faces on every level) from cell beta and the wall
+ * mask. */
 static int build_hier(hier_t *H, int nx, int ny, int nz, double h, const double *beta,
-                      int nu1, int nu2)
+                      int bc, int nu1, int nu2)
 {
     int dims[3 * MAXLEV];
     memset(H, 0, sizeof(*H));
     H->nlev = oracle_levels(nx, ny, nz, dims);
     H->nu1 = nu1;
     H->nu2 = nu2;
+    H->singular = (bc & 63) == 63;
     for (int l = 0; l < H->nlev; ++l) {
         level_t *L = &H->L[l];
         L->nx = dims[3 * l]; L->ny = dims[3 * l + 1]; L->nz = dims[3 * l + 2];
@@ -435,7 +521,7 @@ static int build_hier(hier_t *H, int nx, int ny, int nz, double h, const double 
         L->f = (double *)calloc(n, sizeof(double));
         L->r = (double *)calloc(n, sizeof(double));
         if (l == 0)
-            oracle_face_beta(L->nx, L->ny, L->nz, beta, L->bx, L->by, L->bz);
+            oracle_face_beta_bc(L->nx, L->ny, L->nz, beta, bc, L->bx, L->by, L->bz);
         else {
             level_t *F = &H->L[l - 1];
             oracle_coarsen_faces(F->nx, F->ny, F->nz, F->bx, F->by, F->bz, L->bx, L->by, L->bz);
@@ -480,6 +566,7 @@ static int run_cycles(hier_t *H, const double *f, double *phi, double tol, int m
     size_t n = ncell(L);
     memcpy(L->f, f, sizeof(double) * n);
     memcpy(L->phi, phi, sizeof(double) * n);
+    if (H->singular) remove_mean(n, L->f);
     double nf = norm2(n, L->f);
     if (cycles_out) *cycles_out = 0;
     if (!isfinite(nf)) return OR_NONFINITE;
@@ -502,40 +589,55 @@ static int run_cycles(hier_t *H, const double *f, double *phi, double tol, int m
         if (!isfinite(rn)) { status = OR_NONFINITE; break; }
         if (rn <= tol * nf) status = OR_OK;
     }
+    if (H->singular) remove_mean(n, L->phi);
     memcpy(phi, L->phi, sizeof(double) * n);
     if (cycles_out) *cycles_out = c;
     return status;
 }
 
-/* Solve A phi = f by V(nu1, nu2) cycles from the initial guess in phi until
- * ||f - A phi|| <= tol ||f|| or max_cycles.  hist (nullable, length
- * max_cycles + 1) receives the relative residual before each cycle and after
- * the last one.  Returns 0 converged, 1 not converged, 2 non-finite,
- * 3 bad hierarchy. */
-int oracle_solve(int nx, int ny, int nz, double h, const double *beta, const double *f,
-                 double *phi, double tol, int max_cycles, int nu1, int nu2,
-                 double *hist, int *cycles)
+/* Solve A phi = f (homogeneous walls of the mask bc) by V(nu1, nu2) cycles
+ * from the initial guess in phi until ||f - A phi|| <= tol ||f|| or
+ * max_cycles.  hist (nullable, length max_cycles + 1) receives the relative
+ * residual before each cycle and after the last one.  With every wall
+ * Neumann, f is taken without its mean and phi is returned with zero mean.
+ * Returns 0 converged, 1 not converged, 2 non-finite, 3 bad hierarchy. */
+int oracle_solve_bc(int nx, int ny, int nz, double h, const double *beta, int bc,
+                    const double *f, double *phi, double tol, int max_cycles, int nu1,
+                    int nu2, double *hist, int *cycles)
 {
     hier_t H;
-    if (build_hier(&H, nx, ny, nz, h, beta, nu1, nu2) != 0) { free_hier(&H); return OR_BAD; }
+    if (build_hier(&H, nx, ny, nz, h, beta, bc, nu1, nu2) != 0) {
+        free_hier(&H);
+        return OR_BAD;
+    }
     int s = run_cycles(&H, f, phi, tol, max_cycles, hist, cycles);
     free_hier(&H);
     return s;
 }
 
+/* The solve with every wall Dirichlet. */
+int oracle_solve(int nx, int ny, int nz, double h, const double *beta, const double *f,
+                 double *phi, double tol, int max_cycles, int nu1, int nu2,
+                 double *hist, int *cycles)
+{
+    return oracle_solve_bc(nx, ny, nz, h, beta, 0, f, phi, tol, max_cycles, nu1, nu2, hist,
+                           cycles);
+}
+
 /* dL/dbeta_cell += chain rule of the face products for one right-hand side:
  * dL/dbeta_face = (lambda_n - lambda_c)(phi_n - phi_c)/h^2 on inner faces and
- * lambda_c phi_c / h^2 on wall faces, times d beta_face / d beta_cell =
- * 2 beta_other^2 / (beta_c + beta_other)^2 inside and 2 on walls. */
-void oracle_beta_grad(int nx, int ny, int nz, double h, const double *beta,
-                      const double *phi, const double *lam, double *dbeta)
+ * lambda_c phi_c / h^2 on Dirichlet wall faces, times d beta_face /
+ * d beta_cell = 2 beta_other^2 / (beta_c + beta_other)^2 inside and 2 on
+ * Dirichlet walls; a Neumann wall face (coefficient 0) contributes nothing. */
+void oracle_beta_grad_bc(int nx, int ny, int nz, double h, const double *beta, int bc,
+                         const double *phi, const double *lam, double *dbeta)
 {
     double ih2 = 1.0 / (h * h);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 size_t c = cell(i, j, k, nx, ny);
-                double bc = beta[c], pc = phi[c], lc = lam[c];
+                double b_c = beta[c], pc = phi[c], lc = lam[c];
                 double acc = 0.0;
                 int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k},
                                 {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
@@ -545,9 +647,9 @@ void oracle_beta_grad(int nx, int ny, int nz, double h, const double *beta,
                     if (inside) {
                         size_t o = cell(a, b, d, nx, ny);
                         double g = (lam[o] - lc) * (phi[o] - pc) * ih2;
-                        double s = bc + beta[o];
+                        double s = b_c + beta[o];
                         acc += g * 2.0 * beta[o] * beta[o] / (s * s);
-                    } else {
+                    } else if (!neumann(bc, q)) {
                         acc += 2.0 * lc * pc * ih2;
                     }
                 }
@@ -555,19 +657,35 @@ void oracle_beta_grad(int nx, int ny, int nz, double h, const double *beta,
             }
 }
 
+void oracle_beta_grad(int nx, int ny, int nz, double h, const double *beta,
+                      const double *phi, const double *lam, double *dbeta)
+{
+    oracle_beta_grad_bc(nx, ny, nz, h, beta, 0, phi, lam, dbeta);
+}
+
 /* Adjoint of the solve for one right-hand side: lambda solves A lambda = g
  * (written to lam, which is also dL/df), and dbeta (cell beta gradient) is
  * accumulated.  Returns the solve status of the adjoint solve. */
+int oracle_adjoint_bc(int nx, int ny, int nz, double h, const double *beta, int bc,
+                      const double *phi, const double *g, double *lam, double *dbeta,
+                      double tol, int max_cycles, int *cycles)
+{
+    size_t n = (size_t)nx * ny * nz;
+    memset(lam, 0, sizeof(double) * n);
+    if ((bc & 63) == 63) return OR_BAD;   /* singular A: no adjoint of the gauge */
+    int s = oracle_solve_bc(nx, ny, nz, h, beta, bc, g, lam, tol, max_cycles, 2, 2, NULL,
+                            cycles);
+    if (s == OR_NONFINITE || s == OR_BAD) return s;
+    oracle_beta_grad_bc(nx, ny, nz, h, beta, bc, phi, lam, dbeta);
+    return s;
+}
+
 int oracle_adjoint(int nx, int ny, int nz, double h, const double *beta,
                    const double *phi, const double *g, double *lam, double *dbeta,
                    double tol, int max_cycles, int *cycles)
 {
-    size_t n = (size_t)nx * ny * nz;
-    memset(lam, 0, sizeof(double) * n);
-    int s = oracle_solve(nx, ny, nz, h, beta, g, lam, tol, max_cycles, 2, 2, NULL, cycles);
-    if (s == OR_NONFINITE || s == OR_BAD) return s;
-    oracle_beta_grad(nx, ny, nz, h, beta, phi, lam, dbeta);
-    return s;
+    return oracle_adjoint_bc(nx, ny, nz, h, beta, 0, phi, g, lam, dbeta, tol, max_cycles,
+                             cycles);
 }
 
 /* ------------------------------------------------------------ projection */
@@ -593,16 +711,17 @@ void oracle_divergence(int nx, int ny, int nz, double h, const double *u, const 
 
 /* Velocity correction after the solve: every face velocity loses the face
  * flux beta_face (phi_high - phi_low) / h, with phi = 0 outside the box and
- * the wall faces' doubled beta, so that div(u') = div(u) - A phi. */
-void oracle_correct(int nx, int ny, int nz, double h, const double *beta, const double *phi,
-                    double *u, double *v, double *w)
+ * the wall faces' coefficients of the mask bc (Neumann wall faces keep their
+ * velocity), so that div(u') = div(u) - A phi. */
+void oracle_correct_bc(int nx, int ny, int nz, double h, const double *beta, int bc,
+                       const double *phi, double *u, double *v, double *w)
 {
     size_t nfx = (size_t)nz * ny * (nx + 1), nfy = (size_t)nz * (ny + 1) * nx,
            nfz = (size_t)(nz + 1) * ny * nx;
     double *bx = (double *)malloc(sizeof(double) * nfx);
     double *by = (double *)malloc(sizeof(double) * nfy);
     double *bz = (double *)malloc(sizeof(double) * nfz);
-    oracle_face_beta(nx, ny, nz, beta, bx, by, bz);
+    oracle_face_beta_bc(nx, ny, nz, beta, bc, bx, by, bz);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i <= nx; ++i) {
@@ -627,4 +746,10 @@ void oracle_correct(int nx, int ny, int nz, double h, const double *beta, const 
     free(bx);
     free(by);
     free(bz);
+}
+
+void oracle_correct(int nx, int ny, int nz, double h, const double *beta, const double *phi,
+                    double *u, double *v, double *w)
+{
+    oracle_correct_bc(nx, ny, nz, h, beta, 0, phi, u, v, w);
 }
