@@ -2,7 +2,10 @@
  * mg.h -- C ABI of the GB300 multigrid solver for the cell-centred
  * variable-coefficient Poisson equation
  *
- *        div(beta grad phi) = f        on a box, phi = 0 on its walls.
+ *        div(beta grad phi) = f        on a box,
+ *
+ * each wall either Dirichlet (phi given on the wall; 0 unless lifted, see
+ * mg_bc_lift) or Neumann (outward flux beta dphi/dn given; 0 unless lifted).
  *
  * This is the linear solve of a MAESTRO time step (paper Sec. 1: the
  * velocity constraint of the low-Mach approximation gives a variable-
@@ -14,9 +17,13 @@
  *     ((i+1/2)dx, (j+1/2)dx, (k+1/2)dx); arrays are C order (nz, ny, nx),
  *     x fastest (the torch shape (nz, ny, nx));
  *   - face coefficients: harmonic mean 2 a b / (a + b) of the two cells' beta;
- *     a wall face takes 2 beta of its cell (the wall is dx/2 from the centre);
+ *     a face on a Dirichlet wall takes 2 beta of its cell (the wall is dx/2
+ *     from the centre), a face on a Neumann wall 0 (no flux);
  *   - (A phi)_c = sum over the 6 faces of beta_face (phi_nbr - phi_c) / dx^2,
- *     phi_nbr = 0 outside the box; A is symmetric negative definite;
+ *     phi_nbr = 0 outside the box; A is symmetric negative definite, or
+ *     negative semi-definite with the constants as null space when every
+ *     wall is Neumann (then f loses its mean and phi is returned with zero
+ *     mean: the compatible problem and its zero-mean solution);
  *   - geometric multigrid V(nu1, nu2) cycles, red-black Gauss-Seidel
  *     smoothing (red = (i+j+k) even first), restriction = mean of 8 children,
  *     piecewise-constant prolongation, coarse face = mean of 4 fine faces,
@@ -61,8 +68,16 @@ enum mg_status {
     MG_ERR_UNSUPPORTED = 8    /* shape or option outside what is implemented */
 };
 
-/* boundary conditions: homogeneous Dirichlet (phi = 0 on every wall) */
-enum { MG_BC_DIRICHLET0 = 0 };
+/* Boundary conditions: the bc argument of mg_create / mg_batch_create is a
+ * mask with bit w set when wall w is Neumann, walls numbered x-, x+, y-, y+,
+ * z-, z+ (0..5); a clear bit is a Dirichlet wall.  0 = every wall Dirichlet. */
+enum {
+    MG_BC_DIRICHLET0 = 0,
+    MG_BC_NEUMANN_XLO = 1, MG_BC_NEUMANN_XHI = 2,
+    MG_BC_NEUMANN_YLO = 4, MG_BC_NEUMANN_YHI = 8,
+    MG_BC_NEUMANN_ZLO = 16, MG_BC_NEUMANN_ZHI = 32,
+    MG_BC_NEUMANN_ALL = 63
+};
 
 /* precision of the V-cycles */
 enum {
@@ -115,10 +130,11 @@ typedef struct {
 void mg_default_opts(mg_opts *opts);
 
 /* Create a solver for an n = {nx, ny, nz} box with spacing dx > 0 on the
- * current CUDA device.  Builds the level list and allocates the hierarchy;
- * runs no kernel.  opts may be NULL (defaults).  Errors: INVALID_ARG (n < 1,
- * dx <= 0, bad options), UNSUPPORTED (bc != MG_BC_DIRICHLET0, or a coarsest
- * level above MG_MAX_BOTTOM cells, e.g. a 33^3 box), OOM, CUDA. */
+ * current CUDA device, walls of the mask bc.  Builds the level list and
+ * allocates the hierarchy; runs no kernel.  opts may be NULL (defaults).
+ * Errors: INVALID_ARG (n < 1, dx <= 0, bc outside 0..63, bad options),
+ * UNSUPPORTED (a coarsest level above MG_MAX_BOTTOM cells, e.g. a 33^3 box),
+ * OOM, CUDA. */
 int mg_create(mg_ctx **out, const int n[3], double dx, int bc, const mg_opts *opts);
 
 /* Set cell beta (nx*ny*nz values, all > 0 and finite).  Computes face
@@ -149,9 +165,11 @@ int mg_solve_multi(mg_ctx *ctx, int nrhs, const double *f, double *phi, double t
  *   dLdbeta (ADDED TO)   += sum over right-hand sides and over the 6 faces of
  *       each cell of dL/dbeta_face * d beta_face / d beta_cell, with
  *       dL/dbeta_face = (lambda_n - lambda_c)(phi_n - phi_c)/dx^2 inside and
- *       lambda_c phi_c / dx^2 on walls, d beta_face/d beta_c =
- *       2 beta_n^2 / (beta_c + beta_n)^2 inside and 2 on walls.
- * The forward beta must still be the one set.  Returns as mg_solve_multi. */
+ *       lambda_c phi_c / dx^2 on Dirichlet walls (0 on Neumann walls),
+ *       d beta_face/d beta_c = 2 beta_n^2 / (beta_c + beta_n)^2 inside and 2
+ *       on Dirichlet walls.
+ * The forward beta must still be the one set.  Returns as mg_solve_multi;
+ * UNSUPPORTED when every wall is Neumann (singular A). */
 int mg_adjoint(mg_ctx *ctx, int nrhs, const double *phi, const double *g, double *dLdf,
                double *dLdbeta, double tol, mg_stats *st, void *stream);
 
@@ -162,15 +180,32 @@ int mg_adjoint(mg_ctx *ctx, int nrhs, const double *phi, const double *g, double
  *   mg_project_rhs:     f = div(u, v, w) - S, div = sum of the face
  *                       differences / dx (S may be NULL for 0);
  *   mg_project_correct: u, v, w -= beta_face * (phi_high - phi_low) / dx on
- *                       every face, phi = 0 outside and wall faces with
- *                       2 beta (the operator's own faces), using the beta of
- *                       the last mg_set_beta; then div(u, v, w) = S up to the
- *                       solve's residual.
+ *                       every face, phi = 0 outside and the operator's own
+ *                       wall faces (2 beta on Dirichlet walls, 0 on Neumann
+ *                       walls, whose velocities are left as they are), using
+ *                       the beta of the last mg_set_beta; then
+ *                       div(u, v, w) = S up to the solve's residual.
  * Errors: INVALID_ARG (NULL, no beta set), CUDA. */
 int mg_project_rhs(mg_ctx *ctx, const double *u, const double *v, const double *w,
                    const double *S, double *f, void *stream);
 int mg_project_correct(mg_ctx *ctx, const double *phi, double *u, double *v, double *w,
                        void *stream);
+
+/* Non-zero wall values, lifted into the right-hand side:
+ *   f_out = f - sum over the walls next to each cell of
+ *           2 beta_c g / dx^2   (Dirichlet wall, g = phi on the wall), or
+ *           q / dx              (Neumann wall, q = outward flux beta dphi/dn),
+ * so that mg_solve(f_out) returns the solution with those wall values.
+ * vals packs one value per wall face, walls in the order x-, x+, y-, y+,
+ * z-, z+: an x wall is an (nz, ny) array, a y wall (nz, nx), a z wall
+ * (ny, nx), C order; 2 (ny nz + nz nx + ny nx) values in all.  Each value is
+ * read as Dirichlet or Neumann by the context's wall mask.  Uses the beta of
+ * the last mg_set_beta.  f and f_out (may be equal) are (nz, ny, nx).
+ * Device pointers on the context's device; async.  With every wall Neumann
+ * the problem is compatible when the fluxes balance the integral of f; the
+ * solve removes whatever mean is left.  Errors: INVALID_ARG (NULL, no beta
+ * set), CUDA. */
+int mg_bc_lift(mg_ctx *ctx, const double *vals, const double *f, double *f_out, void *stream);
 
 /* Level list of a context: *nlev levels, dims[3*l .. 3*l+2] = (nx, ny, nz)
  * of level l (dims may be NULL; room for 32 levels). */

@@ -37,10 +37,12 @@ enum { MG_OPS_F64 = 0, MG_OPS_F32 = 1 };
 int mg_layout(const int n[3], long long *P, long long *Q, long long *elems);
 
 /* Face weights from cell beta (contiguous (nz, ny, nx) float64):
- * w = harmonic mean of the two cells' beta / h^2, wall faces 2 beta / h^2.
- * Writes FP64 weights wx, wy, wz in the level layout. */
-int mg_op_face_weights(const int n[3], double h, const double *beta, double *wx, double *wy,
-                       double *wz, void *stream);
+ * w = harmonic mean of the two cells' beta / h^2; a wall face has 2 beta / h^2
+ * (Dirichlet wall) or 0 (Neumann wall), per the wall mask bc of mg.h
+ * (0..63; 0 = every wall Dirichlet).  Writes FP64 weights wx, wy, wz in the
+ * level layout. */
+int mg_op_face_weights(const int n[3], double h, int bc, const double *beta, double *wx,
+                       double *wy, double *wz, void *stream);
 
 /* Coarse weights of an all-even fine level n: w_c = (mean of the 4 fine faces
  * covering the coarse face) / 4, i.e. the coarse face beta is the mean of the
@@ -112,8 +114,11 @@ int mg_op_prolong_add(int prec, const int n_fine[3], const void *phic, void *phi
 
 /* Exact coarsest-level solve set-up: Ainv = A^{-1} as a dense row-major
  * (N, N) FP64 matrix, N = nx*ny*nz <= MG_MAX_BOTTOM, dense index
- * (k*ny + j)*nx + i.  work: N*N doubles of scratch. */
-int mg_op_bottom_inverse(const int n[3], const double *wx, const double *wy,
+ * (k*ny + j)*nx + i.  work: N*N doubles of scratch.  singular != 0 (every
+ * wall Neumann, A singular on the constants): Ainv = -(M + c 1 1^T)^{-1} with
+ * M = -A and c = trace(M) / N^2, so that x = Ainv r solves
+ * A x = r - mean(r); x has zero mean when r has. */
+int mg_op_bottom_inverse(const int n[3], int singular, const double *wx, const double *wy,
                          const double *wz, double *work, double *Ainv, void *stream);
 
 /* phi = Ainv f on the coarsest level (Ainv in the stage precision). */
@@ -161,9 +166,9 @@ int mg_op_refine(const int n[3], const double *wx, const double *wy, const doubl
                  void *stream);
 
 /* Beta gradient of one right-hand side (see mg_adjoint): dbeta += chain of
- * the face products of phi and lambda.  beta, phi, lambda, dbeta are
- * contiguous (nz, ny, nx) float64. */
-int mg_op_beta_grad(const int n[3], double h, const double *beta, const double *phi,
+ * the face products of phi and lambda; Neumann wall faces of the mask bc add
+ * nothing.  beta, phi, lambda, dbeta are contiguous (nz, ny, nx) float64. */
+int mg_op_beta_grad(const int n[3], double h, int bc, const double *beta, const double *phi,
                     const double *lambda, double *dbeta, void *stream);
 
 #ifdef __cplusplus

@@ -74,6 +74,7 @@ _SIGS = {
     "mg_levels": (c_int, [c_void_p, c_int_p, c_int_p]),
     "mg_project_rhs": (c_int, [c_void_p] * 7),
     "mg_project_correct": (c_int, [c_void_p] * 6),
+    "mg_bc_lift": (c_int, [c_void_p] * 5),
     "mg_destroy": (None, [c_void_p]),
     "mg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int_p,
                                 ctypes.POINTER(c_double), c_int, ctypes.POINTER(mg_opts)]),
@@ -89,8 +90,8 @@ _SIGS = {
     "mg_last_error": (ctypes.c_char_p, []),
     # mg_ops.h
     "mg_layout": (c_int, [c_int3, c_ll_p, c_ll_p, c_ll_p]),
-    "mg_op_face_weights": (c_int, [c_int3, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
-                                   c_void_p]),
+    "mg_op_face_weights": (c_int, [c_int3, c_double, c_int, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p]),
     "mg_op_coarsen_weights": (c_int, [c_int3] + [c_void_p] * 7),
     "mg_op_inv_diag": (c_int, [c_int3] + [c_void_p] * 6),
     "mg_op_round_f32": (c_int, [c_int3] + [c_void_p] * 9),
@@ -101,13 +102,13 @@ _SIGS = {
     "mg_op_residual_restrict": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_residual_restrict_red": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_prolong_add": (c_int, [c_int, c_int3, c_void_p, c_void_p, c_void_p]),
-    "mg_op_bottom_inverse": (c_int, [c_int3] + [c_void_p] * 6),
+    "mg_op_bottom_inverse": (c_int, [c_int3, c_int] + [c_void_p] * 6),
     "mg_op_bottom_solve": (c_int, [c_int, c_int3] + [c_void_p] * 4),
     "mg_op_norm_scratch": (c_ll, [c_int3]),
     "mg_op_residual_norm": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_residual_norm_noalloc": (c_int, [c_int, c_int3] + [c_void_p] * 8),
     "mg_op_refine": (c_int, [c_int3] + [c_void_p] * 13),
-    "mg_op_beta_grad": (c_int, [c_int3, c_double] + [c_void_p] * 5),
+    "mg_op_beta_grad": (c_int, [c_int3, c_double, c_int] + [c_void_p] * 5),
 }
 
 

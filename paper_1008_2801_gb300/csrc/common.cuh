@@ -126,6 +126,7 @@ struct SetupBox {
     int cP;
     long long cQ;
     int zc;                             // unused (tile bookkeeping)
+    int bc;                             // wall mask: bit w set = wall w Neumann
 };
 typedef DescSet<SetupBox> SetupSet;
 

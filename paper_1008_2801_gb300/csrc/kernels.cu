@@ -832,28 +832,39 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 
 __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
+// Wall w (0..5 = x-, x+, y-, y+, z-, z+) is Neumann when bit w of the mask is
+// set: its faces carry no flux (weight 0); otherwise it is a Dirichlet wall
+// h/2 from the cell centre (2 beta of the cell).
+__device__ __forceinline__ double wall_beta(int bcm, int w, double b)
+{
+    return ((bcm >> w) & 1) ? 0.0 : 2.0 * b;
+}
+
 // Face weights at position (i, j, k) in [0, nx] x [0, ny] x [0, nz]: harmonic
-// mean of the two cells' beta (2 beta on a wall face) over h^2.
+// mean of the two cells' beta (a wall face: wall_beta) over h^2.
 __device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, long long Q,
-                                                double inv_h2, const double *__restrict__ beta,
-                                                double *wx, double *wy, double *wz, int i, int j,
-                                                int k)
+                                                double inv_h2, int bcm,
+                                                const double *__restrict__ beta, double *wx,
+                                                double *wy, double *wz, int i, int j, int k)
 {
     auto bc = [&](int a, int bb, int c) { return beta[((long long)c * ny + bb) * nx + a]; };
     const long long q = (long long)k * Q + (long long)j * P + i;
     if (j < ny && k < nz) {
-        double v = (i == 0) ? 2.0 * bc(0, j, k)
-                 : (i == nx) ? 2.0 * bc(nx - 1, j, k) : harmonic(bc(i - 1, j, k), bc(i, j, k));
+        double v = (i == 0) ? wall_beta(bcm, 0, bc(0, j, k))
+                 : (i == nx) ? wall_beta(bcm, 1, bc(nx - 1, j, k))
+                             : harmonic(bc(i - 1, j, k), bc(i, j, k));
         wx[q] = v * inv_h2;
     }
     if (i < nx && k < nz) {
-        double v = (j == 0) ? 2.0 * bc(i, 0, k)
-                 : (j == ny) ? 2.0 * bc(i, ny - 1, k) : harmonic(bc(i, j - 1, k), bc(i, j, k));
+        double v = (j == 0) ? wall_beta(bcm, 2, bc(i, 0, k))
+                 : (j == ny) ? wall_beta(bcm, 3, bc(i, ny - 1, k))
+                             : harmonic(bc(i, j - 1, k), bc(i, j, k));
         wy[q] = v * inv_h2;
     }
     if (i < nx && j < ny) {
-        double v = (k == 0) ? 2.0 * bc(i, j, 0)
-                 : (k == nz) ? 2.0 * bc(i, j, nz - 1) : harmonic(bc(i, j, k - 1), bc(i, j, k));
+        double v = (k == 0) ? wall_beta(bcm, 4, bc(i, j, 0))
+                 : (k == nz) ? wall_beta(bcm, 5, bc(i, j, nz - 1))
+                             : harmonic(bc(i, j, k - 1), bc(i, j, k));
         wz[q] = v * inv_h2;
     }
 }
@@ -910,12 +921,19 @@ __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long lon
 
 // The calling CTA assembles M = -A (symmetric positive definite) densely in
 // `a`, inverts it by Gauss-Jordan elimination without pivoting (M is
-// diagonally dominant) and writes A^{-1} = -M^{-1} (FP64, and FP32 if inv32).
+// diagonally dominant, or symmetric positive definite after the shift below)
+// and writes A^{-1} = -M^{-1} (FP64, and FP32 if inv32).  When every wall is
+// Neumann (`singular`), M is only semi-definite with the constants as null
+// space; c 1 1^T with c = trace(M) / n^2 is added, which makes it positive
+// definite: applied to r it gives a solution of M x = r - mean(r) (the
+// constant part of r, which no solution can match, is dropped), and the
+// zero-mean one when r has zero mean.
 __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P, long long Q,
                                                    const double *__restrict__ wx,
                                                    const double *__restrict__ wy,
-                                                   const double *__restrict__ wz, double *a,
-                                                   double *inv64, float *inv32, double *col)
+                                                   const double *__restrict__ wz, bool singular,
+                                                   double *a, double *inv64, float *inv32,
+                                                   double *col)
 {
     const int n = nx * ny * nz;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -936,6 +954,18 @@ __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P
         if (k < nz - 1) a[(long long)r * n + r + nx * ny] = -wu;
     }
     __syncthreads();
+    if (singular) {
+        if (tid == 0) {
+            double tr = 0.0;
+            for (int r = 0; r < n; ++r) tr += a[(long long)r * n + r];
+            col[0] = tr / ((double)n * (double)n);
+        }
+        __syncthreads();
+        const double shift = col[0];
+        __syncthreads();
+        for (long long e = tid; e < (long long)n * n; e += nt) a[e] += shift;
+        __syncthreads();
+    }
     for (int p = 0; p < n; ++p) {
         for (int i = tid; i < n; i += nt) col[i] = a[(long long)i * n + p];
         __syncthreads();
@@ -965,14 +995,14 @@ __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P
 // ---- one box (single-stage entry points): grid over positions
 
 __global__ void k_face_weights(int nx, int ny, int nz, int P, long long Q, double inv_h2,
-                               const double *__restrict__ beta, double *__restrict__ wx,
+                               int bcm, const double *__restrict__ beta, double *__restrict__ wx,
                                double *__restrict__ wy, double *__restrict__ wz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i > nx || j > ny || k > nz) return;
-    face_weights_at(nx, ny, nz, P, Q, inv_h2, beta, wx, wy, wz, i, j, k);
+    face_weights_at(nx, ny, nz, P, Q, inv_h2, bcm, beta, wx, wy, wz, i, j, k);
 }
 
 __global__ void k_coarsen(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
@@ -1015,12 +1045,12 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
                                                          const double *__restrict__ wx,
                                                          const double *__restrict__ wy,
                                                          const double *__restrict__ wz,
-                                                         double *__restrict__ a,
+                                                         int singular, double *__restrict__ a,
                                                          double *__restrict__ inv64,
                                                          float *__restrict__ inv32)
 {
     __shared__ double col[MG_BOTTOM_CELLS];
-    bottom_inverse_cta(nx, ny, nz, P, Q, wx, wy, wz, a, inv64, inv32, col);
+    bottom_inverse_cta(nx, ny, nz, P, Q, wx, wy, wz, singular != 0, a, inv64, inv32, col);
 }
 
 // ---- every box of a level in one launch (the solver's set-up)
@@ -1039,8 +1069,8 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
     tile_extent(kind, B.nx, B.ny, B.nz, ex, ey, ez);
     if (p.x >= ex || p.y >= ey) return;
     if (step == 0)
-        face_weights_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.beta, B.wx, B.wy, B.wz, p.x, p.y,
-                        p.z);
+        face_weights_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy, B.wz, p.x,
+                        p.y, p.z);
     else if (step == 1)
         coarsen_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.cP, B.cQ, B.cwx, B.cwy, B.cwz,
                    p.x, p.y, p.z);
@@ -1057,8 +1087,8 @@ __global__ void __launch_bounds__(1024) k_setup_bottom(SetupSet S)
 {
     __shared__ double col[MG_BOTTOM_CELLS];
     const SetupBox &B = S.boxes[blockIdx.x];
-    bottom_inverse_cta(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.work, B.inv64, B.inv32,
-                       col);
+    bottom_inverse_cta(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, (B.bc & 63) == 63, B.work,
+                       B.inv64, B.inv32, col);
 }
 
 // ----------------------------------------------------- projection steps ----
@@ -1109,11 +1139,12 @@ __global__ void k_project_correct(int nx, int ny, int nz, int P, long long Q, do
         w[((long long)k * ny + j) * nx + i] -= wzf[q] * h * (ph(i, j, k) - ph(i, j, k - 1));
 }
 
-// dbeta += chain of dL/dbeta_face through the harmonic mean (see mg.h).
+// dbeta += chain of dL/dbeta_face through the harmonic mean (see mg.h); a
+// Neumann wall face (bit w of bcm) has no coefficient and adds nothing.
 // Arrays are contiguous (nz, ny, nx).
-__global__ void k_beta_grad(int nx, int ny, int nz, double inv_h2, const double *__restrict__ beta,
-                            const double *__restrict__ phi, const double *__restrict__ lam,
-                            double *__restrict__ dbeta)
+__global__ void k_beta_grad(int nx, int ny, int nz, double inv_h2, int bcm,
+                            const double *__restrict__ beta, const double *__restrict__ phi,
+                            const double *__restrict__ lam, double *__restrict__ dbeta)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1123,23 +1154,116 @@ __global__ void k_beta_grad(int nx, int ny, int nz, double inv_h2, const double 
     const long long c = k * sz + j * sy + i;
     const double bc = beta[c], pc = phi[c], lc = lam[c];
     double acc = 0.0;
-    auto face = [&](bool inside, long long o) {
+    auto face = [&](bool inside, long long o, int w) {
         if (inside) {
             const double bo = beta[o];
             const double g = (lam[o] - lc) * (phi[o] - pc) * inv_h2;
             const double s = bc + bo;
             acc += g * (2.0 * bo * bo / (s * s));
-        } else {
+        } else if (!((bcm >> w) & 1)) {
             acc += 2.0 * lc * pc * inv_h2;
         }
     };
-    face(i > 0, c - sx);
-    face(i < nx - 1, c + sx);
-    face(j > 0, c - sy);
-    face(j < ny - 1, c + sy);
-    face(k > 0, c - sz);
-    face(k < nz - 1, c + sz);
+    face(i > 0, c - sx, 0);
+    face(i < nx - 1, c + sx, 1);
+    face(j > 0, c - sy, 2);
+    face(j < ny - 1, c + sy, 3);
+    face(k > 0, c - sz, 4);
+    face(k < nz - 1, c + sz, 5);
     dbeta[c] += acc;
+}
+
+// ------------------------------------------------------ wall values ----
+//
+// f_out = f - the lift of non-zero wall values, one thread per cell (only
+// cells on the box surface change; the others are copied; f_out may be f).  vals packs one
+// value per wall face, walls in the order x-, x+, y-, y+, z-, z+; an x wall
+// is (nz, ny), a y wall (nz, nx), a z wall (ny, nx), C order.  A Dirichlet
+// value g (phi on the wall) lifts w_wall g, with w_wall = 2 beta_c / h^2 the
+// stored weight of the wall face; a Neumann value q (outward flux
+// beta dphi/dn) lifts q / h.  Walls are taken in order, as in the oracle.
+__global__ void k_bc_lift(int nx, int ny, int nz, int P, long long Q, double inv_h, int bcm,
+                          const double *__restrict__ wx, const double *__restrict__ wy,
+                          const double *__restrict__ wz, const double *__restrict__ vals,
+                          const double *f, double *fout)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny || k >= nz) return;
+    const long long u = ((long long)k * ny + j) * nx + i;
+    const long long c = (long long)k * Q + (long long)j * P + i;
+    double v = f[u];
+    const long long ax = (long long)ny * nz, ay = (long long)nx * nz, az = (long long)nx * ny;
+    const long long o[6] = {0, ax, 2 * ax, 2 * ax + ay, 2 * ax + 2 * ay, 2 * ax + 2 * ay + az};
+    auto term = [&](int w, double wall_w, long long at) {
+        const double g = vals[o[w] + at];
+        v -= ((bcm >> w) & 1) ? g * inv_h : wall_w * g;
+    };
+    if (i == 0) term(0, wx[c], (long long)k * ny + j);
+    if (i == nx - 1) term(1, wx[c + 1], (long long)k * ny + j);
+    if (j == 0) term(2, wy[c], (long long)k * nx + i);
+    if (j == ny - 1) term(3, wy[c + P], (long long)k * nx + i);
+    if (k == 0) term(4, wz[c], (long long)j * nx + i);
+    if (k == nz - 1) term(5, wz[c + Q], (long long)j * nx + i);
+    fout[u] = v;
+}
+
+// ------------------------------------------------------------ means ----
+//
+// With every wall Neumann A is singular (constants): f loses its mean before
+// the solve and phi after it.  Partial sums over TK_COLZ columns (field 0 =
+// f, 1 = phi), then one CTA per box sums them in a fixed order and
+// subtracts the mean from every cell.
+__global__ void __launch_bounds__(kThreads) k_sum_partials(BoxSet<double> S, int field,
+                                                           double *__restrict__ partials)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_COLZ];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<double> &B = S.boxes[b];
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
+    const double *x = field ? B.phi : B.f;
+    double v = 0.0;
+    if (p.x < B.nx && p.y < B.ny) {
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+        for (int k = z0; k < z1; ++k) v += x[(long long)k * B.Q + (long long)p.y * B.P + p.x];
+    }
+    double s = block_sum(v);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_mean_finish(BoxSet<double> S,
+                                                      const double *__restrict__ partials,
+                                                      double *__restrict__ mean)
+{
+    __shared__ double wsum[32];
+    const int b = blockIdx.x;
+    const Box<double> &B = S.boxes[b];
+    const int *ts = S.tstart[TK_COLZ];
+    double s = 0.0;
+    for (int q = ts[b] + (int)threadIdx.x; q < ts[b + 1]; q += 1024) s += partials[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 32; ++w) tot += wsum[w];
+        mean[B.box] = tot / ((double)B.nx * B.ny * B.nz);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int field,
+                                                       const double *__restrict__ mean)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_CELL];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<double> &B = S.boxes[b];
+    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
+    if (p.x >= B.nx || p.y >= B.ny) return;
+    double *x = field ? B.phi : B.f;
+    x[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] -= mean[B.box];
 }
 
 // ----------------------------------------------------------- launchers ----
@@ -1312,11 +1436,11 @@ static inline dim3 grid3(int ex, int ey, int ez)
     return dim3((ex + kTX - 1) / kTX, (ey + kTY - 1) / kTY, ez);
 }
 
-cudaError_t launch_face_weights(int nx, int ny, int nz, double inv_h2, const double *beta,
+cudaError_t launch_face_weights(int nx, int ny, int nz, double inv_h2, int bcm, const double *beta,
                                 double *wx, double *wy, double *wz, cudaStream_t st)
 {
     k_face_weights<<<grid3(nx + 1, ny + 1, nz + 1), block2d(), 0, st>>>(
-        nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny), inv_h2, beta, wx, wy, wz);
+        nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny), inv_h2, bcm, beta, wx, wy, wz);
     return counted(cudaGetLastError());
 }
 
@@ -1349,11 +1473,11 @@ cudaError_t launch_round_f32(int nx, int ny, int nz, const double *wx, const dou
 }
 
 cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, const double *wy,
-                                  const double *wz, double *work, double *inv64, float *inv32,
-                                  cudaStream_t st)
+                                  const double *wz, int singular, double *work, double *inv64,
+                                  float *inv32, cudaStream_t st)
 {
     k_bottom_inverse<<<1, 1024, 0, st>>>(nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny), wx,
-                                         wy, wz, work, inv64, inv32);
+                                         wy, wz, singular, work, inv64, inv32);
     return counted(cudaGetLastError());
 }
 
@@ -1388,11 +1512,35 @@ cudaError_t launch_project_correct(int nx, int ny, int nz, double h, const doubl
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double *beta,
+cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, int bcm, const double *beta,
                              const double *phi, const double *lam, double *dbeta, cudaStream_t st)
 {
-    k_beta_grad<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, inv_h2, beta, phi, lam,
+    k_beta_grad<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, inv_h2, bcm, beta, phi, lam,
                                                          dbeta);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_bc_lift(int nx, int ny, int nz, double inv_h, int bcm, const double *wx,
+                           const double *wy, const double *wz, const double *vals,
+                           const double *f, double *fout, cudaStream_t st)
+{
+    k_bc_lift<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, (int)pitch_row(nx),
+                                                       pitch_plane(nx, ny), inv_h, bcm, wx, wy,
+                                                       wz, vals, f, fout);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *partials, double *mean,
+                               cudaStream_t st)
+{
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    k_sum_partials<<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, field, partials);
+    cudaError_t e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+    k_mean_finish<<<S.nbox, 1024, 0, st>>>(S, partials, mean);
+    e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+    k_sub_mean<<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, field, mean);
     return counted(cudaGetLastError());
 }
 

@@ -118,7 +118,8 @@ cudaError_t launch_scales(int nbox, const int *active, int init, const double *n
                           cudaStream_t st);
 
 // ---- set-up (one box per launch) -----------------------------------------
-cudaError_t launch_face_weights(int nx, int ny, int nz, double inv_h2, const double *beta,
+// bcm: bit w set = wall w (x-, x+, y-, y+, z-, z+) is Neumann (weight 0).
+cudaError_t launch_face_weights(int nx, int ny, int nz, double inv_h2, int bcm, const double *beta,
                                 double *wx, double *wy, double *wz, cudaStream_t st);
 cudaError_t launch_coarsen(int nx, int ny, int nz, const double *wx, const double *wy,
                            const double *wz, double *cwx, double *cwy, double *cwz,
@@ -129,9 +130,10 @@ cudaError_t launch_inv_diag(int nx, int ny, int nz, const double *wx, const doub
 cudaError_t launch_round_f32(int nx, int ny, int nz, const double *wx, const double *wy,
                              const double *wz, const double *invD, float *wx32, float *wy32,
                              float *wz32, float *invD32, cudaStream_t st);
+// singular != 0: every wall Neumann; the constants are shifted out.
 cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, const double *wy,
-                                  const double *wz, double *work, double *inv64, float *inv32,
-                                  cudaStream_t st);
+                                  const double *wz, int singular, double *work, double *inv64,
+                                  float *inv32, cudaStream_t st);
 // ---- set-up of every box of a level in one launch ------------------------
 // step 0: face weights from beta; 1: coarse weights; 2: D and 1/D; 3: FP32
 // copies.
@@ -147,8 +149,15 @@ cudaError_t launch_project_correct(int nx, int ny, int nz, double h, const doubl
                                    const double *wy, const double *wz, const double *phi,
                                    double *u, double *v, double *w, cudaStream_t st);
 
-cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, const double *beta,
-                             const double *phi, const double *lam, double *dbeta,
-                             cudaStream_t st);
+cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, int bcm, const double *beta,
+                             const double *phi, const double *lam, double *dbeta, cudaStream_t st);
+// fout = f - lift of the packed wall values (level-0 FP64 weights, layout of mg.h).
+cudaError_t launch_bc_lift(int nx, int ny, int nz, double inv_h, int bcm, const double *wx,
+                           const double *wy, const double *wz, const double *vals,
+                           const double *f, double *fout, cudaStream_t st);
+// Every box of S: field (0 = f, 1 = phi) -= its mean over the box's cells.
+// partials: TK_COLZ tiles of S; mean: one double per box (written).
+cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *partials, double *mean,
+                               cudaStream_t st);
 
 }  // namespace mg

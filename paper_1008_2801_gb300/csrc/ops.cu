@@ -111,12 +111,12 @@ int mg_layout(const int n[3], long long *P, long long *Q, long long *elems)
     return MG_OK;
 }
 
-int mg_op_face_weights(const int n[3], double h, const double *beta, double *wx, double *wy,
-                       double *wz, void *stream)
+int mg_op_face_weights(const int n[3], double h, int bc, const double *beta, double *wx,
+                       double *wy, double *wz, void *stream)
 {
-    if (bad_dims(n) || !(h > 0.0) || !beta || !wx || !wy || !wz)
+    if (bad_dims(n) || !(h > 0.0) || bc < 0 || bc > 63 || !beta || !wx || !wy || !wz)
         return set_error(MG_ERR_INVALID_ARG, "bad argument");
-    CKO(launch_face_weights(n[0], n[1], n[2], 1.0 / (h * h), beta, logical<double>(wx, n),
+    CKO(launch_face_weights(n[0], n[1], n[2], 1.0 / (h * h), bc, beta, logical<double>(wx, n),
                             logical<double>(wy, n), logical<double>(wz, n), (cudaStream_t)stream));
     return MG_OK;
 }
@@ -303,14 +303,15 @@ int mg_op_prolong_add(int prec, const int n[3], const void *phic, void *phi, voi
     });
 }
 
-int mg_op_bottom_inverse(const int n[3], const double *wx, const double *wy, const double *wz,
-                         double *work, double *Ainv, void *stream)
+int mg_op_bottom_inverse(const int n[3], int singular, const double *wx, const double *wy,
+                         const double *wz, double *work, double *Ainv, void *stream)
 {
     if (bad_dims(n) || !wx || !wy || !wz || !work || !Ainv ||
         (long long)n[0] * n[1] * n[2] > MG_MAX_BOTTOM)
         return set_error(MG_ERR_INVALID_ARG, "bad argument (at most MG_MAX_BOTTOM cells)");
     CKO(launch_bottom_inverse(n[0], n[1], n[2], logical<double>(wx, n), logical<double>(wy, n),
-                              logical<double>(wz, n), work, Ainv, nullptr, (cudaStream_t)stream));
+                              logical<double>(wz, n), singular ? 1 : 0, work, Ainv, nullptr,
+                              (cudaStream_t)stream));
     return MG_OK;
 }
 
@@ -382,12 +383,12 @@ int mg_op_refine(const int n[3], const double *wx, const double *wy, const doubl
     return MG_OK;
 }
 
-int mg_op_beta_grad(const int n[3], double h, const double *beta, const double *phi,
+int mg_op_beta_grad(const int n[3], double h, int bc, const double *beta, const double *phi,
                     const double *lambda, double *dbeta, void *stream)
 {
-    if (bad_dims(n) || !(h > 0.0) || !beta || !phi || !lambda || !dbeta)
+    if (bad_dims(n) || !(h > 0.0) || bc < 0 || bc > 63 || !beta || !phi || !lambda || !dbeta)
         return set_error(MG_ERR_INVALID_ARG, "bad argument");
-    CKO(launch_beta_grad(n[0], n[1], n[2], 1.0 / (h * h), beta, phi, lambda, dbeta,
+    CKO(launch_beta_grad(n[0], n[1], n[2], 1.0 / (h * h), bc, beta, phi, lambda, dbeta,
                          (cudaStream_t)stream));
     return MG_OK;
 }

@@ -369,8 +369,8 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (!out) return set_error(MG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (nbox < 1 || !n || !dx) return set_error(MG_ERR_INVALID_ARG, "need nbox >= 1, n, dx");
-    if (bc != MG_BC_DIRICHLET0)
-        return set_error(MG_ERR_UNSUPPORTED, "only MG_BC_DIRICHLET0 is implemented");
+    if (bc < 0 || bc > MG_BC_NEUMANN_ALL)
+        return set_error(MG_ERR_INVALID_ARG, "bc must be a wall mask in 0..63");
     mg_opts o;
     mg_default_opts(&o);
     if (opts) o = *opts;
@@ -387,6 +387,8 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->opts = o;
     s->has32 = o.precision == MG_MIXED;
     s->tma = s->has32 && o.tma == 1;
+    s->bc = bc;
+    s->singular = bc == MG_BC_NEUMANN_ALL;
     s->off.assign(nbox + 1, 0);
     for (int b = 0; b < nbox; ++b) {
         const int nx = n[b][0], ny = n[b][1], nz = n[b][2];
@@ -433,7 +435,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     bump.take<double>(s->total);      // beta copy
     bump.take<double>(work_elems);    // inverse scratch
     bump.take<double>(ntiles0);       // partials
-    for (int i = 0; i < 6; ++i) bump.take<double>(nbox);
+    for (int i = 0; i < 7; ++i) bump.take<double>(nbox);
     bump.take<int>(nbox);
     bump.take<int>(1);  // error word
     // judge block: hist | rel0 | best | tol | status | cycles | stall | step
@@ -465,6 +467,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->se = real.take<double>(nbox);
     s->sr = real.take<double>(nbox);
     s->sr_inv = real.take<double>(nbox);
+    s->dmean = real.take<double>(nbox);
     s->active = real.take<int>(nbox);
     s->derr = real.take<int>(1);
     s->jbytes = jbytes;
@@ -535,6 +538,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         B.P = (int)pitch_row(d[0]);
         B.Q = pitch_plane(d[0], d[1]);
         B.zc = kSweepZ;
+        B.bc = s->bc;
         if (l == s->nlev[b] - 1) {
             B.work = s->work + work_off[b];
             B.inv64 = s->h64.ainv[b];
@@ -1106,6 +1110,8 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     bool fst = false, pst = false;
     CKS(device_view(s, f, 0, true, stream, &fd, &fst));
     CK(launch_pack(H.fine, s->doff, fd, 1, stream));
+    // every wall Neumann: only the zero-mean part of f is in the range of A
+    if (s->singular) CK(launch_remove_mean(H.fine, 0, s->partials, s->dmean, stream));
     for (int b = 0; b < nbox; ++b) s->hactive[b] = 1;
     CK(cudaMemcpyAsync(s->active, s->hactive, sizeof(int) * nbox, cudaMemcpyHostToDevice, stream));
     if (zero_guess) {
@@ -1233,7 +1239,8 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
         }
     }
 
-    // solution out
+    // solution out (every wall Neumann: the zero-mean solution)
+    if (s->singular) CK(launch_remove_mean(H.fine, 1, s->partials, s->dmean, stream));
     for (int b = 0; b < nbox; ++b) s->hside[b] = side[b];
     CK(cudaMemcpyAsync(s->dside, s->hside, sizeof(int) * nbox, cudaMemcpyHostToDevice, stream));
     bool wrong = false;
@@ -1292,6 +1299,9 @@ int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, doub
 {
     if (!s || !phi || !g || !dLdf || !dLdbeta || nrhs < 1)
         return set_error(MG_ERR_INVALID_ARG, "NULL argument or nrhs < 1");
+    if (s->singular)
+        return set_error(MG_ERR_UNSUPPORTED,
+                         "no adjoint when every wall is Neumann (A is singular)");
     DeviceGuard gd(s->dev);
     cudaGetLastError();  // drop a stale non-sticky error of an earlier call
     int worst = MG_OK;
@@ -1319,8 +1329,9 @@ int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, doub
             const auto &d = s->n[b];
             const long long ob = s->shared ? 0 : s->off[b];
             s->kernels += 1;
-            CK(launch_beta_grad(d[0], d[1], d[2], 1.0 / (s->dx[b] * s->dx[b]), s->beta + ob,
-                                pd + s->off[b], s->stage_b + s->off[b], db + ob, stream));
+            CK(launch_beta_grad(d[0], d[1], d[2], 1.0 / (s->dx[b] * s->dx[b]), s->bc,
+                                s->beta + ob, pd + s->off[b], s->stage_b + s->off[b], db + ob,
+                                stream));
         }
     }
     if (dbst)
@@ -1358,7 +1369,7 @@ static int multi_solver(mg_ctx *ctx, int nrhs, cudaStream_t st, Solver **out)
         std::vector<std::array<int, 3>> n(nrhs, s->n[0]);
         std::vector<double> dx(nrhs, s->dx[0]);
         int rc = solver_create(&ctx->multi, nrhs, reinterpret_cast<const int(*)[3]>(n.data()),
-                               dx.data(), MG_BC_DIRICHLET0, &s->opts, true);
+                               dx.data(), s->bc, &s->opts, true);
         if (rc != MG_OK) {
             ctx->multi = nullptr;
             return rc;
@@ -1465,6 +1476,21 @@ int mg_project_correct(mg_ctx *ctx, const double *phi, double *u, double *v, dou
     const LevelBufs<double> &L = s->h64.lv[0][0];
     CK(launch_project_correct(n[0], n[1], n[2], s->dx[0], L.wx, L.wy, L.wz, phi, u, v, w,
                               (cudaStream_t)stream));
+    s->kernels += 1;
+    return MG_OK;
+}
+
+int mg_bc_lift(mg_ctx *ctx, const double *vals, const double *f, double *f_out, void *stream)
+{
+    if (!ctx || !vals || !f || !f_out) return set_error(MG_ERR_INVALID_ARG, "NULL argument");
+    Solver *s = ctx->s;
+    if (!s->beta_set) return set_error(MG_ERR_INVALID_ARG, "mg_set_beta was not called");
+    DeviceGuard g(s->dev);
+    cudaGetLastError();
+    const auto &n = s->n[0];
+    const LevelBufs<double> &L = s->h64.lv[0][0];
+    CK(launch_bc_lift(n[0], n[1], n[2], 1.0 / s->dx[0], s->bc, L.wx, L.wy, L.wz, vals, f, f_out,
+                      (cudaStream_t)stream));
     s->kernels += 1;
     return MG_OK;
 }

@@ -105,6 +105,9 @@ struct Solver {
     SetupSet setup_bottom{};              // coarsest level of every box
 
     int *derr = nullptr;                  // device error word (bounded waits that gave up)
+    int bc = 0;                           // wall mask: bit w set = wall w Neumann
+    bool singular = false;                // every wall Neumann: A has the constants as null space
+    double *dmean = nullptr;              // [nbox] scratch: removed means
     bool tma = false;                     // FP32 fused sweeps use the TMA kernel
 
     // on-device convergence loop (conditional CUDA graph)

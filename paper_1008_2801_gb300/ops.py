@@ -67,11 +67,11 @@ def get(t, shape, kind="cell"):
     return _view(t, shape, kind).clone()
 
 
-def face_weights(beta: torch.Tensor, h: float):
+def face_weights(beta: torch.Tensor, h: float, bc: int = 0):
     shape = tuple(beta.shape)
     w = [level(shape, device=beta.device) for _ in range(3)]
-    check(_lib.load().mg_op_face_weights(_n(shape), float(h), _p(beta), *map(_p, w), _s(beta)),
-          "mg_op_face_weights")
+    check(_lib.load().mg_op_face_weights(_n(shape), float(h), int(bc), _p(beta), *map(_p, w),
+                                         _s(beta)), "mg_op_face_weights")
     return w
 
 
@@ -150,13 +150,13 @@ def prolong_add(phic, phi, shape):
     return phi
 
 
-def bottom_inverse(w, shape):
+def bottom_inverse(w, shape, singular=False):
     nz, ny, nx = shape
     n = nx * ny * nz
     work = torch.empty(n * n, dtype=torch.float64, device=w[0].device)
     ainv = torch.empty((n, n), dtype=torch.float64, device=w[0].device)
-    check(_lib.load().mg_op_bottom_inverse(_n(shape), *map(_p, w), _p(work), _p(ainv),
-                                           _s(ainv)), "mg_op_bottom_inverse")
+    check(_lib.load().mg_op_bottom_inverse(_n(shape), int(bool(singular)), *map(_p, w), _p(work),
+                                           _p(ainv), _s(ainv)), "mg_op_bottom_inverse")
     return ainv
 
 
@@ -191,9 +191,9 @@ def refine(w, D, f, x, e32, c_e, c_r, shape):
     return x, r32, out
 
 
-def beta_grad(beta, phi, lam, h, dbeta=None):
+def beta_grad(beta, phi, lam, h, dbeta=None, bc=0):
     if dbeta is None:
         dbeta = torch.zeros_like(beta)
-    check(_lib.load().mg_op_beta_grad(_n(tuple(beta.shape)), float(h), _p(beta), _p(phi),
-                                      _p(lam), _p(dbeta), _s(beta)), "mg_op_beta_grad")
+    check(_lib.load().mg_op_beta_grad(_n(tuple(beta.shape)), float(h), int(bc), _p(beta),
+                                      _p(phi), _p(lam), _p(dbeta), _s(beta)), "mg_op_beta_grad")
     return dbeta

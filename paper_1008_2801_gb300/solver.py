@@ -6,7 +6,10 @@ All arithmetic runs in libmgpu.so; this module only passes pointers and the
 current CUDA stream.
 
 The equation is the variable-coefficient Poisson equation of the paper's
-Sec. 1, div(beta grad phi) = f, with phi = 0 on the box walls.
+Sec. 1, div(beta grad phi) = f.  Each wall is Dirichlet or Neumann, chosen by
+``bc``: a mask with bit w set when wall w (x-, x+, y-, y+, z-, z+) is Neumann,
+or a string of six letters "D"/"N" in that order (0 or "DDDDDD": phi = 0 on
+every wall).  Non-zero wall values enter through ``bc_lift``.
 """
 from __future__ import annotations
 
@@ -59,6 +62,25 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     return o
 
 
+def bc_mask(bc) -> int:
+    """Wall mask from an int (0..63) or six letters D/N for x-, x+, y-, y+, z-, z+."""
+    if isinstance(bc, str):
+        if len(bc) != 6 or set(bc.upper()) - {"D", "N"}:
+            raise ValueError("bc string needs six letters D or N (x-, x+, y-, y+, z-, z+)")
+        return sum(1 << w for w, c in enumerate(bc.upper()) if c == "N")
+    bc = int(bc)
+    if not 0 <= bc <= 63:
+        raise ValueError("bc mask must be in 0..63")
+    return bc
+
+
+def wall_shapes(shape):
+    """Shapes of the six wall arrays (x-, x+, y-, y+, z-, z+) of an (nz, ny, nx)
+    box, in the packed order ``bc_lift`` reads."""
+    nz, ny, nx = shape
+    return [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+
+
 def _stats_dict(s: _lib.mg_stats):
     n = max(0, min(s.cycles + 1, _lib.MG_MAX_HIST))
     return {"status": _lib.STATUS_NAMES.get(s.status, str(s.status)), "cycles": s.cycles,
@@ -80,24 +102,26 @@ class Solver:
     """Multigrid solver for one (nz, ny, nx) box with cubic cells of size dx.
 
     precision: "fp64" (everything FP64) or "mixed" (FP32 V-cycles inside an
-    FP64 iterative-refinement loop).  Not thread-safe.
+    FP64 iterative-refinement loop).  bc: wall mask or D/N string (see the
+    module docstring).  Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False):
+                 full_residual=False, tma=False, bc=0):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
         self.dx = float(dx)
         self.precision = precision
+        self.bc = bc_mask(bc)
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
                   full_residual, tma)
         with torch.cuda.device(self.device):
-            check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, 0,
+            check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
         self._beta = None
 
@@ -118,13 +142,40 @@ class Solver:
             check(_lib.load().mg_set_beta(self._h, _ptr(beta), _stream_of(beta)), "mg_set_beta")
         self._beta = beta
 
+    def bc_lift(self, values, f: torch.Tensor, out: torch.Tensor | None = None):
+        """f minus the lift of non-zero wall values (mg_bc_lift).  values: the
+        six wall arrays (x-, x+, y-, y+, z-, z+; see ``wall_shapes``) or one
+        packed float64 tensor; each is phi on a Dirichlet wall, the outward flux
+        beta dphi/dn on a Neumann wall."""
+        if not isinstance(values, torch.Tensor):
+            values = torch.cat([torch.as_tensor(v, dtype=torch.float64).reshape(-1)
+                                for v in values])
+        nz, ny, nx = self.shape
+        values = values.to(device=self.device, dtype=torch.float64).contiguous()
+        _check_tensor(values, "values", 2 * (ny * nz + nz * nx + ny * nx), self.device)
+        _check_tensor(f, "f", self.numel, self.device)
+        if not f.is_cuda:
+            raise ValueError("f must be on the solver's device")
+        if out is None:
+            out = torch.empty_like(f)
+        _check_tensor(out, "out", self.numel, self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().mg_bc_lift(self._h, _ptr(values), _ptr(f), _ptr(out),
+                                         _stream_of(f)), "mg_bc_lift")
+        return out
+
     def solve(self, f: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-10,
               raise_on=("invalid_arg", "cuda", "oom", "nonfinite", "diverged", "timeout",
-                        "unsupported")):
+                        "unsupported"), bc_values=None):
         """Solve A phi = f; returns (phi, stats).  phi (if given) is the initial
         guess and is overwritten.  A leading batch dimension solves several
-        right-hand sides with the same beta."""
+        right-hand sides with the same beta.  bc_values (one box): non-zero
+        wall values, lifted into f first (see ``bc_lift``)."""
         _check_tensor(f, "f", device=self.device)
+        if bc_values is not None:
+            if f.numel() != self.numel:
+                raise ValueError("bc_values need a single right-hand side")
+            f = self.bc_lift(bc_values, f.reshape(self.shape))
         if f.numel() % self.numel:
             raise ValueError("f must hold whole boxes")
         nrhs = f.numel() // self.numel
@@ -236,8 +287,9 @@ class BatchSolver:
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False):
+                 full_residual=False, tma=False, bc=0):
         L = _lib.load()
+        self.bc = bc_mask(bc)
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         nb = len(self.shapes)
         dxs = [float(dx)] * nb if isinstance(dx, (int, float)) else [float(v) for v in dx]
@@ -249,7 +301,7 @@ class BatchSolver:
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
                   full_residual, tma)
         with torch.cuda.device(self.device):
-            check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, 0, ctypes.byref(o)),
+            check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, self.bc, ctypes.byref(o)),
                   "mg_batch_create")
         self.sizes = [s[0] * s[1] * s[2] for s in self.shapes]
         self.total = sum(self.sizes)
@@ -336,12 +388,12 @@ _cache: dict = {}
 
 
 def solve(f: torch.Tensor, beta: torch.Tensor, dx: float, tol: float = 1e-10,
-          precision: str = "fp64"):
+          precision: str = "fp64", bc=0):
     """Functional form: phi with div(beta grad phi) = f (differentiable in f
-    and beta).  Solvers are cached per (shape, dx, precision, device)."""
+    and beta).  Solvers are cached per (shape, dx, precision, walls, device)."""
     shape = tuple(beta.shape)
-    key = (shape, float(dx), precision, f.device)
+    key = (shape, float(dx), precision, bc_mask(bc), f.device)
     s = _cache.get(key)
     if s is None:
-        s = _cache[key] = Solver(shape, dx, precision=precision, device=f.device)
+        s = _cache[key] = Solver(shape, dx, precision=precision, device=f.device, bc=bc)
     return MGSolve.apply(f, beta, s, tol)

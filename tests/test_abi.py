@@ -49,6 +49,26 @@ def test_host_side_argument_checks():
     assert L.mg_op_rbgs_pass(5, n, *([ctypes.c_void_p(16)] * 6), 0, None) == \
         _lib.MG_ERR_INVALID_ARG
     assert L.mg_last_error()
+    # wall masks outside 0..63 are rejected before any device work
+    h = ctypes.c_void_p()
+    for bc in (-1, 64, 1000):
+        assert L.mg_create(ctypes.byref(h), n, 0.1, bc, None) == _lib.MG_ERR_INVALID_ARG
+        assert b"wall mask" in L.mg_last_error()
+    assert L.mg_bc_lift(None, None, None, None, None) == _lib.MG_ERR_INVALID_ARG
+    assert L.mg_op_face_weights(n, 0.1, 64, *([ctypes.c_void_p(16)] * 4), None) == \
+        _lib.MG_ERR_INVALID_ARG
+
+
+def test_wall_mask_parsing():
+    from paper_1008_2801_gb300.solver import bc_mask, wall_shapes
+    assert bc_mask(0) == 0 and bc_mask("DDDDDD") == 0
+    assert bc_mask("NNNNNN") == 63
+    assert bc_mask("NDDDDN") == 1 | 32
+    assert bc_mask("dndndn") == 2 | 8 | 32
+    for bad in ("DDDDD", "DDDDDX", 64, -1):
+        with pytest.raises(ValueError):
+            bc_mask(bad)
+    assert wall_shapes((4, 5, 6)) == [(4, 5), (4, 5), (4, 6), (4, 6), (5, 6), (5, 6)]
 
 
 @pytest.mark.parametrize("n", [(1, 1, 1), (7, 5, 3), (64, 64, 64), (48, 128, 96)])
