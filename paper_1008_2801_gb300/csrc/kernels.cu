@@ -12,6 +12,8 @@
 // guarded level layout described in common.cuh.
 #include "kernels.h"
 
+#include <type_traits>
+
 #include <atomic>
 
 namespace mg {
@@ -33,40 +35,52 @@ __device__ __forceinline__ double fmadd<double>(double a, double b, double c) { 
 template <>
 __device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Gauss-Seidel value of cell c from its six neighbours in src.
+// Gauss-Seidel value of cell c from its six neighbours in src:
+// (sum_f w_f src_nbr - f_c) / D_c, with -f_c as the start of the FMA chain
+// (six FMAs and one multiply: GB300's FP64 pipe is the narrow resource).
+template <class T>
+__device__ __forceinline__ T gs_sum(const T *__restrict__ src, const T *__restrict__ f,
+                                    const T *__restrict__ wx, const T *__restrict__ wy,
+                                    const T *__restrict__ wz, long long c, int P, long long Q)
+{
+    T s = fmadd(wx[c], src[c - 1], -f[c]);
+    s = fmadd(wx[c + 1], src[c + 1], s);
+    s = fmadd(wy[c], src[c - P], s);
+    s = fmadd(wy[c + P], src[c + P], s);
+    s = fmadd(wz[c], src[c - Q], s);
+    return fmadd(wz[c + Q], src[c + Q], s);
+}
+
 template <class T>
 __device__ __forceinline__ T gs_value(const T *__restrict__ src, const T *__restrict__ f,
                                       const T *__restrict__ invD, const T *__restrict__ wx,
                                       const T *__restrict__ wy, const T *__restrict__ wz,
                                       long long c, int P, long long Q)
 {
-    T s = wx[c] * src[c - 1];
-    s = fmadd(wx[c + 1], src[c + 1], s);
-    s = fmadd(wy[c], src[c - P], s);
-    s = fmadd(wy[c + P], src[c + P], s);
-    s = fmadd(wz[c], src[c - Q], s);
-    s = fmadd(wz[c + Q], src[c + Q], s);
-    return (s - f[c]) * invD[c];
+    return gs_sum<T>(src, f, wx, wy, wz, c, P, Q) * invD[c];
 }
 
-// f_c - (A phi)_c.  The diagonal comes from the stored D when given (FP64
-// levels: saves five FP64 adds on GB300's narrow FP64 pipe), else it is
-// summed from the six weights.
-template <class T>
+// f_c - (A phi)_c = f_c + D_c phi_c - sum_f w_f phi_nbr, one FMA chain (seven
+// FP64 operations with the stored D).  HAS_D: the diagonal comes from the
+// stored D (FP64 levels: saves five FP64 adds on GB300's narrow FP64 pipe),
+// else it is summed from the six weights.  It is a template parameter, and
+// kernels branch on it once per box, because a run-time choice inside the
+// stencil is if-converted and then pays for both sides.
+template <class T, bool HAS_D>
 __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__restrict__ f,
                                          const T *__restrict__ wx, const T *__restrict__ wy,
                                          const T *__restrict__ wz, const T *__restrict__ Dg,
                                          long long c, int P, long long Q)
 {
     T a = wx[c], b = wx[c + 1], d = wy[c], e = wy[c + P], g = wz[c], h = wz[c + Q];
-    T s = a * phi[c - 1];
-    s = fmadd(b, phi[c + 1], s);
-    s = fmadd(d, phi[c - P], s);
-    s = fmadd(e, phi[c + P], s);
-    s = fmadd(g, phi[c - Q], s);
-    s = fmadd(h, phi[c + Q], s);
-    const T D = Dg ? Dg[c] : ((a + b) + (d + e)) + (g + h);
-    return f[c] - fmadd(-D, phi[c], s);
+    const T D = HAS_D ? Dg[c] : ((a + b) + (d + e)) + (g + h);
+    T s = fmadd(D, phi[c], f[c]);
+    s = fmadd(-a, phi[c - 1], s);
+    s = fmadd(-b, phi[c + 1], s);
+    s = fmadd(-d, phi[c - P], s);
+    s = fmadd(-e, phi[c + P], s);
+    s = fmadd(-g, phi[c - Q], s);
+    return fmadd(-h, phi[c + Q], s);
 }
 
 template <class T>
@@ -95,6 +109,83 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass(BoxSet<T> S, const int *
     if (j >= ny || i >= nx) return;
     const long long c = (long long)k * Q + (long long)j * P + i;
     B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, P, Q);
+}
+
+// One colour out of place: dst = src with the cells of `color` updated (a
+// thread per red-black pair along x, which holds one cell of each colour; the
+// pair is read and written as one vector, the other cell copied).  The norm
+// variant also sums r_c^2 over the updated cells, where
+// r_c = D_c (phi_c - phi'_c) = f_c - (A src)_c (phi'_c solves row c) is
+// the residual of src at c, formed as D_c src_c - s_c from the update's own
+// sum s_c = sum_f w_f src_nbr - f_c (one extra FMA).  Right after a black
+// pass the black residuals vanish, so a red pass with partials yields
+// ||f - A src||^2 as a by-product (the cycle's convergence norm, taken at the
+// start of the next cycle).
+template <class T>
+__device__ __forceinline__ void oop_pair(const Box<T> &B, int color, int from2, int j, int k,
+                                         int x0, bool norm, double &r2)
+{
+    const int P = B.P;
+    const long long Q = B.Q;
+    const T *__restrict__ src = from2 ? B.phi2 : B.phi;
+    T *__restrict__ dst = from2 ? B.phi : B.phi2;
+    typedef typename Vec2<T>::type V2;
+    const long long c0 = (long long)k * Q + (long long)j * P + x0;
+    V2 pair = *reinterpret_cast<const V2 *>(src + c0);
+    const int odd = (j + k + color) & 1;   // the pair's cell of this colour
+    if (x0 + odd < B.nx) {
+        const long long c = c0 + odd;
+        const T sc = gs_sum<T>(src, B.f, B.wx, B.wy, B.wz, c, P, Q);
+        const T nv = sc * B.invD[c];
+        if (norm) {
+            const T r = fmadd(B.D[c], odd ? pair.y : pair.x, -sc);
+            r2 = fma((double)r, (double)r, r2);
+        }
+        if (odd) pair.y = nv;
+        else pair.x = nv;
+    }
+    *reinterpret_cast<V2 *>(dst + c0) = pair;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, 8) k_rbgs_pass_oop(BoxSet<T> S,
+                                                               const int *__restrict__ active,
+                                                               int color, int from2)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_PAIR];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<T> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    TilePos p = tile_pos(TK_PAIR, B.nx, B.ny, B.nz, t - ts[b]);
+    double unused = 0.0;
+    if (p.y < B.ny && 2 * p.x < B.nx) oop_pair(B, color, from2, p.y, p.z, 2 * p.x, false, unused);
+}
+
+// The same pass with the residual norm: each thread takes its pair through a
+// column of kColZ planes (TK_PCOLZ tiles), so the block reduction of the
+// partial sums (FP64 adds and shuffles, costly on GB300's narrow FP64 pipe)
+// is paid once per kColZ cells instead of once per cell.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_rbgs_pass_oop_norm(BoxSet<T> S,
+                                                                    const int *__restrict__ active,
+                                                                    int color, int from2,
+                                                                    double *__restrict__ partials)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_PCOLZ];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<T> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    TilePos p = tile_pos(TK_PCOLZ, B.nx, B.ny, B.nz, t - ts[b]);
+    double r2 = 0.0;
+    if (p.y < B.ny && 2 * p.x < B.nx) {
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+#pragma unroll 1
+        for (int k = z0; k < z1; ++k) oop_pair(B, color, from2, p.y, k, 2 * p.x, true, r2);
+    }
+    const double sum = block_sum(r2);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = sum;
 }
 
 // -------------------------------------- fused red+black sweep (z-march) ----
@@ -158,13 +249,13 @@ __device__ __forceinline__ void load_red(RedIn<T> &r, bool ok, const T *__restri
 template <class T>
 __device__ __forceinline__ T eval_red(const RedIn<T> &r)
 {
-    T s = r.wxa * r.sw;
+    T s = fmadd(r.wxa, r.sw, -r.f);
     s = fmadd(r.wxb, r.se, s);
     s = fmadd(r.wya, r.ss, s);
     s = fmadd(r.wyb, r.sn, s);
     s = fmadd(r.wza, r.sd, s);
     s = fmadd(r.wzb, r.su, s);
-    return (s - r.f) * r.id;
+    return s * r.id;
 }
 
 template <class T>
@@ -309,13 +400,13 @@ __global__ void __launch_bounds__(kTX * kSweepTY, sizeof(T) == 4 ? 4 : 2) k_rbgs
             const T rv = red[sm][ty + 1][xa + parm - x0 + 1];
             T bv = T(0);
             if (xb < nx) {
-                T s = Bk.wxa * red[sm][ty + 1][lb - 1];
+                T s = fmadd(Bk.wxa, red[sm][ty + 1][lb - 1], -Bk.f);
                 s = fmadd(Bk.wxb, red[sm][ty + 1][lb + 1], s);
                 s = fmadd(Bk.wya, red[sm][ty][lb], s);
                 s = fmadd(Bk.wyb, red[sm][ty + 2][lb], s);
                 s = fmadd(Bk.wza, red[smm][ty + 1][lb], s);
                 s = fmadd(Bk.wzb, red[s0][ty + 1][lb], s);
-                bv = (s - Bk.f) * Bk.id;
+                bv = s * Bk.id;
             }
             const long long c0 = (long long)km * Q + (long long)y * P + xa;
             const T va = parm ? bv : rv;
@@ -351,16 +442,22 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
     TilePos p = tile_pos(TK_COARSE, nx, ny, nz, t - ts[b]);
     const int I = p.x, J = p.y, K = p.z;
     if (I >= nx / 2 || J >= ny / 2) return;
-    T sum = T(0);
+    auto children = [&](auto has_d) {
+        constexpr bool HD = decltype(has_d)::value;
+        T sum = T(0);
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int bb = 0; bb < 2; ++bb)
+            for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const long long q = (long long)(2 * K + c) * Q + (long long)(2 * J + bb) * P + 2 * I + a;
-                sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, q, P, Q);
-            }
+                for (int a = 0; a < 2; ++a) {
+                    const long long q =
+                        (long long)(2 * K + c) * Q + (long long)(2 * J + bb) * P + 2 * I + a;
+                    sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, q, P, Q);
+                }
+        return sum;
+    };
+    const T sum = B.D ? children(std::true_type{}) : children(std::false_type{});
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
     B.fc[cc] = sum * T(0.125);
     B.phic[cc] = T(0);
@@ -388,10 +485,15 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
     if (I >= nx / 2 || J >= ny / 2) return;
     // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c) even
     const long long o = (long long)(2 * K) * Q + (long long)(2 * J) * P + 2 * I;
-    T sum = residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o, P, Q);
-    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + P + 1, P, Q);
-    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + 1, P, Q);
-    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + P, P, Q);
+    auto red4 = [&](auto has_d) {
+        constexpr bool HD = decltype(has_d)::value;
+        T sum = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + P + 1, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + 1, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + P, P, Q);
+        return sum;
+    };
+    const T sum = B.D ? red4(std::true_type{}) : red4(std::false_type{});
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
     B.fc[cc] = sum * T(0.125);
     B.phic[cc] = T(0);
@@ -439,7 +541,8 @@ __global__ void __launch_bounds__(kThreads) k_residual_field(BoxSet<T> S)
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
     const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    B.phi2[c] = residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+    B.phi2[c] = B.D ? residual_at<T, true>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q)
+                    : residual_at<T, false>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
 }
 
 // ------------------------------------------------------------- norms ----
@@ -460,16 +563,22 @@ __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const i
     TilePos p = tile_pos(kind, B.nx, B.ny, B.nz, t - ts[b]);
     double v = 0.0;
     const int ex = mode == 2 ? (B.nx + 1) / 2 : B.nx;
-    if (p.x < ex && p.y < B.ny) {
+    auto column = [&](auto has_d) {
+        constexpr bool HD = decltype(has_d)::value;
         const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
         for (int k = z0; k < z1; ++k) {
             const int x = mode == 2 ? 2 * p.x + ((p.y + k) & 1) : p.x;
             if (x >= B.nx) continue;
             const long long c = (long long)k * B.Q + (long long)p.y * B.P + x;
             const T r = mode == 1 ? B.f[c]
-                                  : residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+                                  : residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P,
+                                                       B.Q);
             v = fma((double)r, (double)r, v);
         }
+    };
+    if (p.x < ex && p.y < B.ny) {
+        if (B.D) column(std::true_type{});
+        else column(std::false_type{});
     }
     double s = block_sum(v);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
@@ -575,14 +684,19 @@ __device__ __forceinline__ void cta_resid_restrict(const Box<T> &B)
     for (int q = threadIdx.x; q < tot; q += CoarseThreads<T>::value) {
         const int I = q % cx, r = q / cx;
         const int J = r % cy, K = r / cy;
-        T sum = T(0);
-        for (int c = 0; c < 2; ++c)
-            for (int bb = 0; bb < 2; ++bb)
-                for (int a = 0; a < 2; ++a) {
-                    const long long g =
-                        (long long)(2 * K + c) * B.Q + (long long)(2 * J + bb) * B.P + 2 * I + a;
-                    sum += residual_at<T>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, g, B.P, B.Q);
-                }
+        auto children = [&](auto has_d) {
+            constexpr bool HD = decltype(has_d)::value;
+            T sum = T(0);
+            for (int c = 0; c < 2; ++c)
+                for (int bb = 0; bb < 2; ++bb)
+                    for (int a = 0; a < 2; ++a) {
+                        const long long g = (long long)(2 * K + c) * B.Q +
+                                            (long long)(2 * J + bb) * B.P + 2 * I + a;
+                        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, g, B.P, B.Q);
+                    }
+            return sum;
+        };
+        const T sum = B.D ? children(std::true_type{}) : children(std::false_type{});
         const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
         B.fc[cc] = sum * T(0.125);
         B.phic[cc] = T(0);
@@ -705,13 +819,19 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
     if (p.x < B.nx && p.y < B.ny) {
         const float cri = (float)c_r_inv[B.box];
         const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
-        for (int k = z0; k < z1; ++k) {
-            const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
-            const double r = residual_at<double>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
-            const float r32 = (float)r * cri;
-            E.f[c] = r32;
-            acc = fmaf(r32, r32, acc);
-        }
+        auto column = [&](auto has_d) {
+            constexpr bool HD = decltype(has_d)::value;
+            for (int k = z0; k < z1; ++k) {
+                const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
+                const double r =
+                    residual_at<double, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+                const float r32 = (float)r * cri;
+                E.f[c] = r32;
+                acc = fmaf(r32, r32, acc);
+            }
+        };
+        if (B.D) column(std::true_type{});
+        else column(std::false_type{});
     }
     double s = block_sum((double)acc);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
@@ -724,6 +844,8 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
 // tol) -> MG_ERR_DIVERGED; five cycles in a row without a 10% gain over the
 // best, or max_cycles reached -> MG_ERR_NOT_CONVERGED.  A decided box is made
 // inactive; the loop continues (graph condition 1) while any box is active.
+// When the norm is taken at the start of the next cycle (look-ahead), the
+// loop starts at step -1: the first call judges nothing (no cycle has run).
 __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restrict__ norm,
                                                 const double *__restrict__ normf,
                                                 int *__restrict__ active, JudgeState J,
@@ -735,6 +857,10 @@ __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restri
     const int c = *J.step + 1;
     for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
         if (!active[b]) continue;
+        if (c == 0) {
+            any = 1;
+            continue;
+        }
         const double rel = norm[b] / normf[b];
         if (c < MG_MAX_HIST) J.hist[(long long)b * MG_MAX_HIST + c] = rel;
         J.cycles[b] = c;
@@ -1271,6 +1397,21 @@ __global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int fie
 static inline dim3 block2d() { return dim3(kTX, kTY); }
 
 template <class T>
+cudaError_t launch_rbgs_pass_oop(const BoxSet<T> &S, const int *active, int color, int from2,
+                                 double *partials, cudaStream_t st)
+{
+    if (partials) {
+        if (S.ntiles[TK_PCOLZ] == 0) return cudaSuccess;
+        k_rbgs_pass_oop_norm<T><<<S.ntiles[TK_PCOLZ], block2d(), 0, st>>>(S, active, color, from2,
+                                                                          partials);
+    } else {
+        if (S.ntiles[TK_PAIR] == 0) return cudaSuccess;
+        k_rbgs_pass_oop<T><<<S.ntiles[TK_PAIR], block2d(), 0, st>>>(S, active, color, from2);
+    }
+    return counted(cudaGetLastError());
+}
+
+template <class T>
 cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, cudaStream_t st)
 {
     if (S.ntiles[TK_PAIR] == 0) return cudaSuccess;
@@ -1546,6 +1687,8 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
 
 #define MG_INSTANTIATE(T)                                                                        \
     template cudaError_t launch_rbgs_pass<T>(const BoxSet<T> &, const int *, int, cudaStream_t);  \
+    template cudaError_t launch_rbgs_pass_oop<T>(const BoxSet<T> &, const int *, int, int, double *, \
+                                                 cudaStream_t);                                      \
     template cudaError_t launch_rbgs_sweep<T>(const BoxSet<T> &, const int *, int, cudaStream_t); \
     template cudaError_t launch_resid_restrict<T>(const BoxSet<T> &, const int *, cudaStream_t);  \
     template cudaError_t launch_resid_restrict_red<T>(const BoxSet<T> &, const int *,             \

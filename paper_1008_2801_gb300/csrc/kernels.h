@@ -14,6 +14,12 @@ long long launch_counter();
 // One red (0) or black (1) Gauss-Seidel pass in place on Box::phi.
 template <class T>
 cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, cudaStream_t st);
+// One colour out of place (from2: phi2 -> phi, else phi -> phi2); partials
+// (FP64, nullable): per TK_PCOLZ tile, the sum of the squared residuals of the
+// source at the updated cells (finish with launch_norm_finish mode 2).
+template <class T>
+cudaError_t launch_rbgs_pass_oop(const BoxSet<T> &S, const int *active, int color, int from2,
+                                 double *partials, cudaStream_t st);
 
 // ---- FP32 fused sweep fed by the Tensor Memory Accelerator (sweep_tma.cu)
 struct SweepMaps;  // seven tensor maps of one box level (device memory, 64-B aligned)
@@ -70,7 +76,7 @@ cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode
 // boxes keep their old value.  copy and inv (nullable) receive the same value
 // and its reciprocal (0 for a zero norm).
 // mult (nullable, per box) scales the norm before it is stored; mode is the
-// partials' mode (their tile kind).
+// partials' tiling, as in launch_norm_partials (0/1 TK_COLZ, 2 TK_PCOLZ).
 template <class T>
 cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const double *partials,
                                double *out, double *copy, double *inv, cudaStream_t st,

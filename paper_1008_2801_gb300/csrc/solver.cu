@@ -500,6 +500,12 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     std::vector<std::pair<int, size_t>> maps64, maps32;
     plan_hier(s, s->h64, blob, p64, &jobs64, &maps64);
     if (s->has32) plan_hier(s, s->h32, blob, p32, &jobs32, &maps32);
+    // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
+    // last (nu2 > 0, so black residuals vanish), single-colour passes on every
+    // box's finest level, and the red-only residual reading
+    s->lookahead = !s->has32 && o.nu1 > 0 && o.nu2 > 0 && !o.full_residual &&
+                   !s->h64.smooth.empty() && s->h64.smooth[0].nbox == nbox &&
+                   !s->h64.fused[0];
     // set-up sets: every box that has level l; boxes that have l + 1; bottoms
     std::vector<SetPlan<SetupBox>> psu;
     s->setup_lv.assign(s->maxlev, SetupSet{});
@@ -604,12 +610,13 @@ void solver_destroy(Solver *s)
 {
     if (!s) return;
     DeviceGuard g(s->dev);
-    for (auto *v : {&s->slots64, &s->slots32, &s->direct})
+    for (auto *v : {&s->slots64, &s->slots32, &s->slots_head, &s->direct})
         for (auto &sl : *v) {
             cudaEventDestroy(sl.b);
             cudaEventDestroy(sl.e);
         }
     for (auto e : s->ev_free) cudaEventDestroy(e);
+    if (s->h64.head) cudaGraphExecDestroy(s->h64.head);
     if (s->h64.graph) cudaGraphExecDestroy(s->h64.graph);
     if (s->h32.graph) cudaGraphExecDestroy(s->h32.graph);
     if (s->loop64) cudaGraphExecDestroy(s->loop64);
@@ -805,8 +812,11 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
     return e;
 }
 
+// head_done: the finest level's first red pass already ran out of place
+// (phi -> phi2, look-ahead); the cycle goes on with the black pass phi2 -> phi.
 template <class T>
-static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st)
+static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
+                                  bool head_done = false)
 {
     cudaError_t e;
     const int nl = (int)H.smooth.size();
@@ -814,7 +824,15 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st)
     for (int l = 0; l < nl; ++l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
-        if ((e = smooth(s, S, s->opts.nu1, l == 0, H.fused[l] != 0, H.maps[l], st)) != cudaSuccess)
+        int nu1 = s->opts.nu1;
+        if (l == 0 && head_done) {
+            int sl = prof_begin(s, MG_PROF_PASS, st);
+            if ((e = launch_rbgs_pass_oop(S, s->active, 1, 1, nullptr, st)) != cudaSuccess)
+                return e;
+            prof_end(s, sl, st);
+            --nu1;
+        }
+        if ((e = smooth(s, S, nu1, l == 0, H.fused[l] != 0, H.maps[l], st)) != cudaSuccess)
             return e;
         int sl = l == 0 ? prof_begin(s, MG_PROF_RESTRICT, st) : -1;
         e = (s->opts.nu1 > 0 && !s->opts.full_residual)
@@ -860,6 +878,27 @@ static cudaError_t enqueue_step64(Solver *s, cudaStream_t st)
     return e;
 }
 
+// Look-ahead head: the finest level's first red pass, out of place, whose
+// partial sums give the residual norm of the iterate it starts from.
+static cudaError_t enqueue_head64(Solver *s, cudaStream_t st)
+{
+    const BoxSet<double> &S = s->h64.smooth[0];
+    int sl = prof_begin(s, MG_PROF_PASS, st);
+    cudaError_t e = launch_rbgs_pass_oop(S, s->active, 0, 0, s->partials, st);
+    if (e != cudaSuccess) return e;
+    prof_end(s, sl, st);
+    sl = prof_begin(s, MG_PROF_NORM, st);
+    e = launch_norm_finish(S, s->active, s->partials, s->dnorm, nullptr, nullptr, st, nullptr, 2);
+    prof_end(s, sl, st);
+    return e;
+}
+
+// Look-ahead tail: the rest of the V-cycle.
+static cudaError_t enqueue_tail64(Solver *s, cudaStream_t st)
+{
+    return enqueue_vcycle(s, s->h64, st, true);
+}
+
 // Mixed: zero the FP32 correction, inner_cycles FP32 V-cycles on r32.
 static cudaError_t enqueue_step32(Solver *s, cudaStream_t st)
 {
@@ -884,11 +923,13 @@ static int run_step(Solver *s, cudaGraphExec_t *graph, std::vector<ProfSlot> *sl
     }
     if (*graph && s->graph_prof != s->prof) {
         // re-capture with (or without) the event nodes
-        cudaGraphExecDestroy(s->h64.graph);
+        if (s->h64.graph) cudaGraphExecDestroy(s->h64.graph);
         s->h64.graph = nullptr;
+        if (s->h64.head) cudaGraphExecDestroy(s->h64.head);
+        s->h64.head = nullptr;
         if (s->h32.graph) cudaGraphExecDestroy(s->h32.graph);
         s->h32.graph = nullptr;
-        for (auto *v : {&s->slots64, &s->slots32}) {
+        for (auto *v : {&s->slots64, &s->slots32, &s->slots_head}) {
             for (auto &sl : *v) {
                 s->ev_free.push_back(sl.b);
                 s->ev_free.push_back(sl.e);
@@ -926,11 +967,20 @@ static int run_step(Solver *s, cudaGraphExec_t *graph, std::vector<ProfSlot> *sl
 
 // ---------------------------------------------- on-device convergence ----
 
-// Body of the FP64 loop: V-cycle, residual norm, decision.
+// Body of the FP64 loop: V-cycle, residual norm, decision.  With look-ahead:
+// head (red pass + norm of the previous iterate), decision, rest of the cycle
+// (which skips the boxes just decided, so their solution stays in phi).
 static cudaError_t enqueue_body64(Solver *s, cudaStream_t st, cudaGraphConditionalHandle h)
 {
-    cudaError_t e = enqueue_step64(s, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (s->lookahead) {
+        if ((e = enqueue_head64(s, st)) != cudaSuccess) return e;
+        if ((e = launch_judge(s->nbox, s->dnorm, s->dnormf, s->active, s->J, h, 1, st)) !=
+            cudaSuccess)
+            return e;
+        return enqueue_tail64(s, st);
+    }
+    if ((e = enqueue_step64(s, st)) != cudaSuccess) return e;
     return launch_judge(s->nbox, s->dnorm, s->dnormf, s->active, s->J, h, 1, st);
 }
 
@@ -1003,6 +1053,8 @@ static int download_judge(Solver *s, std::vector<struct BoxState> &bs, long long
 
 #define RUN64(s, st) run_step(s, &(s)->h64.graph, &(s)->slots64, &(s)->graph_kernels64, enqueue_step64, st)
 #define RUN32(s, st) run_step(s, &(s)->h32.graph, &(s)->slots32, &(s)->graph_kernels32, enqueue_step32, st)
+#define RUNHEAD(s, st) run_step(s, &(s)->h64.head, &(s)->slots_head, &(s)->graph_kernels_head, enqueue_head64, st)
+#define RUNTAIL(s, st) run_step(s, &(s)->h64.graph, &(s)->slots64, &(s)->graph_kernels64, enqueue_tail64, st)
 
 // Per-box bookkeeping of the convergence loop.
 struct BoxState {
@@ -1041,6 +1093,10 @@ static int upload_judge(Solver *s, const std::vector<BoxState> &bs, double tol,
     double *tl = best + nb;
     int *status = reinterpret_cast<int *>(tl + 1);
     int *cycles = status + nb;
+    int *step = cycles + 2 * nb;
+    // look-ahead FP64 loop: the first iteration's norm is of the start
+    // iterate, already judged; the device judge starts one step early
+    *step = (s->lookahead && !s->has32) ? -1 : 0;
     for (int b = 0; b < nb; ++b) {
         hist[(size_t)b * MG_MAX_HIST] = bs[b].rel0;
         rel0[b] = bs[b].rel0;
@@ -1064,7 +1120,7 @@ static int download_judge(Solver *s, std::vector<BoxState> &bs, long long per_it
     const int *status = reinterpret_cast<const int *>(tl + 1);
     const int *cycles = status + nb;
     const int *step = cycles + 2 * nb;
-    s->kernels += per_iter * (long long)*step;
+    s->kernels += per_iter * (long long)(*step + ((s->lookahead && !s->has32) ? 1 : 0));
     for (int b = 0; b < nb; ++b) {
         if (bs[b].done) continue;
         bs[b].status = status[b];
@@ -1180,7 +1236,30 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
         CKS(download_judge(s, bs, s->loop_kernels64, stream));
         any = false;
     }
-    if (!mixed) {
+    if (!mixed && s->lookahead) {
+        // iteration i: head (red pass out of place + norm of iterate i-1),
+        // judge cycle i-1 (from i = 2 on), rest of cycle i for the boxes left
+        for (int i = 1; any; ++i) {
+            CKS(RUNHEAD(s, stream));
+            CKS(read_norms(s, s->dnorm, s->hnorm, stream));
+            if (s->prof) prof_collect(s);
+            if (i >= 2) {
+                bool changed = false;
+                any = false;
+                for (int b = 0; b < nbox; ++b) {
+                    if (bs[b].done) continue;
+                    if (judge(bs[b], s->hnorm[b] / bs[b].nf, tol, i - 1, s->opts.max_cycles)) {
+                        bs[b].done = true;
+                        changed = true;
+                    } else {
+                        any = true;
+                    }
+                }
+                if (changed && any) CKS(upload_active(s, bs, stream));
+            }
+            if (any) CKS(RUNTAIL(s, stream));
+        }
+    } else if (!mixed) {
         for (int c = 1; any; ++c) {
             CKS(RUN64(s, stream));
             CKS(read_norms(s, s->dnorm, s->hnorm, stream));

@@ -35,6 +35,7 @@ struct Hier {
     const CoarseJob<T> *jobs = nullptr;         // [box] device
     int njobs = 0;
     cudaGraphExec_t graph = nullptr;            // captured V-cycle (+ fine norm for FP64)
+    cudaGraphExec_t head = nullptr;             // look-ahead: first red pass + norm
 };
 
 // A timed stretch of one stage class: events recorded before and after it.
@@ -97,7 +98,12 @@ struct Solver {
     long long prof_n[MG_PROF_NKIND] = {};
     long long kernels = 0;                // kernels launched by this solver
     long long cap_kernels = 0;            // kernels enqueued into graph captures
-    long long graph_kernels64 = 0, graph_kernels32 = 0;
+    long long graph_kernels64 = 0, graph_kernels32 = 0, graph_kernels_head = 0;
+    std::vector<ProfSlot> slots_head;     // event slots of the look-ahead head graph
+    // FP64 look-ahead: each cycle starts with an out-of-place red pass that
+    // also yields the previous iterate's residual norm, judged before the
+    // rest of the cycle (no separate norm pass)
+    bool lookahead = false;
 
     // set-up launch sets
     std::vector<SetupSet> setup_lv;       // [level] every box that has the level

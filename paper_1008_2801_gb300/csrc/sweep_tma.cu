@@ -183,13 +183,13 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 2)
     };
     // red value of cell (xx, yy) at plane k from the staged operands
     auto red_at = [&](int k, int xx, int yy) {
-        float s = opv(k, kWxOff, xx, yy) * srcv(k, xx - 1, yy);
+        float s = fmaf(opv(k, kWxOff, xx, yy), srcv(k, xx - 1, yy), -opv(k, kFOff, xx, yy));
         s = fmaf(opv(k, kWxOff, xx + 1, yy), srcv(k, xx + 1, yy), s);
         s = fmaf(opv(k, kWyOff, xx, yy), srcv(k, xx, yy - 1), s);
         s = fmaf(opv(k, kWyOff, xx, yy + 1), srcv(k, xx, yy + 1), s);
         s = fmaf(opv(k, kWzOff, xx, yy), srcv(k - 1, xx, yy), s);
         s = fmaf(opv(k + 1, kWzOff, xx, yy), srcv(k + 1, xx, yy), s);
-        return (s - opv(k, kFOff, xx, yy)) * opv(k, kIdOff, xx, yy);
+        return s * opv(k, kIdOff, xx, yy);
     };
 
     const bool ring_row = ty < 2;
@@ -245,13 +245,14 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 2)
             const float rv = red[sm][ty + 1][xa + parm - x0 + 1];
             float bv = 0.f;
             if (xb < nx) {
-                float s = opv(km, kWxOff, xb, y) * red[sm][ty + 1][lb - 1];
+                float s = fmaf(opv(km, kWxOff, xb, y), red[sm][ty + 1][lb - 1],
+                               -opv(km, kFOff, xb, y));
                 s = fmaf(opv(km, kWxOff, xb + 1, y), red[sm][ty + 1][lb + 1], s);
                 s = fmaf(opv(km, kWyOff, xb, y), red[sm][ty][lb], s);
                 s = fmaf(opv(km, kWyOff, xb, y + 1), red[sm][ty + 2][lb], s);
                 s = fmaf(opv(km, kWzOff, xb, y), red[smm][ty + 1][lb], s);
                 s = fmaf(opv(k, kWzOff, xb, y), red[s0][ty + 1][lb], s);
-                bv = (s - opv(km, kFOff, xb, y)) * opv(km, kIdOff, xb, y);
+                bv = s * opv(km, kIdOff, xb, y);
             }
             const long long c0 = (long long)km * Q + (long long)y * P + xa;
             const float va = parm ? bv : rv;
