@@ -69,7 +69,8 @@ int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, co
 /* One full red-then-black sweep as the solver runs it on large levels
  * (fused, out of place: reads phi_in, writes phi_out; phi_in is not
  * modified).  Equal to a red pass followed by a black pass.  Each CTA marches
- * through zc planes (zc <= 0: 32). */
+ * through zc planes (zc <= 0: 32).  UNSUPPORTED for levels of 2^31 or more
+ * elements (the kernel indexes with 32-bit offsets). */
 int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
                      const void *invD, const void *f, const void *phi_in, void *phi_out, int zc,
                      void *stream);

@@ -26,6 +26,11 @@ constexpr int kTY = 8;    // tile height (threads along y)
 constexpr int kThreads = kTX * kTY;
 constexpr int kSweepZ = 32;   // default planes per CTA of the fused red-black sweep
 constexpr int kSweepTY = 8;   // tile height (rows) of the fused sweep: 64 x 8 cells
+constexpr int kSweepWarps = kSweepTY + 3;        // row warps + 2 ring-row warps + 1 ring-column warp
+constexpr int kSweepThreads = kTX * kSweepWarps;
+// The fused sweep indexes a level with 32-bit offsets: levels of at least
+// this many elements smooth with single-colour passes instead.
+constexpr long long kSweepMaxElems = (1LL << 31) - 1;
 constexpr int kColZ = 16;     // planes per thread of the column kernels (norms)
 
 inline __host__ __device__ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }

@@ -191,105 +191,81 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass_oop_norm(BoxSet<T> S,
 // -------------------------------------- fused red+black sweep (z-march) ----
 //
 // dst = black pass of (red pass of src), out of place.  The CTA owns a tile
-// of 64 x kSweepTY columns and a chunk of zc planes; thread (tx, ty) owns the
-// cell pair (x0 + 2tx, x0 + 2tx + 1) of row y0 + ty, which holds exactly one
-// red and one black cell on every plane.  Marching k upward, step k computes
-// the new red values of plane k (own column plus the red cells of a one-cell
-// ring around the tile, recomputed here because the neighbouring CTA's values
-// are not visible) into a 3-plane shared ring buffer, then the new black
-// values of plane k-1 from the red values of planes k-2, k-1, k, and stores
-// both cells of the pair for plane k-1.  Reading src and writing dst keeps
-// every CTA's inputs unchanged while other CTAs run.
+// of 64 x kSweepTY columns and a chunk of zc planes; in row warp ty, lane tx
+// owns the cell pair (x0 + 2tx, x0 + 2tx + 1) of row y0 + ty, which holds
+// exactly one red and one black cell on every plane.  Marching k upward, step
+// k computes the new red values of plane k (own columns, plus the red cells
+// of a one-cell ring around the tile, recomputed by three ring warps because
+// the neighbouring CTA's values are not visible) into a 4-plane shared ring
+// buffer, then the new black values of plane k-1 from the red values of
+// planes k-2, k-1, k, and stores both cells of the pair for plane k-1.
+// Reading src and writing dst keeps every CTA's inputs unchanged while other
+// CTAs run.
 //
-// The global operands of step k+1 (own red cell, ring cell, and the black
-// cell updated at step k+1) are loaded into registers during step k, before
-// its barriers, so DRAM latency overlaps the barrier waits and arithmetic.
+// Written for few instructions per cell (at 28 bytes a cell in FP32 the sweep
+// is issue-bound before it is DRAM-bound): the ring is balanced over
+// dedicated warps; every thread precomputes the offsets, shared-memory
+// positions and validity of its cells for both colour parities, so a step
+// only adds a plane offset; cells outside the box load from a harmless
+// address and store 0 instead of branching; the march is unrolled by 4, so
+// the ring-buffer slot and the parity are constants in each step; with 4
+// slots one barrier per step suffices (a step writes the slot read two steps
+// earlier, with a barrier between).  The black operands are loaded one step
+// ahead; 56 registers keep 3 CTAs (33 warps) resident per SM.
 
-__device__ __forceinline__ void prefetch_l2(const void *p)
+// A red update's 14 operands and a black update's 8 global ones (its red
+// neighbours come from shared memory).
+template <class T>
+struct SweepRed { T sw, se, ss, sn, sd, su, wxa, wxb, wya, wyb, wza, wzb, f, id; };
+template <class T>
+struct SweepBlack { T wxa, wxb, wya, wyb, wza, wzb, f, id; };
+
+template <class T>
+__device__ __forceinline__ SweepRed<T> sweep_load_red(const T *__restrict__ src, const T *__restrict__ f,
+                                          const T *__restrict__ invD, const T *__restrict__ wx,
+                                          const T *__restrict__ wy, const T *__restrict__ wz,
+                                          int c, int P, int Q)
 {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    SweepRed<T> r;
+    r.sw = src[c - 1]; r.se = src[c + 1]; r.ss = src[c - P]; r.sn = src[c + P];
+    r.sd = src[c - Q]; r.su = src[c + Q];
+    r.wxa = wx[c]; r.wxb = wx[c + 1]; r.wya = wy[c]; r.wyb = wy[c + P]; r.wza = wz[c]; r.wzb = wz[c + Q];
+    r.f = f[c]; r.id = invD[c];
+    return r;
 }
-
 template <class T>
-struct RedIn {  // a Gauss-Seidel update's 14 operands
-    T sw, se, ss, sn, sd, su, wxa, wxb, wya, wyb, wza, wzb, f, id;
-};
-template <class T>
-struct BlackIn {  // a black update's global operands (red neighbours come from smem)
-    T wxa, wxb, wya, wyb, wza, wzb, f, id;
-};
-
-template <class T>
-__device__ __forceinline__ void load_red(RedIn<T> &r, bool ok, const T *__restrict__ src,
-                                         const T *__restrict__ f, const T *__restrict__ invD,
-                                         const T *__restrict__ wx, const T *__restrict__ wy,
-                                         const T *__restrict__ wz, long long c, int P, long long Q)
+__device__ __forceinline__ SweepBlack<T> sweep_load_black(const T *__restrict__ f, const T *__restrict__ invD,
+                                            const T *__restrict__ wx, const T *__restrict__ wy,
+                                            const T *__restrict__ wz, int c, int P, int Q)
 {
-    if (ok) {
-        r.sw = src[c - 1];
-        r.se = src[c + 1];
-        r.ss = src[c - P];
-        r.sn = src[c + P];
-        r.sd = src[c - Q];
-        r.su = src[c + Q];
-        r.wxa = wx[c];
-        r.wxb = wx[c + 1];
-        r.wya = wy[c];
-        r.wyb = wy[c + P];
-        r.wza = wz[c];
-        r.wzb = wz[c + Q];
-        r.f = f[c];
-        r.id = invD[c];
-    } else {
-        r.sw = r.se = r.ss = r.sn = r.sd = r.su = T(0);
-        r.wxa = r.wxb = r.wya = r.wyb = r.wza = r.wzb = r.f = r.id = T(0);
-    }
+    SweepBlack<T> b;
+    b.wxa = wx[c]; b.wxb = wx[c + 1]; b.wya = wy[c]; b.wyb = wy[c + P]; b.wza = wz[c]; b.wzb = wz[c + Q];
+    b.f = f[c]; b.id = invD[c];
+    return b;
 }
-
 template <class T>
-__device__ __forceinline__ T eval_red(const RedIn<T> &r)
+__device__ __forceinline__ T sweep_red_value(const SweepRed<T> &r)
 {
     T s = fmadd(r.wxa, r.sw, -r.f);
-    s = fmadd(r.wxb, r.se, s);
-    s = fmadd(r.wya, r.ss, s);
-    s = fmadd(r.wyb, r.sn, s);
-    s = fmadd(r.wza, r.sd, s);
-    s = fmadd(r.wzb, r.su, s);
+    s = fmadd(r.wxb, r.se, s); s = fmadd(r.wya, r.ss, s); s = fmadd(r.wyb, r.sn, s);
+    s = fmadd(r.wza, r.sd, s); s = fmadd(r.wzb, r.su, s);
     return s * r.id;
 }
 
 template <class T>
-__device__ __forceinline__ void load_black(BlackIn<T> &b, bool ok, const T *__restrict__ f,
-                                           const T *__restrict__ invD, const T *__restrict__ wx,
-                                           const T *__restrict__ wy, const T *__restrict__ wz,
-                                           long long c, int P, long long Q)
+__global__ void __launch_bounds__(kSweepThreads, sizeof(T) == 4 ? 3 : 1)
+k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active, int src_is_phi2)
 {
-    if (ok) {
-        b.wxa = wx[c];
-        b.wxb = wx[c + 1];
-        b.wya = wy[c];
-        b.wyb = wy[c + P];
-        b.wza = wz[c];
-        b.wzb = wz[c + Q];
-        b.f = f[c];
-        b.id = invD[c];
-    } else {
-        b.wxa = b.wxb = b.wya = b.wyb = b.wza = b.wzb = b.f = b.id = T(0);
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(kTX * kSweepTY, sizeof(T) == 4 ? 4 : 2) k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active,
-                                                               int src_is_phi2)
-{
-    __shared__ T red[3][kSweepTY + 2][2 * kTX + 2];
+    constexpr int W = 2 * kTX, SW = W + 2;            // smem row length
+    constexpr int SROWS = kSweepTY + 2, SPLANE = SROWS * SW;
+    __shared__ T red[4 * SPLANE];   // red values of 4 planes (slot = step % 4)
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_SWEEP];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
-    if (active && !active[B.box]) return;  // uniform over the CTA
+    if (active && !active[B.box]) return;
     const int nx = B.nx, ny = B.ny, nz = B.nz, P = B.P;
-    const long long Q = B.Q;
+    const int Q = (int)B.Q;
     const T *__restrict__ src = src_is_phi2 ? B.phi2 : B.phi;
     T *__restrict__ dst = src_is_phi2 ? B.phi : B.phi2;
     const T *__restrict__ f = B.f;
@@ -297,133 +273,104 @@ __global__ void __launch_bounds__(kTX * kSweepTY, sizeof(T) == 4 ? 4 : 2) k_rbgs
     const T *__restrict__ wx = B.wx;
     const T *__restrict__ wy = B.wy;
     const T *__restrict__ wz = B.wz;
-
     const int zc = B.zc;
     const TilePos tp = tile_pos(TK_SWEEP, nx, ny, nz, t - ts[b], zc);
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = 2 * (tp.x - tx);
-    const int y0 = tp.y - ty;
-    const int xa = x0 + 2 * tx;
-    const int y = y0 + ty;
-    const int z0 = tp.z * zc;
-    const int z1 = min(z0 + zc, nz);
-    const bool rowin = y < ny;
+    const int lane = threadIdx.x, wid = threadIdx.y;
+    const int x0 = 2 * (tp.x - lane), y0 = tp.y - wid;
+    const int z0 = tp.z * zc, z1 = min(z0 + zc, nz);
+    const int kf = z0 - 1;                            // first step's plane
+    const bool own = wid < kSweepTY;
+    const bool colw = wid == kSweepTY + 2;
+    const int xa = x0 + 2 * lane;
 
-    // ring role of this thread: a red cell of the row below / above the tile
-    // (ty 0 / 1), of the column left / right of it (ty 2, tx < kSweepTY), or none
-    const bool ring_row = ty < 2;
-    const bool ring_col = ty == 2 && tx < kSweepTY;
-    const int ring_y = ty == 0 ? y0 - 1 : y0 + kSweepTY;           // ring_row
-    const int ring_x = tx < kSweepTY / 2 ? x0 - 1 : x0 + 2 * kTX;   // ring_col
-    const int ring_m = tx % (kSweepTY / 2);
-    // position (x, yy) of the ring cell at plane k, and whether it is inside
-    auto ring_at = [&](int k, int &xx, int &yy) -> bool {
-        if (ring_row) {
-            yy = ring_y;
-            xx = x0 + 2 * tx + ((yy + k) & 1);
-            return yy >= 0 && yy < ny && xx < nx;
-        }
-        xx = ring_x;
-        yy = y0 + 2 * ring_m + ((xx + y0 + k) & 1);
-        return xx >= 0 && xx < nx && yy < ny;
-    };
-    auto own_ok = [&](int k, int &xr) -> bool {
-        xr = xa + ((y + k) & 1);
-        return k >= 0 && k < nz && rowin && xr < nx;
-    };
-    auto cidx = [&](int k, int yy, int xx) { return (long long)k * Q + (long long)yy * P + xx; };
-
-    RedIn<T> R, G;
-    BlackIn<T> Bk;
-    {
-        const int k = z0 - 1;
-        int xr, xx, yy;
-        const bool ok = own_ok(k, xr);
-        load_red(R, ok, src, f, invD, wx, wy, wz, ok ? cidx(k, y, xr) : 0, P, Q);
-        load_red(G, false, src, f, invD, wx, wy, wz, 0, P, Q);
-        load_black(Bk, false, f, invD, wx, wy, wz, 0, P, Q);
-        (void)xx;
-        (void)yy;
+    // this thread's red cell at even (rE) and odd (rO) steps: plane offset 0
+    // (the first step's plane), smem position, validity in x and y
+    int rE, rO, sE, sO;
+    bool vE, vO;
+    bool ractive;        // updates a red cell at every step (own) or at steps with k in [z0, z1)
+    if (!colw) {
+        const int y = own ? y0 + wid : wid == kSweepTY ? y0 - 1 : y0 + kSweepTY;
+        const int srow = own ? wid + 1 : wid == kSweepTY ? 0 : kSweepTY + 1;
+        const int p0 = (y + kf) & 1;                  // red x parity at the first step
+        const bool rowin = y >= 0 && y < ny;
+        rE = kf * Q + y * P + xa + p0;
+        rO = kf * Q + y * P + xa + (p0 ^ 1);
+        sE = srow * SW + 2 * lane + 1 + p0;
+        sO = srow * SW + 2 * lane + 1 + (p0 ^ 1);
+        vE = rowin && xa + p0 < nx;
+        vO = rowin && xa + (p0 ^ 1) < nx;
+        ractive = true;
+    } else {
+        const int xc = lane < kSweepTY / 2 ? x0 - 1 : x0 + W;
+        const int ym = y0 + 2 * (lane % (kSweepTY / 2));
+        const int q0 = (xc + y0 + kf) & 1;            // red row offset at the first step
+        const bool cin = lane < kSweepTY && xc >= 0 && xc < nx;
+        rE = kf * Q + (ym + q0) * P + xc;
+        rO = kf * Q + (ym + (q0 ^ 1)) * P + xc;
+        sE = (ym + q0 - y0 + 1) * SW + xc - x0 + 1;
+        sO = (ym + (q0 ^ 1) - y0 + 1) * SW + xc - x0 + 1;
+        vE = cin && ym + q0 < ny;
+        vO = cin && ym + (q0 ^ 1) < ny;
+        ractive = lane < kSweepTY;
     }
+    const bool ringonly = !own;
+    // own rows: the black cell is the pair's other cell; pair store position
+    const int yo = y0 + wid;
+    const bool orow = own && yo < ny;
+    const int pairo = kf * Q + yo * P + xa;           // pair base at the first step
+    const bool full = xa + 1 < nx, half = xa < nx;
+    const int srowo = (wid + 1) * SW;
+    const int po = (yo + kf) & 1;                     // own rows' p0
+    const int cE = srowo + 2 * lane + 1 + po, cO = srowo + 2 * lane + 1 + (po ^ 1);
 
-    for (int k = z0 - 1; k <= z1; ++k) {
-        const int s0 = (k - z0 + 3) % 3;
-        // (1) red values of plane k from the prefetched operands
-        int xr;
-        const bool own = own_ok(k, xr);
-        const T v_own = own ? eval_red(R) : T(0);
-        int rx = 0, ry = 0;
-        const bool ring_here = (ring_row || ring_col) && k >= z0 && k < z1;
-        const bool ring_in = ring_here && ring_at(k, rx, ry);
-        const T v_ring = ring_in ? eval_red(G) : T(0);
-        // ask L2 for the own column two planes ahead (more bytes in flight
-        // than the registers alone can hold)
-        if (k + 2 <= z1 && k + 2 < nz && rowin) {
-            const long long c2 = cidx(k + 2, y, xa);
-            prefetch_l2(src + c2 + Q);
-            prefetch_l2(f + c2);
-            prefetch_l2(invD + c2);
-            prefetch_l2(wx + c2);
-            prefetch_l2(wy + c2);
-            prefetch_l2(wz + c2 + Q);
-        }
-        // prefetch step k+1: own red at k+1, ring at k+1, black at plane k
-        RedIn<T> Rn, Gn;
-        BlackIn<T> Bn;
-        {
-            int xr1;
-            const bool ok = k + 1 <= z1 && own_ok(k + 1, xr1);
-            load_red(Rn, ok, src, f, invD, wx, wy, wz, ok ? cidx(k + 1, y, xr1) : 0, P, Q);
-            int gx = 0, gy = 0;
-            const bool gok = (ring_row || ring_col) && k + 1 >= z0 && k + 1 < z1 &&
-                             ring_at(k + 1, gx, gy);
-            load_red(Gn, gok, src, f, invD, wx, wy, wz, gok ? cidx(k + 1, gy, gx) : 0, P, Q);
-            const int xb = xa + (((y + k) & 1) ^ 1);
-            const bool bok = k >= z0 && k < z1 && rowin && xb < nx;
-            load_black(Bn, bok, f, invD, wx, wy, wz, bok ? cidx(k, y, xb) : 0, P, Q);
-        }
-        red[s0][ty + 1][xr - x0 + 1] = v_own;
-        if (ring_here) {
-            int gx, gy;
-            ring_at(k, gx, gy);
-            red[s0][gy - y0 + 1][gx - x0 + 1] = v_ring;
+    // first step's red operands
+    SweepBlack<T> bc{};
+    // step j of a block of 6 starting at plane kb (j compile-time: slot j % 3,
+    // parity j & 1).  Red work at plane k = kb + j, black work at plane k - 1.
+    auto step = [&](int kb, int boff, auto J) {
+        constexpr int j = decltype(J)::value, s0 = j % 4, sm = (j + 3) % 4, smm = (j + 2) % 4;
+        constexpr bool odd = j & 1;
+        const int k = kb + j, off = boff + j * Q;
+        const bool vc = (odd ? vO : vE) && k >= 0 && k < nz;
+        const SweepRed<T> rc = sweep_load_red(src, f, invD, wx, wy, wz, vc ? (odd ? rO : rE) + off : 0, P, Q);
+        // this plane's black operands (used at the next step)
+        const bool bv_ok = orow && k >= z0 && k < z1 && (odd ? vE : vO);
+        const SweepBlack<T> bn = sweep_load_black(f, invD, wx, wy, wz, bv_ok ? (odd ? rE : rO) + off : 0, P, Q);
+        if (ractive && (!ringonly || (k >= z0 && k < z1))) {
+            const bool v = (odd ? vO : vE) && k >= 0 && k < nz;
+            const T val = sweep_red_value(rc);
+            red[s0 * SPLANE + (odd ? sO : sE)] = v ? val : T(0);
         }
         __syncthreads();
-        // (2) black values of plane k-1, then store the pair of plane k-1
         const int km = k - 1;
-        if (km >= z0 && km < z1 && rowin) {
-            const int sm = (km - z0 + 3) % 3;
-            const int smm = (km - 1 - z0 + 3) % 3;
-            const int parm = (y + km) & 1;        // red cell of plane k-1 is xa + parm
-            const int xb = xa + (parm ^ 1);
-            const int lb = xb - x0 + 1;
-            const T rv = red[sm][ty + 1][xa + parm - x0 + 1];
-            T bv = T(0);
-            if (xb < nx) {
-                T s = fmadd(Bk.wxa, red[sm][ty + 1][lb - 1], -Bk.f);
-                s = fmadd(Bk.wxb, red[sm][ty + 1][lb + 1], s);
-                s = fmadd(Bk.wya, red[sm][ty][lb], s);
-                s = fmadd(Bk.wyb, red[sm][ty + 2][lb], s);
-                s = fmadd(Bk.wza, red[smm][ty + 1][lb], s);
-                s = fmadd(Bk.wzb, red[s0][ty + 1][lb], s);
-                bv = s * Bk.id;
-            }
-            const long long c0 = (long long)km * Q + (long long)y * P + xa;
-            const T va = parm ? bv : rv;
-            const T vb = parm ? rv : bv;
-            if (xa + 1 < nx) {
-                typename Vec2<T>::type v2;
-                v2.x = va;
-                v2.y = vb;
+        if (orow && km >= z0) {
+            // plane km had parity !odd: its red cell sits at the (odd ? E : O) position
+            const int rpos = odd ? cE : cO;           // red cell of plane km
+            const int lb = odd ? cO : cE;             // black cell of plane km
+            const T rv = red[sm * SPLANE + rpos];
+            T s = fmadd(bc.wxa, red[sm * SPLANE + lb - 1], -bc.f);
+            s = fmadd(bc.wxb, red[sm * SPLANE + lb + 1], s);
+            s = fmadd(bc.wya, red[sm * SPLANE + lb - SW], s);
+            s = fmadd(bc.wyb, red[sm * SPLANE + lb + SW], s);
+            s = fmadd(bc.wza, red[smm * SPLANE + lb], s);
+            s = fmadd(bc.wzb, red[s0 * SPLANE + lb], s);
+            const bool bvalid = odd ? vO : vE;        // black cell of plane km
+            const T bval = bvalid ? s * bc.id : T(0);
+            const bool redfirst = (odd ? po : (po ^ 1)) == 0;  // red is the pair's first cell
+            const T va = redfirst ? rv : bval, vb = redfirst ? bval : rv;
+            const int c0 = pairo + off - Q;
+            if (full) {
+                typename Vec2<T>::type v2; v2.x = va; v2.y = vb;
                 *reinterpret_cast<typename Vec2<T>::type *>(dst + c0) = v2;
-            } else if (xa < nx) {
-                dst[c0] = va;
-            }
+            } else if (half) dst[c0] = va;
         }
-        __syncthreads();
-        R = Rn;
-        G = Gn;
-        Bk = Bn;
+        bc = bn;
+    };
+    for (int kb = kf, boff = 0; kb <= z1; kb += 4, boff += 4 * Q) {
+        step(kb, boff, std::integral_constant<int, 0>{});
+        if (kb + 1 <= z1) step(kb, boff, std::integral_constant<int, 1>{});
+        if (kb + 2 <= z1) step(kb, boff, std::integral_constant<int, 2>{});
+        if (kb + 3 <= z1) step(kb, boff, std::integral_constant<int, 3>{});
     }
 }
 
@@ -956,7 +903,12 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 // kernel (the single-stage entry points) and by a set kernel that covers
 // every box of a level in one launch (the solver).
 
-__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+// weight of a face between cells with coefficients a and b: the harmonic mean
+// 2 a b / (a + b) times 1/h^2, as one quotient (c2 = 2 / h^2)
+__device__ __forceinline__ double harmonic_w(double a, double b, double c2)
+{
+    return (c2 * a) * b / (a + b);
+}
 
 // Wall w (0..5 = x-, x+, y-, y+, z-, z+) is Neumann when bit w of the mask is
 // set: its faces carry no flux (weight 0); otherwise it is a Dirichlet wall
@@ -975,24 +927,19 @@ __device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, l
 {
     auto bc = [&](int a, int bb, int c) { return beta[((long long)c * ny + bb) * nx + a]; };
     const long long q = (long long)k * Q + (long long)j * P + i;
-    if (j < ny && k < nz) {
-        double v = (i == 0) ? wall_beta(bcm, 0, bc(0, j, k))
-                 : (i == nx) ? wall_beta(bcm, 1, bc(nx - 1, j, k))
-                             : harmonic(bc(i - 1, j, k), bc(i, j, k));
-        wx[q] = v * inv_h2;
-    }
-    if (i < nx && k < nz) {
-        double v = (j == 0) ? wall_beta(bcm, 2, bc(i, 0, k))
-                 : (j == ny) ? wall_beta(bcm, 3, bc(i, ny - 1, k))
-                             : harmonic(bc(i, j - 1, k), bc(i, j, k));
-        wy[q] = v * inv_h2;
-    }
-    if (i < nx && j < ny) {
-        double v = (k == 0) ? wall_beta(bcm, 4, bc(i, j, 0))
-                 : (k == nz) ? wall_beta(bcm, 5, bc(i, j, nz - 1))
-                             : harmonic(bc(i, j, k - 1), bc(i, j, k));
-        wz[q] = v * inv_h2;
-    }
+    const double c2 = 2.0 * inv_h2;
+    if (j < ny && k < nz)
+        wx[q] = (i == 0) ? wall_beta(bcm, 0, bc(0, j, k)) * inv_h2
+              : (i == nx) ? wall_beta(bcm, 1, bc(nx - 1, j, k)) * inv_h2
+                          : harmonic_w(bc(i - 1, j, k), bc(i, j, k), c2);
+    if (i < nx && k < nz)
+        wy[q] = (j == 0) ? wall_beta(bcm, 2, bc(i, 0, k)) * inv_h2
+              : (j == ny) ? wall_beta(bcm, 3, bc(i, ny - 1, k)) * inv_h2
+                          : harmonic_w(bc(i, j - 1, k), bc(i, j, k), c2);
+    if (i < nx && j < ny)
+        wz[q] = (k == 0) ? wall_beta(bcm, 4, bc(i, j, 0)) * inv_h2
+              : (k == nz) ? wall_beta(bcm, 5, bc(i, j, nz - 1)) * inv_h2
+                          : harmonic_w(bc(i, j, k - 1), bc(i, j, k), c2);
 }
 
 // Coarse position (I, J, K) in [0, cx] x [0, cy] x [0, cz]; coarse face
@@ -1423,7 +1370,7 @@ template <class T>
 int sweep_ctas_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep<T>, kTX * kSweepTY, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep<T>, kSweepThreads, 0) !=
         cudaSuccess) {
         cudaGetLastError();
         return 4;
@@ -1438,7 +1385,7 @@ cudaError_t launch_rbgs_sweep(const BoxSet<T> &S, const int *active, int src_is_
                               cudaStream_t st)
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
-    k_rbgs_sweep<T><<<S.ntiles[TK_SWEEP], dim3(kTX, kSweepTY), 0, st>>>(S, active, src_is_phi2);
+    k_rbgs_sweep<T><<<S.ntiles[TK_SWEEP], dim3(kTX, kSweepWarps), 0, st>>>(S, active, src_is_phi2);
     return counted(cudaGetLastError());
 }
 

@@ -190,6 +190,8 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
     if (bad_dims(n) || !wx || !wy || !wz || !invD || !f || !phi_in || !phi_out ||
         phi_in == phi_out)
         return set_error(MG_ERR_INVALID_ARG, "bad argument (phi_in and phi_out must differ)");
+    if (level_elems(n[0], n[1], n[2]) > kSweepMaxElems)
+        return set_error(MG_ERR_UNSUPPORTED, "fused sweep: level of 2^31 elements or more");
     DISPATCH(prec, {
         Box<T> B = level_box<T>(n, wx, wy, wz, invD, f, phi_in, phi_out);
         B.zc = zc > 0 ? zc : kSweepZ;

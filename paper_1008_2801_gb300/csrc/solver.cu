@@ -224,30 +224,39 @@ static void patch_set(const SetPlan<D> &p, char *dev)
         p.target->tstart[k] = reinterpret_cast<const int *>(dev + p.ts_off[k]);
 }
 
-// Planes per CTA of the fused sweep for a set of boxes: the grid should fill
-// whole waves of resident CTAs (a second, nearly empty wave doubles the time
-// of a z-marching kernel), while short chunks pay one extra red half-plane
-// per chunk boundary.  Returns the chunk length and its score (fraction of
-// useful work, 1 = perfect).
+// Planes per CTA of the fused sweep for a set of boxes.  A z-marching CTA
+// takes zc + 2 steps (the planes below and above its chunk included), and the
+// CTAs run in waves of `slots` resident ones, so the sweep takes about
+// waves * (zc + 2) steps.  For each chunk count m the shortest chunk length
+// is ceil(nz / m) (equal chunks; a longer one only lengthens the critical
+// path); the m with the fewest steps wins.  Returns zc and its efficiency
+// (steps of useful plane work per resident slot over steps taken, 1 = perfect).
 template <class T>
 static int choose_zc(const std::vector<Box<T>> &boxes, long long slots, double *score)
 {
     int maxnz = 1;
-    for (const auto &B : boxes) maxnz = std::max(maxnz, B.nz);
+    double planes = 0.0;  // tile-planes of useful work
+    for (const auto &B : boxes) {
+        maxnz = std::max(maxnz, B.nz);
+        planes += (double)tiles_of(TK_SWEEP, B.nx, B.ny, B.nz, B.nz) * B.nz;
+    }
     int best = std::min(kSweepZ, maxnz);
-    double best_s = -1.0;
-    for (int Z = 2; Z <= maxnz; ++Z) {
+    double best_cost = -1.0;
+    int last = -1;
+    for (int m = 1; m <= maxnz; ++m) {
+        const int Z = (maxnz + m - 1) / m;
+        if (Z == last) continue;
+        last = Z;
         long long ctas = 0;
         for (const auto &B : boxes) ctas += tiles_of(TK_SWEEP, B.nx, B.ny, B.nz, Z);
         const long long waves = (ctas + slots - 1) / slots;
-        const double fill = (double)ctas / (double)(waves * slots);
-        const double sc = fill * (double)Z / (Z + 1.0);
-        if (sc > best_s + 1e-9) {
-            best_s = sc;
+        const double cost = (double)waves * (Z + 2);
+        if (best_cost < 0.0 || cost < best_cost - 1e-9) {
+            best_cost = cost;
             best = Z;
         }
     }
-    *score = best_s;
+    *score = planes / ((double)slots * best_cost);
     return best;
 }
 
@@ -336,8 +345,10 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
             // FP32: FP64 smoothing is bound by the FP64 pipe, where the red
             // ring the fused sweep recomputes costs more than the DRAM
             // traffic it saves (measured 22% slower at 256^3)
+            bool small = true;  // 32-bit offsets inside the fused sweep
+            for (const auto &B : set) small = small && level_elems(B.nx, B.ny, B.nz) <= kSweepMaxElems;
             const bool ok = score >= 0.7 && sizeof(T) == sizeof(float);
-            H.fused[l] = s->opts.smoother == 2 || (s->opts.smoother == 0 && ok);
+            H.fused[l] = small && (s->opts.smoother == 2 || (s->opts.smoother == 0 && ok));
             size_t moff = 0;
             if (H.fused[l] && tma && s->tma && plan_maps(set, blob, &moff))
                 map_offs->push_back({l, moff});  // else: plain-load sweeps on this level
