@@ -95,6 +95,11 @@ def lib():
             L.oracle_divergence.argtypes = [_I, _I, _I, _F, _D, _D, _D, ctypes.c_void_p, _D]
             L.oracle_correct.argtypes = [_I, _I, _I, _F, _D, _D, DN, DN, DN]
             L.oracle_correct_bc.argtypes = [_I, _I, _I, _F, _D, _I, _D, DN, DN, DN]
+            _M = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+            L.oracle_masked_face_beta.argtypes = [_I, _I, _I, _D, _M, _D, _D, _D]
+            L.oracle_masked_solve.argtypes = [_I, _I, _I, _F, _D, _M, _D, _D, _F, _I,
+                                              ctypes.POINTER(_I)]
+            L.oracle_masked_solve.restype = _I
             _lib = L
     return _lib
 
@@ -305,3 +310,38 @@ def dense_matrix(faces, h, shape):
         e[c] = 1.0
         A[:, c] = apply(faces, h, e.reshape(shape)).ravel()
     return A
+
+
+def masked_face_beta(beta, mask):
+    """Face coefficients of the domain mask != 0 inside beta's box: harmonic
+    mean between domain cells, 2 beta on faces to the outside, 0 elsewhere."""
+    beta = _c(beta)
+    mask = np.ascontiguousarray(mask, dtype=np.int32)
+    nx, ny, nz = _dims(beta)
+    bx = np.empty((nz, ny, nx + 1))
+    by = np.empty((nz, ny + 1, nx))
+    bz = np.empty((nz + 1, ny, nx))
+    lib().oracle_masked_face_beta(nx, ny, nz, beta, mask, bx, by, bz)
+    return bx, by, bz
+
+
+def masked_solve(beta, mask, f, h, tol=1e-13, maxit=100000):
+    """Solve div(beta grad phi) = f on the domain mask != 0 (Dirichlet walls on
+    its boundary) by conjugate gradients; phi = 0 outside.  Returns (phi, info)."""
+    beta, f = _c(beta), _c(f)
+    mask = np.ascontiguousarray(mask, dtype=np.int32)
+    nx, ny, nz = _dims(beta)
+    phi = np.zeros_like(f)
+    it = _I(0)
+    s = lib().oracle_masked_solve(nx, ny, nz, float(h), beta, mask, f, phi, float(tol),
+                                  int(maxit), ctypes.byref(it))
+    return phi, {"status": STATUS[s], "iterations": it.value}
+
+
+def level_mask(los, ns, shape):
+    """Mask over an (nz, ny, nx) bounding box of the union of boxes with lower
+    corners los[b] = (i, j, k) and dims ns[b] = (nx, ny, nz)."""
+    m = np.zeros(shape, dtype=np.int32)
+    for (i, j, k), (a, b, c) in zip(los, ns):
+        m[k:k + c, j:j + b, i:i + a] = 1
+    return m

@@ -49,7 +49,14 @@
  *                removes the mean of f (the compatibility condition) and
  *                returns the zero-mean solution; its coarsest level is solved
  *                with M + c 1 1^T, which is positive definite and exact on
- *                zero-mean right-hand sides.
+ *                zero-mean right-hand sides;
+ *   level        a level of several boxes (paper Sec. 2: the union of
+ *                disjoint rectangular grids of a MultiFAB) is one domain:
+ *                the same operator on the union, faces between cells of two
+ *                boxes are interior faces (harmonic mean), faces on the
+ *                union's boundary are Dirichlet walls.  The oracle takes the
+ *                union as a mask over its bounding box and solves by
+ *                conjugate gradients on the masked operator.
  *
  * Loops over cells run under OpenMP where each iteration is independent; all
  * reductions are serial, so results do not depend on the thread count.
@@ -752,4 +759,99 @@ void oracle_correct(int nx, int ny, int nz, double h, const double *beta, const 
                     double *u, double *v, double *w)
 {
     oracle_correct_bc(nx, ny, nz, h, beta, 0, phi, u, v, w);
+}
+
+/* ------------------------------------------------------ masked domains */
+
+/* Face coefficients of the domain {mask != 0} inside an (nx, ny, nz) box:
+ * between two domain cells the harmonic mean, between a domain cell and a
+ * cell outside the domain (or the box wall) 2 beta of the domain cell (a
+ * Dirichlet wall), between two outside cells 0. */
+void oracle_masked_face_beta(int nx, int ny, int nz, const double *beta, const int *mask,
+                             double *bx, double *by, double *bz)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                int a = i > 0 && mask[cell(i - 1, j, k, nx, ny)];
+                int b = i < nx && mask[cell(i, j, k, nx, ny)];
+                double v = 0.0;
+                if (a && b) v = harmonic(beta[cell(i - 1, j, k, nx, ny)], beta[cell(i, j, k, nx, ny)]);
+                else if (a) v = 2.0 * beta[cell(i - 1, j, k, nx, ny)];
+                else if (b) v = 2.0 * beta[cell(i, j, k, nx, ny)];
+                bx[xface(i, j, k, nx, ny)] = v;
+            }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int a = j > 0 && mask[cell(i, j - 1, k, nx, ny)];
+                int b = j < ny && mask[cell(i, j, k, nx, ny)];
+                double v = 0.0;
+                if (a && b) v = harmonic(beta[cell(i, j - 1, k, nx, ny)], beta[cell(i, j, k, nx, ny)]);
+                else if (a) v = 2.0 * beta[cell(i, j - 1, k, nx, ny)];
+                else if (b) v = 2.0 * beta[cell(i, j, k, nx, ny)];
+                by[yface(i, j, k, nx, ny)] = v;
+            }
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int a = k > 0 && mask[cell(i, j, k - 1, nx, ny)];
+                int b = k < nz && mask[cell(i, j, k, nx, ny)];
+                double v = 0.0;
+                if (a && b) v = harmonic(beta[cell(i, j, k - 1, nx, ny)], beta[cell(i, j, k, nx, ny)]);
+                else if (a) v = 2.0 * beta[cell(i, j, k - 1, nx, ny)];
+                else if (b) v = 2.0 * beta[cell(i, j, k, nx, ny)];
+                bz[zface(i, j, k, nx, ny)] = v;
+            }
+}
+
+/* Solve A phi = f on the domain {mask != 0} by conjugate gradients on
+ * M = -h^2 A (symmetric positive definite on the domain), phi = 0 outside.
+ * Iterates from phi = 0 until ||f - A phi|| <= tol ||f|| over the domain.
+ * Returns 0 converged, 1 not converged within maxit, 2 non-finite. */
+int oracle_masked_solve(int nx, int ny, int nz, double h, const double *beta, const int *mask,
+                        const double *f, double *phi, double tol, int maxit, int *iters)
+{
+    size_t n = (size_t)nx * ny * nz;
+    double *bx = (double *)malloc(sizeof(double) * (size_t)nz * ny * (nx + 1));
+    double *by = (double *)malloc(sizeof(double) * (size_t)nz * (ny + 1) * nx);
+    double *bz = (double *)malloc(sizeof(double) * (size_t)(nz + 1) * ny * nx);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    oracle_masked_face_beta(nx, ny, nz, beta, mask, bx, by, bz);
+    double h2 = h * h, rr = 0.0, ff = 0.0;
+    for (size_t c = 0; c < n; ++c) {
+        phi[c] = 0.0;
+        r[c] = mask[c] ? -h2 * f[c] : 0.0;      /* M phi = -h^2 f */
+        p[c] = r[c];
+        rr += r[c] * r[c];
+    }
+    ff = rr;
+    int status = 1, it = 0;
+    if (!isfinite(ff)) status = 2;
+    else if (ff == 0.0) status = 0;
+    for (; status == 1 && it < maxit; ++it) {
+        if (rr <= tol * tol * ff) { status = 0; break; }
+        oracle_apply(nx, ny, nz, h, bx, by, bz, p, q);
+        double pq = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            q[c] = mask[c] ? -h2 * q[c] : 0.0;
+            pq += p[c] * q[c];
+        }
+        double alpha = rr / pq, rr1 = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            phi[c] += alpha * p[c];
+            r[c] -= alpha * q[c];
+            rr1 += r[c] * r[c];
+        }
+        if (!isfinite(rr1)) { status = 2; break; }
+        double b = rr1 / rr;
+        rr = rr1;
+        for (size_t c = 0; c < n; ++c) p[c] = r[c] + b * p[c];
+    }
+    if (status == 1 && rr <= tol * tol * ff) status = 0;
+    if (iters) *iters = it;
+    free(bx); free(by); free(bz); free(r); free(p); free(q);
+    return status;
 }
