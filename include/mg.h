@@ -227,6 +227,45 @@ int mg_solve_batched(mg_batch *b, const double *f_packed, double *phi_packed, do
                      mg_stats *st, void *stream);
 void mg_batch_destroy(mg_batch *b);
 
+/* ---- a coupled level: boxes of one level solved as one domain ----------
+ * The union of disjoint boxes (paper Sec. 2: the grids of one MultiFAB
+ * level) is one domain: faces between cells of two boxes are interior faces
+ * (harmonic mean), faces on the union's boundary are Dirichlet walls.  Box b
+ * covers cells lo[b] .. lo[b] + n[b] - 1 of a common index space (spacing
+ * dx); its arrays are packed at element offset off[b] = sum_{c<b} cells(c),
+ * each (nz, ny, nx) in C order.  Every box's V-cycle level is coupled to its
+ * neighbours by ghost-cell exchanges before each smoothing pass and residual;
+ * the exchange patterns come from a hash-binned intersection of the boxes
+ * (regions at least as large as any box, keyed by a box's lowest corner,
+ * search of the own and the 26 neighbouring regions: O(N + N^2/M)) and are
+ * computed once at create.  Levels halve while every box's dims are even and
+ * at least 4 and every lower corner is even; the coarsest levels of all boxes
+ * are solved together with a dense inverse (at most MG_MAX_BOTTOM cells in
+ * all).  Smoothing uses single-colour passes with a global red-black
+ * colouring ((i + j + k) of the common index space even = red).
+ * Errors: INVALID_ARG (overlapping boxes, n < 1, dx <= 0, bc != 0),
+ * UNSUPPORTED (coarsest union above MG_MAX_BOTTOM cells), OOM, CUDA.  The
+ * level solve reports one status and one residual history (the union's);
+ * st receives it for every box. */
+typedef struct mg_level mg_level;
+int mg_level_create(mg_level **out, int nbox, const int (*lo)[3], const int (*n)[3], double dx,
+                    int bc, const mg_opts *opts);
+int mg_level_set_beta(mg_level *lv, const double *beta_packed, void *stream);
+int mg_level_solve(mg_level *lv, const double *f_packed, double *phi_packed, double tol,
+                   mg_stats *st, void *stream);
+int mg_level_levels(const mg_level *lv, int *nlev);
+void mg_level_destroy(mg_level *lv);
+
+/* Host-only (no device work): the ghost-exchange records of boxes
+ * (lo[b], n[b]) at one level.  *nrec = number of records; out (nullable)
+ * receives min(*nrec, cap) records of 11 ints: dst box, src box, the patch
+ * origin in dst's local coordinates (a guard position: -1 or n on the face
+ * axis), the same cells in src's local coordinates, and the extents
+ * (ex, ey, ez).  brute != 0 tests all pairs instead of the region bins (for
+ * checking).  INVALID_ARG if two boxes overlap. */
+int mg_level_intersections(int nbox, const int (*lo)[3], const int (*n)[3], int brute,
+                           int *nrec, int *out, int cap);
+
 /* ---- measurement -------------------------------------------------------
  * With profiling on, the solver records CUDA events around each stage class
  * below (as event nodes inside the captured V-cycle graph, so the times are

@@ -75,6 +75,13 @@ _SIGS = {
     "mg_project_rhs": (c_int, [c_void_p] * 7),
     "mg_project_correct": (c_int, [c_void_p] * 6),
     "mg_bc_lift": (c_int, [c_void_p] * 5),
+    "mg_level_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p]),
+    "mg_level_set_beta": (c_int, [c_void_p] * 3),
+    "mg_level_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
+    "mg_level_levels": (c_int, [c_void_p, c_void_p]),
+    "mg_level_destroy": (None, [c_void_p]),
+    "mg_level_intersections": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                       c_int]),
     "mg_destroy": (None, [c_void_p]),
     "mg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int_p,
                                 ctypes.POINTER(c_double), c_int, ctypes.POINTER(mg_opts)]),

@@ -34,11 +34,23 @@ constexpr long long kSweepMaxElems = (1LL << 31) - 1;
 constexpr int kColZ = 16;     // planes per thread of the column kernels (norms)
 
 inline __host__ __device__ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
-inline __host__ __device__ long long pitch_row(int nx) { return round_up((long long)nx + 1, 8); }
-inline __host__ __device__ long long pitch_plane(int nx, int ny) { return pitch_row(nx) * (ny + 1); }
-inline __host__ __device__ long long level_elems(int nx, int ny, int nz)
+// wide: the layout of the boxes of a coupled level, whose guard cells hold
+// neighbour values.  The default layout lets the guard at i = nx of one row
+// share its element with the guard at i = -1 of the next (and likewise the
+// guard rows j = ny and j = -1 of consecutive planes): both are 0 there.  The
+// wide layout gives every guard cell of the six faces its own element:
+// P >= nx + 2 and Q = P (ny + 2); element (i, j, k) is still at (k+1) Q + j P + i.
+inline __host__ __device__ long long pitch_row(int nx, bool wide = false)
 {
-    return pitch_plane(nx, ny) * (nz + 2);
+    return round_up((long long)nx + (wide ? 2 : 1), 8);
+}
+inline __host__ __device__ long long pitch_plane(int nx, int ny, bool wide = false)
+{
+    return pitch_row(nx, wide) * (ny + (wide ? 2 : 1));
+}
+inline __host__ __device__ long long level_elems(int nx, int ny, int nz, bool wide = false)
+{
+    return pitch_plane(nx, ny, wide) * (nz + 2);
 }
 
 // One box at one level, as the cycle kernels see it.
@@ -60,6 +72,8 @@ struct Box {
     long long cQ;    // coarse plane pitch
     int box;         // index of the box in its batch
     int zc;          // planes per CTA of the fused sweep (chosen on the host)
+    int par;         // colour of local cell (0,0,0): (sum of the box's lower corner) % 2 on a
+                     // coupled level (red = global i+j+k even), else 0
 };
 
 // Index spaces that kernels tile: all cells, red-black pairs along x
@@ -132,11 +146,34 @@ struct SetupBox {
     long long cQ;
     int zc;                             // unused (tile bookkeeping)
     int bc;                             // wall mask: bit w set = wall w Neumann
+    const double *betaL;                // coupled level 0: beta in the level layout, guards
+                                        // holding the neighbour box's beta or -1 (no neighbour)
 };
 typedef DescSet<SetupBox> SetupSet;
 
 // The coarse end of one box's V-cycle, run by a single CTA: levels
 // lv[0] (the first level small enough) down to lv[nlev-1] (the coarsest).
+// Ghost exchange of a coupled level: copy the src box's cells of a patch
+// (extents ex, ey, ez; one of them 1) into the dst box's guard cells (local
+// coordinates, guard positions -1 or n).  Box indices refer to the level's
+// launch set.
+struct ExchRec {
+    int dst, src;
+    int di, dj, dk;  // patch origin in dst (guard layer)
+    int si, sj, sk;  // the same cells in src's local coordinates
+    int ex, ey, ez;
+};
+
+// The coarsest levels of a coupled level's boxes, solved together: cell c
+// of box b is union unknown off[b] + c (c in C order of the box).
+struct UnionBottom {
+    int n;               // unknowns (<= MG_MAX_BOTTOM)
+    int nbox;
+    const int *off;      // [nbox + 1]
+    const ExchRec *rec;  // ghost exchange records of the coarsest level
+    int nrec;
+};
+
 constexpr int kMaxCoarse = 10;
 template <class T>
 struct CoarseJob {

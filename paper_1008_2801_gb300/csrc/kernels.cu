@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass(BoxSet<T> S, const int *
     const long long Q = B.Q;
     TilePos p = tile_pos(TK_PAIR, nx, ny, nz, t - ts[b]);
     const int j = p.y, k = p.z;
-    const int i = 2 * p.x + ((j + k + color) & 1);
+    const int i = 2 * p.x + ((j + k + color + B.par) & 1);
     if (j >= ny || i >= nx) return;
     const long long c = (long long)k * Q + (long long)j * P + i;
     B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, P, Q);
@@ -132,7 +132,7 @@ __device__ __forceinline__ void oop_pair(const Box<T> &B, int color, int from2, 
     typedef typename Vec2<T>::type V2;
     const long long c0 = (long long)k * Q + (long long)j * P + x0;
     V2 pair = *reinterpret_cast<const V2 *>(src + c0);
-    const int odd = (j + k + color) & 1;   // the pair's cell of this colour
+    const int odd = (j + k + color + B.par) & 1;   // the pair's cell of this colour
     if (x0 + odd < B.nx) {
         const long long c = c0 + odd;
         const T sc = gs_sum<T>(src, B.f, B.wx, B.wy, B.wz, c, P, Q);
@@ -616,7 +616,7 @@ __device__ __forceinline__ void cta_pass(const Box<T> &B, int color)
         const int p = q % npx;
         const int r = q / npx;
         const int j = r % B.ny, k = r / B.ny;
-        const int i = 2 * p + ((j + k + color) & 1);
+        const int i = 2 * p + ((j + k + color + B.par) & 1);
         if (i >= B.nx) continue;
         const long long c = (long long)k * B.Q + (long long)j * B.P + i;
         B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, B.P, B.Q);
@@ -942,6 +942,28 @@ __device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, l
                           : harmonic_w(bc(i, j, k - 1), bc(i, j, k), c2);
 }
 
+// Face weights of a coupled level's box from beta in the level layout (bl),
+// whose guard cells hold the neighbouring box's beta across an interface or
+// -1 on the union's boundary: an interface face takes the harmonic mean like
+// any inner face (the neighbour computes the same value), a boundary face is
+// a Dirichlet wall (2 beta).
+__device__ __forceinline__ void face_weights_level_at(int nx, int ny, int nz, int P, long long Q,
+                                                      double inv_h2,
+                                                      const double *__restrict__ bl, double *wx,
+                                                      double *wy, double *wz, int i, int j, int k)
+{
+    const long long q = (long long)k * Q + (long long)j * P + i;
+    const double c2 = 2.0 * inv_h2;
+    auto face = [&](double a, double b) {  // a below / left of the face, b above / right
+        if (a < 0.0) return 2.0 * b * inv_h2;
+        if (b < 0.0) return 2.0 * a * inv_h2;
+        return harmonic_w(a, b, c2);
+    };
+    if (j < ny && k < nz) wx[q] = face(bl[q - 1], bl[q]);
+    if (i < nx && k < nz) wy[q] = face(bl[q - P], bl[q]);
+    if (i < nx && j < ny) wz[q] = face(bl[q - Q], bl[q]);
+}
+
 // Coarse position (I, J, K) in [0, cx] x [0, cy] x [0, cz]; coarse face
 // beta = mean of the 4 fine faces, coarse h = 2h: w_c = (sum of 4 w) / 16.
 __device__ __forceinline__ void coarsen_at(int nx, int ny, int nz, int P, long long Q,
@@ -1001,6 +1023,36 @@ __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long lon
 // definite: applied to r it gives a solution of M x = r - mean(r) (the
 // constant part of r, which no solution can match, is dropped), and the
 // zero-mean one when r has zero mean.
+// The block of M = -A of one box inside an n x n matrix a, rows and
+// columns from `at` on (the box's cells in C order): diagonal = sum of the
+// six weights, -w to each neighbour inside the box.  Called by every thread
+// of the CTA.
+__device__ __forceinline__ void assemble_box_block(int nx, int ny, int nz, int P, long long Q,
+                                                   const double *__restrict__ wx,
+                                                   const double *__restrict__ wy,
+                                                   const double *__restrict__ wz, double *a,
+                                                   int n, int at)
+{
+    const int m = nx * ny * nz;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        const int i = r % nx, j = (r / nx) % ny, k = r / (nx * ny);
+        const long long c = (long long)k * Q + (long long)j * P + i;
+        const double ww = wx[c], we = wx[c + 1], ws = wy[c], wn = wy[c + P], wd = wz[c],
+                     wu = wz[c + Q];
+        double *row = a + (long long)(at + r) * n + at;
+        row[r] = ((ww + we) + (ws + wn)) + (wd + wu);
+        if (i > 0) row[r - 1] = -ww;
+        if (i < nx - 1) row[r + 1] = -we;
+        if (j > 0) row[r - nx] = -ws;
+        if (j < ny - 1) row[r + nx] = -wn;
+        if (k > 0) row[r - nx * ny] = -wd;
+        if (k < nz - 1) row[r + nx * ny] = -wu;
+    }
+}
+
+__device__ __forceinline__ void gauss_jordan_cta(double *a, int n, bool singular, double *inv64,
+                                                 float *inv32, double *col);
+
 __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P, long long Q,
                                                    const double *__restrict__ wx,
                                                    const double *__restrict__ wy,
@@ -1009,24 +1061,21 @@ __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P
                                                    double *col)
 {
     const int n = nx * ny * nz;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = 0.0;
+    __syncthreads();
+    assemble_box_block(nx, ny, nz, P, Q, wx, wy, wz, a, n, 0);
+    __syncthreads();
+    gauss_jordan_cta(a, n, singular, inv64, inv32, col);
+}
+
+// In-place Gauss-Jordan inverse of the n x n matrix a (M, symmetric positive
+// definite; with `singular` first shifted by c 1 1^T as described above),
+// written as A^{-1} = -M^{-1} to inv64 (and inv32 when given).
+__device__ __forceinline__ void gauss_jordan_cta(double *a, int n, bool singular, double *inv64,
+                                                 float *inv32, double *col)
+{
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (long long e = tid; e < (long long)n * n; e += nt) a[e] = 0.0;
-    __syncthreads();
-    for (int r = tid; r < n; r += nt) {
-        const int i = r % nx, j = (r / nx) % ny, k = r / (nx * ny);
-        const long long c = (long long)k * Q + (long long)j * P + i;
-        const double ww = wx[c], we = wx[c + 1], ws = wy[c], wn = wy[c + P], wd = wz[c],
-                     wu = wz[c + Q];
-        a[(long long)r * n + r] = ((ww + we) + (ws + wn)) + (wd + wu);
-        if (i > 0) a[(long long)r * n + r - 1] = -ww;
-        if (i < nx - 1) a[(long long)r * n + r + 1] = -we;
-        if (j > 0) a[(long long)r * n + r - nx] = -ws;
-        if (j < ny - 1) a[(long long)r * n + r + nx] = -wn;
-        if (k > 0) a[(long long)r * n + r - nx * ny] = -wd;
-        if (k < nz - 1) a[(long long)r * n + r + nx * ny] = -wu;
-    }
-    __syncthreads();
     if (singular) {
         if (tid == 0) {
             double tr = 0.0;
@@ -1129,7 +1178,7 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
 // ---- every box of a level in one launch (the solver's set-up)
 
 // step 0 faces (TK_FACE), 1 coarsen (TK_CFACE), 2 diagonal (TK_CELL),
-// 3 FP32 copies (TK_FACE)
+// 3 FP32 copies (TK_FACE), 4 faces of a coupled level from betaL (TK_FACE)
 __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
 {
     const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
@@ -1150,6 +1199,9 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
     else if (step == 2)
         inv_diag_at(B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.D,
                     (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
+    else if (step == 4)
+        face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.betaL, B.wx, B.wy, B.wz,
+                              p.x, p.y, p.z);
     else
         round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
                  B.invD32, p.x, p.y, p.z);
@@ -1337,6 +1389,154 @@ __global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int fie
     if (p.x >= B.nx || p.y >= B.ny) return;
     double *x = field ? B.phi : B.f;
     x[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] -= mean[B.box];
+}
+
+// ---------------------------------------------------- coupled levels ----
+//
+// The boxes of a coupled level (one MultiFAB level, paper Sec. 2, solved as
+// one domain) keep their arrays in the wide layout.  Before every kernel
+// that reads a neighbour of a box's cell, the guard cells that face another
+// box receive that box's current values (ghost exchange, one CTA per
+// intersection patch); the other guard cells stay 0, the Dirichlet walls of
+// the union.
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_exchange(BoxSet<T> S, const int *__restrict__ active,
+                                                       const ExchRec *__restrict__ rec)
+{
+    if (active && !active[0]) return;   // one decision for the whole level
+    const ExchRec R = rec[blockIdx.x];
+    const Box<T> &D = S.boxes[R.dst];
+    const Box<T> &F = S.boxes[R.src];
+    const int n = R.ex * R.ey * R.ez;
+    for (int e = threadIdx.y * kTX + threadIdx.x; e < n; e += kThreads) {
+        const int a = e % R.ex, r = e / R.ex;
+        const int bb = r % R.ey, c = r / R.ey;
+        D.phi[(long long)(R.dk + c) * D.Q + (long long)(R.dj + bb) * D.P + R.di + a] =
+            F.phi[(long long)(R.sk + c) * F.Q + (long long)(R.sj + bb) * F.P + R.si + a];
+    }
+}
+
+// The guard cells of the six faces of every box (CTA (box, face)) = v.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_guard_fill(BoxSet<T> S, T v)
+{
+    const Box<T> &B = S.boxes[blockIdx.x];
+    const int face = blockIdx.y;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const int ea = face < 2 ? ny : nx, eb = face < 4 ? nz : ny;
+    for (int e = threadIdx.y * kTX + threadIdx.x; e < ea * eb; e += kThreads) {
+        const int a = e % ea, b = e / ea;
+        int i, j, k;
+        if (face < 2) { i = face ? nx : -1; j = a; k = b; }
+        else if (face < 4) { i = a; j = face == 3 ? ny : -1; k = b; }
+        else { i = a; j = b; k = face == 5 ? nz : -1; }
+        B.phi[(long long)k * B.Q + (long long)j * B.P + i] = v;
+    }
+}
+
+// Dense inverse of the union of the boxes' coarsest levels (one CTA): each
+// box's block as for a single box, plus -w between a box's cell and the cell
+// of the neighbouring box across every interface face (from the coarsest
+// level's exchange records: guard cell of dst <-> cell of src), then
+// Gauss-Jordan.  S: the coarsest level of every box, in union order.
+__global__ void __launch_bounds__(1024) k_union_inverse(SetupSet S, UnionBottom U, double *a,
+                                                        double *inv64, float *inv32)
+{
+    __shared__ double col[MG_BOTTOM_CELLS];
+    const int n = U.n;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = 0.0;
+    __syncthreads();
+    for (int b = 0; b < U.nbox; ++b) {
+        const SetupBox &B = S.boxes[b];
+        assemble_box_block(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, a, n, U.off[b]);
+    }
+    __syncthreads();
+    for (int q = 0; q < U.nrec; ++q) {
+        const ExchRec R = U.rec[q];
+        const SetupBox &D = S.boxes[R.dst];
+        const SetupBox &F = S.boxes[R.src];
+        const int m = R.ex * R.ey * R.ez;
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            const int x = e % R.ex, r = e / R.ex;
+            const int y = r % R.ey, z = r / R.ey;
+            int gi = R.di + x, gj = R.dj + y, gk = R.dk + z;  // guard cell of dst
+            const int si = R.si + x, sj = R.sj + y, sk = R.sk + z;
+            // the dst cell next to the guard, and the weight of the face between
+            int ci = min(max(gi, 0), D.nx - 1), cj = min(max(gj, 0), D.ny - 1),
+                ck = min(max(gk, 0), D.nz - 1);
+            const long long c = (long long)ck * D.Q + (long long)cj * D.P + ci;
+            double w;
+            if (gi < 0) w = D.wx[c];
+            else if (gi >= D.nx) w = D.wx[c + 1];
+            else if (gj < 0) w = D.wy[c];
+            else if (gj >= D.ny) w = D.wy[c + D.P];
+            else if (gk < 0) w = D.wz[c];
+            else w = D.wz[c + D.Q];
+            const int row = U.off[R.dst] + (ck * D.ny + cj) * D.nx + ci;
+            const int cl = U.off[R.src] + (sk * F.ny + sj) * F.nx + si;
+            a[(long long)row * n + cl] = -w;
+        }
+        __syncthreads();
+    }
+    gauss_jordan_cta(a, n, false, inv64, inv32, col);
+}
+
+// Coarsest solve of a coupled level: phi = Ainv f over the union, rows in
+// chunks of 32 per CTA (grid y).  S: coarsest level of every box in union
+// order.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_union_bottom(BoxSet<T> S, UnionBottom U,
+                                                           const T *__restrict__ ainv,
+                                                           const int *__restrict__ active)
+{
+    __shared__ T fs[MG_BOTTOM_CELLS];
+    if (active && !active[0]) return;
+    const int n = U.n;
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    auto locate = [&](int q, int &b, long long &c) {
+        b = find_box(U.off, U.nbox, q);
+        const Box<T> &B = S.boxes[b];
+        const int r = q - U.off[b];
+        const int i = r % B.nx, j = (r / B.nx) % B.ny, k = r / (B.nx * B.ny);
+        c = (long long)k * B.Q + (long long)j * B.P + i;
+    };
+    for (int q = tid; q < n; q += kThreads) {
+        int b;
+        long long c;
+        locate(q, b, c);
+        fs[q] = S.boxes[b].f[c];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    for (int rr = 0; rr < 4; ++rr) {
+        const int r = blockIdx.x * 32 + warp * 4 + rr;
+        if (r >= n) break;
+        const T *row = ainv + (long long)r * n;
+        T acc = T(0);
+        for (int q = lane; q < n; q += 32) acc = fmadd(row[q], fs[q], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            int b;
+            long long c;
+            locate(r, b, c);
+            S.boxes[b].phi[c] = acc;
+        }
+    }
+}
+
+// A coupled level has one residual norm: norm[b] <- sqrt(sum over boxes of
+// norm[b]^2) for every box (a fixed-order sum by one thread).
+__global__ void k_norm_combine(int nbox, double *__restrict__ norm)
+{
+    __shared__ double tot;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nbox; ++b) s += norm[b] * norm[b];
+        tot = sqrt(s);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) norm[b] = tot;
 }
 
 // ----------------------------------------------------------- launchers ----
@@ -1632,6 +1832,44 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
     return counted(cudaGetLastError());
 }
 
+template <class T>
+cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec *rec, int nrec,
+                            cudaStream_t st)
+{
+    if (nrec == 0) return cudaSuccess;
+    k_exchange<T><<<nrec, block2d(), 0, st>>>(S, active, rec);
+    return counted(cudaGetLastError());
+}
+
+template <class T>
+cudaError_t launch_guard_fill(const BoxSet<T> &S, T v, cudaStream_t st)
+{
+    if (S.nbox == 0) return cudaSuccess;
+    k_guard_fill<T><<<dim3(S.nbox, 6), block2d(), 0, st>>>(S, v);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_union_inverse(const SetupSet &S, const UnionBottom &U, double *work,
+                                 double *inv64, float *inv32, cudaStream_t st)
+{
+    k_union_inverse<<<1, 1024, 0, st>>>(S, U, work, inv64, inv32);
+    return counted(cudaGetLastError());
+}
+
+template <class T>
+cudaError_t launch_union_bottom(const BoxSet<T> &S, const UnionBottom &U, const T *ainv,
+                                const int *active, cudaStream_t st)
+{
+    k_union_bottom<T><<<(U.n + 31) / 32, block2d(), 0, st>>>(S, U, ainv, active);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_norm_combine(int nbox, double *norm, cudaStream_t st)
+{
+    k_norm_combine<<<1, 256, 0, st>>>(nbox, norm);
+    return counted(cudaGetLastError());
+}
+
 #define MG_INSTANTIATE(T)                                                                        \
     template cudaError_t launch_rbgs_pass<T>(const BoxSet<T> &, const int *, int, cudaStream_t);  \
     template cudaError_t launch_rbgs_pass_oop<T>(const BoxSet<T> &, const int *, int, int, double *, \
@@ -1650,7 +1888,12 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
     template cudaError_t launch_bottom<T>(const BoxSet<T> &, const int *, int, cudaStream_t);   \
     template cudaError_t launch_zero<T>(const BoxSet<T> &, const int *, cudaStream_t);          \
     template cudaError_t launch_coarse_vcycle<T>(const CoarseJob<T> *, int, const int *, int, int, \
-                                                 cudaStream_t);
+                                                 cudaStream_t);                                     \
+    template cudaError_t launch_exchange<T>(const BoxSet<T> &, const int *, const ExchRec *, int,  \
+                                            cudaStream_t);                                         \
+    template cudaError_t launch_guard_fill<T>(const BoxSet<T> &, T, cudaStream_t);                 \
+    template cudaError_t launch_union_bottom<T>(const BoxSet<T> &, const UnionBottom &, const T *, \
+                                                const int *, cudaStream_t);
 
 MG_INSTANTIATE(double)
 MG_INSTANTIATE(float)

@@ -166,4 +166,22 @@ cudaError_t launch_bc_lift(int nx, int ny, int nz, double inv_h, int bcm, const 
 cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *partials, double *mean,
                                cudaStream_t st);
 
+// ---- coupled levels (the boxes of one level solved as one domain) ---------
+// Copy each record's source patch into the destination box's guard cells.
+template <class T>
+cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec *rec, int nrec,
+                            cudaStream_t st);
+// The guard cells of the six faces of every box of S = v (phi arrays).
+template <class T>
+cudaError_t launch_guard_fill(const BoxSet<T> &S, T v, cudaStream_t st);
+// Dense inverse of the union of the coarsest levels (S in union order).
+cudaError_t launch_union_inverse(const SetupSet &S, const UnionBottom &U, double *work,
+                                 double *inv64, float *inv32, cudaStream_t st);
+// phi = Ainv f on the union of the coarsest levels.
+template <class T>
+cudaError_t launch_union_bottom(const BoxSet<T> &S, const UnionBottom &U, const T *ainv,
+                                const int *active, cudaStream_t st);
+// norm[b] <- sqrt(sum over b of norm[b]^2), for every b.
+cudaError_t launch_norm_combine(int nbox, double *norm, cudaStream_t st);
+
 }  // namespace mg

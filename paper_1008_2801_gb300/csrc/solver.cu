@@ -111,8 +111,8 @@ static void carve(Solver *s, Hier<T> &H, Bump &bump, bool full)
         H.lv[b].resize(s->nlev[b]);
         for (int l = 0; l < s->nlev[b]; ++l) {
             const auto &d = s->dims[b][l];
-            const long long E = level_elems(d[0], d[1], d[2]);
-            const long long Q = pitch_plane(d[0], d[1]);
+            const long long E = level_elems(d[0], d[1], d[2], s->wide);
+            const long long Q = pitch_plane(d[0], d[1], s->wide);
             auto arr = [&]() {
                 T *p = bump.take<T>((size_t)E);
                 return p ? p + Q : nullptr;
@@ -140,8 +140,9 @@ static void carve(Solver *s, Hier<T> &H, Bump &bump, bool full)
         }
         const auto &db = s->dims[b][s->nlev[b] - 1];
         const size_t nb = (size_t)db[0] * db[1] * db[2];
-        H.ainv[b] = (s->shared && b > 0) ? H.ainv[0] : bump.take<T>(nb * nb);
+        if (!s->coupled) H.ainv[b] = (s->shared && b > 0) ? H.ainv[0] : bump.take<T>(nb * nb);
     }
+    if (s->coupled) H.uinv = bump.take<T>((size_t)s->ub.n * s->ub.n);
 }
 
 template <class T>
@@ -161,19 +162,23 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
     B.nx = d[0];
     B.ny = d[1];
     B.nz = d[2];
-    B.P = (int)pitch_row(d[0]);
-    B.Q = pitch_plane(d[0], d[1]);
+    B.P = (int)pitch_row(d[0], s->wide);
+    B.Q = pitch_plane(d[0], d[1], s->wide);
     if (l + 1 < s->nlev[b]) {
         const LevelBufs<T> &C = H.lv[b][l + 1];
         const auto &c = s->dims[b][l + 1];
         B.phic = C.phi;
         B.fc = C.f;
-        B.cP = (int)pitch_row(c[0]);
-        B.cQ = pitch_plane(c[0], c[1]);
+        B.cP = (int)pitch_row(c[0], s->wide);
+        B.cQ = pitch_plane(c[0], c[1], s->wide);
     }
     if (l == s->nlev[b] - 1) B.ainv = H.ainv[b];
     B.box = b;
     B.zc = kSweepZ;
+    if (s->coupled) {
+        const auto &o = s->lo[b][l];
+        B.par = (((o[0] + o[1] + o[2]) % 2) + 2) % 2;
+    }
     return B;
 }
 
@@ -374,18 +379,92 @@ static int validate_opts(const mg_opts *o)
     return MG_OK;
 }
 
+// Level structure of a coupled level: halve while every box's dims are even
+// and at least 4 and every lower corner is even.  Fills dims and lower
+// corners per box and level; returns the level count.
+static int coupled_levels(int nbox, const int (*lo)[3], const int (*n)[3],
+                          std::vector<std::vector<std::array<int, 3>>> &dims,
+                          std::vector<std::vector<std::array<int, 3>>> &los)
+{
+    dims.assign(nbox, {});
+    los.assign(nbox, {});
+    for (int b = 0; b < nbox; ++b) {
+        dims[b].push_back({n[b][0], n[b][1], n[b][2]});
+        los[b].push_back({lo[b][0], lo[b][1], lo[b][2]});
+    }
+    int L = 1;
+    while (L < 32) {
+        bool ok = true;
+        for (int b = 0; b < nbox && ok; ++b)
+            for (int d = 0; d < 3 && ok; ++d) {
+                const int m = dims[b][L - 1][d], c = los[b][L - 1][d];
+                ok = m % 2 == 0 && m >= 4 && c % 2 == 0;
+            }
+        if (!ok) break;
+        for (int b = 0; b < nbox; ++b) {
+            const auto &m = dims[b][L - 1];
+            const auto &c = los[b][L - 1];
+            dims[b].push_back({m[0] / 2, m[1] / 2, m[2] / 2});
+            los[b].push_back({c[0] / 2, c[1] / 2, c[2] / 2});
+        }
+        ++L;
+    }
+    return L;
+}
+
 int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
-                  const mg_opts *opts, bool shared_weights)
+                  const mg_opts *opts, bool shared_weights, const int (*lo)[3])
 {
     if (!out) return set_error(MG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (nbox < 1 || !n || !dx) return set_error(MG_ERR_INVALID_ARG, "need nbox >= 1, n, dx");
     if (bc < 0 || bc > MG_BC_NEUMANN_ALL)
         return set_error(MG_ERR_INVALID_ARG, "bc must be a wall mask in 0..63");
+    const bool coupled = lo != nullptr;
+    if (coupled && bc != 0)
+        return set_error(MG_ERR_INVALID_ARG, "a coupled level has Dirichlet walls (bc = 0)");
     mg_opts o;
     mg_default_opts(&o);
     if (opts) o = *opts;
     CKS(validate_opts(&o));
+    if (coupled) {
+        // ghost exchanges between boxes before every stencil: single-colour
+        // passes, all-cell residuals, per-level launches down to the union's
+        // dense bottom solve
+        o.smoother = 1;
+        o.full_residual = 1;
+        o.coarse_cells = -1;
+        o.tma = 0;
+    }
+    std::vector<std::vector<std::array<int, 3>>> cdims, clos;
+    std::vector<Brick> bricks;
+    int clev = 0, ucells = 0;
+    if (coupled) {
+        for (int b = 0; b < nbox; ++b) {
+            Brick B;
+            for (int d = 0; d < 3; ++d) {
+                if (n[b][d] < 1) return set_error(MG_ERR_INVALID_ARG, "box %d: need n >= 1", b);
+                B.lo[d] = lo[b][d];
+                B.n[d] = n[b][d];
+            }
+            if (dx[b] != dx[0])
+                return set_error(MG_ERR_INVALID_ARG, "a coupled level has one spacing dx");
+            bricks.push_back(B);
+        }
+        int a = 0, c = 0;
+        if (level_check_disjoint(bricks, &a, &c))
+            return set_error(MG_ERR_INVALID_ARG, "boxes %d and %d overlap", a, c);
+        clev = coupled_levels(nbox, lo, n, cdims, clos);
+        for (int b = 0; b < nbox; ++b) {
+            const auto &d = cdims[b][clev - 1];
+            ucells += d[0] * d[1] * d[2];
+        }
+        if (ucells > MG_MAX_BOTTOM)
+            return set_error(MG_ERR_UNSUPPORTED,
+                             "coarsest level of the union has %d cells (> %d): box dims and "
+                             "corners must halve further together",
+                             ucells, MG_MAX_BOTTOM);
+    }
 
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
@@ -400,6 +479,13 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->tma = s->has32 && o.tma == 1;
     s->bc = bc;
     s->singular = bc == MG_BC_NEUMANN_ALL;
+    s->coupled = coupled;
+    s->wide = coupled;
+    if (coupled) {
+        s->lo = clos;
+        s->ub.n = ucells;
+        s->ub.nbox = nbox;
+    }
     s->off.assign(nbox + 1, 0);
     for (int b = 0; b < nbox; ++b) {
         const int nx = n[b][0], ny = n[b][1], nz = n[b][2];
@@ -413,12 +499,12 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         }
         s->n.push_back({nx, ny, nz});
         s->dx.push_back(dx[b]);
-        s->dims.push_back(level_dims(nx, ny, nz));
+        s->dims.push_back(coupled ? cdims[b] : level_dims(nx, ny, nz));
         s->nlev.push_back((int)s->dims.back().size());
         s->maxlev = std::max(s->maxlev, s->nlev.back());
         const std::array<int, 3> db = s->dims.back().back();
         const int cells = db[0] * db[1] * db[2];
-        if (cells > MG_MAX_BOTTOM) {
+        if (!coupled && cells > MG_MAX_BOTTOM) {
             delete s;
             return set_error(MG_ERR_UNSUPPORTED,
                              "box %d: coarsest level %dx%dx%d has %d cells (> %d); the dims "
@@ -442,6 +528,10 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         work_off[b] = work_elems;
         work_elems += nb * nb;
         ntiles0 += (size_t)tiles_of(TK_CELL, s->n[b][0], s->n[b][1], s->n[b][2]);
+    }
+    if (coupled) {  // one dense inverse for the union of the coarsest levels
+        work_elems = (size_t)ucells * ucells;
+        std::fill(work_off.begin(), work_off.end(), 0);
     }
     bump.take<double>(s->total);      // beta copy
     bump.take<double>(work_elems);    // inverse scratch
@@ -537,8 +627,8 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
             B.cwx = C.wx;
             B.cwy = C.wy;
             B.cwz = C.wz;
-            B.cP = (int)pitch_row(c[0]);
-            B.cQ = pitch_plane(c[0], c[1]);
+            B.cP = (int)pitch_row(c[0], s->wide);
+            B.cQ = pitch_plane(c[0], c[1], s->wide);
         }
         if (s->has32) {
             const LevelBufs<float> &M = s->h32.lv[b][l];
@@ -552,10 +642,11 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         B.nx = d[0];
         B.ny = d[1];
         B.nz = d[2];
-        B.P = (int)pitch_row(d[0]);
-        B.Q = pitch_plane(d[0], d[1]);
+        B.P = (int)pitch_row(d[0], s->wide);
+        B.Q = pitch_plane(d[0], d[1], s->wide);
         B.zc = kSweepZ;
         B.bc = s->bc;
+        if (s->coupled && l == 0) B.betaL = L.phi;  // beta is staged in phi during set-up
         if (l == s->nlev[b] - 1) {
             B.work = s->work + work_off[b];
             B.inv64 = s->h64.ainv[b];
@@ -577,6 +668,29 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         std::vector<SetupBox> bot;
         for (int b = 0; b < nsetup; ++b) bot.push_back(setup_box(b, s->nlev[b] - 1));
         psu.push_back(plan_set(blob, &s->setup_bottom, bot));
+    }
+    // coupled level: ghost exchange records of every level (the cached
+    // communication pattern) and the union numbering of the coarsest cells
+    std::vector<size_t> xrec_at;
+    size_t uoff_at = 0;
+    if (coupled) {
+        for (int l = 0; l < clev; ++l) {
+            std::vector<Brick> bl(nbox);
+            for (int b = 0; b < nbox; ++b)
+                for (int d = 0; d < 3; ++d) {
+                    bl[b].lo[d] = clos[b][l][d];
+                    bl[b].n[d] = cdims[b][l][d];
+                }
+            const std::vector<ExchRec> recs = level_exchange(bl);
+            s->nxrec.push_back((int)recs.size());
+            xrec_at.push_back(blob.put(recs.data(), recs.size() * sizeof(ExchRec)));
+        }
+        std::vector<int> uo(nbox + 1, 0);
+        for (int b = 0; b < nbox; ++b) {
+            const auto &d = cdims[b][clev - 1];
+            uo[b + 1] = uo[b] + d[0] * d[1] * d[2];
+        }
+        uoff_at = blob.put(uo.data(), uo.size() * sizeof(int));
     }
     const size_t off_at = blob.put(s->off.data(), s->off.size() * sizeof(long long));
     std::vector<int> zeros(nbox, 0);
@@ -601,6 +715,13 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (s->has32) s->h32.jobs = reinterpret_cast<const CoarseJob<float> *>(s->desc + jobs32);
     s->doff = reinterpret_cast<const long long *>(s->desc + off_at);
     s->dside = reinterpret_cast<int *>(s->desc + side_at);
+    if (coupled) {
+        for (size_t l = 0; l < xrec_at.size(); ++l)
+            s->xrec.push_back(reinterpret_cast<const ExchRec *>(s->desc + xrec_at[l]));
+        s->ub.off = reinterpret_cast<const int *>(s->desc + uoff_at);
+        s->ub.rec = s->xrec[clev - 1];
+        s->ub.nrec = s->nxrec[clev - 1];
+    }
 
     if (cudaMallocHost(&s->hjblock, s->jbytes) != cudaSuccess ||
         cudaMallocHost(&s->hnorm, sizeof(double) * 2 * nbox) != cudaSuccess ||
@@ -709,14 +830,30 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     const long long k0 = launch_counter();
     const long long nbeta = s->shared ? s->off[1] : s->total;
     CK(cudaMemcpyAsync(s->beta, beta, sizeof(double) * nbeta, cudaMemcpyDefault, st));
-    // one launch per step and level over every box
-    CK(launch_setup(s->setup_lv[0], 0, st));
+    if (s->coupled) {
+        // beta into the level layout of level 0 (staged in phi), guard cells
+        // -1 (the union's boundary) except where the exchange brings the
+        // neighbouring box's beta; faces from there
+        CK(launch_guard_fill(s->h64.fine, -1.0, st));
+        CK(launch_pack(s->h64.fine, s->doff, s->beta, 0, st));
+        CK(launch_exchange(s->h64.fine, nullptr, s->xrec[0], s->nxrec[0], st));
+        CK(launch_setup(s->setup_lv[0], 4, st));
+    } else {
+        // one launch per step and level over every box
+        CK(launch_setup(s->setup_lv[0], 0, st));
+    }
     for (size_t l = 0; l < s->setup_coarsen.size(); ++l) CK(launch_setup(s->setup_coarsen[l], 1, st));
     for (int l = 0; l < s->maxlev; ++l) {
         CK(launch_setup(s->setup_lv[l], 2, st));
         if (s->has32) CK(launch_setup(s->setup_lv[l], 3, st));
     }
-    CK(launch_setup_bottom(s->setup_bottom, st));
+    if (s->coupled) {
+        CK(launch_union_inverse(s->setup_bottom, s->ub, s->work, s->h64.uinv,
+                                s->has32 ? s->h32.uinv : nullptr, st));
+        CK(launch_guard_fill(s->h64.fine, 0.0, st));  // Dirichlet zeros again
+    } else {
+        CK(launch_setup_bottom(s->setup_bottom, st));
+    }
     CK(cudaEventRecord(s->ev_setup1, st));
     s->kernels += launch_counter() - k0;
     s->beta_set = true;
@@ -798,9 +935,25 @@ static cudaError_t sweep_launch(Solver *s, const BoxSet<float> &S, const SweepMa
     return launch_rbgs_sweep(S, s->active, src, st);
 }
 
+// Coupled level: fill the guard cells of level lvl's boxes from their
+// neighbours (no-op otherwise).
+template <class T>
+static cudaError_t exch(Solver *s, const BoxSet<T> &S, int lvl, cudaStream_t st)
+{
+    if (!s->coupled) return cudaSuccess;
+    return launch_exchange(S, s->active, s->xrec[lvl], s->nxrec[lvl], st);
+}
+
+// Coupled level: one norm for the union (no-op otherwise).
+static cudaError_t combine(Solver *s, double *norm, cudaStream_t st)
+{
+    if (!s->coupled) return cudaSuccess;
+    return launch_norm_combine(s->nbox, norm, st);
+}
+
 template <class T>
 static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool fused,
-                          const SweepMaps *maps, cudaStream_t st)
+                          const SweepMaps *maps, cudaStream_t st, int lvl = 0)
 {
     cudaError_t e = cudaSuccess;
     int left = nu;
@@ -816,6 +969,7 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
     for (; left > 0; --left) {
         for (int color = 0; color < 2; ++color) {
             int sl = fine ? prof_begin(s, MG_PROF_PASS, st) : -1;
+            if ((e = exch(s, S, lvl, st)) != cudaSuccess) return e;
             if ((e = launch_rbgs_pass(S, s->active, color, st)) != cudaSuccess) return e;
             prof_end(s, sl, st);
         }
@@ -843,9 +997,10 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
             prof_end(s, sl, st);
             --nu1;
         }
-        if ((e = smooth(s, S, nu1, l == 0, H.fused[l] != 0, H.maps[l], st)) != cudaSuccess)
+        if ((e = smooth(s, S, nu1, l == 0, H.fused[l] != 0, H.maps[l], st, l)) != cudaSuccess)
             return e;
         int sl = l == 0 ? prof_begin(s, MG_PROF_RESTRICT, st) : -1;
+        if ((e = exch(s, S, l, st)) != cudaSuccess) return e;
         e = (s->opts.nu1 > 0 && !s->opts.full_residual)
                 ? launch_resid_restrict_red(S, s->active, st)
                 : launch_resid_restrict(S, s->active, st);
@@ -854,9 +1009,11 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     }
     if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
-    if ((e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st)) !=
-        cudaSuccess)
-        return e;
+    if (s->coupled)
+        e = launch_union_bottom(H.bottom, s->ub, H.uinv, s->active, st);
+    else
+        e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st);
+    if (e != cudaSuccess) return e;
     for (int l = nl - 1; l >= 0; --l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
@@ -867,7 +1024,8 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         int sl = l == 0 ? prof_begin(s, MG_PROF_PROLONG, st) : -1;
         if ((e = launch_prolong(S, s->active, st)) != cudaSuccess) return e;
         prof_end(s, sl, st);
-        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, H.maps[l], st)) != cudaSuccess)
+        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, H.maps[l], st, l)) !=
+            cudaSuccess)
             return e;
     }
     prof_end(s, coarse, st);
@@ -881,10 +1039,12 @@ static cudaError_t enqueue_step64(Solver *s, cudaStream_t st)
     if (e != cudaSuccess) return e;
     int sl = prof_begin(s, MG_PROF_NORM, st);
     const int mode = (s->opts.nu2 > 0 && !s->opts.full_residual) ? 2 : 0;
+    if ((e = exch(s, s->h64.fine, 0, st)) != cudaSuccess) return e;
     if ((e = launch_norm_partials(s->h64.fine, s->active, mode, s->partials, st)) != cudaSuccess)
         return e;
     e = launch_norm_finish(s->h64.fine, s->active, s->partials, s->dnorm, nullptr, nullptr, st,
                            nullptr, mode);
+    if (e == cudaSuccess) e = combine(s, s->dnorm, st);
     prof_end(s, sl, st);
     return e;
 }
@@ -1003,12 +1163,14 @@ static cudaError_t enqueue_body32(Solver *s, cudaStream_t st, cudaGraphCondition
     if (e != cudaSuccess) return e;
     if ((e = launch_refine_update(s->h64.fine, s->h32.fine, s->active, s->se, st)) != cudaSuccess)
         return e;
+    if ((e = exch(s, s->h64.fine, 0, st)) != cudaSuccess) return e;
     if ((e = launch_refine_residual(s->h64.fine, s->h32.fine, s->active, s->sr_inv, s->partials,
                                     st)) != cudaSuccess)
         return e;
     if ((e = launch_norm_finish(s->h64.fine, s->active, s->partials, s->dnorm, nullptr, nullptr,
                                 st, s->sr)) != cudaSuccess)
         return e;
+    if ((e = combine(s, s->dnorm, st)) != cudaSuccess) return e;
     if ((e = launch_scales(s->nbox, s->active, 0, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv,
                            st)) != cudaSuccess)
         return e;
@@ -1192,15 +1354,19 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     // leaves r32 = r0 / ||f|| and the scales for the first FP32 cycles.
     CK(launch_norm_partials(H.fine, nullptr, 1, s->partials, stream));
     CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnormf, nullptr, nullptr, stream));
+    CK(combine(s, s->dnormf, stream));
+    CK(exch(s, H.fine, 0, stream));
     if (!mixed) {
         CK(launch_norm_partials(H.fine, nullptr, 0, s->partials, stream));
         CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnorm, nullptr, nullptr, stream));
+        CK(combine(s, s->dnorm, stream));
     } else {
         CK(launch_zero(s->h32.fine, nullptr, stream));
         CK(launch_scales(nbox, nullptr, 1, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv, stream));
         CK(launch_refine_residual(H.fine, s->h32.fine, nullptr, s->sr_inv, s->partials, stream));
         CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnorm, nullptr, nullptr, stream,
                               s->sr));
+        CK(combine(s, s->dnorm, stream));
         CK(launch_scales(nbox, nullptr, 0, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv, stream));
     }
     CK(cudaMemcpyAsync(s->hnorm, s->dnormf, sizeof(double) * nbox, cudaMemcpyDeviceToHost, stream));
@@ -1304,10 +1470,12 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
             s->rec = &s->direct;
             const int sl = prof_begin(s, MG_PROF_REFINE, stream);
             CK(launch_refine_update(H.fine, s->h32.fine, s->active, s->se, stream));
+            CK(exch(s, H.fine, 0, stream));
             CK(launch_refine_residual(H.fine, s->h32.fine, s->active, s->sr_inv, s->partials,
                                       stream));
             CK(launch_norm_finish(H.fine, s->active, s->partials, s->dnorm, nullptr, nullptr,
                                   stream, s->sr));
+            CK(combine(s, s->dnorm, stream));
             prof_end(s, sl, stream);
             s->rec = nullptr;
             CK(launch_scales(nbox, s->active, 0, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv,
@@ -1479,6 +1647,9 @@ static int multi_solver(mg_ctx *ctx, int nrhs, cudaStream_t st, Solver **out)
 struct mg_batch {
     Solver *s;
 };
+struct mg_level {
+    Solver *s;
+};
 
 extern "C" {
 
@@ -1634,6 +1805,47 @@ void mg_batch_destroy(mg_batch *b)
     if (!b) return;
     solver_destroy(b->s);
     delete b;
+}
+
+int mg_level_create(mg_level **out, int nbox, const int (*lo)[3], const int (*n)[3], double dx,
+                    int bc, const mg_opts *opts)
+{
+    if (!out || !lo || !n || nbox < 1) return set_error(MG_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    if (!(dx > 0.0) || !std::isfinite(dx)) return set_error(MG_ERR_INVALID_ARG, "dx must be > 0");
+    std::vector<double> dxs(nbox, dx);
+    Solver *s = nullptr;
+    int rc = solver_create(&s, nbox, n, dxs.data(), bc, opts, false, lo);
+    if (rc != MG_OK) return rc;
+    *out = new mg_level{s};
+    return MG_OK;
+}
+
+int mg_level_set_beta(mg_level *lv, const double *beta, void *stream)
+{
+    if (!lv) return set_error(MG_ERR_INVALID_ARG, "NULL level");
+    return solver_set_beta(lv->s, beta, (cudaStream_t)stream);
+}
+
+int mg_level_solve(mg_level *lv, const double *f, double *phi, double tol, mg_stats *st,
+                   void *stream)
+{
+    if (!lv) return set_error(MG_ERR_INVALID_ARG, "NULL level");
+    return solver_solve(lv->s, f, phi, tol, st, (cudaStream_t)stream, false);
+}
+
+int mg_level_levels(const mg_level *lv, int *nlev)
+{
+    if (!lv || !nlev) return set_error(MG_ERR_INVALID_ARG, "NULL argument");
+    *nlev = lv->s->nlev[0];
+    return MG_OK;
+}
+
+void mg_level_destroy(mg_level *lv)
+{
+    if (!lv) return;
+    solver_destroy(lv->s);
+    delete lv;
 }
 
 static int profile_enable(Solver *s, int on)

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "level.h"
 #include "mg.h"
 
 namespace mg {
@@ -36,6 +37,7 @@ struct Hier {
     int njobs = 0;
     cudaGraphExec_t graph = nullptr;            // captured V-cycle (+ fine norm for FP64)
     cudaGraphExec_t head = nullptr;             // look-ahead: first red pass + norm
+    T *uinv = nullptr;                          // coupled level: dense inverse of the union bottom
 };
 
 // A timed stretch of one stage class: events recorded before and after it.
@@ -104,6 +106,13 @@ struct Solver {
     // also yields the previous iterate's residual norm, judged before the
     // rest of the cycle (no separate norm pass)
     bool lookahead = false;
+    // coupled level (the boxes solved as one domain; mg_level)
+    bool coupled = false;
+    bool wide = false;                               // wide-guard layout (coupled)
+    std::vector<std::vector<std::array<int, 3>>> lo;  // [box][level] lower corners (coupled)
+    std::vector<const ExchRec *> xrec;               // [level] device exchange records
+    std::vector<int> nxrec;                          // [level]
+    UnionBottom ub{};                                // union of the coarsest levels
 
     // set-up launch sets
     std::vector<SetupSet> setup_lv;       // [level] every box that has the level
@@ -127,8 +136,11 @@ struct Solver {
 
 // shared_weights: the nbox boxes are right-hand sides of one box (same dims,
 // dx and beta); weights, diagonals and the coarsest inverse exist once.
+// lo (nullable): lower corners of the boxes of a coupled level (one domain;
+// all dx equal, bc 0); NULL: independent boxes.
 int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
-                  const mg_opts *opts, bool shared_weights = false);
+                  const mg_opts *opts, bool shared_weights = false,
+                  const int (*lo)[3] = nullptr);
 void solver_destroy(Solver *s);
 int solver_set_beta(Solver *s, const double *beta_packed, cudaStream_t st);
 // Solve every box; f/phi packed.  zero_guess ignores phi's input.

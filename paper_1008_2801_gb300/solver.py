@@ -358,6 +358,107 @@ class BatchSolver:
             pass
 
 
+def level_intersections(los, ns, brute=False):
+    """Ghost-exchange records of boxes with lower corners los[b] = (i, j, k)
+    and dims ns[b] = (nx, ny, nz) (host only, no device work): a list of
+    dicts dst, src, d (patch origin in dst), s (in src), e (extents)."""
+    L = _lib.load()
+    nb = len(los)
+    lo = (ctypes.c_int * (3 * nb))(*[int(v) for c in los for v in c])
+    n = (ctypes.c_int * (3 * nb))(*[int(v) for c in ns for v in c])
+    cnt = ctypes.c_int()
+    check(L.mg_level_intersections(nb, lo, n, 1 if brute else 0, ctypes.byref(cnt), None, 0),
+          "mg_level_intersections")
+    buf = (ctypes.c_int * (11 * max(cnt.value, 1)))()
+    check(L.mg_level_intersections(nb, lo, n, 1 if brute else 0, ctypes.byref(cnt), buf,
+                                   cnt.value), "mg_level_intersections")
+    out = []
+    for q in range(cnt.value):
+        v = buf[11 * q:11 * q + 11]
+        out.append({"dst": v[0], "src": v[1], "d": tuple(v[2:5]), "s": tuple(v[5:8]),
+                    "e": tuple(v[8:11])})
+    return out
+
+
+class LevelSolver:
+    """The boxes of one level solved as one domain (mg_level): box b covers
+    cells los[b] .. los[b] + shape - 1 of a common index space, los[b] given
+    as (i, j, k) (x first) and shapes[b] as (nz, ny, nx) like every array
+    here.  Arrays are packed back to back in box order (see ``pack`` /
+    ``unpack``).  Interfaces between boxes are interior faces; the union's
+    boundary has Dirichlet walls (phi = 0)."""
+
+    def __init__(self, los, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
+                 use_graph=True, device=None, inner_cycles=0):
+        L = _lib.load()
+        self.los = [tuple(int(v) for v in c) for c in los]
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        nb = len(self.shapes)
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        lo = (ctypes.c_int * (3 * nb))(*[v for c in self.los for v in c])
+        n = (ctypes.c_int * (3 * nb))(*[v for s in self.shapes for v in (s[2], s[1], s[0])])
+        self._h = ctypes.c_void_p()
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, "passes", 0, inner_cycles)
+        with torch.cuda.device(self.device):
+            check(L.mg_level_create(ctypes.byref(self._h), nb, lo, n, float(dx), 0,
+                                    ctypes.byref(o)), "mg_level_create")
+        self.sizes = [s[0] * s[1] * s[2] for s in self.shapes]
+        self.total = sum(self.sizes)
+
+    def pack(self, arrays):
+        return torch.cat([torch.as_tensor(a).reshape(-1) for a in arrays])
+
+    def unpack(self, packed):
+        out, o = [], 0
+        for s, k in zip(self.shapes, self.sizes):
+            out.append(packed[o:o + k].view(s))
+            o += k
+        return out
+
+    def levels(self):
+        n = ctypes.c_int()
+        check(_lib.load().mg_level_levels(self._h, ctypes.byref(n)), "mg_level_levels")
+        return n.value
+
+    def set_beta(self, beta_packed: torch.Tensor):
+        _check_tensor(beta_packed, "beta", self.total, self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().mg_level_set_beta(self._h, _ptr(beta_packed),
+                                                _stream_of(beta_packed)), "mg_level_set_beta")
+
+    def solve(self, f_packed, phi_packed=None, tol=1e-10):
+        """Returns (phi_packed, stats) with the union's residual history."""
+        _check_tensor(f_packed, "f", self.total, self.device)
+        if phi_packed is None:
+            phi_packed = torch.zeros_like(f_packed)
+        _check_tensor(phi_packed, "phi", self.total, self.device)
+        st = (_lib.mg_stats * len(self.shapes))()
+        with torch.cuda.device(self.device):
+            rc = _lib.load().mg_level_solve(self._h, _ptr(f_packed), _ptr(phi_packed), float(tol),
+                                            st, _stream_of(f_packed))
+        if rc not in _SOFT:
+            raise MGError(rc, "mg_level_solve")
+        return phi_packed, _stats_dict(st[0])
+
+    def close(self):
+        if self._h:
+            _lib.load().mg_level_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class MGSolve(torch.autograd.Function):
     """phi = A(beta)^{-1} f as a differentiable op.
 
