@@ -375,8 +375,9 @@ def run_gpu(args):
 
 
 def run_extra(dev, args):
-    """512^3 FP64 vs mixed, 64 uneven boxes (batched vs sequential) and the
-    8-RHS adjoint; each timed once after one warm-up (not part of value)."""
+    """512^3 FP64 vs mixed, 64 uneven boxes (batched vs sequential), the
+    projection steps, the 256^3 workload as a coupled level of 64 boxes and
+    the 8-RHS adjoint; each timed once after one warm-up (not part of value)."""
     import numpy as np
     import torch
 
@@ -499,6 +500,30 @@ def run_extra(dev, args):
         s.close()
     ex["projection_256^3"] = res
     del u, v, w, S
+
+    # coupled level: the 256^3 workload as 64 boxes of 64^3 solved as one
+    # domain (ghost exchanges between the boxes), next to the single box
+    from paper_1008_2801_gb300 import LevelSolver
+    d = inputs.config(2)
+    n = d["f"].shape[0]
+    m = n // 4
+    los = [(i * m, j * m, k * m) for k in range(4) for j in range(4) for i in range(4)]
+    sl = [(slice(k, k + m), slice(j, j + m), slice(i, i + m)) for (i, j, k) in los]
+    bp = torch.from_numpy(np.concatenate([d["beta"][q].ravel() for q in sl])).to(dev)
+    fp = torch.from_numpy(np.concatenate([d["f"][q].ravel() for q in sl])).to(dev)
+    res = {"boxes": len(los), "box": [m, m, m], "domain": [n, n, n]}
+    for prec in ("fp64", "mixed"):
+        lv = LevelSolver(los, [(m, m, m)] * len(los), d["dx"], precision=prec, device=dev)
+
+        def lvl():
+            lv.set_beta(bp)
+            return lv.solve(fp, tol=TOL)
+        ms, (phi, st) = time_once(lvl)
+        res[prec] = {"cells_per_s": n ** 3 / (ms / 1e3), "ms": ms, "cycles": st["cycles"],
+                     "rel_resid": st["rel_resid"], "status": st["status"], "levels": lv.levels()}
+        lv.close()
+    ex["level_64_boxes_of_64^3"] = res
+    del bp, fp
 
     # adjoint, 128^3 x 8 right-hand sides
     d = inputs.config(5)

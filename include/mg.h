@@ -238,10 +238,10 @@ void mg_batch_destroy(mg_batch *b);
  * the exchange patterns come from a hash-binned intersection of the boxes
  * (regions at least as large as any box, keyed by a box's lowest corner,
  * search of the own and the 26 neighbouring regions: O(N + N^2/M)) and are
- * computed once at create.  Levels halve while every box's dims are even and
- * at least 4 and every lower corner is even; the coarsest levels of all boxes
- * are solved together with a dense inverse (at most MG_MAX_BOTTOM cells in
- * all).  Smoothing uses single-colour passes with a global red-black
+ * computed once at create.  Levels halve while every box's dims and lower
+ * corners are even (boxes may end as single cells); the coarsest levels of
+ * all boxes are solved together with a dense inverse (at most MG_MAX_BOTTOM
+ * cells in all).  Smoothing uses single-colour passes with a global red-black
  * colouring ((i + j + k) of the common index space even = red).
  * Errors: INVALID_ARG (overlapping boxes, n < 1, dx <= 0, bc != 0),
  * UNSUPPORTED (coarsest union above MG_MAX_BOTTOM cells), OOM, CUDA.  The

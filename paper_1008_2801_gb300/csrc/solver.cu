@@ -379,9 +379,11 @@ static int validate_opts(const mg_opts *o)
     return MG_OK;
 }
 
-// Level structure of a coupled level: halve while every box's dims are even
-// and at least 4 and every lower corner is even.  Fills dims and lower
-// corners per box and level; returns the level count.
+// Level structure of a coupled level: halve while every box's dims and
+// lower corners are even (boxes may end as single cells: their neighbours
+// are in other boxes, and a small union keeps the dense coarsest solve,
+// O(n^3) on one SM at set-up, cheap).  Fills dims and lower corners per box
+// and level; returns the level count.
 static int coupled_levels(int nbox, const int (*lo)[3], const int (*n)[3],
                           std::vector<std::vector<std::array<int, 3>>> &dims,
                           std::vector<std::vector<std::array<int, 3>>> &los)
@@ -398,7 +400,7 @@ static int coupled_levels(int nbox, const int (*lo)[3], const int (*n)[3],
         for (int b = 0; b < nbox && ok; ++b)
             for (int d = 0; d < 3 && ok; ++d) {
                 const int m = dims[b][L - 1][d], c = los[b][L - 1][d];
-                ok = m % 2 == 0 && m >= 4 && c % 2 == 0;
+                ok = m % 2 == 0 && m >= 2 && c % 2 == 0;
             }
         if (!ok) break;
         for (int b = 0; b < nbox; ++b) {

@@ -63,7 +63,7 @@ def test_rectangle_tiled_by_boxes_is_the_single_box_solve(cuda_device, precision
     los = [(i, j, k) for k in (0, 16) for j in (0, 16) for i in (0, 16)]
     ns = [(16, 16, 16)] * 8
     st, nlev = _check(los, ns, beta, f, h, cuda_device, precision)
-    assert nlev == 4                      # 16 -> 8 -> 4 -> 2, a 64-cell union bottom
+    assert nlev == 5                      # 16 -> 8 -> 4 -> 2 -> 1: an 8-cell union bottom
     with Solver(beta.shape, h, precision=precision, device=cuda_device) as s:
         s.set_beta(_t(beta, cuda_device))
         one, _ = s.solve(_t(f, cuda_device), tol=TOL)
