@@ -100,6 +100,11 @@ def lib():
             L.oracle_masked_solve.argtypes = [_I, _I, _I, _F, _D, _M, _D, _D, _F, _I,
                                               ctypes.POINTER(_I)]
             L.oracle_masked_solve.restype = _I
+            L.oracle_face_beta_periodic.argtypes = [_I, _I, _I, _D, _I, _D, _D, _D]
+            L.oracle_apply_periodic.argtypes = [_I, _I, _I, _F, _D, _D, _D, _I, _D, _D]
+            L.oracle_periodic_solve.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D, _F, _I,
+                                                ctypes.POINTER(_I)]
+            L.oracle_periodic_solve.restype = _I
             _lib = L
     return _lib
 
@@ -345,3 +350,37 @@ def level_mask(los, ns, shape):
     for (i, j, k), (a, b, c) in zip(los, ns):
         m[k:k + c, j:j + b, i:i + a] = 1
     return m
+
+
+def face_beta_periodic(beta, bc):
+    """Face coefficients with the wall mask bc, whose bits 6, 7, 8 make the x,
+    y, z axis periodic (faces 0 and n: the face between cells n-1 and 0)."""
+    beta = _c(beta)
+    nx, ny, nz = _dims(beta)
+    bx = np.empty((nz, ny, nx + 1))
+    by = np.empty((nz, ny + 1, nx))
+    bz = np.empty((nz + 1, ny, nx))
+    lib().oracle_face_beta_periodic(nx, ny, nz, beta, int(bc), bx, by, bz)
+    return bx, by, bz
+
+
+def apply_periodic(faces, h, phi, bc):
+    """A phi with periodic axes wrapped (faces from face_beta_periodic)."""
+    bx, by, bz = (_c(a) for a in faces)
+    phi = _c(phi)
+    nx, ny, nz = _dims(phi)
+    out = np.empty_like(phi)
+    lib().oracle_apply_periodic(nx, ny, nz, float(h), bx, by, bz, int(bc), phi, out)
+    return out
+
+
+def periodic_solve(beta, f, h, bc, tol=1e-13, maxit=100000):
+    """Solve div(beta grad phi) = f with the walls and periodic axes of bc by
+    conjugate gradients (zero-mean solution when A is singular)."""
+    beta, f = _c(beta), _c(f)
+    nx, ny, nz = _dims(beta)
+    phi = np.zeros_like(f)
+    it = _I(0)
+    s = lib().oracle_periodic_solve(nx, ny, nz, float(h), beta, int(bc), f, phi, float(tol),
+                                    int(maxit), ctypes.byref(it))
+    return phi, {"status": STATUS[s], "iterations": it.value}

@@ -50,6 +50,13 @@
  *                returns the zero-mean solution; its coarsest level is solved
  *                with M + c 1 1^T, which is positive definite and exact on
  *                zero-mean right-hand sides;
+ *   periodic     bits 6, 7, 8 of the wall mask make the x, y or z axis
+ *                periodic: cell n-1 and cell 0 of that axis are neighbours
+ *                across one face (harmonic mean of their beta, stored at
+ *                both face positions 0 and n).  With every axis periodic or
+ *                with Neumann walls on both ends, A is singular and the
+ *                solve is the zero-mean one, as above.  The oracle solves
+ *                periodic boxes by conjugate gradients on the operator;
  *   level        a level of several boxes (paper Sec. 2: the union of
  *                disjoint rectangular grids of a MultiFAB) is one domain:
  *                the same operator on the union, faces between cells of two
@@ -851,6 +858,132 @@ int oracle_masked_solve(int nx, int ny, int nz, double h, const double *beta, co
         for (size_t c = 0; c < n; ++c) p[c] = r[c] + b * p[c];
     }
     if (status == 1 && rr <= tol * tol * ff) status = 0;
+    if (iters) *iters = it;
+    free(bx); free(by); free(bz); free(r); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------- periodic axes */
+
+/* Axis d (0 = x, 1 = y, 2 = z) is periodic when bit 6 + d of bc is set. */
+static int periodic(int bc, int d) { return (bc >> (6 + d)) & 1; }
+
+/* Face coefficients with periodic axes: as oracle_face_beta_bc, except that
+ * on a periodic axis the faces 0 and n are the one face between cells n-1
+ * and 0 (harmonic mean). */
+void oracle_face_beta_periodic(int nx, int ny, int nz, const double *beta, int bc,
+                               double *bx, double *by, double *bz)
+{
+    oracle_face_beta_bc(nx, ny, nz, beta, bc & 63, bx, by, bz);
+    if (periodic(bc, 0))
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j) {
+                double v = harmonic(beta[cell(nx - 1, j, k, nx, ny)], beta[cell(0, j, k, nx, ny)]);
+                bx[xface(0, j, k, nx, ny)] = v;
+                bx[xface(nx, j, k, nx, ny)] = v;
+            }
+    if (periodic(bc, 1))
+        for (int k = 0; k < nz; ++k)
+            for (int i = 0; i < nx; ++i) {
+                double v = harmonic(beta[cell(i, ny - 1, k, nx, ny)], beta[cell(i, 0, k, nx, ny)]);
+                by[yface(i, 0, k, nx, ny)] = v;
+                by[yface(i, ny, k, nx, ny)] = v;
+            }
+    if (periodic(bc, 2))
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double v = harmonic(beta[cell(i, j, nz - 1, nx, ny)], beta[cell(i, j, 0, nx, ny)]);
+                bz[zface(i, j, 0, nx, ny)] = v;
+                bz[zface(i, j, nz, nx, ny)] = v;
+            }
+}
+
+/* phi at (i, j, k) with periodic axes wrapped and 0 outside otherwise. */
+static double value_wrapped(const double *phi, int i, int j, int k, int nx, int ny, int nz, int bc)
+{
+    if (periodic(bc, 0)) i = (i + nx) % nx;
+    if (periodic(bc, 1)) j = (j + ny) % ny;
+    if (periodic(bc, 2)) k = (k + nz) % nz;
+    return value_at(phi, i, j, k, nx, ny, nz);
+}
+
+/* out = A phi with the faces of oracle_face_beta_periodic and wrapped
+ * neighbours on periodic axes. */
+void oracle_apply_periodic(int nx, int ny, int nz, double h, const double *bx, const double *by,
+                           const double *bz, int bc, const double *phi, double *out)
+{
+    double ih2 = 1.0 / (h * h);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double bw = bx[xface(i, j, k, nx, ny)], be = bx[xface(i + 1, j, k, nx, ny)];
+                double bs = by[yface(i, j, k, nx, ny)], bn = by[yface(i, j + 1, k, nx, ny)];
+                double bd = bz[zface(i, j, k, nx, ny)], bu = bz[zface(i, j, k + 1, nx, ny)];
+                double c = phi[cell(i, j, k, nx, ny)];
+                double s = bw * (value_wrapped(phi, i - 1, j, k, nx, ny, nz, bc) - c) +
+                           be * (value_wrapped(phi, i + 1, j, k, nx, ny, nz, bc) - c) +
+                           bs * (value_wrapped(phi, i, j - 1, k, nx, ny, nz, bc) - c) +
+                           bn * (value_wrapped(phi, i, j + 1, k, nx, ny, nz, bc) - c) +
+                           bd * (value_wrapped(phi, i, j, k - 1, nx, ny, nz, bc) - c) +
+                           bu * (value_wrapped(phi, i, j, k + 1, nx, ny, nz, bc) - c);
+                out[cell(i, j, k, nx, ny)] = s * ih2;
+            }
+}
+
+/* Solve A phi = f with the walls and periodic axes of bc by conjugate
+ * gradients on M = -h^2 A.  When A is singular (every axis periodic or with
+ * Neumann walls on both ends) f loses its mean first and phi is returned
+ * with zero mean.  Returns 0 converged, 1 not converged, 2 non-finite. */
+int oracle_periodic_solve(int nx, int ny, int nz, double h, const double *beta, int bc,
+                          const double *f, double *phi, double tol, int maxit, int *iters)
+{
+    size_t n = (size_t)nx * ny * nz;
+    double *bx = (double *)malloc(sizeof(double) * (size_t)nz * ny * (nx + 1));
+    double *by = (double *)malloc(sizeof(double) * (size_t)nz * (ny + 1) * nx);
+    double *bz = (double *)malloc(sizeof(double) * (size_t)(nz + 1) * ny * nx);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    oracle_face_beta_periodic(nx, ny, nz, beta, bc, bx, by, bz);
+    int singular = 1;
+    for (int d = 0; d < 3; ++d)
+        if (!periodic(bc, d) && !(neumann(bc, 2 * d) && neumann(bc, 2 * d + 1))) singular = 0;
+    double h2 = h * h, rr = 0.0;
+    for (size_t c = 0; c < n; ++c) {
+        phi[c] = 0.0;
+        r[c] = -h2 * f[c];
+    }
+    if (singular) remove_mean(n, r);
+    for (size_t c = 0; c < n; ++c) {
+        p[c] = r[c];
+        rr += r[c] * r[c];
+    }
+    double ff = rr;
+    int status = 1, it = 0;
+    if (!isfinite(ff)) status = 2;
+    else if (ff == 0.0) status = 0;
+    for (; status == 1 && it < maxit; ++it) {
+        if (rr <= tol * tol * ff) { status = 0; break; }
+        oracle_apply_periodic(nx, ny, nz, h, bx, by, bz, bc, p, q);
+        double pq = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            q[c] *= -h2;
+            pq += p[c] * q[c];
+        }
+        double alpha = rr / pq, rr1 = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            phi[c] += alpha * p[c];
+            r[c] -= alpha * q[c];
+            rr1 += r[c] * r[c];
+        }
+        if (!isfinite(rr1)) { status = 2; break; }
+        double b = rr1 / rr;
+        rr = rr1;
+        for (size_t c = 0; c < n; ++c) p[c] = r[c] + b * p[c];
+    }
+    if (status == 1 && rr <= tol * tol * ff) status = 0;
+    if (singular) remove_mean(n, phi);
     if (iters) *iters = it;
     free(bx); free(by); free(bz); free(r); free(p); free(q);
     return status;
