@@ -525,6 +525,26 @@ def run_extra(dev, args):
     ex["level_64_boxes_of_64^3"] = res
     del bp, fp
 
+    # wall conditions on the 256^3 workload: every wall Neumann and every
+    # axis periodic (both singular: zero-mean solutions), next to Dirichlet
+    beta = torch.from_numpy(d["beta"]).to(dev)
+    f = torch.from_numpy(d["f"]).to(dev)
+    res = {}
+    for name, bc in (("neumann_all", 63), ("periodic_xyz", 64 | 128 | 256)):
+        res[name] = {}
+        for prec in ("fp64", "mixed"):
+            s = Solver(tuple(f.shape), d["dx"], precision=prec, device=dev, bc=bc)
+
+            def wall_step():
+                s.set_beta(beta)
+                return s.solve(f, tol=TOL)
+            ms, (_, st) = time_once(wall_step)
+            res[name][prec] = {"cells_per_s": f.numel() / (ms / 1e3), "ms": ms,
+                               "cycles": st["cycles"], "status": st["status"]}
+            s.close()
+    ex["walls_256^3"] = res
+    del beta, f
+
     # adjoint, 128^3 x 8 right-hand sides
     d = inputs.config(5)
     beta = torch.from_numpy(d["beta"]).to(dev).requires_grad_(True)

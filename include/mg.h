@@ -70,13 +70,22 @@ enum mg_status {
 
 /* Boundary conditions: the bc argument of mg_create / mg_batch_create is a
  * mask with bit w set when wall w is Neumann, walls numbered x-, x+, y-, y+,
- * z-, z+ (0..5); a clear bit is a Dirichlet wall.  0 = every wall Dirichlet. */
+ * z-, z+ (0..5); a clear bit is a Dirichlet wall.  0 = every wall Dirichlet.
+ * Bits 6, 7, 8 make the x, y, z axis periodic instead (its two wall bits
+ * must be clear): cells n-1 and 0 of that axis are neighbours across one
+ * face (harmonic mean).  Periodic axes are implemented for one box per
+ * context (mg_create; not mg_solve_multi, mg_adjoint, mg_project_correct or
+ * batches: MG_ERR_UNSUPPORTED); such a context smooths with single-colour
+ * passes and fills the periodic guard cells by an exchange before every
+ * stencil.  With every axis periodic or Neumann on both walls, A is
+ * singular: the solve removes the mean of f and returns the zero-mean phi. */
 enum {
     MG_BC_DIRICHLET0 = 0,
     MG_BC_NEUMANN_XLO = 1, MG_BC_NEUMANN_XHI = 2,
     MG_BC_NEUMANN_YLO = 4, MG_BC_NEUMANN_YHI = 8,
     MG_BC_NEUMANN_ZLO = 16, MG_BC_NEUMANN_ZHI = 32,
-    MG_BC_NEUMANN_ALL = 63
+    MG_BC_NEUMANN_ALL = 63,
+    MG_BC_PERIODIC_X = 64, MG_BC_PERIODIC_Y = 128, MG_BC_PERIODIC_Z = 256
 };
 
 /* precision of the V-cycles */
@@ -132,7 +141,8 @@ void mg_default_opts(mg_opts *opts);
 /* Create a solver for an n = {nx, ny, nz} box with spacing dx > 0 on the
  * current CUDA device, walls of the mask bc.  Builds the level list and
  * allocates the hierarchy; runs no kernel.  opts may be NULL (defaults).
- * Errors: INVALID_ARG (n < 1, dx <= 0, bc outside 0..63, bad options),
+ * Errors: INVALID_ARG (n < 1, dx <= 0, bc outside 0..511, a periodic axis
+ * with a Neumann bit, bad options),
  * UNSUPPORTED (a coarsest level above MG_MAX_BOTTOM cells, e.g. a 33^3 box),
  * OOM, CUDA. */
 int mg_create(mg_ctx **out, const int n[3], double dx, int bc, const mg_opts *opts);

@@ -169,6 +169,7 @@ struct ExchRec {
 struct UnionBottom {
     int n;               // unknowns (<= MG_MAX_BOTTOM)
     int nbox;
+    int singular;        // constants in the null space (no Dirichlet wall)
     const int *off;      // [nbox + 1]
     const ExchRec *rec;  // ghost exchange records of the coarsest level
     int nrec;

@@ -948,20 +948,22 @@ __device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, l
 // any inner face (the neighbour computes the same value), a boundary face is
 // a Dirichlet wall (2 beta).
 __device__ __forceinline__ void face_weights_level_at(int nx, int ny, int nz, int P, long long Q,
-                                                      double inv_h2,
+                                                      double inv_h2, int bcm,
                                                       const double *__restrict__ bl, double *wx,
                                                       double *wy, double *wz, int i, int j, int k)
 {
     const long long q = (long long)k * Q + (long long)j * P + i;
     const double c2 = 2.0 * inv_h2;
-    auto face = [&](double a, double b) {  // a below / left of the face, b above / right
-        if (a < 0.0) return 2.0 * b * inv_h2;
-        if (b < 0.0) return 2.0 * a * inv_h2;
+    // a below / left of the face, b above / right; lo/hi: the walls on either
+    // side of axis d (their Dirichlet or Neumann condition from bcm)
+    auto face = [&](double a, double b, int d) {
+        if (a < 0.0) return wall_beta(bcm, 2 * d, b) * inv_h2;
+        if (b < 0.0) return wall_beta(bcm, 2 * d + 1, a) * inv_h2;
         return harmonic_w(a, b, c2);
     };
-    if (j < ny && k < nz) wx[q] = face(bl[q - 1], bl[q]);
-    if (i < nx && k < nz) wy[q] = face(bl[q - P], bl[q]);
-    if (i < nx && j < ny) wz[q] = face(bl[q - Q], bl[q]);
+    if (j < ny && k < nz) wx[q] = face(bl[q - 1], bl[q], 0);
+    if (i < nx && k < nz) wy[q] = face(bl[q - P], bl[q], 1);
+    if (i < nx && j < ny) wz[q] = face(bl[q - Q], bl[q], 2);
 }
 
 // Coarse position (I, J, K) in [0, cx] x [0, cy] x [0, cz]; coarse face
@@ -1200,8 +1202,8 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
         inv_diag_at(B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.D,
                     (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
     else if (step == 4)
-        face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.betaL, B.wx, B.wy, B.wz,
-                              p.x, p.y, p.z);
+        face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.betaL, B.wx, B.wy,
+                              B.wz, p.x, p.y, p.z);
     else
         round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
                  B.invD32, p.x, p.y, p.z);
@@ -1322,6 +1324,7 @@ __global__ void k_bc_lift(int nx, int ny, int nz, int P, long long Q, double inv
     const long long ax = (long long)ny * nz, ay = (long long)nx * nz, az = (long long)nx * ny;
     const long long o[6] = {0, ax, 2 * ax, 2 * ax + ay, 2 * ax + 2 * ay, 2 * ax + 2 * ay + az};
     auto term = [&](int w, double wall_w, long long at) {
+        if ((bcm >> (6 + w / 2)) & 1) return;   // periodic axis: no wall
         const double g = vals[o[w] + at];
         v -= ((bcm >> w) & 1) ? g * inv_h : wall_w * g;
     };
@@ -1437,9 +1440,10 @@ __global__ void __launch_bounds__(kThreads) k_guard_fill(BoxSet<T> S, T v)
 
 // Dense inverse of the union of the boxes' coarsest levels (one CTA): each
 // box's block as for a single box, plus -w between a box's cell and the cell
-// of the neighbouring box across every interface face (from the coarsest
-// level's exchange records: guard cell of dst <-> cell of src), then
-// Gauss-Jordan.  S: the coarsest level of every box, in union order.
+// of the neighbouring box (or, on a periodic axis, of the box itself) across
+// every exchanged face (from the coarsest level's exchange records: guard
+// cell of dst <-> cell of src), then Gauss-Jordan (with the constant shift
+// when A is singular).  S: the coarsest level of every box, in union order.
 __global__ void __launch_bounds__(1024) k_union_inverse(SetupSet S, UnionBottom U, double *a,
                                                         double *inv64, float *inv32)
 {
@@ -1475,11 +1479,13 @@ __global__ void __launch_bounds__(1024) k_union_inverse(SetupSet S, UnionBottom 
             else w = D.wz[c + D.Q];
             const int row = U.off[R.dst] + (ck * D.ny + cj) * D.nx + ci;
             const int cl = U.off[R.src] + (sk * F.ny + sj) * F.nx + si;
-            a[(long long)row * n + cl] = -w;
+            // added, not set: across a periodic axis of 2 cells the same two
+            // cells are also neighbours through the inner face
+            a[(long long)row * n + cl] -= w;
         }
         __syncthreads();
     }
-    gauss_jordan_cta(a, n, false, inv64, inv32, col);
+    gauss_jordan_cta(a, n, U.singular != 0, inv64, inv32, col);
 }
 
 // Coarsest solve of a coupled level: phi = Ainv f over the union, rows in
@@ -1793,10 +1799,11 @@ cudaError_t launch_project_rhs(int nx, int ny, int nz, double h, const double *u
 
 cudaError_t launch_project_correct(int nx, int ny, int nz, double h, const double *wx,
                                    const double *wy, const double *wz, const double *phi,
-                                   double *u, double *v, double *w, cudaStream_t st)
+                                   double *u, double *v, double *w, cudaStream_t st, bool wide)
 {
     k_project_correct<<<grid3(nx + 1, ny + 1, nz + 1), block2d(), 0, st>>>(
-        nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny), h, wx, wy, wz, phi, u, v, w);
+        nx, ny, nz, (int)pitch_row(nx, wide), pitch_plane(nx, ny, wide), h, wx, wy, wz, phi, u,
+        v, w);
     return counted(cudaGetLastError());
 }
 
@@ -1810,11 +1817,11 @@ cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, int bcm, con
 
 cudaError_t launch_bc_lift(int nx, int ny, int nz, double inv_h, int bcm, const double *wx,
                            const double *wy, const double *wz, const double *vals,
-                           const double *f, double *fout, cudaStream_t st)
+                           const double *f, double *fout, cudaStream_t st, bool wide)
 {
-    k_bc_lift<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, (int)pitch_row(nx),
-                                                       pitch_plane(nx, ny), inv_h, bcm, wx, wy,
-                                                       wz, vals, f, fout);
+    k_bc_lift<<<grid3(nx, ny, nz), block2d(), 0, st>>>(nx, ny, nz, (int)pitch_row(nx, wide),
+                                                       pitch_plane(nx, ny, wide), inv_h, bcm, wx,
+                                                       wy, wz, vals, f, fout);
     return counted(cudaGetLastError());
 }
 

@@ -153,14 +153,16 @@ cudaError_t launch_project_rhs(int nx, int ny, int nz, double h, const double *u
                                const double *w, const double *S, double *f, cudaStream_t st);
 cudaError_t launch_project_correct(int nx, int ny, int nz, double h, const double *wx,
                                    const double *wy, const double *wz, const double *phi,
-                                   double *u, double *v, double *w, cudaStream_t st);
+                                   double *u, double *v, double *w, cudaStream_t st,
+                                   bool wide = false);
 
 cudaError_t launch_beta_grad(int nx, int ny, int nz, double inv_h2, int bcm, const double *beta,
                              const double *phi, const double *lam, double *dbeta, cudaStream_t st);
 // fout = f - lift of the packed wall values (level-0 FP64 weights, layout of mg.h).
 cudaError_t launch_bc_lift(int nx, int ny, int nz, double inv_h, int bcm, const double *wx,
                            const double *wy, const double *wz, const double *vals,
-                           const double *f, double *fout, cudaStream_t st);
+                           const double *f, double *fout, cudaStream_t st,
+                           bool wide = false);
 // Every box of S: field (0 = f, 1 = phi) -= its mean over the box's cells.
 // partials: TK_COLZ tiles of S; mean: one double per box (written).
 cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *partials, double *mean,

@@ -144,6 +144,25 @@ std::vector<ExchRec> level_exchange(const std::vector<Brick> &B, bool brute)
     return recs;
 }
 
+std::vector<ExchRec> periodic_exchange(const Brick &b, const int period[3])
+{
+    std::vector<ExchRec> recs;
+    for (int f = 0; f < 6; ++f) {
+        const int d = f / 2;
+        if (period[d] <= 0) continue;
+        Brick img = b;  // the box shifted by one period towards the face
+        img.lo[d] += (f & 1) ? period[d] : -period[d];
+        ExchRec r{};
+        if (intersect(b, f, img, r)) {
+            r.dst = 0;
+            r.src = 0;
+            // src coordinates are relative to the image: those are the box's own
+            recs.push_back(r);
+        }
+    }
+    return recs;
+}
+
 }  // namespace mg
 
 extern "C" int mg_level_intersections(int nbox, const int (*lo)[3], const int (*n)[3],

@@ -26,4 +26,9 @@ int level_check_disjoint(const std::vector<Brick> &B, int *a, int *b);
 // dst, face, src.  brute: test all pairs instead of the region bins.
 std::vector<ExchRec> level_exchange(const std::vector<Brick> &B, bool brute = false);
 
+// Patches of a single box whose axes d with period[d] > 0 are periodic with
+// that period: the guard layer of a periodic face is filled from the box's
+// own cells at the opposite face (src = dst = 0).
+std::vector<ExchRec> periodic_exchange(const Brick &b, const int period[3]);
+
 }  // namespace mg

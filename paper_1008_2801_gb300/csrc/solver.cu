@@ -140,9 +140,9 @@ static void carve(Solver *s, Hier<T> &H, Bump &bump, bool full)
         }
         const auto &db = s->dims[b][s->nlev[b] - 1];
         const size_t nb = (size_t)db[0] * db[1] * db[2];
-        if (!s->coupled) H.ainv[b] = (s->shared && b > 0) ? H.ainv[0] : bump.take<T>(nb * nb);
+        if (!s->xmode) H.ainv[b] = (s->shared && b > 0) ? H.ainv[0] : bump.take<T>(nb * nb);
     }
-    if (s->coupled) H.uinv = bump.take<T>((size_t)s->ub.n * s->ub.n);
+    if (s->xmode) H.uinv = bump.take<T>((size_t)s->ub.n * s->ub.n);
 }
 
 template <class T>
@@ -175,7 +175,7 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
     if (l == s->nlev[b] - 1) B.ainv = H.ainv[b];
     B.box = b;
     B.zc = kSweepZ;
-    if (s->coupled) {
+    if (s->xmode) {
         const auto &o = s->lo[b][l];
         B.par = (((o[0] + o[1] + o[2]) % 2) + 2) % 2;
     }
@@ -420,19 +420,26 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (!out) return set_error(MG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (nbox < 1 || !n || !dx) return set_error(MG_ERR_INVALID_ARG, "need nbox >= 1, n, dx");
-    if (bc < 0 || bc > MG_BC_NEUMANN_ALL)
-        return set_error(MG_ERR_INVALID_ARG, "bc must be a wall mask in 0..63");
+    if (bc < 0 || bc > 511)
+        return set_error(MG_ERR_INVALID_ARG, "bc must be a wall mask in 0..511");
+    for (int d = 0; d < 3; ++d)
+        if (((bc >> (6 + d)) & 1) && ((bc >> (2 * d)) & 3))
+            return set_error(MG_ERR_INVALID_ARG, "axis %d is periodic and has a Neumann wall", d);
     const bool coupled = lo != nullptr;
+    const bool periodic = (bc >> 6) != 0;
     if (coupled && bc != 0)
         return set_error(MG_ERR_INVALID_ARG, "a coupled level has Dirichlet walls (bc = 0)");
+    if (periodic && nbox != 1)
+        return set_error(MG_ERR_UNSUPPORTED,
+                         "periodic axes are implemented for one box per context (mg_create)");
     mg_opts o;
     mg_default_opts(&o);
     if (opts) o = *opts;
     CKS(validate_opts(&o));
-    if (coupled) {
-        // ghost exchanges between boxes before every stencil: single-colour
-        // passes, all-cell residuals, per-level launches down to the union's
-        // dense bottom solve
+    if (coupled || periodic) {
+        // ghost exchanges between boxes (or across periodic faces) before
+        // every stencil: single-colour passes, all-cell residuals, per-level
+        // launches down to the dense bottom solve
         o.smoother = 1;
         o.full_residual = 1;
         o.coarse_cells = -1;
@@ -480,9 +487,13 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->has32 = o.precision == MG_MIXED;
     s->tma = s->has32 && o.tma == 1;
     s->bc = bc;
-    s->singular = bc == MG_BC_NEUMANN_ALL;
+    // A singular (constants in the null space): no axis has a Dirichlet wall
+    s->singular = true;
+    for (int d = 0; d < 3; ++d)
+        if (!((bc >> (6 + d)) & 1) && ((bc >> (2 * d)) & 3) != 3) s->singular = false;
     s->coupled = coupled;
-    s->wide = coupled;
+    s->xmode = coupled || periodic;
+    s->wide = s->xmode;
     if (coupled) {
         s->lo = clos;
         s->ub.n = ucells;
@@ -517,6 +528,12 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         s->off[b + 1] = s->off[b] + (long long)nx * ny * nz;
     }
     s->total = s->off[nbox];
+    if (periodic) {  // one box: corners at 0, its coarsest level is the bottom
+        s->lo.assign(1, std::vector<std::array<int, 3>>(s->nlev[0], {0, 0, 0}));
+        const auto &db = s->dims[0].back();
+        s->ub.n = db[0] * db[1] * db[2];
+        s->ub.nbox = 1;
+    }
 
     // level arrays: dry run for the size, then carve the zero-filled arena
     Bump bump;
@@ -531,8 +548,8 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         work_elems += nb * nb;
         ntiles0 += (size_t)tiles_of(TK_CELL, s->n[b][0], s->n[b][1], s->n[b][2]);
     }
-    if (coupled) {  // one dense inverse for the union of the coarsest levels
-        work_elems = (size_t)ucells * ucells;
+    if (s->xmode) {  // one dense inverse for the union of the coarsest levels
+        work_elems = (size_t)s->ub.n * s->ub.n;
         std::fill(work_off.begin(), work_off.end(), 0);
     }
     bump.take<double>(s->total);      // beta copy
@@ -648,7 +665,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         B.Q = pitch_plane(d[0], d[1], s->wide);
         B.zc = kSweepZ;
         B.bc = s->bc;
-        if (s->coupled && l == 0) B.betaL = L.phi;  // beta is staged in phi during set-up
+        if (s->xmode && l == 0) B.betaL = L.phi;  // beta is staged in phi during set-up
         if (l == s->nlev[b] - 1) {
             B.work = s->work + work_off[b];
             B.inv64 = s->h64.ainv[b];
@@ -675,6 +692,23 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     // communication pattern) and the union numbering of the coarsest cells
     std::vector<size_t> xrec_at;
     size_t uoff_at = 0;
+    if (periodic) {
+        for (int l = 0; l < s->nlev[0]; ++l) {
+            const auto &d = s->dims[0][l];
+            Brick bl;
+            int period[3];
+            for (int q = 0; q < 3; ++q) {
+                bl.lo[q] = 0;
+                bl.n[q] = d[q];
+                period[q] = ((bc >> (6 + q)) & 1) ? d[q] : 0;
+            }
+            const std::vector<ExchRec> recs = periodic_exchange(bl, period);
+            s->nxrec.push_back((int)recs.size());
+            xrec_at.push_back(blob.put(recs.data(), recs.size() * sizeof(ExchRec)));
+        }
+        std::vector<int> uo = {0, s->ub.n};
+        uoff_at = blob.put(uo.data(), uo.size() * sizeof(int));
+    }
     if (coupled) {
         for (int l = 0; l < clev; ++l) {
             std::vector<Brick> bl(nbox);
@@ -717,12 +751,13 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (s->has32) s->h32.jobs = reinterpret_cast<const CoarseJob<float> *>(s->desc + jobs32);
     s->doff = reinterpret_cast<const long long *>(s->desc + off_at);
     s->dside = reinterpret_cast<int *>(s->desc + side_at);
-    if (coupled) {
+    if (s->xmode) {
         for (size_t l = 0; l < xrec_at.size(); ++l)
             s->xrec.push_back(reinterpret_cast<const ExchRec *>(s->desc + xrec_at[l]));
         s->ub.off = reinterpret_cast<const int *>(s->desc + uoff_at);
-        s->ub.rec = s->xrec[clev - 1];
-        s->ub.nrec = s->nxrec[clev - 1];
+        s->ub.rec = s->xrec.back();
+        s->ub.nrec = s->nxrec.back();
+        s->ub.singular = s->singular ? 1 : 0;
     }
 
     if (cudaMallocHost(&s->hjblock, s->jbytes) != cudaSuccess ||
@@ -832,7 +867,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     const long long k0 = launch_counter();
     const long long nbeta = s->shared ? s->off[1] : s->total;
     CK(cudaMemcpyAsync(s->beta, beta, sizeof(double) * nbeta, cudaMemcpyDefault, st));
-    if (s->coupled) {
+    if (s->xmode) {
         // beta into the level layout of level 0 (staged in phi), guard cells
         // -1 (the union's boundary) except where the exchange brings the
         // neighbouring box's beta; faces from there
@@ -849,7 +884,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         CK(launch_setup(s->setup_lv[l], 2, st));
         if (s->has32) CK(launch_setup(s->setup_lv[l], 3, st));
     }
-    if (s->coupled) {
+    if (s->xmode) {
         CK(launch_union_inverse(s->setup_bottom, s->ub, s->work, s->h64.uinv,
                                 s->has32 ? s->h32.uinv : nullptr, st));
         CK(launch_guard_fill(s->h64.fine, 0.0, st));  // Dirichlet zeros again
@@ -942,7 +977,7 @@ static cudaError_t sweep_launch(Solver *s, const BoxSet<float> &S, const SweepMa
 template <class T>
 static cudaError_t exch(Solver *s, const BoxSet<T> &S, int lvl, cudaStream_t st)
 {
-    if (!s->coupled) return cudaSuccess;
+    if (!s->xmode) return cudaSuccess;
     return launch_exchange(S, s->active, s->xrec[lvl], s->nxrec[lvl], st);
 }
 
@@ -1011,7 +1046,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     }
     if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
-    if (s->coupled)
+    if (s->xmode)
         e = launch_union_bottom(H.bottom, s->ub, H.uinv, s->active, st);
     else
         e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st);
@@ -1561,7 +1596,9 @@ int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, doub
         return set_error(MG_ERR_INVALID_ARG, "NULL argument or nrhs < 1");
     if (s->singular)
         return set_error(MG_ERR_UNSUPPORTED,
-                         "no adjoint when every wall is Neumann (A is singular)");
+                         "no adjoint when A is singular (no Dirichlet wall)");
+    if (s->bc >> 6)
+        return set_error(MG_ERR_UNSUPPORTED, "no adjoint with periodic axes");
     DeviceGuard gd(s->dev);
     cudaGetLastError();  // drop a stale non-sticky error of an earlier call
     int worst = MG_OK;
@@ -1737,8 +1774,10 @@ int mg_project_correct(mg_ctx *ctx, const double *phi, double *u, double *v, dou
     cudaGetLastError();
     const auto &n = s->n[0];
     const LevelBufs<double> &L = s->h64.lv[0][0];
+    if (s->bc >> 6)
+        return set_error(MG_ERR_UNSUPPORTED, "projection with periodic axes is not implemented");
     CK(launch_project_correct(n[0], n[1], n[2], s->dx[0], L.wx, L.wy, L.wz, phi, u, v, w,
-                              (cudaStream_t)stream));
+                              (cudaStream_t)stream, s->wide));
     s->kernels += 1;
     return MG_OK;
 }
@@ -1753,7 +1792,7 @@ int mg_bc_lift(mg_ctx *ctx, const double *vals, const double *f, double *f_out, 
     const auto &n = s->n[0];
     const LevelBufs<double> &L = s->h64.lv[0][0];
     CK(launch_bc_lift(n[0], n[1], n[2], 1.0 / s->dx[0], s->bc, L.wx, L.wy, L.wz, vals, f, f_out,
-                      (cudaStream_t)stream));
+                      (cudaStream_t)stream, s->wide));
     s->kernels += 1;
     return MG_OK;
 }

@@ -107,8 +107,9 @@ struct Solver {
     // rest of the cycle (no separate norm pass)
     bool lookahead = false;
     // coupled level (the boxes solved as one domain; mg_level)
-    bool coupled = false;
-    bool wide = false;                               // wide-guard layout (coupled)
+    bool coupled = false;                            // one norm for all boxes (mg_level)
+    bool xmode = false;                              // ghost exchanges: coupled level or periodic axes
+    bool wide = false;                               // wide-guard layout (xmode)
     std::vector<std::vector<std::array<int, 3>>> lo;  // [box][level] lower corners (coupled)
     std::vector<const ExchRec *> xrec;               // [level] device exchange records
     std::vector<int> nxrec;                          // [level]

@@ -8,8 +8,9 @@ current CUDA stream.
 The equation is the variable-coefficient Poisson equation of the paper's
 Sec. 1, div(beta grad phi) = f.  Each wall is Dirichlet or Neumann, chosen by
 ``bc``: a mask with bit w set when wall w (x-, x+, y-, y+, z-, z+) is Neumann,
-or a string of six letters "D"/"N" in that order (0 or "DDDDDD": phi = 0 on
-every wall).  Non-zero wall values enter through ``bc_lift``.
+bits 6-8 for periodic x, y, z axes, or a string of six letters "D"/"N"/"P" in
+that order (0 or "DDDDDD": phi = 0 on every wall; "PPDDDD": periodic in x).
+Non-zero wall values enter through ``bc_lift``.
 """
 from __future__ import annotations
 
@@ -63,14 +64,28 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
 
 
 def bc_mask(bc) -> int:
-    """Wall mask from an int (0..63) or six letters D/N for x-, x+, y-, y+, z-, z+."""
+    """Wall mask from an int (0..511) or six letters for x-, x+, y-, y+, z-, z+:
+    D (Dirichlet), N (Neumann) or P (periodic; both walls of the axis)."""
     if isinstance(bc, str):
-        if len(bc) != 6 or set(bc.upper()) - {"D", "N"}:
-            raise ValueError("bc string needs six letters D or N (x-, x+, y-, y+, z-, z+)")
-        return sum(1 << w for w, c in enumerate(bc.upper()) if c == "N")
+        s = bc.upper()
+        if len(s) != 6 or set(s) - {"D", "N", "P"}:
+            raise ValueError("bc string needs six letters D, N or P (x-, x+, y-, y+, z-, z+)")
+        m = 0
+        for d in range(3):
+            a, b = s[2 * d], s[2 * d + 1]
+            if (a == "P") != (b == "P"):
+                raise ValueError("a periodic axis has P on both walls")
+            if a == "P":
+                m |= 1 << (6 + d)
+            else:
+                m |= (a == "N") << (2 * d) | (b == "N") << (2 * d + 1)
+        return m
     bc = int(bc)
-    if not 0 <= bc <= 63:
-        raise ValueError("bc mask must be in 0..63")
+    if not 0 <= bc <= 511:
+        raise ValueError("bc mask must be in 0..511")
+    for d in range(3):
+        if (bc >> (6 + d)) & 1 and (bc >> (2 * d)) & 3:
+            raise ValueError("a periodic axis cannot have a Neumann wall")
     return bc
 
 

@@ -49,11 +49,11 @@ def test_host_side_argument_checks():
     assert L.mg_op_rbgs_pass(5, n, *([ctypes.c_void_p(16)] * 6), 0, None) == \
         _lib.MG_ERR_INVALID_ARG
     assert L.mg_last_error()
-    # wall masks outside 0..63 are rejected before any device work
+    # wall masks outside 0..511, or periodic axes with a Neumann bit, are
+    # rejected before any device work
     h = ctypes.c_void_p()
-    for bc in (-1, 64, 1000):
+    for bc in (-1, 512, 1000, 64 | 1, 128 | 8, 256 | 48):
         assert L.mg_create(ctypes.byref(h), n, 0.1, bc, None) == _lib.MG_ERR_INVALID_ARG
-        assert b"wall mask" in L.mg_last_error()
     assert L.mg_bc_lift(None, None, None, None, None) == _lib.MG_ERR_INVALID_ARG
     assert L.mg_op_face_weights(n, 0.1, 64, *([ctypes.c_void_p(16)] * 4), None) == \
         _lib.MG_ERR_INVALID_ARG
@@ -65,7 +65,8 @@ def test_wall_mask_parsing():
     assert bc_mask("NNNNNN") == 63
     assert bc_mask("NDDDDN") == 1 | 32
     assert bc_mask("dndndn") == 2 | 8 | 32
-    for bad in ("DDDDD", "DDDDDX", 64, -1):
+    assert bc_mask("PPDNPP") == 64 | 8 | 256
+    for bad in ("DDDDD", "DDDDDX", "PDDDDD", 512, -1, 64 | 2):
         with pytest.raises(ValueError):
             bc_mask(bad)
     assert wall_shapes((4, 5, 6)) == [(4, 5), (4, 5), (4, 6), (4, 6), (5, 6), (5, 6)]
