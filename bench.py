@@ -376,8 +376,10 @@ def run_gpu(args):
 
 def run_extra(dev, args):
     """512^3 FP64 vs mixed, 64 uneven boxes (batched vs sequential), the
-    projection steps, the 256^3 workload as a coupled level of 64 boxes and
-    the 8-RHS adjoint; each timed once after one warm-up (not part of value)."""
+    projection steps, the 256^3 workload as a coupled level of 64 boxes,
+    Neumann and periodic walls, CG with the V-cycle preconditioner (stellar
+    and high-contrast beta) and the 8-RHS adjoint; each timed once after one
+    warm-up (not part of value)."""
     import numpy as np
     import torch
 
@@ -543,7 +545,31 @@ def run_extra(dev, args):
                                "cycles": st["cycles"], "status": st["status"]}
             s.close()
     ex["walls_256^3"] = res
-    del beta, f
+
+    # CG preconditioned by the symmetric V-cycle (krylov): the stellar 256^3
+    # workload, and high-contrast balls (beta jumps by 1e4, not aligned with
+    # coarse cells) where the plain V-cycle iteration stalls
+    res = {}
+    hc = inputs.inclusions(n, 9, contrast=1e4)
+    cases = (("stellar", beta, f, d["dx"]),
+             ("inclusions_1e4", torch.from_numpy(hc["beta"]).to(dev),
+              torch.from_numpy(hc["f"]).to(dev), hc["dx"]))
+    del hc
+    for name, cb, cf, cdx in cases:
+        res[name] = {}
+        for method, kw in (("vcycles", {}), ("pcg", {"krylov": True})):
+            s = Solver(tuple(cf.shape), cdx, device=dev, max_cycles=200, **kw)
+
+            def kry_step():
+                s.set_beta(cb)
+                return s.solve(cf, tol=TOL)
+            ms, (_, st) = time_once(kry_step)
+            res[name][method] = {"cells_per_s": cf.numel() / (ms / 1e3), "ms": ms,
+                                 "cycles": st["cycles"], "status": st["status"],
+                                 "rel_resid": st["rel_resid"]}
+            s.close()
+    ex["krylov_256^3"] = res
+    del beta, f, cases
 
     # adjoint, 128^3 x 8 right-hand sides
     d = inputs.config(5)

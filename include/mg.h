@@ -121,7 +121,20 @@ typedef struct {
                          1: they stage their tiles in a shared-memory ring
                          filled by the Tensor Memory Accelerator (when the
                          driver can encode tensor maps) */
-    int reserved[6];
+    int krylov;       /* 0 (default): the iteration is V-cycles (FP64) or
+                         iterative refinement (mixed); 1: conjugate gradients
+                         preconditioned by one symmetric V-cycle per iteration
+                         (zero start, nu1 red-then-black sweeps going down,
+                         nu2 = nu1 black-then-red sweeps coming up), for
+                         high-contrast beta.  FP64 only, independent boxes
+                         with Dirichlet or Neumann walls (not every wall
+                         Neumann), no periodic axis, not on a coupled level;
+                         otherwise mg_create returns UNSUPPORTED.  cycles in
+                         mg_stats counts CG iterations; the solve ends at
+                         tol, divergence or max_cycles (the rule that stops
+                         V-cycles after 5 cycles without a 10% gain does
+                         not apply: a CG residual is not monotone). */
+    int reserved[5];
 } mg_opts;
 
 typedef struct {
@@ -290,6 +303,7 @@ enum {
     MG_PROF_NORM = 4,      /* finest level: residual norm */
     MG_PROF_COARSE = 5,    /* every coarser level and the coarsest solve */
     MG_PROF_REFINE = 6,    /* mixed precision: FP64 refinement step */
+    MG_PROF_KRYLOV = 7,    /* krylov = 1: the CG vector updates and dot products */
     MG_PROF_NKIND = 16
 };
 typedef struct {

@@ -105,6 +105,11 @@ def lib():
             L.oracle_periodic_solve.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D, _F, _I,
                                                 ctypes.POINTER(_I)]
             L.oracle_periodic_solve.restype = _I
+            L.oracle_vcycle_apply.argtypes = [_I, _I, _I, _F, _D, _I, _I, _I, _D, _D]
+            L.oracle_vcycle_apply.restype = _I
+            L.oracle_pcg_solve.argtypes = [_I, _I, _I, _F, _D, _I, _D, _D, _F, _I, _I, _D,
+                                           ctypes.POINTER(_I)]
+            L.oracle_pcg_solve.restype = _I
             _lib = L
     return _lib
 
@@ -245,6 +250,33 @@ def solve(beta, f, h, tol=1e-13, max_cycles=200, phi0=None, nu1=2, nu2=2, bc=0):
     s = lib().oracle_solve_bc(nx, ny, nz, float(h), beta, int(bc), f, phi, float(tol),
                               int(max_cycles), int(nu1), int(nu2), hist, ctypes.byref(cyc))
     return phi, {"status": STATUS[s], "cycles": cyc.value, "hist": hist[:cyc.value + 1].copy()}
+
+
+def vcycle_apply(beta, h, r, nu=2, sym=True, bc=0):
+    """z = V r: one V(nu, nu) cycle from a zero start on the right-hand side
+    r; sym selects black-then-red post-smoothing (the symmetric cycle)."""
+    beta, r = _c(beta), _c(r)
+    nx, ny, nz = _dims(r)
+    z = np.zeros_like(r)
+    s = lib().oracle_vcycle_apply(nx, ny, nz, float(h), beta, int(bc), int(nu), int(bool(sym)),
+                                  r, z)
+    if s != 0:
+        raise ValueError(f"oracle_vcycle_apply: status {STATUS[s]}")
+    return z
+
+
+def pcg_solve(beta, f, h, tol=1e-13, maxit=200, phi0=None, nu=2, bc=0):
+    """Conjugate gradients on -A phi = -f preconditioned by -V (the
+    symmetric V(nu, nu) cycle); returns (phi, info dict with status,
+    iterations and the relative residual history)."""
+    beta, f = _c(beta), _c(f)
+    nx, ny, nz = _dims(f)
+    phi = np.zeros_like(f) if phi0 is None else _c(phi0).copy()
+    hist = np.zeros(maxit + 1)
+    it = _I(0)
+    s = lib().oracle_pcg_solve(nx, ny, nz, float(h), beta, int(bc), f, phi, float(tol),
+                               int(maxit), int(nu), hist, ctypes.byref(it))
+    return phi, {"status": STATUS[s], "cycles": it.value, "hist": hist[:it.value + 1].copy()}
 
 
 def beta_grad(beta, h, phi, lam, bc=0):

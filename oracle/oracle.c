@@ -57,6 +57,13 @@
  *                with Neumann walls on both ends, A is singular and the
  *                solve is the zero-mean one, as above.  The oracle solves
  *                periodic boxes by conjugate gradients on the operator;
+ *   krylov       (a variant the paper does not describe) conjugate gradients
+ *                on the symmetric positive definite -A, preconditioned by
+ *                one V-cycle from a zero start whose post-smoothing sweeps
+ *                run black then red (the adjoint of the red-then-black
+ *                pre-smoother) with nu1 = nu2: then the cycle is a symmetric
+ *                linear map of its right-hand side, and -V approximates
+ *                (-A)^{-1};
  *   level        a level of several boxes (paper Sec. 2: the union of
  *                disjoint rectangular grids of a MultiFAB) is one domain:
  *                the same operator on the union, faces between cells of two
@@ -374,6 +381,7 @@ typedef struct {
 
 typedef struct {
     int nlev, nu1, nu2;
+    int post_first;          /* colour of each post-smoothing sweep's first pass (0 red) */
     int singular;            /* every wall Neumann: A has the constants as null space */
     level_t L[MAXLEV];
     /* coarsest level: dense Cholesky factor of M = -h^2 A (SPD), plus
@@ -563,8 +571,10 @@ static void vcycle(hier_t *H, int l)
     vcycle(H, l + 1);
     oracle_prolong_add(L->nx, L->ny, L->nz, C->phi, L->phi);
     for (int s = 0; s < H->nu2; ++s) {
-        oracle_rbgs_pass(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, L->f, L->phi, 0);
-        oracle_rbgs_pass(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, L->f, L->phi, 1);
+        oracle_rbgs_pass(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, L->f, L->phi,
+                         H->post_first);
+        oracle_rbgs_pass(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, L->f, L->phi,
+                         1 - H->post_first);
     }
 }
 
@@ -986,5 +996,113 @@ int oracle_periodic_solve(int nx, int ny, int nz, double h, const double *beta, 
     if (singular) remove_mean(n, phi);
     if (iters) *iters = it;
     free(bx); free(by); free(bz); free(r); free(p); free(q);
+    return status;
+}
+
+/* ----------------------------------------------- V-cycle-preconditioned CG */
+
+/* One V(nu, nu) cycle from phi = 0 on the right-hand side r: z = V r.
+ * sym = 1: post-smoothing sweeps black then red (the symmetric cycle);
+ * sym = 0: red then black (the cycle of oracle_solve).  Returns 0, or 3 for
+ * a bad hierarchy. */
+int oracle_vcycle_apply(int nx, int ny, int nz, double h, const double *beta, int bc, int nu,
+                        int sym, const double *r, double *z)
+{
+    hier_t H;
+    if (build_hier(&H, nx, ny, nz, h, beta, bc, nu, nu) != 0) {
+        free_hier(&H);
+        return OR_BAD;
+    }
+    H.post_first = sym ? 1 : 0;
+    level_t *L = &H.L[0];
+    size_t n = ncell(L);
+    memcpy(L->f, r, sizeof(double) * n);
+    memset(L->phi, 0, sizeof(double) * n);
+    vcycle(&H, 0);
+    memcpy(z, L->phi, sizeof(double) * n);
+    free_hier(&H);
+    return OR_OK;
+}
+
+/* Solve A phi = f (homogeneous walls of the mask bc, not every wall Neumann)
+ * by preconditioned conjugate gradients, in the textbook form for the
+ * symmetric positive definite system B x = b with B = -A, b = -f and the
+ * preconditioner C = -V (V the symmetric V(nu, nu) cycle from a zero start):
+ *   r = b - B x, z = C r, p = z;  repeat: q = B p, alpha = <r, z> / <p, q>,
+ *   x += alpha p, r -= alpha q, z = C r, beta = <r, z>_new / <r, z>_old,
+ *   p = z + beta p;
+ * from the initial guess in phi until ||r|| <= tol ||f|| (||r|| is the
+ * recursively updated residual, which equals ||f - A phi|| in exact
+ * arithmetic) or maxit iterations.  hist (nullable, maxit + 1) gets ||r|| /
+ * ||f|| before the first iteration and after each.  Returns 0 converged,
+ * 1 not converged, 2 non-finite, 3 bad hierarchy or every wall Neumann. */
+int oracle_pcg_solve(int nx, int ny, int nz, double h, const double *beta, int bc,
+                     const double *f, double *phi, double tol, int maxit, int nu,
+                     double *hist, int *iters)
+{
+    if (iters) *iters = 0;
+    if ((bc & 63) == 63) return OR_BAD;
+    hier_t H;
+    if (build_hier(&H, nx, ny, nz, h, beta, bc, nu, nu) != 0) {
+        free_hier(&H);
+        return OR_BAD;
+    }
+    H.post_first = 1;
+    level_t *L = &H.L[0];
+    size_t n = ncell(L);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *z = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    double nf = norm2(n, f);
+    int status = OR_NOT_CONVERGED, it = 0;
+    /* r = b - B x = -f + A x */
+    oracle_apply(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, phi, q);
+    for (size_t c = 0; c < n; ++c) r[c] = -f[c] + q[c];
+    double rn = norm2(n, r);
+    if (hist) hist[0] = nf > 0.0 ? rn / nf : 0.0;
+    if (!isfinite(nf) || !isfinite(rn)) status = OR_NONFINITE;
+    else if (nf == 0.0) {
+        memset(phi, 0, sizeof(double) * n);
+        status = OR_OK;
+    } else if (rn <= tol * nf) status = OR_OK;
+    double rz = 0.0;
+    while (status == OR_NOT_CONVERGED && it < maxit) {
+        /* z = C r = -V r */
+        memcpy(L->f, r, sizeof(double) * n);
+        memset(L->phi, 0, sizeof(double) * n);
+        vcycle(&H, 0);
+        double rz1 = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            z[c] = -L->phi[c];
+            rz1 += r[c] * z[c];
+        }
+        if (it == 0) memcpy(p, z, sizeof(double) * n);
+        else {
+            double b = rz1 / rz;
+            for (size_t c = 0; c < n; ++c) p[c] = z[c] + b * p[c];
+        }
+        rz = rz1;
+        /* q = B p = -A p */
+        oracle_apply(L->nx, L->ny, L->nz, L->h, L->bx, L->by, L->bz, p, q);
+        double pq = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            q[c] = -q[c];
+            pq += p[c] * q[c];
+        }
+        double alpha = rz / pq;
+        for (size_t c = 0; c < n; ++c) {
+            phi[c] += alpha * p[c];
+            r[c] -= alpha * q[c];
+        }
+        ++it;
+        rn = norm2(n, r);
+        if (hist) hist[it] = rn / nf;
+        if (!isfinite(rn)) status = OR_NONFINITE;
+        else if (rn <= tol * nf) status = OR_OK;
+    }
+    if (iters) *iters = it;
+    free(r); free(z); free(p); free(q);
+    free_hier(&H);
     return status;
 }

@@ -40,7 +40,7 @@ class mg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("max_cycles", c_int),
                 ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
                 ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
-                ("reserved", c_int * 6)]
+                ("krylov", c_int), ("reserved", c_int * 5)]
 
 
 class mg_stats(ctypes.Structure):
@@ -51,7 +51,7 @@ class mg_stats(ctypes.Structure):
 
 
 MG_PROF_NKIND = 16
-PROF_NAMES = ["sweep", "pass", "restrict", "prolong", "norm", "coarse", "refine"]
+PROF_NAMES = ["sweep", "pass", "restrict", "prolong", "norm", "coarse", "refine", "krylov"]
 
 
 class mg_profile(ctypes.Structure):

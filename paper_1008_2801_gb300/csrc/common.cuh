@@ -195,6 +195,7 @@ struct JudgeState {
     int *step;        // [1] cycles run by the loop
     double *tol;      // [1] relative residual target
     int max_cycles;
+    int stall_limit;  // cycles without a 10% gain that end the solve (0: no such rule)
 };
 
 // Last box b with tstart[b] <= t (tstart ascending, tstart[0] = 0).

@@ -687,7 +687,7 @@ __device__ __forceinline__ void cta_bottom(const Box<T> &B, T *fs)
 template <class T>
 __global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const CoarseJob<T> *__restrict__ jobs,
                                                                   const int *__restrict__ active,
-                                                                  int nu1, int nu2)
+                                                                  int nu1, int nu2, int post_first)
 {
     __shared__ CoarseJob<T> J;
     __shared__ T fs[MG_BOTTOM_CELLS];
@@ -716,9 +716,9 @@ __global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const
         cta_prolong<T>(J.lv[l]);
         __syncthreads();
         for (int s = 0; s < nu2; ++s) {
-            cta_pass<T>(J.lv[l], 0);
+            cta_pass<T>(J.lv[l], post_first);
             __syncthreads();
-            cta_pass<T>(J.lv[l], 1);
+            cta_pass<T>(J.lv[l], 1 - post_first);
             __syncthreads();
         }
     }
@@ -788,8 +788,9 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
 //
 // The same decision as the host loop, per active box, after each cycle:
 // non-finite -> MG_ERR_NONFINITE; rel <= tol -> MG_OK; rel > 1e3 max(rel0,
-// tol) -> MG_ERR_DIVERGED; five cycles in a row without a 10% gain over the
-// best, or max_cycles reached -> MG_ERR_NOT_CONVERGED.  A decided box is made
+// tol) -> MG_ERR_DIVERGED; stall_limit cycles in a row without a 10% gain
+// over the best (V-cycles: 5; CG, whose residual is not monotone: no such
+// rule), or max_cycles reached -> MG_ERR_NOT_CONVERGED.  A decided box is made
 // inactive; the loop continues (graph condition 1) while any box is active.
 // When the norm is taken at the start of the next cycle (look-ahead), the
 // loop starts at step -1: the first call judges nothing (no cycle has run).
@@ -820,7 +821,7 @@ __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restri
             int stall = rel > 0.9 * J.best[b] ? J.stall[b] + 1 : 0;
             J.stall[b] = stall;
             J.best[b] = fmin(J.best[b], rel);
-            done = stall >= 5 || c >= J.max_cycles;
+            done = (J.stall_limit > 0 && stall >= J.stall_limit) || c >= J.max_cycles;
         }
         J.status[b] = st;
         if (done) active[b] = 0;
@@ -1394,6 +1395,127 @@ __global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int fie
     x[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] -= mean[B.box];
 }
 
+// ------------------------------------------------- preconditioned CG ----
+//
+// Conjugate gradients on A x = f (A negative definite: the signs cancel in
+// alpha and beta), preconditioned by one symmetric V-cycle z = V r.  Level-0
+// FP64 arrays of every box: x in phi2, r in f, z in phi (the V-cycle's own
+// solution), p and q in two extra arrays.  Per-box scalars in PcgScalars.
+
+// PcgScalars (kernels.h): rz = <r, z> of the previous iteration (0 before the
+// first), rzn = <r, z> of this one, pq = <p, A p>, beta, alpha; [nbox] each.
+
+// A p at cell c (the operator; D stored on FP64 levels)
+__device__ __forceinline__ double apply_at(const double *__restrict__ p,
+                                           const Box<double> &B, long long c)
+{
+    double s = fma(B.wx[c], p[c - 1], -B.D[c] * p[c]);
+    s = fma(B.wx[c + 1], p[c + 1], s);
+    s = fma(B.wy[c], p[c - B.P], s);
+    s = fma(B.wy[c + B.P], p[c + B.P], s);
+    s = fma(B.wz[c], p[c - B.Q], s);
+    return fma(B.wz[c + B.Q], p[c + B.Q], s);
+}
+
+// op 0: partials of <f, phi> (= <r, z>);
+// op 1: p = z + beta p;
+// op 2: q = A p, partials of <p, q> (a launch of its own: A p reads the
+//       neighbours' p of op 1);
+// op 3: x += alpha p, r -= alpha q, partials of <r, r>, phi = 0 (the next
+//       V-cycle's zero start; z is dead once op 1 has used it);
+// op 4 (start): x = phi (the initial guess), r = f - A x, p = 0, partials
+//       of <r, r>;
+// op 5: phi = x (before a restart from the true residual).
+// Partials per TK_COLZ tile (a thread per column of kColZ planes).
+__global__ void __launch_bounds__(kThreads) k_pcg(BoxSet<double> S, const int *__restrict__ active,
+                                                  int op, double *const *__restrict__ pv,
+                                                  double *const *__restrict__ qv, PcgScalars sc,
+                                                  double *__restrict__ partials)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_COLZ];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<double> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
+    double *P = pv[B.box], *Qa = qv[B.box];
+    double v = 0.0;
+    if (p.x < B.nx && p.y < B.ny) {
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+        const double be = op == 1 ? sc.beta[B.box] : 0.0, al = op == 3 ? sc.alpha[B.box] : 0.0;
+        for (int k = z0; k < z1; ++k) {
+            const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
+            if (op == 0) {
+                v = fma(B.f[c], B.phi[c], v);
+            } else if (op == 1) {
+                P[c] = fma(be, P[c], B.phi[c]);
+            } else if (op == 2) {
+                const double q = apply_at(P, B, c);
+                Qa[c] = q;
+                v = fma(P[c], q, v);
+            } else if (op == 3) {
+                B.phi2[c] = fma(al, P[c], B.phi2[c]);
+                const double r = fma(-al, Qa[c], B.f[c]);
+                B.f[c] = r;
+                B.phi[c] = 0.0;
+                v = fma(r, r, v);
+            } else if (op == 4) {
+                B.phi2[c] = B.phi[c];
+                const double r = residual_at<double, true>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c,
+                                                           B.P, B.Q);
+                B.f[c] = r;
+                P[c] = 0.0;
+                v = fma(r, r, v);
+            } else {
+                B.phi[c] = B.phi2[c];
+            }
+        }
+    }
+    if (op != 1 && op != 5) {
+        const double sum = block_sum(v);
+        if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = sum;
+    }
+}
+
+// Per-box scalars from finished sums.  step 0: rzn done -> beta = rzn / rz
+// (0 on the first iteration), rz = rzn;  step 1: pq done -> alpha = rz / pq.
+__global__ void k_pcg_scalars(int nbox, const int *__restrict__ active, int step, PcgScalars sc)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox || (active && !active[b])) return;
+    if (step == 0) {
+        const double rz = sc.rz[b], rzn = sc.rzn[b];
+        sc.beta[b] = rz != 0.0 ? rzn / rz : 0.0;
+        sc.rz[b] = rzn;
+    } else {
+        const double pq = sc.pq[b];
+        sc.alpha[b] = pq != 0.0 ? sc.rz[b] / pq : 0.0;
+    }
+}
+
+// One CTA per box: out[box] = sum of the box's partials (fixed order), or
+// its square root.
+__global__ void __launch_bounds__(1024) k_sum_finish(BoxSet<double> S, const int *__restrict__ active,
+                                                     const double *__restrict__ partials,
+                                                     double *__restrict__ out, int root)
+{
+    __shared__ double wsum[32];
+    const int b = blockIdx.x;
+    const Box<double> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    const int *ts = S.tstart[TK_COLZ];
+    double s = 0.0;
+    for (int q = ts[b] + (int)threadIdx.x; q < ts[b + 1]; q += 1024) s += partials[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 32; ++w) tot += wsum[w];
+        out[B.box] = root ? sqrt(tot) : tot;
+    }
+}
+
 // ---------------------------------------------------- coupled levels ----
 //
 // The boxes of a coupled level (one MultiFAB level, paper Sec. 2, solved as
@@ -1659,10 +1781,11 @@ cudaError_t launch_bottom(const BoxSet<T> &S, const int *active, int max_cells, 
 
 template <class T>
 cudaError_t launch_coarse_vcycle(const CoarseJob<T> *jobs, int njobs, const int *active, int nu1,
-                                 int nu2, cudaStream_t st)
+                                 int nu2, cudaStream_t st, int post_first)
 {
     if (njobs == 0) return cudaSuccess;
-    k_coarse_vcycle<T><<<njobs, CoarseThreads<T>::value, 0, st>>>(jobs, active, nu1, nu2);
+    k_coarse_vcycle<T><<<njobs, CoarseThreads<T>::value, 0, st>>>(jobs, active, nu1, nu2,
+                                                                  post_first);
     return counted(cudaGetLastError());
 }
 
@@ -1877,6 +2000,25 @@ cudaError_t launch_norm_combine(int nbox, double *norm, cudaStream_t st)
     return counted(cudaGetLastError());
 }
 
+cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, double *const *pv,
+                       double *const *qv, const PcgScalars &sc, double *partials,
+                       double *sum_out, cudaStream_t st)
+{
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    k_pcg<<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, active, op, pv, qv, sc, partials);
+    cudaError_t e = counted(cudaGetLastError());
+    if (e != cudaSuccess || op == 1 || op == 5 || !sum_out) return e;
+    k_sum_finish<<<S.nbox, 1024, 0, st>>>(S, active, partials, sum_out, op >= 3);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgScalars &sc,
+                               cudaStream_t st)
+{
+    k_pcg_scalars<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, active, step, sc);
+    return counted(cudaGetLastError());
+}
+
 #define MG_INSTANTIATE(T)                                                                        \
     template cudaError_t launch_rbgs_pass<T>(const BoxSet<T> &, const int *, int, cudaStream_t);  \
     template cudaError_t launch_rbgs_pass_oop<T>(const BoxSet<T> &, const int *, int, int, double *, \
@@ -1895,7 +2037,7 @@ cudaError_t launch_norm_combine(int nbox, double *norm, cudaStream_t st)
     template cudaError_t launch_bottom<T>(const BoxSet<T> &, const int *, int, cudaStream_t);   \
     template cudaError_t launch_zero<T>(const BoxSet<T> &, const int *, cudaStream_t);          \
     template cudaError_t launch_coarse_vcycle<T>(const CoarseJob<T> *, int, const int *, int, int, \
-                                                 cudaStream_t);                                     \
+                                                 cudaStream_t, int);                                \
     template cudaError_t launch_exchange<T>(const BoxSet<T> &, const int *, const ExchRec *, int,  \
                                             cudaStream_t);                                         \
     template cudaError_t launch_guard_fill<T>(const BoxSet<T> &, T, cudaStream_t);                 \

@@ -87,9 +87,11 @@ template <class T>
 cudaError_t launch_bottom(const BoxSet<T> &S, const int *active, int max_cells, cudaStream_t st);
 
 // The coarse end of the V-cycle of each job's box in one CTA per job.
+// post_first: colour of the first pass of each post-smoothing sweep (0 red,
+// the default; 1 black: the post-smoother is the pre-smoother's adjoint).
 template <class T>
 cudaError_t launch_coarse_vcycle(const CoarseJob<T> *jobs, int njobs, const int *active, int nu1,
-                                 int nu2, cudaStream_t st);
+                                 int nu2, cudaStream_t st, int post_first = 0);
 
 // Mixed-precision refinement on the finest level of every box (FP64 phi = x,
 // f, weights, D in S64; FP32 phi = e, f = r32 in S32):
@@ -185,5 +187,19 @@ cudaError_t launch_union_bottom(const BoxSet<T> &S, const UnionBottom &U, const 
                                 const int *active, cudaStream_t st);
 // norm[b] <- sqrt(sum over b of norm[b]^2), for every b.
 cudaError_t launch_norm_combine(int nbox, double *norm, cudaStream_t st);
+
+// ---- preconditioned CG (level-0 FP64 arrays; see kernels.cu) -------------
+struct PcgScalars {
+    double *rz, *rzn, *pq, *beta, *alpha;  // [nbox] each
+};
+// op 0: <r, z> -> sum_out; 1: p = z + beta p; 2: q = A p and <p, q> -> sum_out;
+// 3: x += alpha p, r -= alpha q, phi = 0 and ||r|| -> sum_out;
+// 4: x = phi, r = f - A x, p = 0 and ||r|| -> sum_out (nullable); 5: phi = x.
+cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, double *const *pv,
+                       double *const *qv, const PcgScalars &sc, double *partials,
+                       double *sum_out, cudaStream_t st);
+// step 0: beta = rzn / rz (0 first), rz = rzn; step 1: alpha = rz / pq.
+cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgScalars &sc,
+                               cudaStream_t st);
 
 }  // namespace mg

@@ -376,6 +376,7 @@ static int validate_opts(const mg_opts *o)
         return set_error(MG_ERR_INVALID_ARG, "smoother must be 0, 1 or 2");
     if (o->inner_cycles < 0 || o->inner_cycles > 8)
         return set_error(MG_ERR_INVALID_ARG, "inner_cycles must be in 0..8");
+    if (o->krylov < 0 || o->krylov > 1) return set_error(MG_ERR_INVALID_ARG, "krylov must be 0 or 1");
     return MG_OK;
 }
 
@@ -436,6 +437,18 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     mg_default_opts(&o);
     if (opts) o = *opts;
     CKS(validate_opts(&o));
+    if (o.krylov) {
+        bool all_neumann = true;
+        for (int d = 0; d < 3; ++d) all_neumann = all_neumann && ((bc >> (2 * d)) & 3) == 3;
+        if (o.precision != MG_FP64 || coupled || periodic || all_neumann)
+            return set_error(MG_ERR_UNSUPPORTED,
+                             "krylov = 1 needs FP64, independent boxes, no periodic axis and a "
+                             "Dirichlet wall");
+        if (o.nu1 != o.nu2 || o.nu1 < 1)
+            return set_error(MG_ERR_UNSUPPORTED,
+                             "krylov = 1 needs nu1 = nu2 >= 1 (a symmetric preconditioner)");
+        o.smoother = 1;  // single-colour passes: the post-smoother runs black first
+    }
     if (coupled || periodic) {
         // ghost exchanges between boxes (or across periodic faces) before
         // every stencil: single-colour passes, all-cell residuals, per-level
@@ -486,6 +499,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->opts = o;
     s->has32 = o.precision == MG_MIXED;
     s->tma = s->has32 && o.tma == 1;
+    s->pcg = o.krylov == 1;
     s->bc = bc;
     // A singular (constants in the null space): no axis has a Dirichlet wall
     s->singular = true;
@@ -552,6 +566,30 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         work_elems = (size_t)s->ub.n * s->ub.n;
         std::fill(work_off.begin(), work_off.end(), 0);
     }
+    // CG: p and q of every box in the level-0 layout (zero guards), the
+    // per-box scalars and the two device pointer tables
+    auto pcg_arrays = [&](Bump &bb, std::vector<double *> &pp, std::vector<double *> &qq) {
+        pp.assign(nbox, nullptr);
+        qq.assign(nbox, nullptr);
+        if (!s->pcg) return;
+        for (int b = 0; b < nbox; ++b) {
+            const long long E = level_elems(s->n[b][0], s->n[b][1], s->n[b][2]);
+            const long long Q = pitch_plane(s->n[b][0], s->n[b][1]);
+            for (auto *v : {&pp, &qq}) {
+                double *a = bb.take<double>((size_t)E);
+                (*v)[b] = a ? a + Q : nullptr;
+            }
+        }
+        s->sc.rz = bb.take<double>(nbox);
+        s->sc.rzn = bb.take<double>(nbox);
+        s->sc.pq = bb.take<double>(nbox);
+        s->sc.beta = bb.take<double>(nbox);
+        s->sc.alpha = bb.take<double>(nbox);
+        s->pcg_p = bb.take<double *>(nbox);
+        s->pcg_q = bb.take<double *>(nbox);
+    };
+    std::vector<double *> pcg_p, pcg_q;
+    pcg_arrays(bump, pcg_p, pcg_q);
     bump.take<double>(s->total);      // beta copy
     bump.take<double>(work_elems);    // inverse scratch
     bump.take<double>(ntiles0);       // partials
@@ -578,6 +616,16 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     real.base = s->arena;
     carve(s, s->h64, real, true);
     if (s->has32) carve(s, s->h32, real, true);
+    pcg_arrays(real, pcg_p, pcg_q);
+    if (s->pcg) {
+        e = cudaMemcpy(s->pcg_p, pcg_p.data(), sizeof(double *) * nbox, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(s->pcg_q, pcg_q.data(), sizeof(double *) * nbox, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            solver_destroy(s);
+            return set_error(MG_ERR_CUDA, "CG pointer tables: %s", cudaGetErrorString(e));
+        }
+    }
     s->beta = real.take<double>(s->total);
     s->work = real.take<double>(work_elems);
     s->partials = real.take<double>(ntiles0);
@@ -610,6 +658,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         q += sizeof(int) * nbox;
         s->J.step = reinterpret_cast<int *>(q);
         s->J.max_cycles = o.max_cycles;
+        s->J.stall_limit = o.krylov ? 0 : 5;
     }
 
     // launch-set descriptors (+ packed offsets and side flags)
@@ -623,7 +672,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
     // last (nu2 > 0, so black residuals vanish), single-colour passes on every
     // box's finest level, and the red-only residual reading
-    s->lookahead = !s->has32 && o.nu1 > 0 && o.nu2 > 0 && !o.full_residual &&
+    s->lookahead = !s->has32 && !s->pcg && o.nu1 > 0 && o.nu2 > 0 && !o.full_residual &&
                    !s->h64.smooth.empty() && s->h64.smooth[0].nbox == nbox &&
                    !s->h64.fused[0];
     // set-up sets: every box that has level l; boxes that have l + 1; bottoms
@@ -790,6 +839,7 @@ void solver_destroy(Solver *s)
     if (s->h32.graph) cudaGraphExecDestroy(s->h32.graph);
     if (s->loop64) cudaGraphExecDestroy(s->loop64);
     if (s->loop32) cudaGraphExecDestroy(s->loop32);
+    if (s->loop_pcg) cudaGraphExecDestroy(s->loop_pcg);
     if (s->hjblock) cudaFreeHost(s->hjblock);
     if (s->arena) cudaFree(s->arena);
     if (s->desc) cudaFree(s->desc);
@@ -988,13 +1038,15 @@ static cudaError_t combine(Solver *s, double *norm, cudaStream_t st)
     return launch_norm_combine(s->nbox, norm, st);
 }
 
+// reverse: black before red in each sweep (single-colour passes only).
 template <class T>
 static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool fused,
-                          const SweepMaps *maps, cudaStream_t st, int lvl = 0)
+                          const SweepMaps *maps, cudaStream_t st, int lvl = 0,
+                          bool reverse = false)
 {
     cudaError_t e = cudaSuccess;
     int left = nu;
-    if (fused) {
+    if (fused && !reverse) {
         for (; left >= 2; left -= 2) {
             for (int src = 0; src < 2; ++src) {
                 int sl = fine ? prof_begin(s, MG_PROF_SWEEP, st) : -1;
@@ -1007,7 +1059,9 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
         for (int color = 0; color < 2; ++color) {
             int sl = fine ? prof_begin(s, MG_PROF_PASS, st) : -1;
             if ((e = exch(s, S, lvl, st)) != cudaSuccess) return e;
-            if ((e = launch_rbgs_pass(S, s->active, color, st)) != cudaSuccess) return e;
+            if ((e = launch_rbgs_pass(S, s->active, reverse ? 1 - color : color, st)) !=
+                cudaSuccess)
+                return e;
             prof_end(s, sl, st);
         }
     }
@@ -1016,9 +1070,12 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
 
 // head_done: the finest level's first red pass already ran out of place
 // (phi -> phi2, look-ahead); the cycle goes on with the black pass phi2 -> phi.
+// sym: post-smoothing sweeps run black then red, the adjoint of the
+// pre-smoother, so that with nu1 = nu2 and a zero start the cycle is a
+// symmetric linear operator (the CG preconditioner).
 template <class T>
 static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
-                                  bool head_done = false)
+                                  bool head_done = false, bool sym = false)
 {
     cudaError_t e;
     const int nl = (int)H.smooth.size();
@@ -1049,7 +1106,8 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
     if (s->xmode)
         e = launch_union_bottom(H.bottom, s->ub, H.uinv, s->active, st);
     else
-        e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st);
+        e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st,
+                                 sym ? 1 : 0);
     if (e != cudaSuccess) return e;
     for (int l = nl - 1; l >= 0; --l) {
         const BoxSet<T> &S = H.smooth[l];
@@ -1061,7 +1119,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         int sl = l == 0 ? prof_begin(s, MG_PROF_PROLONG, st) : -1;
         if ((e = launch_prolong(S, s->active, st)) != cudaSuccess) return e;
         prof_end(s, sl, st);
-        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, H.maps[l], st, l)) !=
+        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, H.maps[l], st, l, sym)) !=
             cudaSuccess)
             return e;
     }
@@ -1214,6 +1272,39 @@ static cudaError_t enqueue_body32(Solver *s, cudaStream_t st, cudaGraphCondition
     return launch_judge(s->nbox, s->dnorm, s->dnormf, s->active, s->J, h, 1, st);
 }
 
+// One CG iteration (krylov = 1) on every active box: z = V r (phi was zeroed
+// by the previous iteration's update or at the start), rz = <r, z>,
+// beta = rz / rz_prev, p = z + beta p, q = A p, alpha = rz / <p, q>,
+// x += alpha p, r -= alpha q, ||r|| into dnorm.  A and the V-cycle are both
+// negative definite; the signs cancel in alpha and beta.
+static cudaError_t enqueue_pcg(Solver *s, cudaStream_t st)
+{
+    cudaError_t e = enqueue_vcycle(s, s->h64, st, false, true);
+    if (e != cudaSuccess) return e;
+    const BoxSet<double> &F = s->h64.fine;
+    const int sl = prof_begin(s, MG_PROF_KRYLOV, st);
+    if ((e = launch_pcg(F, s->active, 0, s->pcg_p, s->pcg_q, s->sc, s->partials, s->sc.rzn, st)) !=
+            cudaSuccess ||
+        (e = launch_pcg_scalars(s->nbox, s->active, 0, s->sc, st)) != cudaSuccess ||
+        (e = launch_pcg(F, s->active, 1, s->pcg_p, s->pcg_q, s->sc, nullptr, nullptr, st)) !=
+            cudaSuccess ||
+        (e = launch_pcg(F, s->active, 2, s->pcg_p, s->pcg_q, s->sc, s->partials, s->sc.pq, st)) !=
+            cudaSuccess ||
+        (e = launch_pcg_scalars(s->nbox, s->active, 1, s->sc, st)) != cudaSuccess ||
+        (e = launch_pcg(F, s->active, 3, s->pcg_p, s->pcg_q, s->sc, s->partials, s->dnorm, st)) !=
+            cudaSuccess)
+        return e;
+    prof_end(s, sl, st);
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_body_pcg(Solver *s, cudaStream_t st, cudaGraphConditionalHandle h)
+{
+    cudaError_t e = enqueue_pcg(s, st);
+    if (e != cudaSuccess) return e;
+    return launch_judge(s->nbox, s->dnorm, s->dnormf, s->active, s->J, h, 1, st);
+}
+
 // Run the whole convergence loop as one graph launch: a conditional WHILE
 // node whose body is captured once and whose condition the judge kernel sets.
 template <class F>
@@ -1277,7 +1368,9 @@ struct BoxState {
 };
 
 // Judge box b after a cycle with relative residual rel; returns true if done.
-static bool judge(BoxState &B, double rel, double tol, int cycle, int max_cycles)
+// stall_limit: cycles without a 10% gain that end the solve (0: no such rule).
+static bool judge(BoxState &B, double rel, double tol, int cycle, int max_cycles,
+                  int stall_limit = 5)
 {
     if (B.nh < MG_MAX_HIST) B.hist[B.nh++] = rel;
     B.cycles = cycle;
@@ -1287,7 +1380,10 @@ static bool judge(BoxState &B, double rel, double tol, int cycle, int max_cycles
     if (rel > 0.9 * B.best) ++B.stall;
     else B.stall = 0;
     B.best = std::min(B.best, rel);
-    if (B.stall >= 5 || cycle >= max_cycles) { B.status = MG_ERR_NOT_CONVERGED; return true; }
+    if ((stall_limit > 0 && B.stall >= stall_limit) || cycle >= max_cycles) {
+        B.status = MG_ERR_NOT_CONVERGED;
+        return true;
+    }
     return false;
 }
 
@@ -1444,6 +1540,85 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     CKS(upload_active(s, bs, stream));
 
     const bool device_loop = s->opts.use_graph && !s->prof;
+    if (s->pcg) {
+        // start: x = phi0 (into phi2), r = f - A x0 (into f), p = 0, then
+        // phi = 0 (the first preconditioner's zero start), rz_prev = 0.  The
+        // iteration judges the recursively updated residual; a box it
+        // declares converged is checked against its true residual f - A x,
+        // and restarts from it (at most 3 times) if that is above tol.
+        if (any) {
+            CK(launch_pcg(H.fine, nullptr, 4, s->pcg_p, s->pcg_q, s->sc, s->partials, nullptr,
+                          stream));
+            CK(launch_zero(H.fine, nullptr, stream));
+            CK(cudaMemsetAsync(s->sc.rz, 0, sizeof(double) * nbox, stream));
+            for (int b = 0; b < nbox; ++b) side[b] = 1;
+        }
+        if (device_loop && any) {
+            CKS(upload_judge(s, bs, tol, stream));
+            CKS(run_loop(s, &s->loop_pcg, &s->loop_kernels_pcg, enqueue_body_pcg, stream));
+            CKS(download_judge(s, bs, s->loop_kernels_pcg, stream));
+            any = false;
+        }
+        std::vector<char> ran(nbox, 0);
+        for (int b = 0; b < nbox; ++b) ran[b] = !bs[b].done || bs[b].cycles > 0;
+        for (int restart = 0;; ++restart) {
+            // host loop: the boxes still running (all of them without the
+            // device loop, the restarted ones after a check)
+            while (any) {
+                s->rec = &s->direct;
+                CK(enqueue_pcg(s, stream));
+                s->rec = nullptr;
+                CKS(read_norms(s, s->dnorm, s->hnorm, stream));
+                if (s->prof) prof_collect(s);
+                bool changed = false;
+                any = false;
+                for (int b = 0; b < nbox; ++b) {
+                    if (bs[b].done) continue;
+                    if (judge(bs[b], s->hnorm[b] / bs[b].nf, tol, bs[b].cycles + 1,
+                              s->opts.max_cycles, 0)) {
+                        bs[b].done = true;
+                        changed = true;
+                    } else {
+                        any = true;
+                    }
+                }
+                if (changed && any) CKS(upload_active(s, bs, stream));
+            }
+            // true residual of the boxes the iteration calls converged
+            bool check = false;
+            for (int b = 0; b < nbox; ++b) {
+                s->hactive[b] = ran[b] && bs[b].status == MG_OK && bs[b].cycles > 0;
+                check = check || s->hactive[b];
+            }
+            if (!check) break;
+            CK(cudaMemcpyAsync(s->active, s->hactive, sizeof(int) * nbox, cudaMemcpyHostToDevice,
+                               stream));
+            CK(launch_pcg(H.fine, s->active, 5, s->pcg_p, s->pcg_q, s->sc, nullptr, nullptr,
+                          stream));
+            CK(launch_pack(H.fine, s->doff, fd, 1, stream));
+            CK(launch_pcg(H.fine, s->active, 4, s->pcg_p, s->pcg_q, s->sc, s->partials, s->dnorm,
+                          stream));
+            CKS(read_norms(s, s->dnorm, s->hnorm, stream));
+            for (int b = 0; b < nbox; ++b) {
+                if (!s->hactive[b]) continue;
+                const double rel = s->hnorm[b] / bs[b].nf;
+                ran[b] = 0;  // checked
+                if (bs[b].nh > 0) bs[b].hist[bs[b].nh - 1] = rel;
+                if (rel <= tol || restart >= 3 || bs[b].cycles >= s->opts.max_cycles) {
+                    if (rel > tol) bs[b].status = MG_ERR_NOT_CONVERGED;
+                    continue;
+                }
+                bs[b].done = false;  // restart from the true residual
+                bs[b].status = MG_ERR_NOT_CONVERGED;
+                ran[b] = 1;
+                any = true;
+            }
+            if (!any) break;
+            CKS(upload_active(s, bs, stream));
+            CK(launch_zero(H.fine, s->active, stream));
+            CK(cudaMemsetAsync(s->sc.rz, 0, sizeof(double) * nbox, stream));
+        }
+    }
     if (!mixed && device_loop && any) {
         CKS(upload_judge(s, bs, tol, stream));
         CKS(run_loop(s, &s->loop64, &s->loop_kernels64, enqueue_body64, stream));

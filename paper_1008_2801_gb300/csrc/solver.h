@@ -126,6 +126,14 @@ struct Solver {
     double *dmean = nullptr;              // [nbox] scratch: removed means
     bool tma = false;                     // FP32 fused sweeps use the TMA kernel
 
+    // conjugate gradients preconditioned by a symmetric V-cycle (krylov = 1):
+    // level-0 FP64 x in phi2, r in f, z in phi; p and q per box
+    bool pcg = false;
+    double **pcg_p = nullptr, **pcg_q = nullptr;  // device [nbox] arrays of level-0 pointers
+    PcgScalars sc{};
+    cudaGraphExec_t loop_pcg = nullptr;
+    long long loop_kernels_pcg = 0;
+
     // on-device convergence loop (conditional CUDA graph)
     char *jblock = nullptr;               // device: judge state block
     char *hjblock = nullptr;              // pinned host mirror

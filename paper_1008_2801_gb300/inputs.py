@@ -19,6 +19,11 @@ run (a centrally condensed stellar density profile, beta = 1/rho):
   removed.  Draw order from ``numpy.random.default_rng(seed)``: noise, then f,
   then (where used) targets, each in C order (nz, ny, nx).
 * ``batched``: many boxes of uneven size, each with its own stellar profile.
+* ``inclusions``: high-contrast beta, 1 in a background with random balls
+  where beta = contrast (centres ~ U[0.1, 0.9]^3, radii ~ U[0.04, 0.1] of the
+  box's x extent), f ~ U[-1, 1]; draw order centres, radii, f.  The
+  coefficient jumps are not aligned with coarse cells, the case where a
+  V-cycle iteration slows down and CG with a V-cycle preconditioner does not.
 
 Arrays are float64 numpy arrays in C order with shape (nz, ny, nx), x fastest;
 cell centres are at x_i = (i + 1/2) dx.
@@ -33,6 +38,7 @@ __all__ = [
     "stellar",
     "batched",
     "adjoint_case",
+    "inclusions",
     "config",
     "BATCH_SIZES",
 ]
@@ -112,6 +118,29 @@ def stellar(n, seed: int, dx: float | None = None, nrhs: int = 0):
         out["f_batch"] = fb
         out["phi_target"] = tgt
     return out
+
+
+def inclusions(n, seed: int, contrast: float = 1e4, count: int = 24,
+               dx: float | None = None):
+    """High-contrast beta (1 outside, ``contrast`` inside random balls) and
+    random f on an (nx, ny, nz) box (``n`` an int for a cube); dx defaults to
+    1/nx.  Returns dict(beta, f, dx)."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    nx, ny, nz = n
+    if dx is None:
+        dx = 1.0 / nx
+    rng = np.random.default_rng(seed)
+    ext = np.array([nx, ny, nz], dtype=np.float64) * dx
+    centres = rng.uniform(0.1, 0.9, (count, 3)) * ext
+    radii = rng.uniform(0.04, 0.1, count) * ext[0]
+    z, y, x = cell_centres(n, dx)
+    inside = np.zeros((nz, ny, nx), dtype=bool)
+    for c, r in zip(centres, radii):
+        inside |= (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= r * r
+    beta = np.where(inside, float(contrast), 1.0)
+    f = rng.uniform(-1.0, 1.0, (nz, ny, nx))
+    return {"beta": beta, "f": f, "dx": dx}
 
 
 def batched(nbox: int = 64, seed: int = 4, sizes=BATCH_SIZES, dx: float = 1.0 / 128):

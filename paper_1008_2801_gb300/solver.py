@@ -49,7 +49,7 @@ def _check_tensor(t, name, numel=None, device=None):
 
 
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
-          full_residual=False, tma=False):
+          full_residual=False, tma=False, krylov=False):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -60,6 +60,7 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.inner_cycles = int(inner_cycles)
     o.full_residual = 1 if full_residual else 0
     o.tma = 1 if tma else 0
+    o.krylov = 1 if krylov else 0
     return o
 
 
@@ -118,12 +119,14 @@ class Solver:
 
     precision: "fp64" (everything FP64) or "mixed" (FP32 V-cycles inside an
     FP64 iterative-refinement loop).  bc: wall mask or D/N string (see the
-    module docstring).  Not thread-safe.
+    module docstring).  krylov: conjugate gradients preconditioned by one
+    symmetric V-cycle per iteration instead of plain V-cycles (FP64, for
+    high-contrast beta).  Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0):
+                 full_residual=False, tma=False, bc=0, krylov=False):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -134,7 +137,7 @@ class Solver:
             "cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma)
+                  full_residual, tma, krylov)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
@@ -302,7 +305,7 @@ class BatchSolver:
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0):
+                 full_residual=False, tma=False, bc=0, krylov=False):
         L = _lib.load()
         self.bc = bc_mask(bc)
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -314,7 +317,7 @@ class BatchSolver:
         d = (ctypes.c_double * nb)(*dxs)
         self._h = ctypes.c_void_p()
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma)
+                  full_residual, tma, krylov)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, self.bc, ctypes.byref(o)),
                   "mg_batch_create")
@@ -365,6 +368,12 @@ class BatchSolver:
         if self._h:
             _lib.load().mg_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:
