@@ -181,6 +181,10 @@ struct CoarseJob {
     int nlev;
     int box;
     Box<T> lv[kMaxCoarse];
+    // periodic axes: the level's self-exchange records (copied into the
+    // box's own guard cells before every pass and residual), else 0
+    const ExchRec *rec[kMaxCoarse];
+    int nrec[kMaxCoarse];
 };
 
 // Per-box convergence state of a solve, kept on the device so that the

@@ -12,6 +12,7 @@
 // guarded level layout described in common.cuh.
 #include "kernels.h"
 
+#include <algorithm>
 #include <type_traits>
 
 #include <atomic>
@@ -430,17 +431,23 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
     TilePos p = tile_pos(TK_COARSE, nx, ny, nz, t - ts[b]);
     const int I = p.x, J = p.y, K = p.z;
     if (I >= nx / 2 || J >= ny / 2) return;
-    // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c) even
+    // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c+par) even,
+    // par the parity of the box's lower corner in the level's index space
     const long long o = (long long)(2 * K) * Q + (long long)(2 * J) * P + 2 * I;
-    auto red4 = [&](auto has_d) {
-        constexpr bool HD = decltype(has_d)::value;
-        T sum = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + P + 1, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + 1, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, o + Q + P, P, Q);
+    auto red4 = [&](auto has_d, auto odd) {
+        constexpr bool HD = decltype(has_d)::value, OD = decltype(odd)::value;
+        const long long c0 = OD ? o + 1 : o, c1 = OD ? o + P : o + P + 1,
+                        c2 = OD ? o + Q : o + Q + 1, c3 = OD ? o + Q + P + 1 : o + Q + P;
+        T sum = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c0, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c1, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c2, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c3, P, Q);
         return sum;
     };
-    const T sum = B.D ? red4(std::true_type{}) : red4(std::false_type{});
+    const T sum = B.D ? (B.par ? red4(std::true_type{}, std::true_type{})
+                               : red4(std::true_type{}, std::false_type{}))
+                      : (B.par ? red4(std::false_type{}, std::true_type{})
+                               : red4(std::false_type{}, std::false_type{}));
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
     B.fc[cc] = sum * T(0.125);
     B.phic[cc] = T(0);
@@ -514,7 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const i
         constexpr bool HD = decltype(has_d)::value;
         const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
         for (int k = z0; k < z1; ++k) {
-            const int x = mode == 2 ? 2 * p.x + ((p.y + k) & 1) : p.x;
+            const int x = mode == 2 ? 2 * p.x + ((p.y + k + B.par) & 1) : p.x;
             if (x >= B.nx) continue;
             const long long c = (long long)k * B.Q + (long long)p.y * B.P + x;
             const T r = mode == 1 ? B.f[c]
@@ -623,6 +630,23 @@ __device__ __forceinline__ void cta_pass(const Box<T> &B, int color)
     }
 }
 
+// Periodic axes: fill the box's guard cells from its own opposite faces
+// (records whose source is the box itself); the caller synchronises.
+template <class T>
+__device__ __forceinline__ void cta_exchange(const Box<T> &B, const ExchRec *rec, int nrec)
+{
+    for (int q = 0; q < nrec; ++q) {
+        const ExchRec R = rec[q];
+        const int n = R.ex * R.ey * R.ez;
+        for (int e = threadIdx.x; e < n; e += CoarseThreads<T>::value) {
+            const int a = e % R.ex, r = e / R.ex;
+            const int bb = r % R.ey, c = r / R.ey;
+            B.phi[(long long)(R.dk + c) * B.Q + (long long)(R.dj + bb) * B.P + R.di + a] =
+                B.phi[(long long)(R.sk + c) * B.Q + (long long)(R.sj + bb) * B.P + R.si + a];
+        }
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void cta_resid_restrict(const Box<T> &B)
 {
@@ -700,13 +724,21 @@ __global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const
     __syncthreads();
     if (active && !active[J.box]) return;  // uniform over the CTA
     const int nl = J.nlev;
+    auto exch = [&](int l) {
+        if (J.nrec[l] == 0) return;
+        cta_exchange<T>(J.lv[l], J.rec[l], J.nrec[l]);
+        __syncthreads();
+    };
     for (int l = 0; l + 1 < nl; ++l) {
         for (int s = 0; s < nu1; ++s) {
+            exch(l);
             cta_pass<T>(J.lv[l], 0);
             __syncthreads();
+            exch(l);
             cta_pass<T>(J.lv[l], 1);
             __syncthreads();
         }
+        exch(l);
         cta_resid_restrict<T>(J.lv[l]);
         __syncthreads();
     }
@@ -716,8 +748,10 @@ __global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const
         cta_prolong<T>(J.lv[l]);
         __syncthreads();
         for (int s = 0; s < nu2; ++s) {
+            exch(l);
             cta_pass<T>(J.lv[l], post_first);
             __syncthreads();
+            exch(l);
             cta_pass<T>(J.lv[l], 1 - post_first);
             __syncthreads();
         }
@@ -1534,7 +1568,8 @@ __global__ void __launch_bounds__(kThreads) k_exchange(BoxSet<T> S, const int *_
     const Box<T> &D = S.boxes[R.dst];
     const Box<T> &F = S.boxes[R.src];
     const int n = R.ex * R.ey * R.ez;
-    for (int e = threadIdx.y * kTX + threadIdx.x; e < n; e += kThreads) {
+    const int stride = kThreads * gridDim.y;  // a record's cells over gridDim.y CTAs
+    for (int e = blockIdx.y * kThreads + threadIdx.y * kTX + threadIdx.x; e < n; e += stride) {
         const int a = e % R.ex, r = e / R.ex;
         const int bb = r % R.ey, c = r / R.ey;
         D.phi[(long long)(R.dk + c) * D.Q + (long long)(R.dj + bb) * D.P + R.di + a] =
@@ -1964,10 +1999,12 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
 
 template <class T>
 cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec *rec, int nrec,
-                            cudaStream_t st)
+                            int max_cells, cudaStream_t st)
 {
     if (nrec == 0) return cudaSuccess;
-    k_exchange<T><<<nrec, block2d(), 0, st>>>(S, active, rec);
+    // about 4 cells per thread on the largest record (a 256^2 face: 64 CTAs)
+    const int chunks = std::max(1, std::min(1024, (max_cells + 4 * kThreads - 1) / (4 * kThreads)));
+    k_exchange<T><<<dim3(nrec, chunks), block2d(), 0, st>>>(S, active, rec);
     return counted(cudaGetLastError());
 }
 
@@ -2039,7 +2076,7 @@ cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgS
     template cudaError_t launch_coarse_vcycle<T>(const CoarseJob<T> *, int, const int *, int, int, \
                                                  cudaStream_t, int);                                \
     template cudaError_t launch_exchange<T>(const BoxSet<T> &, const int *, const ExchRec *, int,  \
-                                            cudaStream_t);                                         \
+                                            int, cudaStream_t);                                         \
     template cudaError_t launch_guard_fill<T>(const BoxSet<T> &, T, cudaStream_t);                 \
     template cudaError_t launch_union_bottom<T>(const BoxSet<T> &, const UnionBottom &, const T *, \
                                                 const int *, cudaStream_t);

@@ -172,7 +172,7 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
         B.cP = (int)pitch_row(c[0], s->wide);
         B.cQ = pitch_plane(c[0], c[1], s->wide);
     }
-    if (l == s->nlev[b] - 1) B.ainv = H.ainv[b];
+    if (l == s->nlev[b] - 1) B.ainv = s->xmode ? H.uinv : H.ainv[b];
     B.box = b;
     B.zc = kSweepZ;
     if (s->xmode) {
@@ -385,6 +385,13 @@ static int validate_opts(const mg_opts *o)
 // are in other boxes, and a small union keeps the dense coarsest solve,
 // O(n^3) on one SM at set-up, cheap).  Fills dims and lower corners per box
 // and level; returns the level count.
+static int max_record_cells(const std::vector<ExchRec> &recs)
+{
+    int m = 0;
+    for (const ExchRec &r : recs) m = std::max(m, r.ex * r.ey * r.ez);
+    return m;
+}
+
 static int coupled_levels(int nbox, const int (*lo)[3], const int (*n)[3],
                           std::vector<std::vector<std::array<int, 3>>> &dims,
                           std::vector<std::vector<std::array<int, 3>>> &los)
@@ -451,11 +458,12 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     }
     if (coupled || periodic) {
         // ghost exchanges between boxes (or across periodic faces) before
-        // every stencil: single-colour passes, all-cell residuals, per-level
-        // launches down to the dense bottom solve
+        // every stencil: single-colour passes; a coupled level launches
+        // every level down to the dense bottom solve of the union (a
+        // periodic box runs its coarse levels in the one-CTA kernel, which
+        // does its own exchanges)
         o.smoother = 1;
-        o.full_residual = 1;
-        o.coarse_cells = -1;
+        if (coupled) o.coarse_cells = -1;
         o.tma = 0;
     }
     std::vector<std::vector<std::array<int, 3>>> cdims, clos;
@@ -672,7 +680,9 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
     // last (nu2 > 0, so black residuals vanish), single-colour passes on every
     // box's finest level, and the red-only residual reading
-    s->lookahead = !s->has32 && !s->pcg && o.nu1 > 0 && o.nu2 > 0 && !o.full_residual &&
+    // (not with ghost exchanges: they fill phi's guard cells, not phi2's)
+    s->lookahead = !s->has32 && !s->pcg && !s->xmode && o.nu1 > 0 && o.nu2 > 0 &&
+                   !o.full_residual &&
                    !s->h64.smooth.empty() && s->h64.smooth[0].nbox == nbox &&
                    !s->h64.fused[0];
     // set-up sets: every box that has level l; boxes that have l + 1; bottoms
@@ -753,6 +763,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
             }
             const std::vector<ExchRec> recs = periodic_exchange(bl, period);
             s->nxrec.push_back((int)recs.size());
+            s->xmax.push_back(max_record_cells(recs));
             xrec_at.push_back(blob.put(recs.data(), recs.size() * sizeof(ExchRec)));
         }
         std::vector<int> uo = {0, s->ub.n};
@@ -768,6 +779,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
                 }
             const std::vector<ExchRec> recs = level_exchange(bl);
             s->nxrec.push_back((int)recs.size());
+            s->xmax.push_back(max_record_cells(recs));
             xrec_at.push_back(blob.put(recs.data(), recs.size() * sizeof(ExchRec)));
         }
         std::vector<int> uo(nbox + 1, 0);
@@ -784,6 +796,19 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (e != cudaSuccess) {
         solver_destroy(s);
         return set_error(MG_ERR_OOM, "cudaMalloc(descriptors): %s", cudaGetErrorString(e));
+    }
+    if (periodic) {
+        // the coarse jobs' exchange records, now that their address is known
+        auto link = [&](size_t at, int lc, auto *tag) {
+            using J = std::remove_pointer_t<decltype(tag)>;
+            J *job = reinterpret_cast<J *>(blob.bytes.data() + at);
+            for (int l = 0; l < job->nlev; ++l) {
+                job->rec[l] = reinterpret_cast<const ExchRec *>(s->desc + xrec_at[lc + l]);
+                job->nrec[l] = s->nxrec[lc + l];
+            }
+        };
+        link(jobs64, s->h64.lc[0], (CoarseJob<double> *)nullptr);
+        if (s->has32) link(jobs32, s->h32.lc[0], (CoarseJob<float> *)nullptr);
     }
     e = cudaMemcpy(s->desc, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -923,7 +948,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         // neighbouring box's beta; faces from there
         CK(launch_guard_fill(s->h64.fine, -1.0, st));
         CK(launch_pack(s->h64.fine, s->doff, s->beta, 0, st));
-        CK(launch_exchange(s->h64.fine, nullptr, s->xrec[0], s->nxrec[0], st));
+        CK(launch_exchange(s->h64.fine, nullptr, s->xrec[0], s->nxrec[0], s->xmax[0], st));
         CK(launch_setup(s->setup_lv[0], 4, st));
     } else {
         // one launch per step and level over every box
@@ -1028,7 +1053,7 @@ template <class T>
 static cudaError_t exch(Solver *s, const BoxSet<T> &S, int lvl, cudaStream_t st)
 {
     if (!s->xmode) return cudaSuccess;
-    return launch_exchange(S, s->active, s->xrec[lvl], s->nxrec[lvl], st);
+    return launch_exchange(S, s->active, s->xrec[lvl], s->nxrec[lvl], s->xmax[lvl], st);
 }
 
 // Coupled level: one norm for the union (no-op otherwise).
@@ -1103,7 +1128,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     }
     if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
-    if (s->xmode)
+    if (s->coupled)
         e = launch_union_bottom(H.bottom, s->ub, H.uinv, s->active, st);
     else
         e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st,

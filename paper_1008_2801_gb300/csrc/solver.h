@@ -113,6 +113,7 @@ struct Solver {
     std::vector<std::vector<std::array<int, 3>>> lo;  // [box][level] lower corners (coupled)
     std::vector<const ExchRec *> xrec;               // [level] device exchange records
     std::vector<int> nxrec;                          // [level]
+    std::vector<int> xmax;                           // [level] cells of the largest record
     UnionBottom ub{};                                // union of the coarsest levels
 
     // set-up launch sets
