@@ -225,9 +225,8 @@ def run_gpu(args):
 
     def timed(solver, steps, warm, prof):
         def step():
-            phi.zero_()
             solver.set_beta(beta)
-            return solver.solve(f, phi=phi, tol=TOL)[1]
+            return solver.solve(f, phi=phi, tol=TOL, zero_guess=True)[1]
         solver.profile(prof)
         for _ in range(warm):
             st = step()
@@ -300,7 +299,7 @@ def run_gpu(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "cells_per_gpu": N, "tol": TOL,
-                      "step": "mg_set_beta + mg_solve (phi0 = 0)", "cycles": st64["cycles"],
+                      "step": "mg_set_beta + mg_solve_ex (MG_ZERO_GUESS: phi0 = 0)", "cycles": st64["cycles"],
                       "rel_resid": st64["rel_resid"],
                       "l2": "inputs larger than L2 (working set ~1 GB > 129 MB)",
                       "parallelism": f"independent box per GPU x {world}"},
@@ -341,18 +340,18 @@ def run_gpu(args):
     se = Solver((n, n, n), d["dx"], precision="fp64", device=dev)
     tot = 0.0
     for it in range(max(args.warmup, 3) + args.steps):
-        ph.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         se.set_beta(bh)
-        se.solve(fh, phi=ph, tol=TOL)
+        se.solve(fh, phi=ph, tol=TOL, zero_guess=True)
         t1 = time.perf_counter()
         if it >= max(args.warmup, 3):
             tot += t1 - t0
     e2e_ms = max_over_ranks(tot / args.steps * 1e3, dev)
     out["e2e"] = {"value": world * N / (e2e_ms / 1e3), "unit": "cells/s", "ms_per_step": e2e_ms,
-                  "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N,
-                  "path": "mg_set_beta + mg_solve on pinned host buffers (copies inside)"}
+                  "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N,
+                  "path": "mg_set_beta + mg_solve_ex (MG_ZERO_GUESS) on pinned host buffers "
+                          "(beta and f copied in, phi out, inside the calls)"}
     se.close()
 
     # CPU oracle on this machine's host cores (rank 0, N = 1 only)
@@ -411,9 +410,8 @@ def run_extra(dev, args):
         phi = torch.zeros_like(f)
 
         def go():
-            phi.zero_()
             s.set_beta(beta)
-            return s.solve(f, phi=phi, tol=TOL)[1]
+            return s.solve(f, phi=phi, tol=TOL, zero_guess=True)[1]
         ms, st = time_once(go)
         res[prec] = {"cells_per_s": N / (ms / 1e3), "ms": ms, "cycles": st["cycles"],
                      "rel_resid": st["rel_resid"]}
@@ -438,9 +436,8 @@ def run_extra(dev, args):
         phi = torch.zeros_like(fp)
 
         def go():
-            phi.zero_()
             bs.set_beta(bp)
-            return bs.solve(fp, phi, tol=TOL)[1]
+            return bs.solve(fp, phi, tol=TOL, zero_guess=True)[1]
         ms, sts = time_once(go)
         res[f"batched_{prec}"] = {"cells_per_s": N / (ms / 1e3), "ms": ms,
                                   "max_cycles": max(s["cycles"] for s in sts),

@@ -169,12 +169,24 @@ int mg_set_beta(mg_ctx *ctx, const double *beta_cell, void *stream);
 
 /* Solve A phi = f.  phi holds the initial guess on entry (zeros for none)
  * and the solution on return.  tol > 0 is the relative residual target.
- * st may be NULL.  Synchronises the stream once per cycle to read the
- * residual norm.  Returns OK, NOT_CONVERGED or DIVERGED (phi = last iterate),
- * NONFINITE (phi unspecified), INVALID_ARG (no beta set, NULL, tol <= 0), CUDA.
- * f = 0 gives phi = 0 and OK. */
+ * st may be NULL.  With use_graph (default) the whole cycle loop runs on the
+ * device and the call synchronises the stream once at the end; otherwise once
+ * per cycle.  Host (not device) f and phi are copied in and out inside the
+ * call; host inputs are read on the context's own copy stream, concurrently
+ * with work already queued on `stream` (a set-up from mg_set_beta), so they
+ * must hold their values when the call is made.  Returns OK, NOT_CONVERGED
+ * or DIVERGED (phi = last iterate), NONFINITE (phi unspecified), INVALID_ARG
+ * (no beta set, NULL, tol <= 0), CUDA.  f = 0 gives phi = 0 and OK. */
 int mg_solve(mg_ctx *ctx, const double *f, double *phi, double tol, mg_stats *st,
              void *stream);
+
+/* Flags of the _ex solves. */
+#define MG_ZERO_GUESS 1  /* phi is output only: the iteration starts from 0
+                            (host phi is then not copied in) */
+
+/* mg_solve / mg_solve_multi (nrhs >= 1) with flags. */
+int mg_solve_ex(mg_ctx *ctx, int nrhs, const double *f, double *phi, double tol, int flags,
+                mg_stats *st, void *stream);
 
 /* Same as mg_solve for nrhs right-hand sides packed back to back (each
  * nx*ny*nz values) that share beta; st may be NULL or an array of nrhs.
@@ -248,6 +260,8 @@ int mg_batch_set_beta(mg_batch *b, const double *beta_packed, void *stream);
 /* st may be NULL or an array of nbox; returns the worst status over boxes. */
 int mg_solve_batched(mg_batch *b, const double *f_packed, double *phi_packed, double tol,
                      mg_stats *st, void *stream);
+int mg_solve_batched_ex(mg_batch *b, const double *f_packed, double *phi_packed, double tol,
+                        int flags, mg_stats *st, void *stream);
 void mg_batch_destroy(mg_batch *b);
 
 /* ---- a coupled level: boxes of one level solved as one domain ----------
@@ -276,6 +290,8 @@ int mg_level_create(mg_level **out, int nbox, const int (*lo)[3], const int (*n)
 int mg_level_set_beta(mg_level *lv, const double *beta_packed, void *stream);
 int mg_level_solve(mg_level *lv, const double *f_packed, double *phi_packed, double tol,
                    mg_stats *st, void *stream);
+int mg_level_solve_ex(mg_level *lv, const double *f_packed, double *phi_packed, double tol,
+                      int flags, mg_stats *st, void *stream);
 int mg_level_levels(const mg_level *lv, int *nlev);
 void mg_level_destroy(mg_level *lv);
 

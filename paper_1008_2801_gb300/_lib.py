@@ -28,6 +28,7 @@ MG_FP64, MG_MIXED = 0, 1
 MG_OPS_F64, MG_OPS_F32 = 0, 1
 MG_MAX_BOTTOM = 1024
 MG_MAX_HIST = 128
+MG_ZERO_GUESS = 1
 
 STATUS_NAMES = {
     MG_OK: "ok", MG_ERR_INVALID_ARG: "invalid_arg", MG_ERR_CUDA: "cuda", MG_ERR_OOM: "oom",
@@ -69,6 +70,8 @@ _SIGS = {
                          c_void_p]),
     "mg_solve_multi": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double,
                                ctypes.POINTER(mg_stats), c_void_p]),
+    "mg_solve_ex": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int,
+                            ctypes.POINTER(mg_stats), c_void_p]),
     "mg_adjoint": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
                            ctypes.POINTER(mg_stats), c_void_p]),
     "mg_levels": (c_int, [c_void_p, c_int_p, c_int_p]),
@@ -78,6 +81,8 @@ _SIGS = {
     "mg_level_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p]),
     "mg_level_set_beta": (c_int, [c_void_p] * 3),
     "mg_level_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p]),
+    "mg_level_solve_ex": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p,
+                                  c_void_p]),
     "mg_level_levels": (c_int, [c_void_p, c_void_p]),
     "mg_level_destroy": (None, [c_void_p]),
     "mg_level_intersections": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
@@ -88,6 +93,8 @@ _SIGS = {
     "mg_batch_set_beta": (c_int, [c_void_p, c_void_p, c_void_p]),
     "mg_solve_batched": (c_int, [c_void_p, c_void_p, c_void_p, c_double,
                                  ctypes.POINTER(mg_stats), c_void_p]),
+    "mg_solve_batched_ex": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int,
+                                    ctypes.POINTER(mg_stats), c_void_p]),
     "mg_batch_destroy": (None, [c_void_p]),
     "mg_profile_enable": (c_int, [c_void_p, c_int]),
     "mg_profile_read": (c_int, [c_void_p, ctypes.POINTER(mg_profile), c_int]),

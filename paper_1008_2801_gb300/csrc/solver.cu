@@ -839,6 +839,8 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         cudaMallocHost(&s->hactive, sizeof(int) * nbox) != cudaSuccess ||
         cudaMallocHost(&s->hside, sizeof(int) * (nbox + 1)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&s->ev_setup0) != cudaSuccess ||
         cudaEventCreate(&s->ev_setup1) != cudaSuccess) {
         solver_destroy(s);
@@ -873,6 +875,8 @@ void solver_destroy(Solver *s)
     if (s->hactive) cudaFreeHost(s->hactive);
     if (s->hside) cudaFreeHost(s->hside);
     if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_setup0) cudaEventDestroy(s->ev_setup0);
     if (s->ev_setup1) cudaEventDestroy(s->ev_setup1);
     delete s;
@@ -911,8 +915,10 @@ static double *stage_buf(Solver *s, int which)
 
 // Device view of a packed caller array: the pointer itself, or staging
 // buffer `which` (0..2) holding a copy (copy_in: host -> stage on the stream).
+// side: copy a host array in on the copy stream (the caller's stream waits
+// for it), so that it overlaps work already queued on st.
 static int device_view(Solver *s, const double *p, int which, bool copy_in, cudaStream_t st,
-                       const double **dv, bool *staged, long long count = -1)
+                       const double **dv, bool *staged, long long count = -1, bool side = false)
 {
     bool wrong = false;
     if (is_device_ptr(p, s->dev, &wrong)) {
@@ -924,8 +930,14 @@ static int device_view(Solver *s, const double *p, int which, bool copy_in, cuda
     CKS(ensure_stage(s));
     double *stage = stage_buf(s, which);
     if (count < 0) count = s->total;
-    if (copy_in)
+    if (copy_in && side) {
+        CK(cudaMemcpyAsync(stage, p, sizeof(double) * count, cudaMemcpyHostToDevice, s->copy));
+        CK(cudaEventRecord(s->ev_in, s->copy));
+        CK(cudaStreamWaitEvent(st, s->ev_in, 0));
+    } else if (copy_in) {
+        CK(cudaStreamWaitEvent(st, s->ev_in, 0));  // an earlier side copy into the buffer
         CK(cudaMemcpyAsync(stage, p, sizeof(double) * count, cudaMemcpyHostToDevice, st));
+    }
     *dv = stage;
     *staged = true;
     return MG_OK;
@@ -1479,7 +1491,7 @@ static int read_norms(Solver *s, const double *dev, double *host, cudaStream_t s
 }
 
 int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *st,
-                 cudaStream_t stream, bool zero_guess)
+                 cudaStream_t stream, bool zero_guess, bool side_copy)
 {
     if (!s || !f || !phi) return set_error(MG_ERR_INVALID_ARG, "NULL argument");
     if (!(tol > 0.0)) return set_error(MG_ERR_INVALID_ARG, "tol must be > 0");
@@ -1492,10 +1504,14 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     const bool mixed = s->has32;
     Hier<double> &H = s->h64;
 
-    // inputs into the level layout
+    // inputs into the level layout; host inputs come in on the copy stream
+    // when the staging buffers are idle (the previous staged call returned
+    // after synchronising), overlapping e.g. a set-up still running
+    const bool side_in = side_copy && s->stage_clean;
+    s->stage_clean = false;
     const double *fd = nullptr, *pd = nullptr;
     bool fst = false, pst = false;
-    CKS(device_view(s, f, 0, true, stream, &fd, &fst));
+    CKS(device_view(s, f, 0, true, stream, &fd, &fst, -1, side_in));
     CK(launch_pack(H.fine, s->doff, fd, 1, stream));
     // every wall Neumann: only the zero-mean part of f is in the range of A
     if (s->singular) CK(launch_remove_mean(H.fine, 0, s->partials, s->dmean, stream));
@@ -1504,7 +1520,7 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     if (zero_guess) {
         CK(launch_zero(H.fine, nullptr, stream));
     } else {
-        CKS(device_view(s, phi, 1, true, stream, &pd, &pst));
+        CKS(device_view(s, phi, 1, true, stream, &pd, &pst, -1, side_in));
         CK(launch_pack(H.fine, s->doff, pd, 0, stream));
     }
     // ||f|| and the starting residual r0 = f - A phi0.  In mixed precision
@@ -1750,6 +1766,7 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     }
     CK(cudaMemcpyAsync(s->hside + nbox, s->derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    s->stage_clean = true;
     (void)fst;
     (void)pst;
     s->kernels += (launch_counter() - k0) - (s->cap_kernels - c0);
@@ -1812,7 +1829,8 @@ int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, doub
     for (int r = 0; r < nrhs; ++r) {
         const size_t o = (size_t)r * s->total;
         int rc = solver_solve(s, g + o, dLdf + o, tol, st ? st + (size_t)r * s->nbox : nullptr,
-                              stream, true);
+                              stream, true, false);
+        s->stage_clean = false;  // the gradient below still reads staging buffers
         if (rc != MG_OK && rc != MG_ERR_NOT_CONVERGED && rc != MG_ERR_DIVERGED) return rc;
         worst = worse(worst, rc);
         // lambda sits in the level-0 phi arrays; phi of this right-hand side
@@ -1834,6 +1852,7 @@ int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, doub
     if (dbst)
         CK(cudaMemcpyAsync(dLdbeta, db, sizeof(double) * nbeta, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    s->stage_clean = true;
     if (worst != MG_OK) set_error(worst, "adjoint solve status %d", worst);
     return worst;
 }
@@ -1929,6 +1948,18 @@ int mg_solve(mg_ctx *ctx, const double *f, double *phi, double tol, mg_stats *st
     return solver_solve(ctx->s, f, phi, tol, st, (cudaStream_t)stream, false);
 }
 
+int mg_solve_ex(mg_ctx *ctx, int nrhs, const double *f, double *phi, double tol, int flags,
+                mg_stats *st, void *stream)
+{
+    if (!ctx || nrhs < 1 || !f || !phi)
+        return set_error(MG_ERR_INVALID_ARG, "NULL argument or nrhs < 1");
+    if (flags & ~MG_ZERO_GUESS) return set_error(MG_ERR_INVALID_ARG, "unknown flags");
+    const bool zero = (flags & MG_ZERO_GUESS) != 0;
+    if (nrhs == 1) return solver_solve(ctx->s, f, phi, tol, st, (cudaStream_t)stream, zero);
+    Solver *m = nullptr;
+    CKS(multi_solver(ctx, nrhs, (cudaStream_t)stream, &m));
+    return solver_solve(m, f, phi, tol, st, (cudaStream_t)stream, zero);
+}
 int mg_solve_multi(mg_ctx *ctx, int nrhs, const double *f, double *phi, double tol, mg_stats *st,
                    void *stream)
 {
@@ -2040,6 +2071,13 @@ int mg_solve_batched(mg_batch *b, const double *f, double *phi, double tol, mg_s
     if (!b) return set_error(MG_ERR_INVALID_ARG, "NULL batch");
     return solver_solve(b->s, f, phi, tol, st, (cudaStream_t)stream, false);
 }
+int mg_solve_batched_ex(mg_batch *b, const double *f, double *phi, double tol, int flags,
+                        mg_stats *st, void *stream)
+{
+    if (!b) return set_error(MG_ERR_INVALID_ARG, "NULL batch");
+    if (flags & ~MG_ZERO_GUESS) return set_error(MG_ERR_INVALID_ARG, "unknown flags");
+    return solver_solve(b->s, f, phi, tol, st, (cudaStream_t)stream, (flags & MG_ZERO_GUESS) != 0);
+}
 
 void mg_batch_destroy(mg_batch *b)
 {
@@ -2073,6 +2111,13 @@ int mg_level_solve(mg_level *lv, const double *f, double *phi, double tol, mg_st
 {
     if (!lv) return set_error(MG_ERR_INVALID_ARG, "NULL level");
     return solver_solve(lv->s, f, phi, tol, st, (cudaStream_t)stream, false);
+}
+int mg_level_solve_ex(mg_level *lv, const double *f, double *phi, double tol, int flags,
+                      mg_stats *st, void *stream)
+{
+    if (!lv) return set_error(MG_ERR_INVALID_ARG, "NULL level");
+    if (flags & ~MG_ZERO_GUESS) return set_error(MG_ERR_INVALID_ARG, "unknown flags");
+    return solver_solve(lv->s, f, phi, tol, st, (cudaStream_t)stream, (flags & MG_ZERO_GUESS) != 0);
 }
 
 int mg_level_levels(const mg_level *lv, int *nlev)

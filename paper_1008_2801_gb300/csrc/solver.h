@@ -82,6 +82,11 @@ struct Solver {
     int *hside = nullptr;          // pinned [nbox + 1]; the last is the error word's copy
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;  // packed staging
     cudaStream_t cap = nullptr;    // capture stream
+    // host inputs of a solve are copied in on this stream, concurrently with
+    // work already queued on the caller's stream (e.g. mg_set_beta's set-up)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_in = nullptr;   // the copy-in is done
+    bool stage_clean = false;      // the staging buffers are idle (last staged call returned OK)
     cudaEvent_t ev_setup0 = nullptr, ev_setup1 = nullptr;
     bool beta_set = false;
     float t_setup_ms = 0.f;
@@ -154,8 +159,10 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
 void solver_destroy(Solver *s);
 int solver_set_beta(Solver *s, const double *beta_packed, cudaStream_t st);
 // Solve every box; f/phi packed.  zero_guess ignores phi's input.
+// side_copy: host inputs may be copied in on the solver's copy stream
+// (false when the caller still has stage-buffer work queued on stream).
 int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *st,
-                 cudaStream_t stream, bool zero_guess);
+                 cudaStream_t stream, bool zero_guess, bool side_copy = true);
 int solver_adjoint(Solver *s, int nrhs, const double *phi, const double *g, double *dLdf,
                    double *dLdbeta, double tol, mg_stats *st, cudaStream_t stream);
 

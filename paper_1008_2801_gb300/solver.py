@@ -184,11 +184,13 @@ class Solver:
 
     def solve(self, f: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-10,
               raise_on=("invalid_arg", "cuda", "oom", "nonfinite", "diverged", "timeout",
-                        "unsupported"), bc_values=None):
+                        "unsupported"), bc_values=None, zero_guess: bool | None = None):
         """Solve A phi = f; returns (phi, stats).  phi (if given) is the initial
-        guess and is overwritten.  A leading batch dimension solves several
-        right-hand sides with the same beta.  bc_values (one box): non-zero
-        wall values, lifted into f first (see ``bc_lift``)."""
+        guess and is overwritten; with zero_guess (the default when phi is not
+        given) the iteration starts from 0 and phi is output only.  A leading
+        batch dimension solves several right-hand sides with the same beta.
+        bc_values (one box): non-zero wall values, lifted into f first (see
+        ``bc_lift``)."""
         _check_tensor(f, "f", device=self.device)
         if bc_values is not None:
             if f.numel() != self.numel:
@@ -197,17 +199,17 @@ class Solver:
         if f.numel() % self.numel:
             raise ValueError("f must hold whole boxes")
         nrhs = f.numel() // self.numel
+        if zero_guess is None:
+            zero_guess = phi is None
         if phi is None:
-            phi = torch.zeros_like(f)
+            phi = torch.empty_like(f)
         _check_tensor(phi, "phi", f.numel(), self.device)
         st = (_lib.mg_stats * nrhs)()
         L = _lib.load()
+        flags = _lib.MG_ZERO_GUESS if zero_guess else 0
         with torch.cuda.device(self.device):
-            if nrhs == 1:
-                rc = L.mg_solve(self._h, _ptr(f), _ptr(phi), float(tol), st, _stream_of(f))
-            else:
-                rc = L.mg_solve_multi(self._h, nrhs, _ptr(f), _ptr(phi), float(tol), st,
-                                      _stream_of(f))
+            rc = L.mg_solve_ex(self._h, nrhs, _ptr(f), _ptr(phi), float(tol), flags, st,
+                               _stream_of(f))
         stats = [_stats_dict(s) for s in st]
         if _lib.STATUS_NAMES.get(rc) in raise_on:
             raise MGError(rc, "mg_solve")
@@ -341,15 +343,19 @@ class BatchSolver:
                                                 _stream_of(beta_packed)), "mg_batch_set_beta")
         self._beta = beta_packed
 
-    def solve(self, f_packed, phi_packed=None, tol=1e-10):
+    def solve(self, f_packed, phi_packed=None, tol=1e-10, zero_guess=None):
+        """Returns (phi_packed, per-box stats); zero_guess as in Solver.solve."""
         _check_tensor(f_packed, "f", self.total, self.device)
+        if zero_guess is None:
+            zero_guess = phi_packed is None
         if phi_packed is None:
-            phi_packed = torch.zeros_like(f_packed)
+            phi_packed = torch.empty_like(f_packed)
         _check_tensor(phi_packed, "phi", self.total, self.device)
         st = (_lib.mg_stats * len(self.shapes))()
+        flags = _lib.MG_ZERO_GUESS if zero_guess else 0
         with torch.cuda.device(self.device):
-            rc = _lib.load().mg_solve_batched(self._h, _ptr(f_packed), _ptr(phi_packed),
-                                              float(tol), st, _stream_of(f_packed))
+            rc = _lib.load().mg_solve_batched_ex(self._h, _ptr(f_packed), _ptr(phi_packed),
+                                                 float(tol), flags, st, _stream_of(f_packed))
         if rc not in _SOFT:
             raise MGError(rc, "mg_solve_batched")
         return phi_packed, [_stats_dict(s) for s in st]
@@ -451,16 +457,20 @@ class LevelSolver:
             check(_lib.load().mg_level_set_beta(self._h, _ptr(beta_packed),
                                                 _stream_of(beta_packed)), "mg_level_set_beta")
 
-    def solve(self, f_packed, phi_packed=None, tol=1e-10):
-        """Returns (phi_packed, stats) with the union's residual history."""
+    def solve(self, f_packed, phi_packed=None, tol=1e-10, zero_guess=None):
+        """Returns (phi_packed, stats) with the union's residual history;
+        zero_guess as in Solver.solve."""
         _check_tensor(f_packed, "f", self.total, self.device)
+        if zero_guess is None:
+            zero_guess = phi_packed is None
         if phi_packed is None:
-            phi_packed = torch.zeros_like(f_packed)
+            phi_packed = torch.empty_like(f_packed)
         _check_tensor(phi_packed, "phi", self.total, self.device)
         st = (_lib.mg_stats * len(self.shapes))()
+        flags = _lib.MG_ZERO_GUESS if zero_guess else 0
         with torch.cuda.device(self.device):
-            rc = _lib.load().mg_level_solve(self._h, _ptr(f_packed), _ptr(phi_packed), float(tol),
-                                            st, _stream_of(f_packed))
+            rc = _lib.load().mg_level_solve_ex(self._h, _ptr(f_packed), _ptr(phi_packed),
+                                               float(tol), flags, st, _stream_of(f_packed))
         if rc not in _SOFT:
             raise MGError(rc, "mg_level_solve")
         return phi_packed, _stats_dict(st[0])
