@@ -105,7 +105,11 @@ typedef struct {
     int max_cycles;   /* V-cycles (FP64) or refinement steps (mixed); default 100 */
     int use_graph;    /* 1 (default): replay each V-cycle as a captured CUDA graph */
     int smoother;     /* 0 auto (default), 1 single-colour in-place passes,
-                         2 fused two-colour out-of-place sweeps */
+                         2 fused two-colour out-of-place sweeps (FP32 levels;
+                         FP64 levels always use passes: their f, 1/D and D
+                         are stored colour-split, each row's red cells
+                         before its black ones, so that a pass reads only
+                         its own colour of them) */
     int coarse_cells; /* levels of at most this many cells run inside one CTA
                          per box (the coarse end of the V-cycle as a single
                          launch); 0 default (4096 in FP32 V-cycles, 1024 in

@@ -74,7 +74,44 @@ struct Box {
     int zc;          // planes per CTA of the fused sweep (chosen on the host)
     int par;         // colour of local cell (0,0,0): (sum of the box's lower corner) % 2 on a
                      // coupled level (red = global i+j+k even), else 0
+    int rb;          // 1: f, invD and D are colour-split (see split_at); 0: natural layout
+    int cpar;        // par of the next-coarser level (its f index when rb)
 };
+
+// Element of cell (i, j, k) in a colour-split array (FP64 levels' f, 1/D and
+// D): each row keeps its cells of one colour together, red (i + j + k + par
+// even) at [0, P/2) and black at [P/2, P), each in x order, so that a pass
+// over one colour reads only that colour's sectors.  Guard positions are
+// never addressed this way.
+__host__ __device__ __forceinline__ long long split_at(int i, int j, int k, int par, int P,
+                                                       long long Q)
+{
+    return (long long)k * Q + (long long)j * P + (((i + j + k + par) & 1) ? (P >> 1) : 0) + (i >> 1);
+}
+
+// Colour-split f / invD / D in use: only FP64 levels split (a compile-time
+// false for FP32 boxes, so their kernels carry no split arithmetic).
+template <class T>
+__host__ __device__ __forceinline__ bool split_on(const Box<T> &B)
+{
+    return sizeof(T) == sizeof(double) && B.rb;
+}
+
+// Index of coarse cell (I, J, K) in the next-coarser level's f.
+template <class T>
+__host__ __device__ __forceinline__ long long cfidx(const Box<T> &B, int I, int J, int K)
+{
+    return split_on(B) ? split_at(I, J, K, B.cpar, B.cP, B.cQ)
+                : (long long)K * B.cQ + (long long)J * B.cP + I;
+}
+
+// Index of cell (i, j, k) in the box's f / invD / D arrays.
+template <class T>
+__host__ __device__ __forceinline__ long long fidx(const Box<T> &B, int i, int j, int k)
+{
+    return split_on(B) ? split_at(i, j, k, B.par, B.P, B.Q)
+                       : (long long)k * B.Q + (long long)j * B.P + i;
+}
 
 // Index spaces that kernels tile: all cells, red-black pairs along x
 // (ceil(nx/2) per row), the cells of the next-coarser level, pairs along x
@@ -148,6 +185,7 @@ struct SetupBox {
     int bc;                             // wall mask: bit w set = wall w Neumann
     const double *betaL;                // coupled level 0: beta in the level layout, guards
                                         // holding the neighbour box's beta or -1 (no neighbour)
+    int par, rb;                        // colour parity; invD and D colour-split (split_at)
 };
 typedef DescSet<SetupBox> SetupSet;
 

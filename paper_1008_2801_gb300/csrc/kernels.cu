@@ -39,12 +39,14 @@ __device__ __forceinline__ float fmadd<float>(float a, float b, float c) { retur
 // Gauss-Seidel value of cell c from its six neighbours in src:
 // (sum_f w_f src_nbr - f_c) / D_c, with -f_c as the start of the FMA chain
 // (six FMAs and one multiply: GB300's FP64 pipe is the narrow resource).
+// cf: the cell's element in f and invD (c, or its colour-split position).
 template <class T>
 __device__ __forceinline__ T gs_sum(const T *__restrict__ src, const T *__restrict__ f,
                                     const T *__restrict__ wx, const T *__restrict__ wy,
-                                    const T *__restrict__ wz, long long c, int P, long long Q)
+                                    const T *__restrict__ wz, long long c, long long cf, int P,
+                                    long long Q)
 {
-    T s = fmadd(wx[c], src[c - 1], -f[c]);
+    T s = fmadd(wx[c], src[c - 1], -f[cf]);
     s = fmadd(wx[c + 1], src[c + 1], s);
     s = fmadd(wy[c], src[c - P], s);
     s = fmadd(wy[c + P], src[c + P], s);
@@ -56,9 +58,9 @@ template <class T>
 __device__ __forceinline__ T gs_value(const T *__restrict__ src, const T *__restrict__ f,
                                       const T *__restrict__ invD, const T *__restrict__ wx,
                                       const T *__restrict__ wy, const T *__restrict__ wz,
-                                      long long c, int P, long long Q)
+                                      long long c, long long cf, int P, long long Q)
 {
-    return gs_sum<T>(src, f, wx, wy, wz, c, P, Q) * invD[c];
+    return gs_sum<T>(src, f, wx, wy, wz, c, cf, P, Q) * invD[cf];
 }
 
 // f_c - (A phi)_c = f_c + D_c phi_c - sum_f w_f phi_nbr, one FMA chain (seven
@@ -71,11 +73,11 @@ template <class T, bool HAS_D>
 __device__ __forceinline__ T residual_at(const T *__restrict__ phi, const T *__restrict__ f,
                                          const T *__restrict__ wx, const T *__restrict__ wy,
                                          const T *__restrict__ wz, const T *__restrict__ Dg,
-                                         long long c, int P, long long Q)
+                                         long long c, long long cf, int P, long long Q)
 {
     T a = wx[c], b = wx[c + 1], d = wy[c], e = wy[c + P], g = wz[c], h = wz[c + Q];
-    const T D = HAS_D ? Dg[c] : ((a + b) + (d + e)) + (g + h);
-    T s = fmadd(D, phi[c], f[c]);
+    const T D = HAS_D ? Dg[cf] : ((a + b) + (d + e)) + (g + h);
+    T s = fmadd(D, phi[c], f[cf]);
     s = fmadd(-a, phi[c - 1], s);
     s = fmadd(-b, phi[c + 1], s);
     s = fmadd(-d, phi[c - P], s);
@@ -109,7 +111,9 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass(BoxSet<T> S, const int *
     const int i = 2 * p.x + ((j + k + color + B.par) & 1);
     if (j >= ny || i >= nx) return;
     const long long c = (long long)k * Q + (long long)j * P + i;
-    B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, P, Q);
+    const long long cf =
+        split_on(B) ? (long long)k * Q + (long long)j * P + (color ? (P >> 1) : 0) + p.x : c;
+    B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, cf, P, Q);
 }
 
 // One colour out of place: dst = src with the cells of `color` updated (a
@@ -136,10 +140,13 @@ __device__ __forceinline__ void oop_pair(const Box<T> &B, int color, int from2, 
     const int odd = (j + k + color + B.par) & 1;   // the pair's cell of this colour
     if (x0 + odd < B.nx) {
         const long long c = c0 + odd;
-        const T sc = gs_sum<T>(src, B.f, B.wx, B.wy, B.wz, c, P, Q);
-        const T nv = sc * B.invD[c];
+        const long long cf =
+            split_on(B) ? (long long)k * Q + (long long)j * P + (color ? (P >> 1) : 0) + (x0 >> 1)
+                        : c;
+        const T sc = gs_sum<T>(src, B.f, B.wx, B.wy, B.wz, c, cf, P, Q);
+        const T nv = sc * B.invD[cf];
         if (norm) {
-            const T r = fmadd(B.D[c], odd ? pair.y : pair.x, -sc);
+            const T r = fmadd(B.D[cf], odd ? pair.y : pair.x, -sc);
             r2 = fma((double)r, (double)r, r2);
         }
         if (odd) pair.y = nv;
@@ -401,13 +408,14 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
                 for (int a = 0; a < 2; ++a) {
                     const long long q =
                         (long long)(2 * K + c) * Q + (long long)(2 * J + bb) * P + 2 * I + a;
-                    sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, q, P, Q);
+                    sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, q,
+                                              fidx(B, 2 * I + a, 2 * J + bb, 2 * K + c), P, Q);
                 }
         return sum;
     };
     const T sum = B.D ? children(std::true_type{}) : children(std::false_type{});
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
-    B.fc[cc] = sum * T(0.125);
+    B.fc[cfidx(B, I, J, K)] = sum * T(0.125);
     B.phic[cc] = T(0);
 }
 
@@ -434,14 +442,20 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
     // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c+par) even,
     // par the parity of the box's lower corner in the level's index space
     const long long o = (long long)(2 * K) * Q + (long long)(2 * J) * P + 2 * I;
+    // colour-split f and D: a red child (i, j, k) of this block sits at
+    // element I of row (j, k)'s red half
+    const long long of = (long long)(2 * K) * Q + (long long)(2 * J) * P + I;
     auto red4 = [&](auto has_d, auto odd) {
         constexpr bool HD = decltype(has_d)::value, OD = decltype(odd)::value;
         const long long c0 = OD ? o + 1 : o, c1 = OD ? o + P : o + P + 1,
                         c2 = OD ? o + Q : o + Q + 1, c3 = OD ? o + Q + P + 1 : o + Q + P;
-        T sum = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c0, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c1, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c2, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c3, P, Q);
+        const bool sp = split_on(B);
+        const long long f0 = sp ? of : c0, f1 = sp ? of + P : c1, f2 = sp ? of + Q : c2,
+                        f3 = sp ? of + Q + P : c3;
+        T sum = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c0, f0, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c1, f1, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c2, f2, P, Q);
+        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c3, f3, P, Q);
         return sum;
     };
     const T sum = B.D ? (B.par ? red4(std::true_type{}, std::true_type{})
@@ -449,7 +463,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
                       : (B.par ? red4(std::false_type{}, std::true_type{})
                                : red4(std::false_type{}, std::false_type{}));
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
-    B.fc[cc] = sum * T(0.125);
+    B.fc[cfidx(B, I, J, K)] = sum * T(0.125);
     B.phic[cc] = T(0);
 }
 
@@ -495,8 +509,9 @@ __global__ void __launch_bounds__(kThreads) k_residual_field(BoxSet<T> S)
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
     const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    B.phi2[c] = B.D ? residual_at<T, true>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q)
-                    : residual_at<T, false>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+    const long long cf = fidx(B, p.x, p.y, p.z);
+    B.phi2[c] = B.D ? residual_at<T, true>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, cf, B.P, B.Q)
+                    : residual_at<T, false>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, cf, B.P, B.Q);
 }
 
 // ------------------------------------------------------------- norms ----
@@ -524,9 +539,10 @@ __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const i
             const int x = mode == 2 ? 2 * p.x + ((p.y + k + B.par) & 1) : p.x;
             if (x >= B.nx) continue;
             const long long c = (long long)k * B.Q + (long long)p.y * B.P + x;
-            const T r = mode == 1 ? B.f[c]
-                                  : residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P,
-                                                       B.Q);
+            const long long cf = fidx(B, x, p.y, k);
+            const T r = mode == 1 ? B.f[cf]
+                                  : residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, cf,
+                                                       B.P, B.Q);
             v = fma((double)r, (double)r, v);
         }
     };
@@ -583,7 +599,7 @@ __global__ void __launch_bounds__(kThreads) k_bottom(BoxSet<T> S, const int *__r
     const int tid = threadIdx.y * kTX + threadIdx.x;
     for (int q = tid; q < n; q += kThreads) {
         const int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
-        fs[q] = B.f[(long long)k * B.Q + (long long)j * B.P + i];
+        fs[q] = B.f[fidx(B, i, j, k)];
     }
     __syncthreads();
     const int lane = threadIdx.x, warp = threadIdx.y;
@@ -626,7 +642,10 @@ __device__ __forceinline__ void cta_pass(const Box<T> &B, int color)
         const int i = 2 * p + ((j + k + color + B.par) & 1);
         if (i >= B.nx) continue;
         const long long c = (long long)k * B.Q + (long long)j * B.P + i;
-        B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, B.P, B.Q);
+        const long long cf =
+            split_on(B) ? (long long)k * B.Q + (long long)j * B.P + (color ? (B.P >> 1) : 0) + p
+                        : c;
+        B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, cf, B.P, B.Q);
     }
 }
 
@@ -663,13 +682,15 @@ __device__ __forceinline__ void cta_resid_restrict(const Box<T> &B)
                     for (int a = 0; a < 2; ++a) {
                         const long long g = (long long)(2 * K + c) * B.Q +
                                             (long long)(2 * J + bb) * B.P + 2 * I + a;
-                        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, g, B.P, B.Q);
+                        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, g,
+                                                  fidx(B, 2 * I + a, 2 * J + bb, 2 * K + c),
+                                                  B.P, B.Q);
                     }
             return sum;
         };
         const T sum = B.D ? children(std::true_type{}) : children(std::false_type{});
         const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
-        B.fc[cc] = sum * T(0.125);
+        B.fc[cfidx(B, I, J, K)] = sum * T(0.125);
         B.phic[cc] = T(0);
     }
 }
@@ -692,7 +713,7 @@ __device__ __forceinline__ void cta_bottom(const Box<T> &B, T *fs)
     const int nx = B.nx, ny = B.ny, n = nx * ny * B.nz;
     for (int q = threadIdx.x; q < n; q += CoarseThreads<T>::value) {
         const int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
-        fs[q] = B.f[(long long)k * B.Q + (long long)j * B.P + i];
+        fs[q] = B.f[fidx(B, i, j, k)];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -804,8 +825,8 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
             constexpr bool HD = decltype(has_d)::value;
             for (int k = z0; k < z1; ++k) {
                 const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
-                const double r =
-                    residual_at<double, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c, B.P, B.Q);
+                const double r = residual_at<double, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c,
+                                                         fidx(B, p.x, p.y, k), B.P, B.Q);
                 const float r32 = (float)r * cri;
                 E.f[c] = r32;
                 acc = fmaf(r32, r32, acc);
@@ -880,8 +901,8 @@ __global__ void __launch_bounds__(kThreads) k_pack(BoxSet<double> S, const long 
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
     const long long u = off[B.box] + ((long long)p.z * B.ny + p.y) * B.nx + p.x;
-    const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    (to_f ? B.f : B.phi)[c] = user[u];
+    if (to_f) B.f[fidx(B, p.x, p.y, p.z)] = user[u];
+    else B.phi[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] = user[u];
 }
 
 __global__ void __launch_bounds__(kThreads) k_unpack(BoxSet<double> S, const long long *__restrict__ off,
@@ -1027,28 +1048,29 @@ __device__ __forceinline__ void coarsen_at(int nx, int ny, int nz, int P, long l
 __device__ __forceinline__ void inv_diag_at(int P, long long Q, const double *__restrict__ wx,
                                             const double *__restrict__ wy,
                                             const double *__restrict__ wz, double *invD,
-                                            double *Dout, long long c)
+                                            double *Dout, long long c, long long cf)
 {
     const double D = ((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]);
-    invD[c] = 1.0 / D;
-    if (Dout) Dout[c] = D;
+    invD[cf] = 1.0 / D;
+    if (Dout) Dout[cf] = D;
 }
 
 // Every stored weight (and the inverse diagonal) at position (i, j, k) in
-// [0, nx] x [0, ny] x [0, nz], rounded to FP32.
+// [0, nx] x [0, ny] x [0, nz], rounded to FP32 (the FP32 copies are in the
+// natural layout; the FP64 invD is colour-split when rb).
 __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long long Q,
                                          const double *__restrict__ wx,
                                          const double *__restrict__ wy,
                                          const double *__restrict__ wz,
                                          const double *__restrict__ invD, float *wx32,
                                          float *wy32, float *wz32, float *invD32, int i, int j,
-                                         int k)
+                                         int k, int rb = 0, int par = 0)
 {
     const long long q = (long long)k * Q + (long long)j * P + i;
     if (j < ny && k < nz) wx32[q] = (float)wx[q];
     if (i < nx && k < nz) wy32[q] = (float)wy[q];
     if (i < nx && j < ny) wz32[q] = (float)wz[q];
-    if (i < nx && j < ny && k < nz) invD32[q] = (float)invD[q];
+    if (i < nx && j < ny && k < nz) invD32[q] = (float)invD[rb ? split_at(i, j, k, par, P, Q) : q];
 }
 
 // The calling CTA assembles M = -A (symmetric positive definite) densely in
@@ -1184,7 +1206,8 @@ __global__ void k_inv_diag(int nx, int ny, int nz, int P, long long Q, const dou
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= nx || j >= ny || k >= nz) return;
-    inv_diag_at(P, Q, wx, wy, wz, invD, Dout, (long long)k * Q + (long long)j * P + i);
+    const long long c = (long long)k * Q + (long long)j * P + i;
+    inv_diag_at(P, Q, wx, wy, wz, invD, Dout, c, c);
 }
 
 __global__ void k_round_f32(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
@@ -1235,13 +1258,15 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
                    p.x, p.y, p.z);
     else if (step == 2)
         inv_diag_at(B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.D,
-                    (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
+                    (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
+                    B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
+                         : (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
     else if (step == 4)
         face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.betaL, B.wx, B.wy,
                               B.wz, p.x, p.y, p.z);
     else
         round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
-                 B.invD32, p.x, p.y, p.z);
+                 B.invD32, p.x, p.y, p.z, B.rb, B.par);
 }
 
 // One CTA per box: the coarsest level's dense inverse.
@@ -1386,11 +1411,12 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(BoxSet<double> S, int
     const int b = find_box(ts, S.nbox, t);
     const Box<double> &B = S.boxes[b];
     TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
-    const double *x = field ? B.phi : B.f;
     double v = 0.0;
     if (p.x < B.nx && p.y < B.ny) {
         const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
-        for (int k = z0; k < z1; ++k) v += x[(long long)k * B.Q + (long long)p.y * B.P + p.x];
+        for (int k = z0; k < z1; ++k)
+            v += field ? B.phi[(long long)k * B.Q + (long long)p.y * B.P + p.x]
+                       : B.f[fidx(B, p.x, p.y, k)];
     }
     double s = block_sum(v);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
@@ -1425,8 +1451,8 @@ __global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int fie
     const Box<double> &B = S.boxes[b];
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
-    double *x = field ? B.phi : B.f;
-    x[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] -= mean[B.box];
+    if (field) B.phi[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] -= mean[B.box];
+    else B.f[fidx(B, p.x, p.y, p.z)] -= mean[B.box];
 }
 
 // ------------------------------------------------- preconditioned CG ----
@@ -1439,11 +1465,11 @@ __global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int fie
 // PcgScalars (kernels.h): rz = <r, z> of the previous iteration (0 before the
 // first), rzn = <r, z> of this one, pq = <p, A p>, beta, alpha; [nbox] each.
 
-// A p at cell c (the operator; D stored on FP64 levels)
+// A p at cell c (the operator; D stored on FP64 levels, element cf)
 __device__ __forceinline__ double apply_at(const double *__restrict__ p,
-                                           const Box<double> &B, long long c)
+                                           const Box<double> &B, long long c, long long cf)
 {
-    double s = fma(B.wx[c], p[c - 1], -B.D[c] * p[c]);
+    double s = fma(B.wx[c], p[c - 1], -B.D[cf] * p[c]);
     s = fma(B.wx[c + 1], p[c + 1], s);
     s = fma(B.wy[c], p[c - B.P], s);
     s = fma(B.wy[c + B.P], p[c + B.P], s);
@@ -1479,25 +1505,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg(BoxSet<double> S, const int *_
         const double be = op == 1 ? sc.beta[B.box] : 0.0, al = op == 3 ? sc.alpha[B.box] : 0.0;
         for (int k = z0; k < z1; ++k) {
             const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
+            const long long cf = fidx(B, p.x, p.y, k);
             if (op == 0) {
-                v = fma(B.f[c], B.phi[c], v);
+                v = fma(B.f[cf], B.phi[c], v);
             } else if (op == 1) {
                 P[c] = fma(be, P[c], B.phi[c]);
             } else if (op == 2) {
-                const double q = apply_at(P, B, c);
+                const double q = apply_at(P, B, c, cf);
                 Qa[c] = q;
                 v = fma(P[c], q, v);
             } else if (op == 3) {
                 B.phi2[c] = fma(al, P[c], B.phi2[c]);
-                const double r = fma(-al, Qa[c], B.f[c]);
-                B.f[c] = r;
+                const double r = fma(-al, Qa[c], B.f[cf]);
+                B.f[cf] = r;
                 B.phi[c] = 0.0;
                 v = fma(r, r, v);
             } else if (op == 4) {
                 B.phi2[c] = B.phi[c];
                 const double r = residual_at<double, true>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c,
-                                                           B.P, B.Q);
-                B.f[c] = r;
+                                                           cf, B.P, B.Q);
+                B.f[cf] = r;
                 P[c] = 0.0;
                 v = fma(r, r, v);
             } else {
@@ -1657,18 +1684,19 @@ __global__ void __launch_bounds__(kThreads) k_union_bottom(BoxSet<T> S, UnionBot
     if (active && !active[0]) return;
     const int n = U.n;
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    auto locate = [&](int q, int &b, long long &c) {
+    auto locate = [&](int q, int &b, long long &c, long long &cf) {
         b = find_box(U.off, U.nbox, q);
         const Box<T> &B = S.boxes[b];
         const int r = q - U.off[b];
         const int i = r % B.nx, j = (r / B.nx) % B.ny, k = r / (B.nx * B.ny);
         c = (long long)k * B.Q + (long long)j * B.P + i;
+        cf = fidx(B, i, j, k);
     };
     for (int q = tid; q < n; q += kThreads) {
         int b;
-        long long c;
-        locate(q, b, c);
-        fs[q] = S.boxes[b].f[c];
+        long long c, cf;
+        locate(q, b, c, cf);
+        fs[q] = S.boxes[b].f[cf];
     }
     __syncthreads();
     const int lane = threadIdx.x, warp = threadIdx.y;
@@ -1681,8 +1709,8 @@ __global__ void __launch_bounds__(kThreads) k_union_bottom(BoxSet<T> S, UnionBot
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) {
             int b;
-            long long c;
-            locate(r, b, c);
+            long long c, cf;
+            locate(r, b, c, cf);
             S.boxes[b].phi[c] = acc;
         }
     }

@@ -176,9 +176,16 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
     B.box = b;
     B.zc = kSweepZ;
     if (s->xmode) {
-        const auto &o = s->lo[b][l];
-        B.par = (((o[0] + o[1] + o[2]) % 2) + 2) % 2;
+        auto parity = [&](int lev) {
+            const auto &o = s->lo[b][lev];
+            return (((o[0] + o[1] + o[2]) % 2) + 2) % 2;
+        };
+        B.par = parity(l);
+        if (l + 1 < s->nlev[b]) B.cpar = parity(l + 1);
     }
+    // FP64 levels keep f, 1/D and D colour-split: a single-colour pass then
+    // reads only its own colour's sectors of them
+    B.rb = sizeof(T) == sizeof(double) ? 1 : 0;
     return B;
 }
 
@@ -352,8 +359,11 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
             // traffic it saves (measured 22% slower at 256^3)
             bool small = true;  // 32-bit offsets inside the fused sweep
             for (const auto &B : set) small = small && level_elems(B.nx, B.ny, B.nz) <= kSweepMaxElems;
-            const bool ok = score >= 0.7 && sizeof(T) == sizeof(float);
-            H.fused[l] = small && (s->opts.smoother == 2 || (s->opts.smoother == 0 && ok));
+            const bool ok = score >= 0.7;
+            // (FP64 levels never: their f and 1/D are colour-split, which
+            // the fused sweep does not read)
+            H.fused[l] = small && sizeof(T) == sizeof(float) &&
+                         (s->opts.smoother == 2 || (s->opts.smoother == 0 && ok));
             size_t moff = 0;
             if (H.fused[l] && tma && s->tma && plan_maps(set, blob, &moff))
                 map_offs->push_back({l, moff});  // else: plain-load sweeps on this level
@@ -725,6 +735,11 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         B.zc = kSweepZ;
         B.bc = s->bc;
         if (s->xmode && l == 0) B.betaL = L.phi;  // beta is staged in phi during set-up
+        B.rb = 1;                                  // FP64 invD and D colour-split
+        if (s->xmode) {
+            const auto &o = s->lo[b][l];
+            B.par = (((o[0] + o[1] + o[2]) % 2) + 2) % 2;
+        }
         if (l == s->nlev[b] - 1) {
             B.work = s->work + work_off[b];
             B.inv64 = s->h64.ainv[b];
