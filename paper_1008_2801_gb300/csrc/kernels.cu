@@ -1051,26 +1051,31 @@ __device__ __forceinline__ void inv_diag_at(int P, long long Q, const double *__
                                             double *Dout, long long c, long long cf)
 {
     const double D = ((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]);
-    invD[cf] = 1.0 / D;
+    if (invD) invD[cf] = 1.0 / D;   // NULL: mixed precision, whose FP64 levels never smooth
     if (Dout) Dout[cf] = D;
 }
 
 // Every stored weight (and the inverse diagonal) at position (i, j, k) in
 // [0, nx] x [0, ny] x [0, nz], rounded to FP32 (the FP32 copies are in the
-// natural layout; the FP64 invD is colour-split when rb).
+// natural layout; the FP64 invD and D are colour-split when rb).  Without an
+// FP64 invD the FP32 one is the FP32 reciprocal of the rounded D.
 __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long long Q,
                                          const double *__restrict__ wx,
                                          const double *__restrict__ wy,
                                          const double *__restrict__ wz,
                                          const double *__restrict__ invD, float *wx32,
                                          float *wy32, float *wz32, float *invD32, int i, int j,
-                                         int k, int rb = 0, int par = 0)
+                                         int k, int rb = 0, int par = 0,
+                                         const double *__restrict__ D = nullptr)
 {
     const long long q = (long long)k * Q + (long long)j * P + i;
     if (j < ny && k < nz) wx32[q] = (float)wx[q];
     if (i < nx && k < nz) wy32[q] = (float)wy[q];
     if (i < nx && j < ny) wz32[q] = (float)wz[q];
-    if (i < nx && j < ny && k < nz) invD32[q] = (float)invD[rb ? split_at(i, j, k, par, P, Q) : q];
+    if (i < nx && j < ny && k < nz) {
+        const long long cf = rb ? split_at(i, j, k, par, P, Q) : q;
+        invD32[q] = invD ? (float)invD[cf] : 1.0f / (float)D[cf];
+    }
 }
 
 // The calling CTA assembles M = -A (symmetric positive definite) densely in
@@ -1266,7 +1271,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
                               B.wz, p.x, p.y, p.z);
     else
         round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
-                 B.invD32, p.x, p.y, p.z, B.rb, B.par);
+                 B.invD32, p.x, p.y, p.z, B.rb, B.par, B.D);
 }
 
 // One CTA per box: the coarsest level's dense inverse.

@@ -707,7 +707,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         B.wx = L.wx;
         B.wy = L.wy;
         B.wz = L.wz;
-        B.invD = L.invD;
+        B.invD = s->has32 ? nullptr : L.invD;  // mixed: FP64 levels never smooth
         B.D = L.D;
         if (l + 1 < s->nlev[b]) {
             const LevelBufs<double> &C = s->h64.lv[b][l + 1];
@@ -1544,12 +1544,17 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     CK(launch_norm_partials(H.fine, nullptr, 1, s->partials, stream));
     CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnormf, nullptr, nullptr, stream));
     CK(combine(s, s->dnormf, stream));
-    CK(exch(s, H.fine, 0, stream));
-    if (!mixed) {
+    if (!mixed && zero_guess) {
+        // phi0 = 0: the starting residual is f itself
+        CK(cudaMemcpyAsync(s->dnorm, s->dnormf, sizeof(double) * nbox, cudaMemcpyDeviceToDevice,
+                           stream));
+    } else if (!mixed) {
+        CK(exch(s, H.fine, 0, stream));
         CK(launch_norm_partials(H.fine, nullptr, 0, s->partials, stream));
         CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnorm, nullptr, nullptr, stream));
         CK(combine(s, s->dnorm, stream));
     } else {
+        CK(exch(s, H.fine, 0, stream));
         CK(launch_zero(s->h32.fine, nullptr, stream));
         CK(launch_scales(nbox, nullptr, 1, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv, stream));
         CK(launch_refine_residual(H.fine, s->h32.fine, nullptr, s->sr_inv, s->partials, stream));
