@@ -336,6 +336,8 @@ int mg_profile_enable(mg_ctx *ctx, int on);
 int mg_profile_read(mg_ctx *ctx, mg_profile *out, int reset);
 int mg_batch_profile_enable(mg_batch *b, int on);
 int mg_batch_profile_read(mg_batch *b, mg_profile *out, int reset);
+int mg_level_profile_enable(mg_level *lv, int on);
+int mg_level_profile_read(mg_level *lv, mg_profile *out, int reset);
 
 const char *mg_error_string(int status);
 const char *mg_last_error(void);

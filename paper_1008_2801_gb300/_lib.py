@@ -100,6 +100,8 @@ _SIGS = {
     "mg_profile_read": (c_int, [c_void_p, ctypes.POINTER(mg_profile), c_int]),
     "mg_batch_profile_enable": (c_int, [c_void_p, c_int]),
     "mg_batch_profile_read": (c_int, [c_void_p, ctypes.POINTER(mg_profile), c_int]),
+    "mg_level_profile_enable": (c_int, [c_void_p, c_int]),
+    "mg_level_profile_read": (c_int, [c_void_p, ctypes.POINTER(mg_profile), c_int]),
     "mg_error_string": (ctypes.c_char_p, [c_int]),
     "mg_last_error": (ctypes.c_char_p, []),
     # mg_ops.h

@@ -1593,19 +1593,21 @@ __global__ void __launch_bounds__(1024) k_sum_finish(BoxSet<double> S, const int
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_exchange(BoxSet<T> S, const int *__restrict__ active,
-                                                       const ExchRec *__restrict__ rec)
+                                                       const ExchRec *__restrict__ rec, int second)
 {
     if (active && !active[0]) return;   // one decision for the whole level
     const ExchRec R = rec[blockIdx.x];
     const Box<T> &D = S.boxes[R.dst];
     const Box<T> &F = S.boxes[R.src];
+    T *__restrict__ dphi = second ? D.phi2 : D.phi;          // second: the phi2 arrays
+    const T *__restrict__ fphi = second ? F.phi2 : F.phi;
     const int n = R.ex * R.ey * R.ez;
     const int stride = kThreads * gridDim.y;  // a record's cells over gridDim.y CTAs
     for (int e = blockIdx.y * kThreads + threadIdx.y * kTX + threadIdx.x; e < n; e += stride) {
         const int a = e % R.ex, r = e / R.ex;
         const int bb = r % R.ey, c = r / R.ey;
-        D.phi[(long long)(R.dk + c) * D.Q + (long long)(R.dj + bb) * D.P + R.di + a] =
-            F.phi[(long long)(R.sk + c) * F.Q + (long long)(R.sj + bb) * F.P + R.si + a];
+        dphi[(long long)(R.dk + c) * D.Q + (long long)(R.dj + bb) * D.P + R.di + a] =
+            fphi[(long long)(R.sk + c) * F.Q + (long long)(R.sj + bb) * F.P + R.si + a];
     }
 }
 
@@ -2032,12 +2034,12 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
 
 template <class T>
 cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec *rec, int nrec,
-                            int max_cells, cudaStream_t st)
+                            int max_cells, cudaStream_t st, int second)
 {
     if (nrec == 0) return cudaSuccess;
     // about 4 cells per thread on the largest record (a 256^2 face: 64 CTAs)
     const int chunks = std::max(1, std::min(1024, (max_cells + 4 * kThreads - 1) / (4 * kThreads)));
-    k_exchange<T><<<dim3(nrec, chunks), block2d(), 0, st>>>(S, active, rec);
+    k_exchange<T><<<dim3(nrec, chunks), block2d(), 0, st>>>(S, active, rec, second);
     return counted(cudaGetLastError());
 }
 
@@ -2109,7 +2111,7 @@ cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgS
     template cudaError_t launch_coarse_vcycle<T>(const CoarseJob<T> *, int, const int *, int, int, \
                                                  cudaStream_t, int);                                \
     template cudaError_t launch_exchange<T>(const BoxSet<T> &, const int *, const ExchRec *, int,  \
-                                            int, cudaStream_t);                                         \
+                                            int, cudaStream_t, int);                                         \
     template cudaError_t launch_guard_fill<T>(const BoxSet<T> &, T, cudaStream_t);                 \
     template cudaError_t launch_union_bottom<T>(const BoxSet<T> &, const UnionBottom &, const T *, \
                                                 const int *, cudaStream_t);

@@ -174,7 +174,7 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
 // Copy each record's source patch into the destination box's guard cells.
 template <class T>
 cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec *rec, int nrec,
-                            int max_cells, cudaStream_t st);
+                            int max_cells, cudaStream_t st, int second = 0);
 // The guard cells of the six faces of every box of S = v (phi arrays).
 template <class T>
 cudaError_t launch_guard_fill(const BoxSet<T> &S, T v, cudaStream_t st);

@@ -690,9 +690,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
     // last (nu2 > 0, so black residuals vanish), single-colour passes on every
     // box's finest level, and the red-only residual reading
-    // (not with ghost exchanges: they fill phi's guard cells, not phi2's)
-    s->lookahead = !s->has32 && !s->pcg && !s->xmode && o.nu1 > 0 && o.nu2 > 0 &&
-                   !o.full_residual &&
+    s->lookahead = !s->has32 && !s->pcg && o.nu1 > 0 && o.nu2 > 0 && !o.full_residual &&
                    !s->h64.smooth.empty() && s->h64.smooth[0].nbox == nbox &&
                    !s->h64.fused[0];
     // set-up sets: every box that has level l; boxes that have l + 1; bottoms
@@ -1076,11 +1074,14 @@ static cudaError_t sweep_launch(Solver *s, const BoxSet<float> &S, const SweepMa
 
 // Coupled level: fill the guard cells of level lvl's boxes from their
 // neighbours (no-op otherwise).
+// second: fill phi2's guard cells (the out-of-place passes of the look-ahead).
 template <class T>
-static cudaError_t exch(Solver *s, const BoxSet<T> &S, int lvl, cudaStream_t st)
+static cudaError_t exch(Solver *s, const BoxSet<T> &S, int lvl, cudaStream_t st,
+                        bool second = false)
 {
     if (!s->xmode) return cudaSuccess;
-    return launch_exchange(S, s->active, s->xrec[lvl], s->nxrec[lvl], s->xmax[lvl], st);
+    return launch_exchange(S, s->active, s->xrec[lvl], s->nxrec[lvl], s->xmax[lvl], st,
+                           second ? 1 : 0);
 }
 
 // Coupled level: one norm for the union (no-op otherwise).
@@ -1138,6 +1139,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         int nu1 = s->opts.nu1;
         if (l == 0 && head_done) {
             int sl = prof_begin(s, MG_PROF_PASS, st);
+            if ((e = exch(s, S, 0, st, true)) != cudaSuccess) return e;
             if ((e = launch_rbgs_pass_oop(S, s->active, 1, 1, nullptr, st)) != cudaSuccess)
                 return e;
             prof_end(s, sl, st);
@@ -1202,11 +1204,14 @@ static cudaError_t enqueue_head64(Solver *s, cudaStream_t st)
 {
     const BoxSet<double> &S = s->h64.smooth[0];
     int sl = prof_begin(s, MG_PROF_PASS, st);
-    cudaError_t e = launch_rbgs_pass_oop(S, s->active, 0, 0, s->partials, st);
+    cudaError_t e = exch(s, S, 0, st);
+    if (e != cudaSuccess) return e;
+    e = launch_rbgs_pass_oop(S, s->active, 0, 0, s->partials, st);
     if (e != cudaSuccess) return e;
     prof_end(s, sl, st);
     sl = prof_begin(s, MG_PROF_NORM, st);
     e = launch_norm_finish(S, s->active, s->partials, s->dnorm, nullptr, nullptr, st, nullptr, 2);
+    if (e == cudaSuccess) e = combine(s, s->dnorm, st);
     prof_end(s, sl, st);
     return e;
 }
@@ -2211,6 +2216,16 @@ int mg_batch_profile_read(mg_batch *b, mg_profile *out, int reset)
 {
     if (!b) return set_error(MG_ERR_INVALID_ARG, "NULL batch");
     return profile_read(b->s, out, reset);
+}
+int mg_level_profile_enable(mg_level *lv, int on)
+{
+    if (!lv) return set_error(MG_ERR_INVALID_ARG, "NULL level");
+    return profile_enable(lv->s, on);
+}
+int mg_level_profile_read(mg_level *lv, mg_profile *out, int reset)
+{
+    if (!lv) return set_error(MG_ERR_INVALID_ARG, "NULL level");
+    return profile_read(lv->s, out, reset);
 }
 
 const char *mg_error_string(int s)

@@ -475,6 +475,16 @@ class LevelSolver:
             raise MGError(rc, "mg_level_solve")
         return phi_packed, _stats_dict(st[0])
 
+    def profile(self, on: bool = True):
+        check(_lib.load().mg_level_profile_enable(self._h, 1 if on else 0),
+              "mg_level_profile_enable")
+
+    def read_profile(self, reset: bool = False):
+        p = _lib.mg_profile()
+        check(_lib.load().mg_level_profile_read(self._h, ctypes.byref(p), 1 if reset else 0),
+              "mg_level_profile_read")
+        return _profile_dict(p)
+
     def close(self):
         if self._h:
             _lib.load().mg_level_destroy(self._h)
