@@ -37,7 +37,8 @@ METRIC = "MG solves: cells/s to 1e-10 rel residual, FP64 vs mixed; smoother HBM 
 TOL = 1e-10
 WORKLOAD = "stellar-profile beta (rho_c=1, core 0.3, 1% noise), f~U[-1,1] mean removed, 256^3, dx=1/256, Dirichlet walls, V(2,2) RBGS to 1e-10 rel residual"
 
-# compulsory bytes per cell of one launch (kernel table)
+# compulsory bytes per cell of one launch: each array a kernel must read or
+# write, counted once (a colour pass reads half of f and 1/D, writes half of phi)
 BYTES_PER_CELL = {("sweep", 8): 56, ("sweep", 4): 28, ("pass", 8): 44, ("pass", 4): 22,
                   ("restrict", 8): 41, ("restrict", 4): 20.5, ("refine", 8): 60}
 # FP64 flops per cell of one launch: a Gauss-Seidel update is 6 FMA + 1 mul =
