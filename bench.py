@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MG solves: cells/s to 1e-10 rel residual, FP64 vs mixed; smoother HBM GB/s"
 TOL = 1e-10
-WORKLOAD = "stellar-profile beta (rho_c=1, core 0.3, 1% noise), f~U[-1,1] mean removed, 256^3, dx=1/256, Dirichlet walls, V(2,2) RBGS to 1e-10 rel residual"
+WORKLOAD = ("stellar-profile beta (rho_c=1, core 0.3, 1% noise), f~U[-1,1] mean removed, "
+            "{n}^3, dx=1/{n}, Dirichlet walls, V(2,2) RBGS to 1e-10 rel residual")
 
 # compulsory bytes per cell of one launch: each array a kernel must read or
 # write, counted once (a colour pass reads half of f and 1/D, writes half of phi)
@@ -299,7 +300,7 @@ def run_gpu(args):
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "cells_per_gpu": N, "tol": TOL,
+           "config": {"workload": WORKLOAD.format(n=n), "cells_per_gpu": N, "tol": TOL,
                       "step": "mg_set_beta + mg_solve_ex (MG_ZERO_GUESS: phi0 = 0)", "cycles": st64["cycles"],
                       "rel_resid": st64["rel_resid"],
                       "l2": "inputs larger than L2 (working set ~1 GB > 129 MB)",
@@ -628,7 +629,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": world,
         "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": N, "tol": TOL},
+        "config": {"workload": WORKLOAD.format(n=n), "cells": N, "tol": TOL},
         "cpu_baseline": {"value": v, "unit": "cells/s", "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
