@@ -27,6 +27,41 @@ static inline cudaError_t counted(cudaError_t e)
     return e;
 }
 
+// Programmatic dependent launch.  The kernels of the solve loop are launched
+// with cudaLaunchAttributeProgrammaticStreamSerialization, so that a kernel's
+// CTAs can be scheduled while its predecessor's last CTAs drain (the cycle is
+// a chain of many short, dependent launches on the coarse levels); each such
+// kernel first waits for the predecessor grid to complete and its writes to
+// be visible.  The wait is a no-op in a plain launch.  MG_PDL=0 in the
+// environment launches them plainly.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+static bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *v = getenv("MG_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return counted(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
 // ------------------------------------------------------------ helpers ----
 
 template <class T>
@@ -99,6 +134,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_rbgs_pass(BoxSet<T> S, const int *__restrict__ active,
                                                         int color)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_PAIR];
     const int b = find_box(ts, S.nbox, t);
@@ -160,6 +196,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_rbgs_pass_oop(BoxSet<T> S,
                                                                const int *__restrict__ active,
                                                                int color, int from2)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_PAIR];
     const int b = find_box(ts, S.nbox, t);
@@ -180,6 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass_oop_norm(BoxSet<T> S,
                                                                     int color, int from2,
                                                                     double *__restrict__ partials)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_PCOLZ];
     const int b = find_box(ts, S.nbox, t);
@@ -264,6 +302,7 @@ template <class T>
 __global__ void __launch_bounds__(kSweepThreads, sizeof(T) == 4 ? 3 : 1)
 k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active, int src_is_phi2)
 {
+    pdl_wait();
     constexpr int W = 2 * kTX, SW = W + 2;            // smem row length
     constexpr int SROWS = kSweepTY + 2, SPLANE = SROWS * SW;
     __shared__ T red[4 * SPLANE];   // red values of 4 planes (slot = step % 4)
@@ -387,6 +426,7 @@ k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active, int src_is_phi2)
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const int *__restrict__ active)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
@@ -429,6 +469,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
                                                                  const int *__restrict__ active)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
@@ -474,6 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__restrict__ active)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
@@ -523,6 +565,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const int *__restrict__ active,
                                                             int mode, double *__restrict__ partials)
 {
+    pdl_wait();
     const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
     const int t = blockIdx.x;
     const int *ts = S.tstart[kind];
@@ -564,6 +607,7 @@ __global__ void __launch_bounds__(1024) k_norm_finish(BoxSet<T> S, const int *__
                                                       double *__restrict__ inv,
                                                       const double *__restrict__ mult, int kind)
 {
+    pdl_wait();
     __shared__ double wsum[32];
     const int b = blockIdx.x;
     const Box<T> &B = S.boxes[b];
@@ -734,6 +778,7 @@ __global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const
                                                                   const int *__restrict__ active,
                                                                   int nu1, int nu2, int post_first)
 {
+    pdl_wait();
     __shared__ CoarseJob<T> J;
     __shared__ T fs[MG_BOTTOM_CELLS];
     {
@@ -793,6 +838,7 @@ __global__ void __launch_bounds__(kThreads) k_refine_update(BoxSet<double> S64, 
                                                             const int *__restrict__ active,
                                                             const double *__restrict__ c_e)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S64.tstart[TK_CELL];
     const int b = find_box(ts, S64.nbox, t);
@@ -810,6 +856,7 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
                                                               const double *__restrict__ c_r_inv,
                                                               double *__restrict__ partials)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S64.tstart[TK_COLZ];
     const int b = find_box(ts, S64.nbox, t);
@@ -854,6 +901,7 @@ __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restri
                                                 int *__restrict__ active, JudgeState J,
                                                 cudaGraphConditionalHandle handle, int use_handle)
 {
+    pdl_wait();
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -894,6 +942,7 @@ __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restri
 __global__ void __launch_bounds__(kThreads) k_pack(BoxSet<double> S, const long long *__restrict__ off,
                                                    const double *__restrict__ user, int to_f)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_CELL];
     const int b = find_box(ts, S.nbox, t);
@@ -909,6 +958,7 @@ __global__ void __launch_bounds__(kThreads) k_unpack(BoxSet<double> S, const lon
                                                      double *__restrict__ user,
                                                      const int *__restrict__ side)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_CELL];
     const int b = find_box(ts, S.nbox, t);
@@ -924,6 +974,7 @@ __global__ void __launch_bounds__(kThreads) k_unpack(BoxSet<double> S, const lon
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_zero(BoxSet<T> S, const int *__restrict__ active)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_CELL];
     const int b = find_box(ts, S.nbox, t);
@@ -938,6 +989,7 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
                          const double *__restrict__ norm, const double *__restrict__ normf,
                          double *__restrict__ se, double *__restrict__ sr, double *__restrict__ sr_inv)
 {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
     if (init) {
@@ -1411,6 +1463,7 @@ __global__ void k_bc_lift(int nx, int ny, int nz, int P, long long Q, double inv
 __global__ void __launch_bounds__(kThreads) k_sum_partials(BoxSet<double> S, int field,
                                                            double *__restrict__ partials)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COLZ];
     const int b = find_box(ts, S.nbox, t);
@@ -1431,6 +1484,7 @@ __global__ void __launch_bounds__(1024) k_mean_finish(BoxSet<double> S,
                                                       const double *__restrict__ partials,
                                                       double *__restrict__ mean)
 {
+    pdl_wait();
     __shared__ double wsum[32];
     const int b = blockIdx.x;
     const Box<double> &B = S.boxes[b];
@@ -1450,6 +1504,7 @@ __global__ void __launch_bounds__(1024) k_mean_finish(BoxSet<double> S,
 __global__ void __launch_bounds__(kThreads) k_sub_mean(BoxSet<double> S, int field,
                                                        const double *__restrict__ mean)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_CELL];
     const int b = find_box(ts, S.nbox, t);
@@ -1497,6 +1552,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(BoxSet<double> S, const int *_
                                                   double *const *__restrict__ qv, PcgScalars sc,
                                                   double *__restrict__ partials)
 {
+    pdl_wait();
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COLZ];
     const int b = find_box(ts, S.nbox, t);
@@ -1547,6 +1603,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(BoxSet<double> S, const int *_
 // (0 on the first iteration), rz = rzn;  step 1: pq done -> alpha = rz / pq.
 __global__ void k_pcg_scalars(int nbox, const int *__restrict__ active, int step, PcgScalars sc)
 {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox || (active && !active[b])) return;
     if (step == 0) {
@@ -1565,6 +1622,7 @@ __global__ void __launch_bounds__(1024) k_sum_finish(BoxSet<double> S, const int
                                                      const double *__restrict__ partials,
                                                      double *__restrict__ out, int root)
 {
+    pdl_wait();
     __shared__ double wsum[32];
     const int b = blockIdx.x;
     const Box<double> &B = S.boxes[b];
@@ -1595,6 +1653,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_exchange(BoxSet<T> S, const int *__restrict__ active,
                                                        const ExchRec *__restrict__ rec, int second)
 {
+    pdl_wait();
     if (active && !active[0]) return;   // one decision for the whole level
     const ExchRec R = rec[blockIdx.x];
     const Box<T> &D = S.boxes[R.dst];
@@ -1687,6 +1746,7 @@ __global__ void __launch_bounds__(kThreads) k_union_bottom(BoxSet<T> S, UnionBot
                                                            const T *__restrict__ ainv,
                                                            const int *__restrict__ active)
 {
+    pdl_wait();
     __shared__ T fs[MG_BOTTOM_CELLS];
     if (active && !active[0]) return;
     const int n = U.n;
@@ -1727,6 +1787,7 @@ __global__ void __launch_bounds__(kThreads) k_union_bottom(BoxSet<T> S, UnionBot
 // norm[b]^2) for every box (a fixed-order sum by one thread).
 __global__ void k_norm_combine(int nbox, double *__restrict__ norm)
 {
+    pdl_wait();
     __shared__ double tot;
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -1747,21 +1808,19 @@ cudaError_t launch_rbgs_pass_oop(const BoxSet<T> &S, const int *active, int colo
 {
     if (partials) {
         if (S.ntiles[TK_PCOLZ] == 0) return cudaSuccess;
-        k_rbgs_pass_oop_norm<T><<<S.ntiles[TK_PCOLZ], block2d(), 0, st>>>(S, active, color, from2,
-                                                                          partials);
-    } else {
-        if (S.ntiles[TK_PAIR] == 0) return cudaSuccess;
-        k_rbgs_pass_oop<T><<<S.ntiles[TK_PAIR], block2d(), 0, st>>>(S, active, color, from2);
+        return pdl_launch(k_rbgs_pass_oop_norm<T>, dim3(S.ntiles[TK_PCOLZ]), block2d(), 0, st, S,
+                          active, color, from2, partials);
     }
-    return counted(cudaGetLastError());
+    if (S.ntiles[TK_PAIR] == 0) return cudaSuccess;
+    return pdl_launch(k_rbgs_pass_oop<T>, dim3(S.ntiles[TK_PAIR]), block2d(), 0, st, S, active,
+                      color, from2);
 }
 
 template <class T>
 cudaError_t launch_rbgs_pass(const BoxSet<T> &S, const int *active, int color, cudaStream_t st)
 {
     if (S.ntiles[TK_PAIR] == 0) return cudaSuccess;
-    k_rbgs_pass<T><<<S.ntiles[TK_PAIR], block2d(), 0, st>>>(S, active, color);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_rbgs_pass<T>, dim3(S.ntiles[TK_PAIR]), block2d(), 0, st, S, active, color);
 }
 
 template <class T>
@@ -1783,32 +1842,30 @@ cudaError_t launch_rbgs_sweep(const BoxSet<T> &S, const int *active, int src_is_
                               cudaStream_t st)
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
-    k_rbgs_sweep<T><<<S.ntiles[TK_SWEEP], dim3(kTX, kSweepWarps), 0, st>>>(S, active, src_is_phi2);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_rbgs_sweep<T>, dim3(S.ntiles[TK_SWEEP]), dim3(kTX, kSweepWarps), 0, st, S,
+                      active, src_is_phi2);
 }
 
 template <class T>
 cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    k_resid_restrict<T><<<S.ntiles[TK_COARSE], block2d(), 0, st>>>(S, active);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_resid_restrict<T>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S, active);
 }
 
 template <class T>
 cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    k_resid_restrict_red<T><<<S.ntiles[TK_COARSE], block2d(), 0, st>>>(S, active);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_resid_restrict_red<T>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S,
+                      active);
 }
 
 template <class T>
 cudaError_t launch_prolong(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    k_prolong<T><<<S.ntiles[TK_COARSE], block2d(), 0, st>>>(S, active);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_prolong<T>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S, active);
 }
 
 template <class T>
@@ -1825,8 +1882,8 @@ cudaError_t launch_norm_partials(const BoxSet<T> &S, const int *active, int mode
 {
     const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
     if (S.ntiles[kind] == 0) return cudaSuccess;
-    k_norm_partials<T><<<S.ntiles[kind], block2d(), 0, st>>>(S, active, mode, partials);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_norm_partials<T>, dim3(S.ntiles[kind]), block2d(), 0, st, S, active, mode,
+                      partials);
 }
 
 template <class T>
@@ -1836,8 +1893,8 @@ cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const doub
 {
     if (S.nbox == 0) return cudaSuccess;
     const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
-    k_norm_finish<T><<<S.nbox, 1024, 0, st>>>(S, active, partials, out, copy, inv, mult, kind);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_norm_finish<T>, dim3(S.nbox), dim3(1024), 0, st, S, active, partials, out,
+                      copy, inv, mult, kind);
 }
 
 template <class T>
@@ -1854,17 +1911,16 @@ cudaError_t launch_coarse_vcycle(const CoarseJob<T> *jobs, int njobs, const int 
                                  int nu2, cudaStream_t st, int post_first)
 {
     if (njobs == 0) return cudaSuccess;
-    k_coarse_vcycle<T><<<njobs, CoarseThreads<T>::value, 0, st>>>(jobs, active, nu1, nu2,
-                                                                  post_first);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_coarse_vcycle<T>, dim3(njobs), dim3(CoarseThreads<T>::value), 0, st, jobs,
+                      active, nu1, nu2, post_first);
 }
 
 cudaError_t launch_refine_update(const BoxSet<double> &S64, const BoxSet<float> &S32,
                                  const int *active, const double *c_e, cudaStream_t st)
 {
     if (S64.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_refine_update<<<S64.ntiles[TK_CELL], block2d(), 0, st>>>(S64, S32, active, c_e);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_refine_update, dim3(S64.ntiles[TK_CELL]), block2d(), 0, st, S64, S32,
+                      active, c_e);
 }
 
 cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float> &S32,
@@ -1872,50 +1928,46 @@ cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float
                                    cudaStream_t st)
 {
     if (S64.ntiles[TK_COLZ] == 0) return cudaSuccess;
-    k_refine_residual<<<S64.ntiles[TK_COLZ], block2d(), 0, st>>>(S64, S32, active, c_r_inv,
-                                                                  partials);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_refine_residual, dim3(S64.ntiles[TK_COLZ]), block2d(), 0, st, S64, S32,
+                      active, c_r_inv, partials);
 }
 
 cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int *active,
                          const JudgeState &J, cudaGraphConditionalHandle handle, int use_handle,
                          cudaStream_t st)
 {
-    k_judge<<<1, nbox < 1024 ? ((nbox + 31) / 32) * 32 : 1024, 0, st>>>(nbox, norm, normf, active,
-                                                                        J, handle, use_handle);
-    return counted(cudaGetLastError());
+    const int threads = nbox < 1024 ? ((nbox + 31) / 32) * 32 : 1024;
+    return pdl_launch(k_judge, dim3(1), dim3(threads), 0, st, nbox, norm, normf, active, J,
+                      handle, use_handle);
 }
 
 cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,
                         int to_f, cudaStream_t st)
 {
     if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_pack<<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, off, user, to_f);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_pack, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, off, user, to_f);
 }
 
 cudaError_t launch_unpack(const BoxSet<double> &S, const long long *off, double *user,
                           const int *side, cudaStream_t st)
 {
     if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_unpack<<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, off, user, side);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_unpack, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, off, user, side);
 }
 
 template <class T>
 cudaError_t launch_zero(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    k_zero<T><<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, active);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_zero<T>, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, active);
 }
 
 cudaError_t launch_scales(int nbox, const int *active, int init, const double *norm,
                           const double *normf, double *se, double *sr, double *sr_inv,
                           cudaStream_t st)
 {
-    k_scales<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, active, init, norm, normf, se, sr, sr_inv);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_scales, dim3((nbox + 127) / 128), dim3(128), 0, st, nbox, active, init,
+                      norm, normf, se, sr, sr_inv);
 }
 
 static inline dim3 grid3(int ex, int ey, int ez)
@@ -2022,14 +2074,12 @@ cudaError_t launch_remove_mean(const BoxSet<double> &S, int field, double *parti
                                cudaStream_t st)
 {
     if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
-    k_sum_partials<<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, field, partials);
-    cudaError_t e = counted(cudaGetLastError());
+    cudaError_t e = pdl_launch(k_sum_partials, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, field,
+                               partials);
     if (e != cudaSuccess) return e;
-    k_mean_finish<<<S.nbox, 1024, 0, st>>>(S, partials, mean);
-    e = counted(cudaGetLastError());
+    e = pdl_launch(k_mean_finish, dim3(S.nbox), dim3(1024), 0, st, S, partials, mean);
     if (e != cudaSuccess) return e;
-    k_sub_mean<<<S.ntiles[TK_CELL], block2d(), 0, st>>>(S, field, mean);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_sub_mean, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, field, mean);
 }
 
 template <class T>
@@ -2039,8 +2089,7 @@ cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec
     if (nrec == 0) return cudaSuccess;
     // about 4 cells per thread on the largest record (a 256^2 face: 64 CTAs)
     const int chunks = std::max(1, std::min(1024, (max_cells + 4 * kThreads - 1) / (4 * kThreads)));
-    k_exchange<T><<<dim3(nrec, chunks), block2d(), 0, st>>>(S, active, rec, second);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_exchange<T>, dim3(nrec, chunks), block2d(), 0, st, S, active, rec, second);
 }
 
 template <class T>
@@ -2062,14 +2111,13 @@ template <class T>
 cudaError_t launch_union_bottom(const BoxSet<T> &S, const UnionBottom &U, const T *ainv,
                                 const int *active, cudaStream_t st)
 {
-    k_union_bottom<T><<<(U.n + 31) / 32, block2d(), 0, st>>>(S, U, ainv, active);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_union_bottom<T>, dim3((U.n + 31) / 32), block2d(), 0, st, S, U, ainv,
+                      active);
 }
 
 cudaError_t launch_norm_combine(int nbox, double *norm, cudaStream_t st)
 {
-    k_norm_combine<<<1, 256, 0, st>>>(nbox, norm);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_norm_combine, dim3(1), dim3(256), 0, st, nbox, norm);
 }
 
 cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, double *const *pv,
@@ -2077,18 +2125,19 @@ cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, doubl
                        double *sum_out, cudaStream_t st)
 {
     if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
-    k_pcg<<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, active, op, pv, qv, sc, partials);
-    cudaError_t e = counted(cudaGetLastError());
+    cudaError_t e =
+        pdl_launch(k_pcg, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, active, op, pv, qv, sc,
+                   partials);
     if (e != cudaSuccess || op == 1 || op == 5 || !sum_out) return e;
-    k_sum_finish<<<S.nbox, 1024, 0, st>>>(S, active, partials, sum_out, op >= 3);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_sum_finish, dim3(S.nbox), dim3(1024), 0, st, S, active, partials, sum_out,
+                      op >= 3);
 }
 
 cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgScalars &sc,
                                cudaStream_t st)
 {
-    k_pcg_scalars<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, active, step, sc);
-    return counted(cudaGetLastError());
+    return pdl_launch(k_pcg_scalars, dim3((nbox + 127) / 128), dim3(128), 0, st, nbox, active,
+                      step, sc);
 }
 
 #define MG_INSTANTIATE(T)                                                                        \
