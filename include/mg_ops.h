@@ -143,8 +143,10 @@ int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy
  * sums live in a file-scope device array of 65536 doubles (512 KiB, held on
  * every GPU that loads the library until the process exits) instead of
  * caller scratch; it calls no cudaMalloc, cudaFree or allocating routine.
- * Limit: ceil(nx/32) * ceil(ny/8) * ceil(nz/16) <= 65536 (e.g. 512^3 uses
- * 32768); larger boxes return MG_ERR_INVALID_ARG before anything runs.
+ * Limit: column tiles <= 65536, a tile being 32 x 8 columns of 16 planes
+ * (ceil(nx/32) * ceil(ny/8) * ceil(nz/16) when nx is a multiple of 32, else
+ * ceil(nx*ny/256) * ceil(nz/16); e.g. 512^3 uses 32768); larger boxes return
+ * MG_ERR_INVALID_ARG before anything runs.
  * The first call on a device, with that device current, looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
  * stream capture.  Every call reuses the array and overwrites the slots it

@@ -145,11 +145,25 @@ inline __host__ __device__ void tile_extent(int kind, int nx, int ny, int nz, in
 
 inline __host__ __device__ int tile_rows(int kind) { return kind == TK_SWEEP ? kSweepTY : kTY; }
 
+// A row that does not fill whole warps (ex not a multiple of kTX, as in the
+// boxes of a batch with 48 or 96 cells a side) would leave lanes idle in
+// every tile, so such index spaces are tiled flat: a CTA takes kTX * rows
+// consecutive positions of a plane in row-major order (a warp may span two
+// rows).  The fused sweep and the set-up faces keep their 2D tiles.
+inline __host__ __device__ bool tile_flat(int kind, int ex)
+{
+    return kind != TK_SWEEP && kind != TK_FACE && kind != TK_CFACE && ex % kTX != 0;
+}
+
 inline __host__ __device__ int tiles_of(int kind, int nx, int ny, int nz, int zc = kSweepZ)
 {
     int ex, ey, ez;
     tile_extent(kind, nx, ny, nz, ex, ey, ez, zc);
     const int ty = tile_rows(kind);
+    if (tile_flat(kind, ex)) {
+        const long long per = (long long)kTX * ty;
+        return (int)(((long long)ex * ey + per - 1) / per) * ez;
+    }
     return ((ex + kTX - 1) / kTX) * ((ey + ty - 1) / ty) * ez;
 }
 
@@ -162,6 +176,7 @@ struct DescSet {
     const int *tstart[TK_NKIND];
     int ntiles[TK_NKIND];
     int nbox;
+    int flat;      // bit k: some box of the set tiles kind k flat (tile_flat)
 };
 template <class T>
 using BoxSet = DescSet<Box<T>>;
@@ -256,12 +271,26 @@ __device__ __forceinline__ int find_box(const int *__restrict__ tstart, int nbox
 struct TilePos {
     int x, y, z;
 };
+// FLAT = false: the caller knows that no box of its set is tiled flat (the
+// set's flat bit for the kind is clear), which keeps the flat decode out of
+// the kernel.
+template <bool FLAT = true>
 __device__ __forceinline__ TilePos tile_pos(int kind, int nx, int ny, int nz, int local,
                                             int zc = kSweepZ)
 {
     int ex, ey, ez;
     tile_extent(kind, nx, ny, nz, ex, ey, ez, zc);
     const int rows = tile_rows(kind);
+    if (FLAT && tile_flat(kind, ex)) {
+        const int per = kTX * rows;
+        const int tpp = (int)(((long long)ex * ey + per - 1) / per);   // tiles per plane
+        const int q = (local % tpp) * per + (int)threadIdx.y * kTX + (int)threadIdx.x;
+        TilePos p;
+        p.x = q % ex;
+        p.y = q / ex;      // ey or more past the plane's last position: no cell
+        p.z = local / tpp;
+        return p;
+    }
     int ntx = (ex + kTX - 1) / kTX, nty = (ey + rows - 1) / rows;
     int tx = local % ntx;
     local /= ntx;

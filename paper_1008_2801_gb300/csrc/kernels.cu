@@ -423,7 +423,7 @@ k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active, int src_is_phi2)
 
 // ------------------------------------------- residual + restriction ----
 
-template <class T>
+template <class T, bool FC>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const int *__restrict__ active)
 {
     pdl_wait();
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
     if (active && !active[B.box]) return;
     const int nx = B.nx, ny = B.ny, nz = B.nz, P = B.P;
     const long long Q = B.Q;
-    TilePos p = tile_pos(TK_COARSE, nx, ny, nz, t - ts[b]);
+    TilePos p = tile_pos<FC>(TK_COARSE, nx, ny, nz, t - ts[b]);
     const int I = p.x, J = p.y, K = p.z;
     if (I >= nx / 2 || J >= ny / 2) return;
     auto children = [&](auto has_d) {
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
 // 4 red children of each coarse cell (the black 4 count as zero): half the
 // stencil work of k_resid_restrict, the same coarse right-hand side to
 // rounding.  Valid only when the last operation on phi was a black pass.
-template <class T>
+template <class T, bool FC>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
                                                                  const int *__restrict__ active)
 {
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
     if (active && !active[B.box]) return;
     const int nx = B.nx, ny = B.ny, nz = B.nz, P = B.P;
     const long long Q = B.Q;
-    TilePos p = tile_pos(TK_COARSE, nx, ny, nz, t - ts[b]);
+    TilePos p = tile_pos<FC>(TK_COARSE, nx, ny, nz, t - ts[b]);
     const int I = p.x, J = p.y, K = p.z;
     if (I >= nx / 2 || J >= ny / 2) return;
     // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c+par) even,
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
 
 // One thread per coarse cell: its correction is added to the 8 children (two
 // rows of two planes, each child pair one vector store when nx allows).
-template <class T>
+template <class T, bool FC>
 __global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__restrict__ active)
 {
     pdl_wait();
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    TilePos p = tile_pos(TK_COARSE, B.nx, B.ny, B.nz, t - ts[b]);
+    TilePos p = tile_pos<FC>(TK_COARSE, B.nx, B.ny, B.nz, t - ts[b]);
     const int I = p.x, J = p.y, K = p.z;
     if (I >= B.nx / 2 || J >= B.ny / 2) return;
     const T e = B.phic[(long long)K * B.cQ + (long long)J * B.cP + I];
@@ -1850,14 +1850,21 @@ template <class T>
 cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    return pdl_launch(k_resid_restrict<T>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S, active);
+    if (S.flat & (1 << TK_COARSE))
+        return pdl_launch(k_resid_restrict<T, true>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st,
+                          S, active);
+    return pdl_launch(k_resid_restrict<T, false>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S,
+                      active);
 }
 
 template <class T>
 cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    return pdl_launch(k_resid_restrict_red<T>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S,
+    if (S.flat & (1 << TK_COARSE))
+        return pdl_launch(k_resid_restrict_red<T, true>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st,
+                          S, active);
+    return pdl_launch(k_resid_restrict_red<T, false>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S,
                       active);
 }
 
@@ -1865,7 +1872,11 @@ template <class T>
 cudaError_t launch_prolong(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    return pdl_launch(k_prolong<T>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S, active);
+    if (S.flat & (1 << TK_COARSE))
+        return pdl_launch(k_prolong<T, true>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st,
+                          S, active);
+    return pdl_launch(k_prolong<T, false>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S,
+                      active);
 }
 
 template <class T>

@@ -132,7 +132,7 @@ int run(const int n[3], const void *wx, const void *wy, const void *wz, const vo
     if (tiles > kNoallocTiles)
         return set_error(MG_ERR_INVALID_ARG,
                          "mg_op_residual_norm_noalloc: %lld column tiles exceed the static "
-                         "scratch of %d (ceil(nx/32)*ceil(ny/8)*ceil(nz/16) must be <= %d)",
+                         "scratch of %d (32 x 8 columns of 16 planes each; at most %d)",
                          tiles, kNoallocTiles, kNoallocTiles);
     double *part = nullptr;
     int rc = scratch_address(&part);

@@ -52,6 +52,9 @@ struct TempSet {
             h.ts[k][0] = 0;
             h.ts[k][1] = tiles_of(k, B.nx, B.ny, B.nz, B.zc);
             S.ntiles[k] = h.ts[k][1];
+            int ex, ey, ez;
+            tile_extent(k, B.nx, B.ny, B.nz, ex, ey, ez, B.zc);
+            if (tile_flat(k, ex)) S.flat |= 1 << k;
         }
         CKO(cudaMallocAsync(&mem, sizeof h, st));
         CKO(cudaMemcpyAsync(mem, &h, sizeof h, cudaMemcpyHostToDevice, st));

@@ -219,9 +219,13 @@ static SetPlan<D> plan_set(DescBlob &blob, DescSet<D> *target, const std::vector
     p.boxes_off = blob.put(boxes.data(), boxes.size() * sizeof(D));
     for (int k = 0; k < TK_NKIND; ++k) {
         std::vector<int> ts(boxes.size() + 1, 0);
-        for (size_t i = 0; i < boxes.size(); ++i)
-            ts[i + 1] = ts[i] + tiles_of(k, boxes[i].nx, boxes[i].ny, boxes[i].nz,
-                                         boxes[i].zc > 0 ? boxes[i].zc : kSweepZ);
+        for (size_t i = 0; i < boxes.size(); ++i) {
+            const int zc = boxes[i].zc > 0 ? boxes[i].zc : kSweepZ;
+            ts[i + 1] = ts[i] + tiles_of(k, boxes[i].nx, boxes[i].ny, boxes[i].nz, zc);
+            int ex, ey, ez;
+            tile_extent(k, boxes[i].nx, boxes[i].ny, boxes[i].nz, ex, ey, ez, zc);
+            if (tile_flat(k, ex)) target->flat |= 1 << k;
+        }
         target->ntiles[k] = ts.back();
         p.ts_off[k] = blob.put(ts.data(), ts.size() * sizeof(int));
     }
