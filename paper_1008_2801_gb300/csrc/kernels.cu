@@ -1143,11 +1143,12 @@ __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long lon
 // columns from `at` on (the box's cells in C order): diagonal = sum of the
 // six weights, -w to each neighbour inside the box.  Called by every thread
 // of the CTA.
+template <class R>
 __device__ __forceinline__ void assemble_box_block(int nx, int ny, int nz, int P, long long Q,
                                                    const double *__restrict__ wx,
                                                    const double *__restrict__ wy,
-                                                   const double *__restrict__ wz, double *a,
-                                                   int n, int at)
+                                                   const double *__restrict__ wz, R *a, int n,
+                                                   int at)
 {
     const int m = nx * ny * nz;
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
@@ -1155,29 +1156,33 @@ __device__ __forceinline__ void assemble_box_block(int nx, int ny, int nz, int P
         const long long c = (long long)k * Q + (long long)j * P + i;
         const double ww = wx[c], we = wx[c + 1], ws = wy[c], wn = wy[c + P], wd = wz[c],
                      wu = wz[c + Q];
-        double *row = a + (long long)(at + r) * n + at;
-        row[r] = ((ww + we) + (ws + wn)) + (wd + wu);
-        if (i > 0) row[r - 1] = -ww;
-        if (i < nx - 1) row[r + 1] = -we;
-        if (j > 0) row[r - nx] = -ws;
-        if (j < ny - 1) row[r + nx] = -wn;
-        if (k > 0) row[r - nx * ny] = -wd;
-        if (k < nz - 1) row[r + nx * ny] = -wu;
+        R *row = a + (long long)(at + r) * n + at;
+        row[r] = (R)(((ww + we) + (ws + wn)) + (wd + wu));
+        if (i > 0) row[r - 1] = (R)-ww;
+        if (i < nx - 1) row[r + 1] = (R)-we;
+        if (j > 0) row[r - nx] = (R)-ws;
+        if (j < ny - 1) row[r + nx] = (R)-wn;
+        if (k > 0) row[r - nx * ny] = (R)-wd;
+        if (k < nz - 1) row[r + nx * ny] = (R)-wu;
     }
 }
 
-__device__ __forceinline__ void gauss_jordan_cta(double *a, int n, bool singular, double *inv64,
-                                                 float *inv32, double *col);
+template <class R>
+__device__ __forceinline__ void gauss_jordan_cta(R *a, int n, bool singular, double *inv64,
+                                                 float *inv32, R *col);
 
+// The coarsest level's inverse in precision R (double: A^{-1} to inv64 and
+// its rounding to inv32; float, when no FP64 inverse is wanted: inv32 only).
+// a: n x n scratch of R; col: 2n of R (shared memory).
+template <class R>
 __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P, long long Q,
                                                    const double *__restrict__ wx,
                                                    const double *__restrict__ wy,
                                                    const double *__restrict__ wz, bool singular,
-                                                   double *a, double *inv64, float *inv32,
-                                                   double *col)
+                                                   R *a, double *inv64, float *inv32, R *col)
 {
     const int n = nx * ny * nz;
-    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = 0.0;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = R(0);
     __syncthreads();
     assemble_box_block(nx, ny, nz, P, Q, wx, wy, wz, a, n, 0);
     __syncthreads();
@@ -1186,46 +1191,58 @@ __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P
 
 // In-place Gauss-Jordan inverse of the n x n matrix a (M, symmetric positive
 // definite; with `singular` first shifted by c 1 1^T as described above),
-// written as A^{-1} = -M^{-1} to inv64 (and inv32 when given).
-__device__ __forceinline__ void gauss_jordan_cta(double *a, int n, bool singular, double *inv64,
-                                                 float *inv32, double *col)
+// written as A^{-1} = -M^{-1} to inv64 and/or inv32 (either may be NULL).
+// Pivots are taken in order, without exchanges (M is diagonally dominant or
+// positive definite), and only the upper triangle is kept: after pivots
+// 0..p an entry with exactly one index <= p is the negative of its mirror and
+// every other entry equals its mirror, so the lower triangle follows from
+// the upper one and each pivot costs n^2/2 updates instead of n^2 (the FP64
+// pipe of the single SM that inverts a box is the limit).  col: 2n of R.
+template <class R>
+__device__ __forceinline__ void gauss_jordan_cta(R *a, int n, bool singular, double *inv64,
+                                                 float *inv32, R *col)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    R *rowv = col + n;
     if (singular) {
         if (tid == 0) {
-            double tr = 0.0;
+            R tr = R(0);
             for (int r = 0; r < n; ++r) tr += a[(long long)r * n + r];
-            col[0] = tr / ((double)n * (double)n);
+            col[0] = tr / ((R)n * (R)n);
         }
         __syncthreads();
-        const double shift = col[0];
+        const R shift = col[0];
         __syncthreads();
         for (long long e = tid; e < (long long)n * n; e += nt) a[e] += shift;
         __syncthreads();
     }
     for (int p = 0; p < n; ++p) {
-        for (int i = tid; i < n; i += nt) col[i] = a[(long long)i * n + p];
+        // column p (the entries below the diagonal mirror those of row p)
+        for (int i = tid; i < n; i += nt)
+            col[i] = i <= p ? a[(long long)i * n + p] : a[(long long)p * n + i];
         __syncthreads();
-        const double piv = col[p];
-        for (int j = tid; j < n; j += nt) {
-            const double v = (j == p) ? 1.0 : a[(long long)p * n + j];
-            a[(long long)p * n + j] = v / piv;
-        }
+        const R ip = R(1) / col[p];
+        // new row p: a_pj / a_pp (a_pj for j < p is minus its stored mirror)
+        for (int j = tid; j < n; j += nt)
+            rowv[j] = j == p ? ip
+                             : (j > p ? a[(long long)p * n + j] : -a[(long long)j * n + p]) * ip;
         __syncthreads();
         for (int i = warp; i < n; i += nw) {
-            if (i == p) continue;
-            const double ci = col[i];
-            for (int j = lane; j < n; j += 32) {
-                const double v = (j == p) ? 0.0 : a[(long long)i * n + j];
-                a[(long long)i * n + j] = v - ci * a[(long long)p * n + j];
+            const R ci = col[i];
+            R *ar = a + (long long)i * n;
+            for (int j = i + lane; j < n; j += 32) {
+                if (i == p) ar[j] = rowv[j];                 // row p (j >= p; j = p: 1 / a_pp)
+                else if (j == p) ar[j] = -ci * ip;           // column p above the diagonal
+                else ar[j] -= ci * rowv[j];
             }
         }
         __syncthreads();
     }
     for (long long e = tid; e < (long long)n * n; e += nt) {
-        const double v = -a[e];
-        inv64[e] = v;
+        const int i = (int)(e / n), j = (int)(e % n);
+        const double v = -(double)(i <= j ? a[e] : a[(long long)j * n + i]);
+        if (inv64) inv64[e] = v;
         if (inv32) inv32[e] = (float)v;
     }
 }
@@ -1288,8 +1305,8 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
                                                          double *__restrict__ inv64,
                                                          float *__restrict__ inv32)
 {
-    __shared__ double col[MG_BOTTOM_CELLS];
-    bottom_inverse_cta(nx, ny, nz, P, Q, wx, wy, wz, singular != 0, a, inv64, inv32, col);
+    __shared__ double col[2 * MG_BOTTOM_CELLS];
+    bottom_inverse_cta<double>(nx, ny, nz, P, Q, wx, wy, wz, singular != 0, a, inv64, inv32, col);
 }
 
 // ---- every box of a level in one launch (the solver's set-up)
@@ -1326,13 +1343,21 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
                  B.invD32, p.x, p.y, p.z, B.rb, B.par, B.D);
 }
 
-// One CTA per box: the coarsest level's dense inverse.
+// One CTA per box: the coarsest level's dense inverse, in FP64 when an FP64
+// inverse is wanted, else (mixed precision, whose FP64 levels never solve)
+// in FP32 straight away.
 __global__ void __launch_bounds__(1024) k_setup_bottom(SetupSet S)
 {
-    __shared__ double col[MG_BOTTOM_CELLS];
+    __shared__ double col[2 * MG_BOTTOM_CELLS];
     const SetupBox &B = S.boxes[blockIdx.x];
-    bottom_inverse_cta(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, (B.bc & 63) == 63, B.work,
-                       B.inv64, B.inv32, col);
+    const bool singular = (B.bc & 63) == 63;
+    if (B.inv64)
+        bottom_inverse_cta<double>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular, B.work,
+                                   B.inv64, B.inv32, col);
+    else
+        bottom_inverse_cta<float>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
+                                  reinterpret_cast<float *>(B.work), nullptr, B.inv32,
+                                  reinterpret_cast<float *>(col));
 }
 
 // ----------------------------------------------------- projection steps ----
@@ -1697,7 +1722,7 @@ __global__ void __launch_bounds__(kThreads) k_guard_fill(BoxSet<T> S, T v)
 __global__ void __launch_bounds__(1024) k_union_inverse(SetupSet S, UnionBottom U, double *a,
                                                         double *inv64, float *inv32)
 {
-    __shared__ double col[MG_BOTTOM_CELLS];
+    __shared__ double col[2 * MG_BOTTOM_CELLS];
     const int n = U.n;
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = 0.0;
     __syncthreads();

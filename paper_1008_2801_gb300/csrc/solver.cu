@@ -744,7 +744,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         }
         if (l == s->nlev[b] - 1) {
             B.work = s->work + work_off[b];
-            B.inv64 = s->h64.ainv[b];
+            B.inv64 = s->has32 ? nullptr : s->h64.ainv[b];  // mixed: FP32 inverse only
             B.inv32 = s->has32 ? s->h32.ainv[b] : nullptr;
         }
         return B;
