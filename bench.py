@@ -556,7 +556,8 @@ def run_extra(dev, args):
     del hc
     for name, cb, cf, cdx in cases:
         res[name] = {}
-        for method, kw in (("vcycles", {}), ("pcg", {"krylov": True})):
+        for method, kw in (("vcycles", {}), ("pcg", {"krylov": True}),
+                           ("pcg_mixed", {"krylov": True, "precision": "mixed"})):
             s = Solver(tuple(cf.shape), cdx, device=dev, max_cycles=200, **kw)
 
             def kry_step():

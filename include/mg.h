@@ -130,8 +130,10 @@ typedef struct {
                          preconditioned by one symmetric V-cycle per iteration
                          (zero start, nu1 red-then-black sweeps going down,
                          nu2 = nu1 black-then-red sweeps coming up), for
-                         high-contrast beta.  FP64 only, independent boxes
-                         with Dirichlet or Neumann walls (not every wall
+                         high-contrast beta.  With MG_MIXED the V-cycle
+                         runs in FP32 on r / ||r|| (CG, its vectors and the
+                         residual stay FP64).  Independent boxes with
+                         Dirichlet or Neumann walls (not every wall
                          Neumann), no periodic axis, not on a coupled level;
                          otherwise mg_create returns UNSUPPORTED.  cycles in
                          mg_stats counts CG iterations; the solve ends at

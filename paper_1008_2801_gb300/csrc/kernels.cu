@@ -1624,6 +1624,33 @@ __global__ void __launch_bounds__(kThreads) k_pcg(BoxSet<double> S, const int *_
     }
 }
 
+// Mixed-precision preconditioner (the FP32 V-cycle applied to the FP64 r):
+// op 0: the FP32 right-hand side r / ||r|| and a zero FP32 start;
+// op 1: z = ||r|| e, the FP32 solution scaled back into the FP64 phi.
+// nrm: ||r|| per box (the last CG update's, or the start's).
+__global__ void __launch_bounds__(kThreads) k_pcg_mixed(BoxSet<double> S64, BoxSet<float> S32,
+                                                        const int *__restrict__ active, int op,
+                                                        const double *__restrict__ nrm)
+{
+    pdl_wait();
+    const int t = blockIdx.x;
+    const int *ts = S64.tstart[TK_CELL];
+    const int b = find_box(ts, S64.nbox, t);
+    const Box<double> &B = S64.boxes[b];
+    const Box<float> &E = S32.boxes[b];
+    if (active && !active[B.box]) return;
+    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
+    if (p.x >= B.nx || p.y >= B.ny) return;
+    const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
+    const double s = nrm[B.box];
+    if (op == 0) {
+        E.f[c] = s > 0.0 ? (float)(B.f[fidx(B, p.x, p.y, p.z)] / s) : 0.0f;
+        E.phi[c] = 0.0f;
+    } else {
+        B.phi[c] = s * (double)E.phi[c];
+    }
+}
+
 // Per-box scalars from finished sums.  step 0: rzn done -> beta = rzn / rz
 // (0 on the first iteration), rz = rzn;  step 1: pq done -> alpha = rz / pq.
 __global__ void k_pcg_scalars(int nbox, const int *__restrict__ active, int step, PcgScalars sc)
@@ -2167,6 +2194,14 @@ cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, doubl
     if (e != cudaSuccess || op == 1 || op == 5 || !sum_out) return e;
     return pdl_launch(k_sum_finish, dim3(S.nbox), dim3(1024), 0, st, S, active, partials, sum_out,
                       op >= 3);
+}
+
+cudaError_t launch_pcg_mixed(const BoxSet<double> &S64, const BoxSet<float> &S32, const int *active,
+                             int op, const double *nrm, cudaStream_t st)
+{
+    if (S64.ntiles[TK_CELL] == 0) return cudaSuccess;
+    return pdl_launch(k_pcg_mixed, dim3(S64.ntiles[TK_CELL]), block2d(), 0, st, S64, S32, active,
+                      op, nrm);
 }
 
 cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgScalars &sc,

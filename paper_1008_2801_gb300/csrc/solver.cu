@@ -461,9 +461,9 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (o.krylov) {
         bool all_neumann = true;
         for (int d = 0; d < 3; ++d) all_neumann = all_neumann && ((bc >> (2 * d)) & 3) == 3;
-        if (o.precision != MG_FP64 || coupled || periodic || all_neumann)
+        if (coupled || periodic || all_neumann)
             return set_error(MG_ERR_UNSUPPORTED,
-                             "krylov = 1 needs FP64, independent boxes, no periodic axis and a "
+                             "krylov = 1 needs independent boxes, no periodic axis and a "
                              "Dirichlet wall");
         if (o.nu1 != o.nu2 || o.nu1 < 1)
             return set_error(MG_ERR_UNSUPPORTED,
@@ -1340,8 +1340,18 @@ static cudaError_t enqueue_body32(Solver *s, cudaStream_t st, cudaGraphCondition
 // negative definite; the signs cancel in alpha and beta.
 static cudaError_t enqueue_pcg(Solver *s, cudaStream_t st)
 {
-    cudaError_t e = enqueue_vcycle(s, s->h64, st, false, true);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (s->has32) {
+        // mixed: the symmetric V-cycle in FP32 on r / ||r||, scaled back
+        if ((e = launch_pcg_mixed(s->h64.fine, s->h32.fine, s->active, 0, s->dnorm, st)) !=
+                cudaSuccess ||
+            (e = enqueue_vcycle(s, s->h32, st, false, true)) != cudaSuccess ||
+            (e = launch_pcg_mixed(s->h64.fine, s->h32.fine, s->active, 1, s->dnorm, st)) !=
+                cudaSuccess)
+            return e;
+    } else if ((e = enqueue_vcycle(s, s->h64, st, false, true)) != cudaSuccess) {
+        return e;
+    }
     const BoxSet<double> &F = s->h64.fine;
     const int sl = prof_begin(s, MG_PROF_KRYLOV, st);
     if ((e = launch_pcg(F, s->active, 0, s->pcg_p, s->pcg_q, s->sc, s->partials, s->sc.rzn, st)) !=
@@ -1617,8 +1627,8 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
         // declares converged is checked against its true residual f - A x,
         // and restarts from it (at most 3 times) if that is above tol.
         if (any) {
-            CK(launch_pcg(H.fine, nullptr, 4, s->pcg_p, s->pcg_q, s->sc, s->partials, nullptr,
-                          stream));
+            CK(launch_pcg(H.fine, nullptr, 4, s->pcg_p, s->pcg_q, s->sc, s->partials, s->dnorm,
+                          stream));   // ||r0|| (the mixed preconditioner's first scale)
             CK(launch_zero(H.fine, nullptr, stream));
             CK(cudaMemsetAsync(s->sc.rz, 0, sizeof(double) * nbox, stream));
             for (int b = 0; b < nbox; ++b) side[b] = 1;

@@ -120,8 +120,9 @@ class Solver:
     precision: "fp64" (everything FP64) or "mixed" (FP32 V-cycles inside an
     FP64 iterative-refinement loop).  bc: wall mask or D/N string (see the
     module docstring).  krylov: conjugate gradients preconditioned by one
-    symmetric V-cycle per iteration instead of plain V-cycles (FP64, for
-    high-contrast beta).  Not thread-safe.
+    symmetric V-cycle per iteration instead of plain V-cycles, for
+    high-contrast beta (with "mixed" the V-cycle runs in FP32, CG in FP64).
+    Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,

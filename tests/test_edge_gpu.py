@@ -32,8 +32,6 @@ def _t(a, dev):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_degenerate_shapes(cuda_device, shape, precision, krylov):
-    if krylov and precision == "mixed":
-        pytest.skip("krylov is FP64 only")
     beta, f, h = _case(shape, 50)
     with Solver(shape, h, precision=precision, device=cuda_device, krylov=krylov) as s:
         s.set_beta(_t(beta, cuda_device))

@@ -129,9 +129,41 @@ def test_several_right_hand_sides(cuda_device):
         _check(beta, fs[k], h, phi[k], sts[k])
 
 
+@pytest.mark.parametrize("contrast", [None, 1e4, 1e6])
+def test_mixed_precision_preconditioner(cuda_device, contrast):
+    # CG and its vectors in FP64, the symmetric V-cycle in FP32 on r / ||r||:
+    # the same solution in at most half again as many iterations
+    beta, f, h = _case((32, 32, 64), 50, contrast)
+    phi, st = _solve(beta, f, h, cuda_device, precision="mixed")
+    assert st["status"] == "ok", st
+    ref, info = O.pcg_solve(beta, f, h, tol=1e-13, maxit=400)
+    assert np.linalg.norm(phi - ref) <= 1e-9 * np.linalg.norm(ref)
+    r = O.residual(O.face_beta(beta), h, f, phi)
+    assert O.norm2(r) <= TOL * 1.01 * O.norm2(f)
+    _, st64 = _solve(beta, f, h, cuda_device)
+    # an FP32 cycle is symmetric and linear only to FP32 rounding, which CG
+    # feels more as beta's contrast grows (1e6: about a third more iterations)
+    assert st["cycles"] <= st64["cycles"] * 1.5 + 2, (st["cycles"], st64["cycles"])
+
+
+def test_mixed_batched_boxes(cuda_device):
+    shapes = [(16, 32, 24), (32, 32, 32), (8, 16, 64)]
+    cases = [_case(s, 60 + i, 1e3) for i, s in enumerate(shapes)]
+    h = cases[0][2]
+    with BatchSolver(shapes, h, device=cuda_device, krylov=True, precision="mixed",
+                     max_cycles=400) as b:
+        b.set_beta(b.pack([_t(c[0], cuda_device) for c in cases]))
+        phi, st = b.solve(b.pack([_t(c[1], cuda_device) for c in cases]), tol=TOL)
+        parts = [p.cpu().numpy() for p in b.unpack(phi)]
+    for (beta, f, _), p, s in zip(cases, parts, st):
+        assert s["status"] == "ok", s
+        ref, _ = O.pcg_solve(beta, f, h, tol=1e-13, maxit=400)
+        assert np.linalg.norm(p - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
 def test_unsupported_uses(cuda_device):
     shape = (8, 8, 8)
-    for kw in ({"precision": "mixed"}, {"bc": 63}, {"bc": 64}, {"nu1": 2, "nu2": 1}):
+    for kw in ({"bc": 63}, {"bc": 64}, {"nu1": 2, "nu2": 1}):
         with pytest.raises(MGError) as e:
             Solver(shape, 0.1, device=cuda_device, krylov=True, **kw)
         assert e.value.name == "unsupported", kw
