@@ -140,7 +140,9 @@ typedef struct {
                          tol, divergence or max_cycles (the rule that stops
                          V-cycles after 5 cycles without a 10% gain does
                          not apply: a CG residual is not monotone). */
-    int reserved[5];
+    int max_norm;     /* 1: also report rel_resid_max in mg_stats (one more
+                         pass over the level after the solve); 0 (default) */
+    int reserved[4];
 } mg_opts;
 
 typedef struct {
@@ -152,6 +154,8 @@ typedef struct {
     double hist[MG_MAX_HIST];  /* rel_resid after cycle c (hist[0] = rel_resid0) */
     float t_setup_ms;          /* mg_set_beta wall time of the last set-up */
     float t_solve_ms;          /* wall time of this call */
+    double rel_resid_max;      /* max |f - A phi| / max |f| at return (opts.max_norm = 1;
+                                  else 0) */
 } mg_stats;
 
 /* Fill *opts with the defaults above. */

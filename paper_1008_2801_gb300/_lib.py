@@ -41,14 +41,14 @@ class mg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("max_cycles", c_int),
                 ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
                 ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
-                ("krylov", c_int), ("reserved", c_int * 5)]
+                ("krylov", c_int), ("max_norm", c_int), ("reserved", c_int * 4)]
 
 
 class mg_stats(ctypes.Structure):
     _fields_ = [("cycles", c_int), ("status", c_int), ("norm_f", c_double),
                 ("rel_resid0", c_double), ("rel_resid", c_double),
                 ("hist", c_double * MG_MAX_HIST), ("t_setup_ms", ctypes.c_float),
-                ("t_solve_ms", ctypes.c_float)]
+                ("t_solve_ms", ctypes.c_float), ("rel_resid_max", c_double)]
 
 
 MG_PROF_NKIND = 16

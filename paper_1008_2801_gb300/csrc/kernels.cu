@@ -597,6 +597,64 @@ __global__ void __launch_bounds__(kThreads) k_norm_partials(BoxSet<T> S, const i
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = s;
 }
 
+// Max norms for the solve's statistics (FP64 level 0): field 0 max |f|,
+// field 1 max |f - A phi| with phi from phi2 for the boxes whose side flag is
+// set.  Per TK_COLZ tile, then one CTA per box takes the max over its tiles.
+__global__ void __launch_bounds__(kThreads) k_max_partials(BoxSet<double> S,
+                                                           const int *__restrict__ side,
+                                                           int field, double *__restrict__ partials)
+{
+    const int t = blockIdx.x;
+    const int *ts = S.tstart[TK_COLZ];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<double> &B = S.boxes[b];
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
+    const double *phi = (side && side[B.box]) ? B.phi2 : B.phi;
+    double v = 0.0;
+    if (p.x < B.nx && p.y < B.ny) {
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+        for (int k = z0; k < z1; ++k) {
+            const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
+            const long long cf = fidx(B, p.x, p.y, k);
+            const double r =
+                field == 0 ? B.f[cf]
+                           : residual_at<double, true>(phi, B.f, B.wx, B.wy, B.wz, B.D, c, cf,
+                                                       B.P, B.Q);
+            v = fmax(v, fabs(r));
+        }
+    }
+    __shared__ double wmax[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    if ((tid & 31) == 0) wmax[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, wmax[w]);
+        partials[t] = m;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_max_finish(BoxSet<double> S,
+                                                     const double *__restrict__ partials,
+                                                     double *__restrict__ out)
+{
+    __shared__ double wmax[32];
+    const int b = blockIdx.x;
+    const Box<double> &B = S.boxes[b];
+    const int *ts = S.tstart[TK_COLZ];
+    double m = 0.0;
+    for (int q = ts[b] + (int)threadIdx.x; q < ts[b + 1]; q += 1024) m = fmax(m, partials[q]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < 32; ++w) r = fmax(r, wmax[w]);
+        out[B.box] = r;
+    }
+}
+
 // One CTA of 1024 threads per box: thread q adds partials q, q + 1024, ...
 // in order, then a fixed shuffle tree and an ordered sum of the 32 warps.
 template <class T>
@@ -2194,6 +2252,17 @@ cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, doubl
     if (e != cudaSuccess || op == 1 || op == 5 || !sum_out) return e;
     return pdl_launch(k_sum_finish, dim3(S.nbox), dim3(1024), 0, st, S, active, partials, sum_out,
                       op >= 3);
+}
+
+cudaError_t launch_max_norm(const BoxSet<double> &S, const int *side, int field,
+                            double *partials, double *out, cudaStream_t st)
+{
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    k_max_partials<<<S.ntiles[TK_COLZ], block2d(), 0, st>>>(S, side, field, partials);
+    cudaError_t e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+    k_max_finish<<<S.nbox, 1024, 0, st>>>(S, partials, out);
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_pcg_mixed(const BoxSet<double> &S64, const BoxSet<float> &S32, const int *active,

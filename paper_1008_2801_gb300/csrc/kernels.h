@@ -199,6 +199,10 @@ cudaError_t launch_pcg(const BoxSet<double> &S, const int *active, int op, doubl
                        double *const *qv, const PcgScalars &sc, double *partials,
                        double *sum_out, cudaStream_t st);
 // step 0: beta = rzn / rz (0 first), rz = rzn; step 1: alpha = rz / pq.
+// out[box] = max |f| (field 0) or max |f - A phi| (field 1; phi2 where
+// side[box] is set) over the box's level-0 cells.
+cudaError_t launch_max_norm(const BoxSet<double> &S, const int *side, int field,
+                            double *partials, double *out, cudaStream_t st);
 // Mixed precision: op 0: FP32 f = r / nrm, FP32 phi = 0; op 1: FP64 phi =
 // nrm * FP32 phi (the preconditioned residual z).
 cudaError_t launch_pcg_mixed(const BoxSet<double> &S64, const BoxSet<float> &S32, const int *active,

@@ -1793,6 +1793,19 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     if (s->singular) CK(launch_remove_mean(H.fine, 1, s->partials, s->dmean, stream));
     for (int b = 0; b < nbox; ++b) s->hside[b] = side[b];
     CK(cudaMemcpyAsync(s->dside, s->hside, sizeof(int) * nbox, cudaMemcpyHostToDevice, stream));
+    // max-norm statistics: max |f - A phi| / max |f| of the returned solution
+    const bool want_max = s->opts.max_norm && st;
+    if (want_max) {
+        if (s->pcg) CK(launch_pack(H.fine, s->doff, fd, 1, stream));  // f held CG's residual
+        if (s->xmode)
+            CK(launch_exchange(H.fine, nullptr, s->xrec[0], s->nxrec[0], s->xmax[0], stream));
+        CK(launch_max_norm(H.fine, s->dside, 0, s->partials, s->dmean, stream));
+        CK(launch_max_norm(H.fine, s->dside, 1, s->partials, s->dinv, stream));
+        CK(cudaMemcpyAsync(s->hnorm, s->dmean, sizeof(double) * nbox, cudaMemcpyDeviceToHost,
+                           stream));
+        CK(cudaMemcpyAsync(s->hnorm + nbox, s->dinv, sizeof(double) * nbox,
+                           cudaMemcpyDeviceToHost, stream));
+    }
     bool wrong = false;
     if (is_device_ptr(phi, s->dev, &wrong)) {
         if (wrong) return set_error(MG_ERR_INVALID_ARG, "phi on another device");
@@ -1836,6 +1849,7 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
             for (int i = 0; i < bs[b].nh; ++i) o.hist[i] = bs[b].hist[i];
             o.t_setup_ms = s->t_setup_ms;
             o.t_solve_ms = ms;
+            if (want_max && s->hnorm[b] > 0.0) o.rel_resid_max = s->hnorm[nbox + b] / s->hnorm[b];
         }
     }
     if (worst != MG_OK)

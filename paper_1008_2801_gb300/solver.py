@@ -49,7 +49,7 @@ def _check_tensor(t, name, numel=None, device=None):
 
 
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
-          full_residual=False, tma=False, krylov=False):
+          full_residual=False, tma=False, krylov=False, max_norm=False):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -61,6 +61,7 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.full_residual = 1 if full_residual else 0
     o.tma = 1 if tma else 0
     o.krylov = 1 if krylov else 0
+    o.max_norm = 1 if max_norm else 0
     return o
 
 
@@ -101,7 +102,8 @@ def _stats_dict(s: _lib.mg_stats):
     n = max(0, min(s.cycles + 1, _lib.MG_MAX_HIST))
     return {"status": _lib.STATUS_NAMES.get(s.status, str(s.status)), "cycles": s.cycles,
             "norm_f": s.norm_f, "rel_resid0": s.rel_resid0, "rel_resid": s.rel_resid,
-            "hist": list(s.hist[:n]), "t_setup_ms": s.t_setup_ms, "t_solve_ms": s.t_solve_ms}
+            "hist": list(s.hist[:n]), "t_setup_ms": s.t_setup_ms, "t_solve_ms": s.t_solve_ms,
+            "rel_resid_max": s.rel_resid_max}
 
 
 _SOFT = (_lib.MG_OK, _lib.MG_ERR_NOT_CONVERGED)
@@ -127,7 +129,7 @@ class Solver:
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0, krylov=False):
+                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -138,7 +140,7 @@ class Solver:
             "cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov)
+                  full_residual, tma, krylov, max_norm)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
@@ -308,7 +310,7 @@ class BatchSolver:
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0, krylov=False):
+                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False):
         L = _lib.load()
         self.bc = bc_mask(bc)
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -320,7 +322,7 @@ class BatchSolver:
         d = (ctypes.c_double * nb)(*dxs)
         self._h = ctypes.c_void_p()
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov)
+                  full_residual, tma, krylov, max_norm)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, self.bc, ctypes.byref(o)),
                   "mg_batch_create")
