@@ -143,6 +143,16 @@ typedef struct {
     int max_norm;     /* 1: also report rel_resid_max in mg_stats (one more
                          pass over the level after the solve); 0 (default) */
     int reserved[4];
+    /* Device memory of the context (its arena, launch descriptors and host
+     * staging buffers) comes from dev_alloc(bytes, alloc_user) when set (NULL
+     * on failure: MG_ERR_OOM) and goes back through dev_free(ptr,
+     * alloc_user), e.g. a framework's caching allocator; NULL: cudaMalloc /
+     * cudaFree.  Called on the host, with the context's device current, from
+     * mg_create, the first host-buffer solve and mg_destroy (never while a
+     * stream is being captured).  Pinned host buffers are not affected. */
+    void *(*dev_alloc)(size_t bytes, void *alloc_user);
+    void (*dev_free)(void *ptr, void *alloc_user);
+    void *alloc_user;
 } mg_opts;
 
 typedef struct {

@@ -37,11 +37,16 @@ STATUS_NAMES = {
 }
 
 
+DEV_ALLOC = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p)
+DEV_FREE = ctypes.CFUNCTYPE(None, c_void_p, c_void_p)
+
+
 class mg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("max_cycles", c_int),
                 ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
                 ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
-                ("krylov", c_int), ("max_norm", c_int), ("reserved", c_int * 4)]
+                ("krylov", c_int), ("max_norm", c_int), ("reserved", c_int * 4),
+                ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_user", c_void_p)]
 
 
 class mg_stats(ctypes.Structure):

@@ -88,6 +88,23 @@ static std::vector<std::array<int, 3>> level_dims(int nx, int ny, int nz)
 
 // ------------------------------------------------------------ building ----
 
+// Device memory of a context: the caller's allocator when given, else
+// cudaMalloc / cudaFree.
+static cudaError_t dev_malloc(const Solver *s, void **p, size_t bytes)
+{
+    if (s->opts.dev_alloc) {
+        *p = s->opts.dev_alloc(bytes, s->opts.alloc_user);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+static void dev_free(const Solver *s, void *p)
+{
+    if (!p) return;
+    if (s->opts.dev_free) s->opts.dev_free(p, s->opts.alloc_user);
+    else cudaFree(p);
+}
+
 // Bump allocator over a byte arena (dry run computes the size).
 struct Bump {
     char *base = nullptr;
@@ -391,6 +408,8 @@ static int validate_opts(const mg_opts *o)
     if (o->inner_cycles < 0 || o->inner_cycles > 8)
         return set_error(MG_ERR_INVALID_ARG, "inner_cycles must be in 0..8");
     if (o->krylov < 0 || o->krylov > 1) return set_error(MG_ERR_INVALID_ARG, "krylov must be 0 or 1");
+    if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr))
+        return set_error(MG_ERR_INVALID_ARG, "dev_alloc and dev_free come together");
     return MG_OK;
 }
 
@@ -623,7 +642,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
                           sizeof(int) * (3 * (size_t)nbox + 1);
     bump.take<char>(jbytes);
     const size_t bytes = bump.used;
-    cudaError_t e = cudaMalloc(&s->arena, bytes);
+    cudaError_t e = dev_malloc(s, reinterpret_cast<void **>(&s->arena), bytes);
     if (e != cudaSuccess) {
         delete s;
         return set_error(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
@@ -809,7 +828,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     const size_t off_at = blob.put(s->off.data(), s->off.size() * sizeof(long long));
     std::vector<int> zeros(nbox, 0);
     const size_t side_at = blob.put(zeros.data(), zeros.size() * sizeof(int));
-    e = cudaMalloc(&s->desc, blob.bytes.size());
+    e = dev_malloc(s, reinterpret_cast<void **>(&s->desc), blob.bytes.size());
     if (e != cudaSuccess) {
         solver_destroy(s);
         return set_error(MG_ERR_OOM, "cudaMalloc(descriptors): %s", cudaGetErrorString(e));
@@ -872,6 +891,9 @@ void solver_destroy(Solver *s)
 {
     if (!s) return;
     DeviceGuard g(s->dev);
+    // a caller's allocator may hand the memory out again at once: let the
+    // context's queued work (e.g. a set-up without a solve yet) finish first
+    if (s->opts.dev_free) cudaDeviceSynchronize();
     for (auto *v : {&s->slots64, &s->slots32, &s->slots_head, &s->direct})
         for (auto &sl : *v) {
             cudaEventDestroy(sl.b);
@@ -885,9 +907,9 @@ void solver_destroy(Solver *s)
     if (s->loop32) cudaGraphExecDestroy(s->loop32);
     if (s->loop_pcg) cudaGraphExecDestroy(s->loop_pcg);
     if (s->hjblock) cudaFreeHost(s->hjblock);
-    if (s->arena) cudaFree(s->arena);
-    if (s->desc) cudaFree(s->desc);
-    if (s->stage_a) cudaFree(s->stage_a);
+    dev_free(s, s->arena);
+    dev_free(s, s->desc);
+    dev_free(s, s->stage_a);
     if (s->hnorm) cudaFreeHost(s->hnorm);
     if (s->hactive) cudaFreeHost(s->hactive);
     if (s->hside) cudaFreeHost(s->hside);
@@ -919,7 +941,11 @@ static bool is_device_ptr(const void *p, int dev, bool *wrong_dev)
 static int ensure_stage(Solver *s)
 {
     if (s->stage_a) return MG_OK;
-    CK(cudaMalloc(&s->stage_a, sizeof(double) * 3 * (size_t)s->total));
+    const cudaError_t e =
+        dev_malloc(s, reinterpret_cast<void **>(&s->stage_a), sizeof(double) * 3 * (size_t)s->total);
+    if (e != cudaSuccess)
+        return set_error(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
+                         "staging buffers: %s", cudaGetErrorString(e));
     s->stage_b = s->stage_a + s->total;
     s->stage_c = s->stage_b + s->total;
     return MG_OK;

@@ -48,8 +48,25 @@ def _check_tensor(t, name, numel=None, device=None):
         raise ValueError(f"{name} is on {t.device}, solver on {device}")
 
 
+def _torch_allocator(device):
+    """dev_alloc / dev_free callbacks that take the context's device memory
+    from PyTorch's caching allocator (they must outlive the context)."""
+    index = torch.device(device).index
+
+    def alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), index)
+        except RuntimeError:          # out of memory: the library reports MG_ERR_OOM
+            return None
+
+    def free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _lib.DEV_ALLOC(alloc), _lib.DEV_FREE(free)
+
+
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
-          full_residual=False, tma=False, krylov=False, max_norm=False):
+          full_residual=False, tma=False, krylov=False, max_norm=False, hooks=None):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -62,6 +79,8 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.tma = 1 if tma else 0
     o.krylov = 1 if krylov else 0
     o.max_norm = 1 if max_norm else 0
+    if hooks is not None:
+        o.dev_alloc, o.dev_free = hooks
     return o
 
 
@@ -124,12 +143,14 @@ class Solver:
     module docstring).  krylov: conjugate gradients preconditioned by one
     symmetric V-cycle per iteration instead of plain V-cycles, for
     high-contrast beta (with "mixed" the V-cycle runs in FP32, CG in FP64).
-    Not thread-safe.
+    allocator: "torch" takes the context's device memory from PyTorch's
+    caching allocator instead of cudaMalloc.  Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False):
+                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
+                 allocator=None):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -139,8 +160,9 @@ class Solver:
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
+        self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov, max_norm)
+                  full_residual, tma, krylov, max_norm, self._hooks)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
@@ -310,7 +332,8 @@ class BatchSolver:
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False):
+                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
+                 allocator=None):
         L = _lib.load()
         self.bc = bc_mask(bc)
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -321,8 +344,9 @@ class BatchSolver:
         n = (ctypes.c_int * (3 * nb))(*[v for s in self.shapes for v in (s[2], s[1], s[0])])
         d = (ctypes.c_double * nb)(*dxs)
         self._h = ctypes.c_void_p()
+        self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov, max_norm)
+                  full_residual, tma, krylov, max_norm, self._hooks)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, self.bc, ctypes.byref(o)),
                   "mg_batch_create")
