@@ -306,6 +306,10 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (working set ~1 GB > 129 MB)",
                       "parallelism": f"independent box per GPU x {world}"},
            "roofline": roof, "stage_ms_per_step": stage_ms,
+           "split": {"setup_ms": round(st64["t_setup_ms"], 4),
+                     "solve_ms": round(ms_max - st64["t_setup_ms"], 4),
+                     "solve_cells_per_s": world * N / ((ms_max - st64["t_setup_ms"]) / 1e3),
+                     "note": "step = set-up (mg_set_beta, CUDA events) + solve; value counts both"},
            "stage_timing": f"CUDA events around each stage in a second timed pass of the same "
                            f"{args.steps} steps ({ms_prof:.3f} ms/step with events, host-judged loop)",
            "gpu_launches": prof0["kernels"], "clocks": clocks}
@@ -364,6 +368,18 @@ def run_gpu(args):
                                "kind": "oracle",
                                "sample": f"one full oracle solve of the {n}^3 workload to 1e-10 "
                                          f"({info['cycles']} V-cycles, {t:.1f} s)"}
+        # the same oracle on one thread, over a bounded number of V-cycles
+        threads = oracle.num_threads()
+        oracle.set_threads(1)
+        m1 = max(1, min(info["cycles"], 2))
+        t0 = time.perf_counter()
+        oracle.solve(d["beta"], d["f"], d["dx"], tol=1e-300, max_cycles=m1)
+        t1 = (time.perf_counter() - t0) / m1 * info["cycles"]
+        oracle.set_threads(threads)
+        out["cpu_baseline"]["one_thread"] = {
+            "value": N / t1, "unit": "cells/s",
+            "sample": f"{m1} oracle V-cycles on 1 thread, scaled to the {info['cycles']} of a "
+                      f"full solve"}
         ref, _ = oracle.solve(d["beta"], d["f"], d["dx"], tol=1e-13, phi0=ref10)
         nr = np.linalg.norm(ref)
         out["error_vs_oracle"] = {"fp64": float(np.linalg.norm(phi64 - ref) / nr),
