@@ -39,8 +39,10 @@ WORKLOAD = ("stellar-profile beta (rho_c=1, core 0.3, 1% noise), f~U[-1,1] mean 
             "{n}^3, dx=1/{n}, Dirichlet walls, V(2,2) RBGS to 1e-10 rel residual")
 
 # compulsory bytes per cell of one launch: each array a kernel must read or
-# write, counted once (a colour pass reads half of f and 1/D, writes half of phi)
-BYTES_PER_CELL = {("sweep", 8): 56, ("sweep", 4): 28, ("pass", 8): 44, ("pass", 4): 22,
+# write, counted once (a colour pass reads half of f and 1/D, writes half of
+# phi; the fused sweep reads phi, f and the three weights, computes 1/D from
+# the weights, and writes phi')
+BYTES_PER_CELL = {("sweep", 8): 48, ("sweep", 4): 24, ("pass", 8): 44, ("pass", 4): 22,
                   ("restrict", 8): 41, ("restrict", 4): 20.5, ("refine", 8): 60}
 # FP64 flops per cell of one launch: a Gauss-Seidel update is 6 FMA + 1 mul =
 # 13 flop; a sweep updates every cell, a single-colour pass half
@@ -56,6 +58,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--size", type=int, default=256)
+    # mixed form: the fused FP32 sweep fed by TMA copies (opt-in kernel)
+    ap.add_argument("--tma", action="store_true")
     return ap.parse_args()
 
 
@@ -316,7 +320,7 @@ def run_gpu(args):
     s64.close()
 
     # mixed precision on the same input
-    smx = Solver((n, n, n), d["dx"], precision="mixed", device=dev)
+    smx = Solver((n, n, n), d["dx"], precision="mixed", device=dev, tma=args.tma)
     msm, stm, _, _ = timed(smx, args.steps, max(args.warmup, 3), False)
     msm = max_over_ranks(msm, dev)
     phimx = phi.cpu().numpy()
@@ -331,11 +335,15 @@ def run_gpu(args):
     if "sweep" in finem:
         kt32 = finem["sweep"]["ms"] / finem["sweep"]["launches"] / 1e3
         b32 = BYTES_PER_CELL[("sweep", 4)] * N
-        mixed["roofline"] = {"bound": "hbm", "kernel": "k_rbgs_sweep (FP32, finest level)",
+        kname = ("k_rbgs_sweep_tma (FP32, finest level, TMA-staged operands)" if args.tma
+                 else "k_rbgs_sweep (FP32, finest level)")
+        mixed["roofline"] = {"bound": "hbm", "kernel": kname,
                              "achieved": round(b32 / kt32 / 1e9, 1), "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": round(b32 / kt32 / 1e9 / peaks["hbm_gbs"], 4),
-                             "traffic": stored_traffic("rbgs_sweep_f32"),
+                             "traffic": None if args.tma else stored_traffic("rbgs_sweep_f32"),
                              "launch_ms": round(kt32 * 1e3, 4), "peak_source": peaks_src}
+        if args.tma:
+            mixed["tma"] = True
     out["mixed"] = mixed
     smx.close()
 

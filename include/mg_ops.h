@@ -68,12 +68,14 @@ int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, co
 
 /* One full red-then-black sweep as the solver runs it on large levels
  * (fused, out of place: reads phi_in, writes phi_out; phi_in is not
- * modified).  Equal to a red pass followed by a black pass.  Each CTA marches
+ * modified).  Equal to a red pass followed by a black pass.  The sweep reads
+ * no inverse diagonal: each update takes the correctly rounded reciprocal of
+ * D = ((wx- + wx+) + (wy- + wy+)) + (wz- + wz+), summed from the six weights
+ * it loads (in FP64 the value mg_op_inv_diag stores).  Each CTA marches
  * through zc planes (zc <= 0: 32).  UNSUPPORTED for levels of 2^31 or more
  * elements (the kernel indexes with 32-bit offsets). */
 int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                     const void *invD, const void *f, const void *phi_in, void *phi_out, int zc,
-                     void *stream);
+                     const void *f, const void *phi_in, void *phi_out, int zc, void *stream);
 
 /* The same sweep in FP32 with its operand tiles staged by the Tensor Memory
  * Accelerator (bulk tensor copies into shared memory, completion counted by
@@ -83,8 +85,8 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
  * encode tensor maps or the level is too small for one copy box (needs
  * nx >= 64 and ny >= 11). */
 int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const float *wz,
-                         const float *invD, const float *f, const float *phi_in, float *phi_out,
-                         int zc, void *stream);
+                         const float *f, const float *phi_in, float *phi_out, int zc,
+                         void *stream);
 
 /* In the residual stages below, D (nullable) is the stored diagonal of
  * mg_op_inv_diag in the stage precision; when NULL it is summed from the six

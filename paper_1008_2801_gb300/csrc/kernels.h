@@ -22,15 +22,15 @@ cudaError_t launch_rbgs_pass_oop(const BoxSet<T> &S, const int *active, int colo
                                  double *partials, cudaStream_t st);
 
 // ---- FP32 fused sweep fed by the Tensor Memory Accelerator (sweep_tma.cu)
-struct SweepMaps;  // seven tensor maps of one box level (device memory, 64-B aligned)
+struct SweepMaps;  // six tensor maps of one box level (device memory, 64-B aligned)
 size_t sweep_maps_size();
 // The TMA sweep serves levels whose rows and planes hold a whole copy box.
 bool sweep_tma_fits(int nx, int ny);
 // Encode the maps from the arrays' allocation bases (logical (0, 0, -1));
 // false if the driver offers no encoder.
 bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_base,
-                       const float *phi2_base, const float *f_base, const float *invD_base,
-                       const float *wx_base, const float *wy_base, const float *wz_base);
+                       const float *phi2_base, const float *f_base, const float *wx_base,
+                       const float *wy_base, const float *wz_base);
 int sweep_tma_ctas_per_sm();
 // Same result as launch_rbgs_sweep<float>; *err is set to 1 if a bounded
 // wait on a tile copy gave up (the CTA then stops).

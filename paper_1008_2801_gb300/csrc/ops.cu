@@ -187,16 +187,15 @@ int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, co
 }
 
 int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
-                     const void *invD, const void *f, const void *phi_in, void *phi_out, int zc,
-                     void *stream)
+                     const void *f, const void *phi_in, void *phi_out, int zc, void *stream)
 {
-    if (bad_dims(n) || !wx || !wy || !wz || !invD || !f || !phi_in || !phi_out ||
+    if (bad_dims(n) || !wx || !wy || !wz || !f || !phi_in || !phi_out ||
         phi_in == phi_out)
         return set_error(MG_ERR_INVALID_ARG, "bad argument (phi_in and phi_out must differ)");
     if (level_elems(n[0], n[1], n[2]) > kSweepMaxElems)
         return set_error(MG_ERR_UNSUPPORTED, "fused sweep: level of 2^31 elements or more");
     DISPATCH(prec, {
-        Box<T> B = level_box<T>(n, wx, wy, wz, invD, f, phi_in, phi_out);
+        Box<T> B = level_box<T>(n, wx, wy, wz, nullptr, f, phi_in, phi_out);
         B.zc = zc > 0 ? zc : kSweepZ;
         return with_set(B, (cudaStream_t)stream, [&](const BoxSet<T> &S) {
             return launch_rbgs_sweep(S, nullptr, 0, (cudaStream_t)stream);
@@ -205,21 +204,21 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
 }
 
 int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const float *wz,
-                         const float *invD, const float *f, const float *phi_in, float *phi_out,
-                         int zc, void *stream)
+                         const float *f, const float *phi_in, float *phi_out, int zc,
+                         void *stream)
 {
-    if (bad_dims(n) || !wx || !wy || !wz || !invD || !f || !phi_in || !phi_out ||
+    if (bad_dims(n) || !wx || !wy || !wz || !f || !phi_in || !phi_out ||
         phi_in == phi_out)
         return set_error(MG_ERR_INVALID_ARG, "bad argument (phi_in and phi_out must differ)");
     cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
-    Box<float> B = level_box<float>(n, wx, wy, wz, invD, f, phi_in, phi_out);
+    Box<float> B = level_box<float>(n, wx, wy, wz, nullptr, f, phi_in, phi_out);
     B.zc = zc > 0 ? zc : kSweepZ;
     std::vector<char> host(sweep_maps_size() + 64);
     SweepMaps *m = reinterpret_cast<SweepMaps *>(round_up((long long)(uintptr_t)host.data(), 64));
     if (!sweep_tma_fits(n[0], n[1]))
         return set_error(MG_ERR_UNSUPPORTED, "level too small for the TMA sweep (nx >= 64, ny >= 11)");
-    if (!encode_sweep_maps(m, n[0], n[1], n[2], phi_in, phi_out, f, invD, wx, wy, wz))
+    if (!encode_sweep_maps(m, n[0], n[1], n[2], phi_in, phi_out, f, wx, wy, wz))
         return set_error(MG_ERR_UNSUPPORTED, "tensor maps cannot be encoded on this driver");
     TempSet<float> ts;
     int rc = ts.make(B, st);

@@ -318,8 +318,7 @@ static bool plan_maps(const std::vector<Box<T>> &set, DescBlob &blob, size_t *of
         const long long Q = B.Q;
         auto lb = [&](const T *p) { return reinterpret_cast<const float *>(p - Q); };
         if (!encode_sweep_maps(reinterpret_cast<SweepMaps *>(base + i * one), B.nx, B.ny, B.nz,
-                               lb(B.phi), lb(B.phi2), lb(B.f), lb(B.invD), lb(B.wx), lb(B.wy),
-                               lb(B.wz)))
+                               lb(B.phi), lb(B.phi2), lb(B.f), lb(B.wx), lb(B.wy), lb(B.wz)))
             return false;
     }
     *off = blob.put(base, one * set.size());

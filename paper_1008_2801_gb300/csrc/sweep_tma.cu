@@ -5,10 +5,12 @@
 // 64 x 8 tile and a chunk of planes, marches upward, computes the new red
 // values of plane k (its tile plus a one-cell ring) and the new black values
 // of plane k-1, out of place.  Here every operand comes from shared memory:
-// one thread issues, per plane, six tiled bulk tensor copies (phi with a
-// 2-cell halo, f, 1/D and the three face-weight arrays with a 1-cell halo)
-// into a 4-stage ring, two planes ahead of the plane being computed, and an
-// mbarrier per stage counts the bytes in.  Waits are bounded: a wait that
+// one thread issues, per plane, five tiled bulk tensor copies (phi with a
+// 2-cell halo, f and the three face-weight arrays with a 1-cell halo) into a
+// 4-stage ring, two planes ahead of the plane being computed, and an
+// mbarrier per stage counts the bytes in.  Like the plain sweep it computes
+// 1/D from the six weights, so a stage is 15.1 KB and three CTAs (68 KB of
+// shared memory each) fit on an SM.  Waits are bounded: a wait that
 // gives up sets the error word and the CTA stops (after waiting, again
 // bounded, for its copies in flight), so a failure is reported, never hung.
 //
@@ -38,12 +40,11 @@ constexpr int kOpBytes = kOpRows * kTileW * 4;
 constexpr int kWyBytes = kWyRows * kTileW * 4;
 constexpr int kSrcOff = 0;
 constexpr int kFOff = kSrcOff + pad128(kSrcBytes);
-constexpr int kIdOff = kFOff + pad128(kOpBytes);
-constexpr int kWxOff = kIdOff + pad128(kOpBytes);
+constexpr int kWxOff = kFOff + pad128(kOpBytes);
 constexpr int kWyOff = kWxOff + pad128(kOpBytes);
 constexpr int kWzOff = kWyOff + pad128(kWyBytes);
 constexpr int kStageBytes = kWzOff + pad128(kOpBytes);
-constexpr unsigned kTxBytes = kSrcBytes + 4 * kOpBytes + kWyBytes;  // bytes landing per stage
+constexpr unsigned kTxBytes = kSrcBytes + 3 * kOpBytes + kWyBytes;  // bytes landing per stage
 constexpr int kRedBytes = 3 * (kSweepTY + 2) * (2 * kTX + 2) * 4;
 constexpr int kSmemBytes = kStages * kStageBytes + pad128(kRedBytes) + 128;
 
@@ -104,14 +105,14 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map)
 
 }  // namespace
 
-// Tensor maps of one box at one level: phi, phi2, f, 1/D, wx, wy, wz.
+// Tensor maps of one box at one level: phi, phi2, f, wx, wy, wz.
 struct alignas(64) SweepMaps {
-    CUtensorMap m[7];
+    CUtensorMap m[6];
 };
 
 namespace {
 
-__global__ void __launch_bounds__(kTX * kSweepTY, 2)
+__global__ void __launch_bounds__(kTX * kSweepTY, 3)
     k_rbgs_sweep_tma(BoxSet<float> S, const SweepMaps *__restrict__ maps,
                      const int *__restrict__ active, int src_is_phi2, int *__restrict__ err)
 {
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 2)
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int i = 0; i < 7; ++i) tensormap_acquire(&M.m[i]);
+        for (int i = 0; i < 6; ++i) tensormap_acquire(&M.m[i]);
     }
     __syncthreads();
 
@@ -165,10 +166,9 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 2)
         const int zt = p + 1;  // tensor z of logical plane p (guard plane first)
         tma_load_3d(smem_addr(base + kSrcOff), msrc, bar, x0 - 4, y0 - 2, zt);
         tma_load_3d(smem_addr(base + kFOff), &M.m[2], bar, x0 - 4, y0 - 1, zt);
-        tma_load_3d(smem_addr(base + kIdOff), &M.m[3], bar, x0 - 4, y0 - 1, zt);
-        tma_load_3d(smem_addr(base + kWxOff), &M.m[4], bar, x0 - 4, y0 - 1, zt);
-        tma_load_3d(smem_addr(base + kWyOff), &M.m[5], bar, x0 - 4, y0 - 1, zt);
-        tma_load_3d(smem_addr(base + kWzOff), &M.m[6], bar, x0 - 4, y0 - 1, zt);
+        tma_load_3d(smem_addr(base + kWxOff), &M.m[3], bar, x0 - 4, y0 - 1, zt);
+        tma_load_3d(smem_addr(base + kWyOff), &M.m[4], bar, x0 - 4, y0 - 1, zt);
+        tma_load_3d(smem_addr(base + kWzOff), &M.m[5], bar, x0 - 4, y0 - 1, zt);
     };
     if (tid == 0)
         for (int p = pfirst; p < pfirst + kStages && p <= plast; ++p) issue(p);
@@ -189,7 +189,11 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 2)
         s = fmaf(opv(k, kWyOff, xx, yy + 1), srcv(k, xx, yy + 1), s);
         s = fmaf(opv(k, kWzOff, xx, yy), srcv(k - 1, xx, yy), s);
         s = fmaf(opv(k + 1, kWzOff, xx, yy), srcv(k + 1, xx, yy), s);
-        return s * opv(k, kIdOff, xx, yy);
+        // 1/D from the six weights, as the plain sweep computes it
+        const float d = ((opv(k, kWxOff, xx, yy) + opv(k, kWxOff, xx + 1, yy)) +
+                         (opv(k, kWyOff, xx, yy) + opv(k, kWyOff, xx, yy + 1))) +
+                        (opv(k, kWzOff, xx, yy) + opv(k + 1, kWzOff, xx, yy));
+        return s * __frcp_rn(d);
     };
 
     const bool ring_row = ty < 2;
@@ -252,7 +256,10 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 2)
                 s = fmaf(opv(km, kWyOff, xb, y + 1), red[sm][ty + 2][lb], s);
                 s = fmaf(opv(km, kWzOff, xb, y), red[smm][ty + 1][lb], s);
                 s = fmaf(opv(k, kWzOff, xb, y), red[s0][ty + 1][lb], s);
-                bv = s * opv(km, kIdOff, xb, y);
+                const float d = ((opv(km, kWxOff, xb, y) + opv(km, kWxOff, xb + 1, y)) +
+                                 (opv(km, kWyOff, xb, y) + opv(km, kWyOff, xb, y + 1))) +
+                                (opv(km, kWzOff, xb, y) + opv(k, kWzOff, xb, y));
+                bv = s * __frcp_rn(d);
             }
             const long long c0 = (long long)km * Q + (long long)y * P + xa;
             const float va = parm ? bv : rv;
@@ -306,11 +313,11 @@ EncodeTiledFn encoder()
 
 }  // namespace
 
-// Encode the seven maps of a box level (arrays given by their allocation
+// Encode the six maps of a box level (arrays given by their allocation
 // base = logical (0, 0, -1)).  Returns false if the driver cannot.
 bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_base,
-                       const float *phi2_base, const float *f_base, const float *invD_base,
-                       const float *wx_base, const float *wy_base, const float *wz_base)
+                       const float *phi2_base, const float *f_base, const float *wx_base,
+                       const float *wy_base, const float *wz_base)
 {
     EncodeTiledFn fn = encoder();
     if (!fn) return false;
@@ -322,9 +329,9 @@ bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_
     const cuuint32_t box_src[3] = {kTileW, kSrcRows, 1};
     const cuuint32_t box_op[3] = {kTileW, kOpRows, 1};
     const cuuint32_t box_wy[3] = {kTileW, kWyRows, 1};
-    const float *base[7] = {phi_base, phi2_base, f_base, invD_base, wx_base, wy_base, wz_base};
-    const cuuint32_t *box[7] = {box_src, box_src, box_op, box_op, box_op, box_wy, box_op};
-    for (int i = 0; i < 7; ++i) {
+    const float *base[6] = {phi_base, phi2_base, f_base, wx_base, wy_base, wz_base};
+    const cuuint32_t *box[6] = {box_src, box_src, box_op, box_op, box_wy, box_op};
+    for (int i = 0; i < 6; ++i) {
         CUresult r = fn(&out->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                         const_cast<float *>(base[i]), dims, strides, box[i], ones,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -336,14 +343,23 @@ bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_
 
 size_t sweep_maps_size() { return sizeof(SweepMaps); }
 
+// The ring's dynamic shared memory, and the largest shared-memory carveout so
+// that three CTAs fit on an SM.
+static void set_smem_attributes()
+{
+    cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSmemBytes);
+    cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+}
+
 // Levels whose rows and planes hold a whole copy box (72 x 12).
 bool sweep_tma_fits(int nx, int ny) { return pitch_row(nx) >= kTileW && ny + 1 >= kSrcRows; }
 
 int sweep_tma_ctas_per_sm()
 {
     int n = 0;
-    cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSmemBytes);
+    set_smem_attributes();
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep_tma, kTX * kSweepTY,
                                                       kSmemBytes) != cudaSuccess) {
         cudaGetLastError();
@@ -357,10 +373,7 @@ cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps,
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
     static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBytes);
-    });
+    std::call_once(once, [] { set_smem_attributes(); });
     k_rbgs_sweep_tma<<<S.ntiles[TK_SWEEP], dim3(kTX, kSweepTY), kSmemBytes, st>>>(
         S, maps, active, src_is_phi2, err);
     return cudaGetLastError();

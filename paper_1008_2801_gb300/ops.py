@@ -105,20 +105,21 @@ def rbgs_pass(w, invD, f, phi, shape, color):
     return phi
 
 
-def rbgs_sweep(w, invD, f, phi_in, shape, phi_out=None, zc=0):
+def rbgs_sweep(w, f, phi_in, shape, phi_out=None, zc=0):
+    """Fused red+black sweep, out of place (1/D from the weights)."""
     if phi_out is None:
         phi_out = torch.zeros_like(phi_in)
-    check(_lib.load().mg_op_rbgs_sweep(_PREC[phi_in.dtype], _n(shape), *map(_p, w), _p(invD),
-                                       _p(f), _p(phi_in), _p(phi_out), int(zc), _s(phi_in)),
+    check(_lib.load().mg_op_rbgs_sweep(_PREC[phi_in.dtype], _n(shape), *map(_p, w), _p(f),
+                                       _p(phi_in), _p(phi_out), int(zc), _s(phi_in)),
           "mg_op_rbgs_sweep")
     return phi_out
 
 
-def rbgs_sweep_tma(w, invD, f, phi_in, shape, phi_out=None, zc=0):
+def rbgs_sweep_tma(w, f, phi_in, shape, phi_out=None, zc=0):
     """FP32 fused sweep with TMA-staged tiles (bitwise equal to rbgs_sweep)."""
     if phi_out is None:
         phi_out = torch.zeros_like(phi_in)
-    check(_lib.load().mg_op_rbgs_sweep_tma(_n(shape), *map(_p, w), _p(invD), _p(f), _p(phi_in),
+    check(_lib.load().mg_op_rbgs_sweep_tma(_n(shape), *map(_p, w), _p(f), _p(phi_in),
                                            _p(phi_out), int(zc), _s(phi_in)),
           "mg_op_rbgs_sweep_tma")
     return phi_out

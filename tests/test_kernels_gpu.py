@@ -112,7 +112,7 @@ def test_fused_sweep_equals_red_then_black(cuda_device, shape, dtype, zc):
     ft = _level(shape, f, cuda_device, dtype)
     pin = _level(shape, phi, cuda_device, dtype)
     before = pin.clone()
-    out = K.rbgs_sweep(w, invD, ft, pin, shape, zc=zc)
+    out = K.rbgs_sweep(w, ft, pin, shape, zc=zc)
     assert torch.equal(pin, before)  # out of place
     faces = O.face_beta(beta)
     ref = O.rbgs_pass(faces, h, f, O.rbgs_pass(faces, h, f, phi, 0), 1)
@@ -134,12 +134,12 @@ def test_fused_sweep_equals_red_then_black(cuda_device, shape, dtype, zc):
 def test_tma_sweep_is_bitwise_the_plain_sweep(cuda_device, shape, zc):
     # same arithmetic in the same order; only the operand staging differs
     beta, f, phi, h = _case(shape, 14)
-    w, invD = _weights(beta, h, shape, cuda_device, torch.float32)
+    w, _ = _weights(beta, h, shape, cuda_device, torch.float32)
     ft = _level(shape, f, cuda_device, torch.float32)
     pin = _level(shape, phi, cuda_device, torch.float32)
     before = pin.clone()
-    a = K.rbgs_sweep(w, invD, ft, pin, shape, zc=zc)
-    b = K.rbgs_sweep_tma(w, invD, ft, pin, shape, zc=zc)
+    a = K.rbgs_sweep(w, ft, pin, shape, zc=zc)
+    b = K.rbgs_sweep_tma(w, ft, pin, shape, zc=zc)
     assert torch.equal(pin, before)
     assert torch.equal(a, b)
     full = b.cpu()
