@@ -261,16 +261,34 @@ __global__ void __launch_bounds__(kThreads) k_rbgs_pass_oop_norm(BoxSet<T> S,
 
 // A red update's 13 operands and a black update's 7 global ones (its red
 // neighbours come from shared memory).  The diagonal is the sum of the six
-// face weights the update loads anyway, so its reciprocal is computed (one
-// correctly rounded reciprocal) instead of read: 4 of 28 bytes a cell less
-// in FP32, and for FP64 the same value as the stored 1/D.
+// face weights the update loads anyway, so its reciprocal is computed
+// instead of read: 4 of 28 bytes a cell less in FP32 (the correctly rounded
+// FP32 reciprocal), and for FP64 the set-up's rcp64, i.e. the stored 1/D.
 template <class T>
 struct SweepRed { T sw, se, ss, sn, sd, su, wxa, wxb, wya, wyb, wza, wzb, f; };
 template <class T>
 struct SweepBlack { T wxa, wxb, wya, wyb, wza, wzb, f; };
 
+// 1/d in FP64 without an FP64 division, whose iterations occupy GB300's
+// narrow FP64 pipe: Newton-Raphson for the reciprocal (Muller et al.,
+// Handbook of Floating-Point Arithmetic, on iterations for 1/d) from an FP32
+// seed.  With y0 = the FP32 reciprocal of d rounded to FP32, d y0 = 1 - e
+// with |e| < 2^-22; one cubic step y = y0 (1 + e + e^2) = (1 - e^3) / d,
+// e computed by a fused multiply-add, is within 2^-66 of 1/d before its one
+// rounding, hence within one ulp (and nearly always the correctly rounded
+// value).  A d whose FP32 reciprocal is not a normal finite number (d = 0,
+// |d| beyond FP32's normal range, NaN) takes the division.
+__device__ __forceinline__ double rcp64(double d)
+{
+    const float s = __frcp_rn(__double2float_rn(d));
+    if (!(fabsf(s) >= 1.17549435e-38f && fabsf(s) <= 3.40282347e38f)) return 1.0 / d;
+    const double y = (double)s;
+    const double e = fma(-d, y, 1.0);
+    return fma(fma(e, e, e), y, y);
+}
+
 __device__ __forceinline__ float rcp_rn(float d) { return __frcp_rn(d); }
-__device__ __forceinline__ double rcp_rn(double d) { return __drcp_rn(d); }
+__device__ __forceinline__ double rcp_rn(double d) { return rcp64(d); }
 
 // 1 / D from a cell's six face weights, summed in the set-up's order
 template <class T>
@@ -1083,10 +1101,11 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 // every box of a level in one launch (the solver).
 
 // weight of a face between cells with coefficients a and b: the harmonic mean
-// 2 a b / (a + b) times 1/h^2, as one quotient (c2 = 2 / h^2)
+// 2 a b / (a + b) times 1/h^2 (c2 = 2 / h^2), the quotient taken through
+// rcp64 (within a few ulp of the correctly rounded quotient)
 __device__ __forceinline__ double harmonic_w(double a, double b, double c2)
 {
-    return (c2 * a) * b / (a + b);
+    return (c2 * a) * b * rcp64(a + b);
 }
 
 // Wall w (0..5 = x-, x+, y-, y+, z-, z+) is Neumann when bit w of the mask is
@@ -1174,7 +1193,7 @@ __device__ __forceinline__ void inv_diag_at(int P, long long Q, const double *__
                                             double *Dout, long long c, long long cf)
 {
     const double D = ((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]);
-    if (invD) invD[cf] = 1.0 / D;   // NULL: mixed precision, whose FP64 levels never smooth
+    if (invD) invD[cf] = rcp64(D);  // NULL: mixed precision, whose FP64 levels never smooth
     if (Dout) Dout[cf] = D;
 }
 
