@@ -4,7 +4,7 @@ Every stage is called through the C ABI (include/mg_ops.h) on the same
 seeded inputs the oracle gets, and compared element by element.
 
 Tolerances, from the arithmetic: each output is a sum of at most 8 products
-(plus one multiply by a stored reciprocal), so its rounding error is below
+(plus one multiply by the reciprocal of the diagonal, stored or computed), so its rounding error is below
 about 10 u * (sum of |terms|), u = 2^-53 in FP64 and 2^-24 in FP32.  The
 tests allow 1e-13 (FP64) and 1e-5 (FP32) times that term scale, i.e. 100x
 headroom; the FP32 kernels are compared with the FP64 oracle.
@@ -68,6 +68,29 @@ def test_face_weights_and_inverse_diagonal(cuda_device, shape):
     bx, by, bz = faces
     D = (bx[:, :, :-1] + bx[:, :, 1:] + by[:, :-1, :] + by[:, 1:, :] + bz[:-1] + bz[1:]) / h ** 2
     assert np.max(np.abs(invD * D - 1.0)) <= 1e-14
+
+
+def test_inverse_diagonal_over_the_fp64_range(cuda_device):
+    # 1/D without an FP64 division (FP32 seed, one cubic Newton step): within
+    # one ulp of the correctly rounded reciprocal, and equal to it but for
+    # rare near-midpoint cases, for D log-uniform over 1e-300..1e300; values
+    # whose FP32 reciprocal is not normal and finite take the division
+    m = 4096
+    shape = (1, m, 1)           # nx = nz = 1: each cell owns its two x faces
+    rng = np.random.default_rng(7)
+    d = 10.0 ** rng.uniform(-300, 300, m)
+    d[:10] = [1e-45, 1.2e-38, 2.0 ** -126, 3.4e38, 3.5e38, 2.0 ** 127, 1.0, 3.0, 1e-300, 1e300]
+    wx = np.zeros((1, m, 2))
+    wx[0, :, 0] = d              # D = d + 0 + 0 + 0 + 0 + 0 exactly
+    w = (_level(shape, wx, cuda_device, kind="x"),
+         _level(shape, np.zeros((1, m + 1, 1)), cuda_device, kind="y"),
+         _level(shape, np.zeros((2, m, 1)), cuda_device, kind="z"))
+    got = K.get(K.inv_diag(w, shape), shape).cpu().numpy().ravel()
+    want = 1.0 / d
+    assert np.all(np.abs(got - want) <= np.spacing(want))
+    assert np.mean(got == want) >= 0.99
+    exact = [0, 2, 3, 4, 5, 6, 8, 9]     # the division fallback and powers of two
+    np.testing.assert_array_equal(got[exact], want[exact])
 
 
 @pytest.mark.parametrize("shape", EVEN)
