@@ -330,6 +330,8 @@ def run_gpu(args):
              "refinement_steps": stm["cycles"], "fp32_vcycles_per_step": 2,
              "rel_resid": stm["rel_resid"],
              "speedup_vs_fp64": ms_max / msm,
+             "split": {"setup_ms": round(stm["t_setup_ms"], 4),
+                       "solve_ms": round(msm - stm["t_setup_ms"], 4)},
              "stage_ms_per_step": {k: round(v["ms"] / max(args.steps, 1), 4)
                                    for k, v in finem.items()}}
     if "sweep" in finem:
