@@ -415,15 +415,19 @@ def run_extra(dev, args):
     ex = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def time_once(fn):
+    def time_once(fn, reps=3):
+        # one warm-up call, then the median of reps timed calls
         fn()
         torch.cuda.synchronize(dev)
-        a, b = ev(), ev()
-        a.record()
-        r = fn()
-        b.record()
-        torch.cuda.synchronize(dev)
-        return a.elapsed_time(b), r
+        ts = []
+        for _ in range(reps):
+            a, b = ev(), ev()
+            a.record()
+            r = fn()
+            b.record()
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return sorted(ts)[len(ts) // 2], r
 
     # 512^3
     d = inputs.config(3)
@@ -468,6 +472,7 @@ def run_extra(dev, args):
             return bs.solve(fp, phi, tol=TOL, zero_guess=True)[1]
         ms, sts = time_once(go)
         res[f"batched_{prec}"] = {"cells_per_s": N / (ms / 1e3), "ms": ms,
+                                  "setup_ms": round(sts[0]["t_setup_ms"], 3),
                                   "max_cycles": max(s["cycles"] for s in sts),
                                   "all_ok": all(s["status"] == "ok" for s in sts)}
         bs.close()

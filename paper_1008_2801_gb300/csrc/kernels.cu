@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include <atomic>
+#include <mutex>
 
 namespace mg {
 
@@ -1229,67 +1230,90 @@ __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long lon
 // definite: applied to r it gives a solution of M x = r - mean(r) (the
 // constant part of r, which no solution can match, is dropped), and the
 // zero-mean one when r has zero mean.
-// The block of M = -A of one box inside an n x n matrix a, rows and
-// columns from `at` on (the box's cells in C order): diagonal = sum of the
-// six weights, -w to each neighbour inside the box.  Called by every thread
-// of the CTA.
-template <class R>
+// Storage of the symmetric matrix M being inverted.  Only entries (i, j)
+// with i <= j are stored, written or read.  Full: row-major n x n (global
+// scratch, any n; the lower triangle is left alone).  Packed: the upper
+// triangle row by row, n (n + 1) / 2 entries (shared memory when it fits;
+// row i holds (i, i..n-1) from i n - i (i - 1) / 2 on).
+template <class R, bool PACKED>
+struct SymStore {
+    R *a;
+    int n;
+    __device__ __forceinline__ long long size() const
+    {
+        return PACKED ? (long long)n * (n + 1) / 2 : (long long)n * n;
+    }
+    // entry (i, i); entry (i, j), j >= i, is row(i)[j - i]
+    __device__ __forceinline__ R *row(int i) const
+    {
+        return a + (PACKED ? (long long)i * n - (long long)i * (i - 1) / 2 : (long long)i * n + i);
+    }
+    __device__ __forceinline__ R &operator()(int i, int j) const { return row(i)[j - i]; }
+};
+
+// Packed FP64 / FP32 matrices up to this size are inverted in shared memory
+// (n <= 231 in FP64, n <= 328 in FP32).
+constexpr int kPackedBottomBytes = 200 * 1024;
+
+// The upper triangle of the block of M = -A of one box, rows and columns
+// from `at` on (the box's cells in C order): diagonal = sum of the six
+// weights, -w to each later neighbour inside the box (the earlier ones are
+// the mirrors).  Called by every thread of the CTA.
+template <class S>
 __device__ __forceinline__ void assemble_box_block(int nx, int ny, int nz, int P, long long Q,
                                                    const double *__restrict__ wx,
                                                    const double *__restrict__ wy,
-                                                   const double *__restrict__ wz, R *a, int n,
-                                                   int at)
+                                                   const double *__restrict__ wz, S a, int at)
 {
+    using R = typename std::remove_reference<decltype(*a.a)>::type;
     const int m = nx * ny * nz;
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
         const int i = r % nx, j = (r / nx) % ny, k = r / (nx * ny);
         const long long c = (long long)k * Q + (long long)j * P + i;
         const double ww = wx[c], we = wx[c + 1], ws = wy[c], wn = wy[c + P], wd = wz[c],
                      wu = wz[c + Q];
-        R *row = a + (long long)(at + r) * n + at;
-        row[r] = (R)(((ww + we) + (ws + wn)) + (wd + wu));
-        if (i > 0) row[r - 1] = (R)-ww;
-        if (i < nx - 1) row[r + 1] = (R)-we;
-        if (j > 0) row[r - nx] = (R)-ws;
-        if (j < ny - 1) row[r + nx] = (R)-wn;
-        if (k > 0) row[r - nx * ny] = (R)-wd;
-        if (k < nz - 1) row[r + nx * ny] = (R)-wu;
+        R *row = a.row(at + r);
+        row[0] = (R)(((ww + we) + (ws + wn)) + (wd + wu));
+        if (i < nx - 1) row[1] = (R)-we;
+        if (j < ny - 1) row[nx] = (R)-wn;
+        if (k < nz - 1) row[nx * ny] = (R)-wu;
     }
 }
 
-template <class R>
-__device__ __forceinline__ void gauss_jordan_cta(R *a, int n, bool singular, double *inv64,
+template <class R, class S>
+__device__ __forceinline__ void gauss_jordan_cta(S a, int n, bool singular, double *inv64,
                                                  float *inv32, R *col);
 
 // The coarsest level's inverse in precision R (double: A^{-1} to inv64 and
 // its rounding to inv32; float, when no FP64 inverse is wanted: inv32 only).
-// a: n x n scratch of R; col: 2n of R (shared memory).
-template <class R>
+// a: the matrix storage (SymStore of R, n = the box's cells); col: 2n of R
+// (shared memory).
+template <class R, class S>
 __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P, long long Q,
                                                    const double *__restrict__ wx,
                                                    const double *__restrict__ wy,
                                                    const double *__restrict__ wz, bool singular,
-                                                   R *a, double *inv64, float *inv32, R *col)
+                                                   S a, double *inv64, float *inv32, R *col)
 {
-    const int n = nx * ny * nz;
-    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = R(0);
+    for (long long e = threadIdx.x; e < a.size(); e += blockDim.x) a.a[e] = R(0);
     __syncthreads();
-    assemble_box_block(nx, ny, nz, P, Q, wx, wy, wz, a, n, 0);
+    assemble_box_block(nx, ny, nz, P, Q, wx, wy, wz, a, 0);
     __syncthreads();
-    gauss_jordan_cta(a, n, singular, inv64, inv32, col);
+    gauss_jordan_cta(a, a.n, singular, inv64, inv32, col);
 }
 
-// In-place Gauss-Jordan inverse of the n x n matrix a (M, symmetric positive
-// definite; with `singular` first shifted by c 1 1^T as described above),
-// written as A^{-1} = -M^{-1} to inv64 and/or inv32 (either may be NULL).
-// Pivots are taken in order, without exchanges (M is diagonally dominant or
-// positive definite), and only the upper triangle is kept: after pivots
-// 0..p an entry with exactly one index <= p is the negative of its mirror and
-// every other entry equals its mirror, so the lower triangle follows from
-// the upper one and each pivot costs n^2/2 updates instead of n^2 (the FP64
-// pipe of the single SM that inverts a box is the limit).  col: 2n of R.
-template <class R>
-__device__ __forceinline__ void gauss_jordan_cta(R *a, int n, bool singular, double *inv64,
+// In-place Gauss-Jordan inverse of M (symmetric positive definite; with
+// `singular` first shifted by c 1 1^T as described above), written as
+// A^{-1} = -M^{-1} to inv64 and/or inv32 (either may be NULL).  Pivots are
+// taken in order, without exchanges (M is diagonally dominant or positive
+// definite), and only the upper triangle is kept: after pivots 0..p an entry
+// with exactly one index <= p is the negative of its mirror and every other
+// entry equals its mirror, so the lower triangle follows from the upper one
+// and each pivot costs n^2/2 updates instead of n^2 (the FP64 pipe of the
+// single SM that inverts a box is the limit once the matrix sits in shared
+// memory).  a: SymStore of R; col: 2n of R.
+template <class R, class S>
+__device__ __forceinline__ void gauss_jordan_cta(S a, int n, bool singular, double *inv64,
                                                  float *inv32, R *col)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -1298,40 +1322,38 @@ __device__ __forceinline__ void gauss_jordan_cta(R *a, int n, bool singular, dou
     if (singular) {
         if (tid == 0) {
             R tr = R(0);
-            for (int r = 0; r < n; ++r) tr += a[(long long)r * n + r];
+            for (int r = 0; r < n; ++r) tr += a(r, r);
             col[0] = tr / ((R)n * (R)n);
         }
         __syncthreads();
         const R shift = col[0];
         __syncthreads();
-        for (long long e = tid; e < (long long)n * n; e += nt) a[e] += shift;
+        for (long long e = tid; e < a.size(); e += nt) a.a[e] += shift;
         __syncthreads();
     }
     for (int p = 0; p < n; ++p) {
         // column p (the entries below the diagonal mirror those of row p)
-        for (int i = tid; i < n; i += nt)
-            col[i] = i <= p ? a[(long long)i * n + p] : a[(long long)p * n + i];
+        for (int i = tid; i < n; i += nt) col[i] = i <= p ? a(i, p) : a(p, i);
         __syncthreads();
         const R ip = R(1) / col[p];
         // new row p: a_pj / a_pp (a_pj for j < p is minus its stored mirror)
         for (int j = tid; j < n; j += nt)
-            rowv[j] = j == p ? ip
-                             : (j > p ? a[(long long)p * n + j] : -a[(long long)j * n + p]) * ip;
+            rowv[j] = j == p ? ip : (j > p ? a(p, j) : -a(j, p)) * ip;
         __syncthreads();
         for (int i = warp; i < n; i += nw) {
             const R ci = col[i];
-            R *ar = a + (long long)i * n;
+            R *ar = a.row(i);
             for (int j = i + lane; j < n; j += 32) {
-                if (i == p) ar[j] = rowv[j];                 // row p (j >= p; j = p: 1 / a_pp)
-                else if (j == p) ar[j] = -ci * ip;           // column p above the diagonal
-                else ar[j] -= ci * rowv[j];
+                if (i == p) ar[j - i] = rowv[j];             // row p (j >= p; j = p: 1 / a_pp)
+                else if (j == p) ar[j - i] = -ci * ip;       // column p above the diagonal
+                else ar[j - i] -= ci * rowv[j];
             }
         }
         __syncthreads();
     }
     for (long long e = tid; e < (long long)n * n; e += nt) {
         const int i = (int)(e / n), j = (int)(e % n);
-        const double v = -(double)(i <= j ? a[e] : a[(long long)j * n + i]);
+        const double v = -(double)(i <= j ? a(i, j) : a(j, i));
         if (inv64) inv64[e] = v;
         if (inv32) inv32[e] = (float)v;
     }
@@ -1393,10 +1415,18 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
                                                          const double *__restrict__ wz,
                                                          int singular, double *__restrict__ a,
                                                          double *__restrict__ inv64,
-                                                         float *__restrict__ inv32)
+                                                         float *__restrict__ inv32, int packed)
 {
     __shared__ double col[2 * MG_BOTTOM_CELLS];
-    bottom_inverse_cta<double>(nx, ny, nz, P, Q, wx, wy, wz, singular != 0, a, inv64, inv32, col);
+    extern __shared__ __align__(16) unsigned char bottom_packed[];
+    const int n = nx * ny * nz;
+    if (packed)
+        bottom_inverse_cta<double>(nx, ny, nz, P, Q, wx, wy, wz, singular != 0,
+                                   SymStore<double, true>{reinterpret_cast<double *>(bottom_packed), n},
+                                   inv64, inv32, col);
+    else
+        bottom_inverse_cta<double>(nx, ny, nz, P, Q, wx, wy, wz, singular != 0,
+                                   SymStore<double, false>{a, n}, inv64, inv32, col);
 }
 
 // ---- every box of a level in one launch (the solver's set-up)
@@ -1435,19 +1465,38 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
 
 // One CTA per box: the coarsest level's dense inverse, in FP64 when an FP64
 // inverse is wanted, else (mixed precision, whose FP64 levels never solve)
-// in FP32 straight away.
-__global__ void __launch_bounds__(1024) k_setup_bottom(SetupSet S)
+// in FP32 straight away; a matrix whose packed upper triangle fits in the
+// launch's dynamic shared memory (packed_bytes, at most kPackedBottomBytes)
+// is inverted there, a larger one in the box's global scratch.
+__global__ void __launch_bounds__(1024) k_setup_bottom(SetupSet S, int packed_bytes)
 {
     __shared__ double col[2 * MG_BOTTOM_CELLS];
+    extern __shared__ __align__(16) unsigned char bottom_packed[];
     const SetupBox &B = S.boxes[blockIdx.x];
     const bool singular = (B.bc & 63) == 63;
-    if (B.inv64)
-        bottom_inverse_cta<double>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular, B.work,
-                                   B.inv64, B.inv32, col);
-    else
-        bottom_inverse_cta<float>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
-                                  reinterpret_cast<float *>(B.work), nullptr, B.inv32,
-                                  reinterpret_cast<float *>(col));
+    const int n = B.nx * B.ny * B.nz;
+    const long long tri = (long long)n * (n + 1) / 2;
+    if (B.inv64) {
+        if (tri * (long long)sizeof(double) <= packed_bytes)
+            bottom_inverse_cta<double>(
+                B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
+                SymStore<double, true>{reinterpret_cast<double *>(bottom_packed), n}, B.inv64,
+                B.inv32, col);
+        else
+            bottom_inverse_cta<double>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
+                                       SymStore<double, false>{B.work, n}, B.inv64, B.inv32, col);
+    } else {
+        float *colf = reinterpret_cast<float *>(col);
+        if (tri * (long long)sizeof(float) <= packed_bytes)
+            bottom_inverse_cta<float>(
+                B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
+                SymStore<float, true>{reinterpret_cast<float *>(bottom_packed), n}, nullptr,
+                B.inv32, colf);
+        else
+            bottom_inverse_cta<float>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
+                                      SymStore<float, false>{reinterpret_cast<float *>(B.work), n},
+                                      nullptr, B.inv32, colf);
+    }
 }
 
 // ----------------------------------------------------- projection steps ----
@@ -1841,11 +1890,12 @@ __global__ void __launch_bounds__(1024) k_union_inverse(SetupSet S, UnionBottom 
 {
     __shared__ double col[2 * MG_BOTTOM_CELLS];
     const int n = U.n;
+    const SymStore<double, false> M{a, n};
     for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) a[e] = 0.0;
     __syncthreads();
     for (int b = 0; b < U.nbox; ++b) {
         const SetupBox &B = S.boxes[b];
-        assemble_box_block(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, a, n, U.off[b]);
+        assemble_box_block(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, M, U.off[b]);
     }
     __syncthreads();
     for (int q = 0; q < U.nrec; ++q) {
@@ -1877,7 +1927,7 @@ __global__ void __launch_bounds__(1024) k_union_inverse(SetupSet S, UnionBottom 
         }
         __syncthreads();
     }
-    gauss_jordan_cta(a, n, U.singular != 0, inv64, inv32, col);
+    gauss_jordan_cta(M, n, U.singular != 0, inv64, inv32, col);
 }
 
 // Coarsest solve of a coupled level: phi = Ainv f over the union, rows in
@@ -2164,12 +2214,34 @@ cudaError_t launch_round_f32(int nx, int ny, int nz, const double *wx, const dou
     return counted(cudaGetLastError());
 }
 
+int packed_bottom_bytes(int n, bool fp64)
+{
+    const long long b = (long long)n * (n + 1) / 2 * (fp64 ? 8 : 4);
+    return b <= kPackedBottomBytes ? (int)b : 0;
+}
+
+// the dense inverses' packed matrices: dynamic shared memory beyond 48 KB
+static void bottom_smem_attributes()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_bottom_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kPackedBottomBytes);
+        cudaFuncSetAttribute(k_setup_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kPackedBottomBytes);
+        cudaGetLastError();
+    });
+}
+
 cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, const double *wy,
                                   const double *wz, int singular, double *work, double *inv64,
                                   float *inv32, cudaStream_t st)
 {
-    k_bottom_inverse<<<1, 1024, 0, st>>>(nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny), wx,
-                                         wy, wz, singular, work, inv64, inv32);
+    const int packed = packed_bottom_bytes(nx * ny * nz, true);
+    bottom_smem_attributes();
+    k_bottom_inverse<<<1, 1024, packed, st>>>(nx, ny, nz, (int)pitch_row(nx), pitch_plane(nx, ny),
+                                              wx, wy, wz, singular, work, inv64, inv32,
+                                              packed > 0 ? 1 : 0);
     return counted(cudaGetLastError());
 }
 
@@ -2181,10 +2253,11 @@ cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st)
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_setup_bottom(const SetupSet &S, cudaStream_t st)
+cudaError_t launch_setup_bottom(const SetupSet &S, int packed_bytes, cudaStream_t st)
 {
     if (S.nbox == 0) return cudaSuccess;
-    k_setup_bottom<<<S.nbox, 1024, 0, st>>>(S);
+    bottom_smem_attributes();
+    k_setup_bottom<<<S.nbox, 1024, packed_bytes, st>>>(S, packed_bytes);
     return counted(cudaGetLastError());
 }
 

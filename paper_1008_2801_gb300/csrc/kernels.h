@@ -147,7 +147,12 @@ cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, cons
 // copies.
 cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st);
 // The coarsest level's dense inverse, one CTA per box.
-cudaError_t launch_setup_bottom(const SetupSet &S, cudaStream_t st);
+// packed_bytes: dynamic shared memory for the packed upper triangles (the
+// largest packed_bottom_bytes over the boxes; 0: every matrix in scratch)
+cudaError_t launch_setup_bottom(const SetupSet &S, int packed_bytes, cudaStream_t st);
+// Bytes of the packed upper triangle of an n-cell coarsest matrix if it is
+// inverted in shared memory, else 0.
+int packed_bottom_bytes(int n, bool fp64);
 
 // Projection steps (natural layouts): f = div(u, v, w) - S (S nullable), and
 // u, v, w -= beta_face grad(phi) using the level-0 weights.

@@ -780,6 +780,10 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     {
         std::vector<SetupBox> bot;
         for (int b = 0; b < nsetup; ++b) bot.push_back(setup_box(b, s->nlev[b] - 1));
+        s->bottom_packed = 0;
+        for (const SetupBox &B : bot)
+            s->bottom_packed = std::max(s->bottom_packed,
+                                        packed_bottom_bytes(B.nx * B.ny * B.nz, B.inv64 != nullptr));
         psu.push_back(plan_set(blob, &s->setup_bottom, bot));
     }
     // coupled level: ghost exchange records of every level (the cached
@@ -875,7 +879,10 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         cudaMallocHost(&s->hside, sizeof(int) * (nbox + 1)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&s->ev_setup0) != cudaSuccess ||
         cudaEventCreate(&s->ev_setup1) != cudaSuccess) {
         solver_destroy(s);
@@ -914,7 +921,10 @@ void solver_destroy(Solver *s)
     if (s->hside) cudaFreeHost(s->hside);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->side) cudaStreamDestroy(s->side);
     if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->ev_setup0) cudaEventDestroy(s->ev_setup0);
     if (s->ev_setup1) cudaEventDestroy(s->ev_setup1);
     delete s;
@@ -1009,6 +1019,15 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         CK(launch_setup(s->setup_lv[0], 0, st));
     }
     for (size_t l = 0; l < s->setup_coarsen.size(); ++l) CK(launch_setup(s->setup_coarsen[l], 1, st));
+    // the dense coarsest inverses need the coarsest weights only: forked to
+    // the side stream (one CTA per box, on as many SMs), they overlap the
+    // diagonal and FP32 steps of the finer levels on the others
+    if (!s->xmode) {
+        CK(cudaEventRecord(s->ev_fork, st));
+        CK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, s->side));
+        CK(cudaEventRecord(s->ev_join, s->side));
+    }
     for (int l = 0; l < s->maxlev; ++l) {
         CK(launch_setup(s->setup_lv[l], 2, st));
         if (s->has32) CK(launch_setup(s->setup_lv[l], 3, st));
@@ -1018,7 +1037,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
                                 s->has32 ? s->h32.uinv : nullptr, st));
         CK(launch_guard_fill(s->h64.fine, 0.0, st));  // Dirichlet zeros again
     } else {
-        CK(launch_setup_bottom(s->setup_bottom, st));
+        CK(cudaStreamWaitEvent(st, s->ev_join, 0));
     }
     CK(cudaEventRecord(s->ev_setup1, st));
     s->kernels += launch_counter() - k0;

@@ -86,6 +86,10 @@ struct Solver {
     // work already queued on the caller's stream (e.g. mg_set_beta's set-up)
     cudaStream_t copy = nullptr;
     cudaEvent_t ev_in = nullptr;   // the copy-in is done
+    // the set-up's coarsest inverses run on this stream, concurrently with the
+    // diagonal and FP32 steps of the finer levels (fork / join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool stage_clean = false;      // the staging buffers are idle (last staged call returned OK)
     cudaEvent_t ev_setup0 = nullptr, ev_setup1 = nullptr;
     bool beta_set = false;
@@ -125,6 +129,7 @@ struct Solver {
     std::vector<SetupSet> setup_lv;       // [level] every box that has the level
     std::vector<SetupSet> setup_coarsen;  // [level] boxes that have level + 1
     SetupSet setup_bottom{};              // coarsest level of every box
+    int bottom_packed = 0;                // dynamic shared memory of k_setup_bottom (packed matrices)
 
     int *derr = nullptr;                  // device error word (bounded waits that gave up)
     int bc = 0;                           // wall mask: bit w set = wall w Neumann
