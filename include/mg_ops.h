@@ -40,7 +40,9 @@ int mg_layout(const int n[3], long long *P, long long *Q, long long *elems);
  * w = harmonic mean of the two cells' beta / h^2; a wall face has 2 beta / h^2
  * (Dirichlet wall) or 0 (Neumann wall), per the wall mask bc of mg.h
  * (0..63; 0 = every wall Dirichlet).  Writes FP64 weights wx, wy, wz in the
- * level layout. */
+ * level layout.  The harmonic mean 2ab/(a+b) is taken as (2a/h^2) b times a
+ * reciprocal of a + b within one ulp (see mg_op_inv_diag), so a weight is
+ * within a few ulp of the correctly rounded value. */
 int mg_op_face_weights(const int n[3], double h, int bc, const double *beta, double *wx,
                        double *wy, double *wz, void *stream);
 
@@ -52,7 +54,9 @@ int mg_op_coarsen_weights(const int n_fine[3], const double *wx, const double *w
                           void *stream);
 
 /* D = sum of the 6 face weights of each cell (the negated diagonal of A),
- * invD = 1 / D, FP64.  D may be NULL. */
+ * invD = 1 / D, FP64, within one ulp (no FP64 division: the FP32
+ * reciprocal refined by one cubic Newton step; D outside FP32's normal
+ * range takes the division).  D may be NULL. */
 int mg_op_inv_diag(const int n[3], const double *wx, const double *wy, const double *wz,
                    double *invD, double *D, void *stream);
 
@@ -69,9 +73,10 @@ int mg_op_rbgs_pass(int prec, const int n[3], const void *wx, const void *wy, co
 /* One full red-then-black sweep as the solver runs it on large levels
  * (fused, out of place: reads phi_in, writes phi_out; phi_in is not
  * modified).  Equal to a red pass followed by a black pass.  The sweep reads
- * no inverse diagonal: each update takes the correctly rounded reciprocal of
+ * no inverse diagonal: each update takes the reciprocal of
  * D = ((wx- + wx+) + (wy- + wy+)) + (wz- + wz+), summed from the six weights
- * it loads (in FP64 the value mg_op_inv_diag stores).  Each CTA marches
+ * it loads (FP32: correctly rounded; FP64: the value mg_op_inv_diag
+ * stores).  Each CTA marches
  * through zc planes (zc <= 0: 32).  UNSUPPORTED for levels of 2^31 or more
  * elements (the kernel indexes with 32-bit offsets). */
 int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, const void *wz,
