@@ -1433,10 +1433,10 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
 
 // step 0 faces (TK_FACE), 1 coarsen (TK_CFACE), 2 diagonal (TK_CELL),
 // 3 FP32 copies (TK_FACE), 4 faces of a coupled level from betaL (TK_FACE)
-__global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step)
+__global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step, int t0)
 {
     const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
-    const int t = blockIdx.x;
+    const int t = blockIdx.x + t0;
     const int *ts = S.tstart[kind];
     const int b = find_box(ts, S.nbox, t);
     const SetupBox &B = S.boxes[b];
@@ -2249,7 +2249,14 @@ cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st)
 {
     const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
     if (S.ntiles[kind] == 0) return cudaSuccess;
-    k_setup<<<S.ntiles[kind], block2d(), 0, st>>>(S, step);
+    k_setup<<<S.ntiles[kind], block2d(), 0, st>>>(S, step, 0);
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_setup_tiles(const SetupSet &S, int step, int t0, int t1, cudaStream_t st)
+{
+    if (t1 <= t0) return cudaSuccess;
+    k_setup<<<t1 - t0, block2d(), 0, st>>>(S, step, t0);
     return counted(cudaGetLastError());
 }
 

@@ -146,6 +146,9 @@ cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, cons
 // step 0: face weights from beta; 1: coarse weights; 2: D and 1/D; 3: FP32
 // copies.
 cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st);
+// Tiles [t0, t1) of one step (tiles are numbered plane by plane, so a range
+// of whole planes of a one-box set is a range of tiles).
+cudaError_t launch_setup_tiles(const SetupSet &S, int step, int t0, int t1, cudaStream_t st);
 // The coarsest level's dense inverse, one CTA per box.
 // packed_bytes: dynamic shared memory for the packed upper triangles (the
 // largest packed_bottom_bytes over the boxes; 0: every matrix in scratch)

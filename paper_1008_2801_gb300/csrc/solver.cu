@@ -454,6 +454,13 @@ static int coupled_levels(int nbox, const int (*lo)[3], const int (*n)[3],
     return L;
 }
 
+static bool create_events(cudaEvent_t *e, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreateWithFlags(&e[i], cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+}
+
 int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
                   const mg_opts *opts, bool shared_weights, const int (*lo)[3])
 {
@@ -883,6 +890,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        !create_events(s->ev_slab, Solver::kBetaSlabs) ||
         cudaEventCreate(&s->ev_setup0) != cudaSuccess ||
         cudaEventCreate(&s->ev_setup1) != cudaSuccess) {
         solver_destroy(s);
@@ -925,6 +933,8 @@ void solver_destroy(Solver *s)
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
+    for (cudaEvent_t &e : s->ev_slab)
+        if (e) cudaEventDestroy(e);
     if (s->ev_setup0) cudaEventDestroy(s->ev_setup0);
     if (s->ev_setup1) cudaEventDestroy(s->ev_setup1);
     delete s;
@@ -945,6 +955,17 @@ static bool is_device_ptr(const void *p, int dev, bool *wrong_dev)
         return true;
     }
     return a.type == cudaMemoryTypeManaged;
+}
+
+// Page-locked host memory (cudaMallocHost / cudaHostRegister).
+static bool is_pinned_host(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
 }
 
 static int ensure_stage(Solver *s)
@@ -1005,7 +1026,37 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     CK(cudaEventRecord(s->ev_setup0, st));
     const long long k0 = launch_counter();
     const long long nbeta = s->shared ? s->off[1] : s->total;
-    CK(cudaMemcpyAsync(s->beta, beta, sizeof(double) * nbeta, cudaMemcpyDefault, st));
+    // one box, beta in pinned host memory: copied in by slabs of planes on
+    // the copy stream (after the caller's stream has finished with the
+    // previous beta), each slab's face weights launched once it is in
+    // (face positions of planes [a, b) read beta planes a-1 .. b-1)
+    const int nx = s->n[0][0], ny = s->n[0][1], nz = s->n[0][2];
+    const long long plane = (long long)nx * ny;
+    int slabs = (int)std::max<long long>(
+        1, std::min<long long>(Solver::kBetaSlabs, (long long)sizeof(double) * nbeta >> 22));  // >= 4 MiB each
+    if (s->xmode || !(s->nbox == 1 || s->shared) || !is_pinned_host(beta) || nz < 2 * slabs)
+        slabs = 1;
+    if (slabs > 1) {
+        int ex, ey, ez;
+        tile_extent(TK_FACE, nx, ny, nz, ex, ey, ez);
+        const int per_plane = tiles_of(TK_FACE, nx, ny, nz) / ez;
+        const int zs = (nz + slabs - 1) / slabs;
+        CK(cudaEventRecord(s->ev_fork, st));
+        CK(cudaStreamWaitEvent(s->copy, s->ev_fork, 0));
+        for (int c = 0, a = 0; a < nz; ++c, a += zs) {
+            const int b = std::min(nz, a + zs);
+            CK(cudaMemcpyAsync(s->beta + a * plane, beta + a * plane,
+                               sizeof(double) * plane * (b - a), cudaMemcpyHostToDevice, s->copy));
+            CK(cudaEventRecord(s->ev_slab[c], s->copy));
+        }
+        for (int c = 0, a = 0; a < nz; ++c, a += zs) {
+            const int b = a + zs >= nz ? nz + 1 : a + zs;  // the last slab takes the top faces
+            CK(cudaStreamWaitEvent(st, s->ev_slab[c], 0));
+            CK(launch_setup_tiles(s->setup_lv[0], 0, a * per_plane, b * per_plane, st));
+        }
+    } else {
+        CK(cudaMemcpyAsync(s->beta, beta, sizeof(double) * nbeta, cudaMemcpyDefault, st));
+    }
     if (s->xmode) {
         // beta into the level layout of level 0 (staged in phi), guard cells
         // -1 (the union's boundary) except where the exchange brings the
@@ -1014,7 +1065,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         CK(launch_pack(s->h64.fine, s->doff, s->beta, 0, st));
         CK(launch_exchange(s->h64.fine, nullptr, s->xrec[0], s->nxrec[0], s->xmax[0], st));
         CK(launch_setup(s->setup_lv[0], 4, st));
-    } else {
+    } else if (slabs == 1) {
         // one launch per step and level over every box
         CK(launch_setup(s->setup_lv[0], 0, st));
     }

@@ -90,6 +90,10 @@ struct Solver {
     // diagonal and FP32 steps of the finer levels (fork / join events)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // a one-box host beta is copied in by slabs of planes on the copy stream,
+    // the face-weight step of each slab starting as soon as it has landed
+    static constexpr int kBetaSlabs = 8;
+    cudaEvent_t ev_slab[kBetaSlabs] = {};
     bool stage_clean = false;      // the staging buffers are idle (last staged call returned OK)
     cudaEvent_t ev_setup0 = nullptr, ev_setup1 = nullptr;
     bool beta_set = false;

@@ -88,3 +88,24 @@ def test_batched_and_level_zero_guess_ignore_phi(cuda_device):
         want, _ = lv.solve(fp, tol=TOL)
         got, st = lv.solve(fp, torch.full_like(fp, float("nan")), tol=TOL, zero_guess=True)
         assert st["status"] == "ok" and torch.equal(got, want)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(112, 128, 128), (96, 128, 128), (128, 128, 192)])
+def test_host_beta_by_slabs_matches_device_beta(cuda_device, shape, precision):
+    # a pinned host beta of 4 MiB or more is copied in by slabs of planes,
+    # each slab's face weights starting when it has landed (3 slabs of 38,
+    # 38 and 36 planes in the first shape, 6 in the last): the set-up, and so
+    # the solution, is the device beta's bit for bit, also when a second
+    # set-up follows
+    beta, f, h = _case(shape, 9)
+    assert beta.numel() * 8 >= 2 << 22
+    with Solver(tuple(f.shape), h, precision=precision, device=cuda_device) as s:
+        s.set_beta(beta.to(cuda_device))
+        want, _ = s.solve(f.to(cuda_device), tol=TOL)
+        bh = beta.pin_memory()
+        for _ in range(2):
+            s.set_beta(bh)
+            got, st = s.solve(f.to(cuda_device), tol=TOL)
+            assert st["status"] == "ok"
+            assert torch.equal(got, want)
