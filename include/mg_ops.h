@@ -166,12 +166,13 @@ int mg_op_residual_norm_noalloc(int prec, const int n[3], const void *wx, const 
 
 /* Mixed-precision refinement step on the finest level (FP64 x, f, weights,
  * D; FP32 correction e and scaled residual r32):
- *   x += (*c_e) e  (in place);  r = f - A64 x;  r32 = float(r) * float(1/(*c_r));
+ *   x += (*c_e) e  (in place), then e = 0;  r = f - A64 x;
+ *   r32 = float(r) * float(1/(*c_r));
  *   *out = (*c_r) * ||r32||_2  (= ||r||_2 to FP32 accuracy; fixed-order
  *   reduction through `partials`).
  * c_e and c_r are device doubles, c_r > 0. */
 int mg_op_refine(const int n[3], const double *wx, const double *wy, const double *wz,
-                 const double *D, const double *f, double *x, const float *e, float *r32,
+                 const double *D, const double *f, double *x, float *e, float *r32,
                  const double *c_e, const double *c_r, double *partials, double *out,
                  void *stream);
 

@@ -917,7 +917,7 @@ __global__ void __launch_bounds__(CoarseThreads<T>::value) k_coarse_vcycle(const
 // ------------------------------------------------ mixed refinement step ----
 //
 // FP64 iterative refinement around FP32 V-cycles, in two passes per step:
-//   k_refine_update:   x += c_e e               (in place, pointwise)
+//   k_refine_update:   x += c_e e, then e = 0   (in place, pointwise)
 //   k_refine_residual: r = f - A64 x;  r32 = float(r) * float(1 / c_r);
 //                      partial sums of r32^2 (FP32 per column, FP64 per CTA)
 // so ||r|| = c_r * sqrt(sum r32^2).  Only the update, the residual and their
@@ -938,7 +938,9 @@ __global__ void __launch_bounds__(kThreads) k_refine_update(BoxSet<double> S64, 
     TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
     const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    B.phi[c] = fma(c_e[B.box], (double)E.phi[c], B.phi[c]);
+    const float e = E.phi[c];
+    B.phi[c] = fma(c_e[B.box], (double)e, B.phi[c]);
+    E.phi[c] = 0.f;   // the next step's FP32 cycles start from e = 0
 }
 
 __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64, BoxSet<float> S32,
@@ -1118,27 +1120,42 @@ __device__ __forceinline__ double wall_beta(int bcm, int w, double b)
 }
 
 // Face weights at position (i, j, k) in [0, nx] x [0, ny] x [0, nz]: harmonic
-// mean of the two cells' beta (a wall face: wall_beta) over h^2.
+// mean of the two cells' beta (a wall face: wall_beta) over h^2; with W32
+// (mixed precision's finest level) also their FP32 roundings, the values
+// the rounding step would write (a compile-time choice: a run-time test
+// would cost the FP64-bound FP64 path its predicated conversions).
+template <bool W32>
 __device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, long long Q,
                                                 double inv_h2, int bcm,
                                                 const double *__restrict__ beta, double *wx,
-                                                double *wy, double *wz, int i, int j, int k)
+                                                double *wy, double *wz, int i, int j, int k,
+                                                float *wx32 = nullptr, float *wy32 = nullptr,
+                                                float *wz32 = nullptr)
 {
     auto bc = [&](int a, int bb, int c) { return beta[((long long)c * ny + bb) * nx + a]; };
     const long long q = (long long)k * Q + (long long)j * P + i;
     const double c2 = 2.0 * inv_h2;
-    if (j < ny && k < nz)
-        wx[q] = (i == 0) ? wall_beta(bcm, 0, bc(0, j, k)) * inv_h2
-              : (i == nx) ? wall_beta(bcm, 1, bc(nx - 1, j, k)) * inv_h2
-                          : harmonic_w(bc(i - 1, j, k), bc(i, j, k), c2);
-    if (i < nx && k < nz)
-        wy[q] = (j == 0) ? wall_beta(bcm, 2, bc(i, 0, k)) * inv_h2
-              : (j == ny) ? wall_beta(bcm, 3, bc(i, ny - 1, k)) * inv_h2
-                          : harmonic_w(bc(i, j - 1, k), bc(i, j, k), c2);
-    if (i < nx && j < ny)
-        wz[q] = (k == 0) ? wall_beta(bcm, 4, bc(i, j, 0)) * inv_h2
-              : (k == nz) ? wall_beta(bcm, 5, bc(i, j, nz - 1)) * inv_h2
-                          : harmonic_w(bc(i, j, k - 1), bc(i, j, k), c2);
+    if (j < ny && k < nz) {
+        const double v = (i == 0) ? wall_beta(bcm, 0, bc(0, j, k)) * inv_h2
+                       : (i == nx) ? wall_beta(bcm, 1, bc(nx - 1, j, k)) * inv_h2
+                                   : harmonic_w(bc(i - 1, j, k), bc(i, j, k), c2);
+        wx[q] = v;
+        if (W32) wx32[q] = (float)v;
+    }
+    if (i < nx && k < nz) {
+        const double v = (j == 0) ? wall_beta(bcm, 2, bc(i, 0, k)) * inv_h2
+                       : (j == ny) ? wall_beta(bcm, 3, bc(i, ny - 1, k)) * inv_h2
+                                   : harmonic_w(bc(i, j - 1, k), bc(i, j, k), c2);
+        wy[q] = v;
+        if (W32) wy32[q] = (float)v;
+    }
+    if (i < nx && j < ny) {
+        const double v = (k == 0) ? wall_beta(bcm, 4, bc(i, j, 0)) * inv_h2
+                       : (k == nz) ? wall_beta(bcm, 5, bc(i, j, nz - 1)) * inv_h2
+                                   : harmonic_w(bc(i, j, k - 1), bc(i, j, k), c2);
+        wz[q] = v;
+        if (W32) wz32[q] = (float)v;
+    }
 }
 
 // Face weights of a coupled level's box from beta in the level layout (bl),
@@ -1188,14 +1205,19 @@ __device__ __forceinline__ void coarsen_at(int nx, int ny, int nz, int P, long l
                    wz[at(2 * I, 2 * J + 1, 2 * K)] + wz[at(2 * I + 1, 2 * J + 1, 2 * K)]) * 0.0625;
 }
 
+template <bool W32 = false>
 __device__ __forceinline__ void inv_diag_at(int P, long long Q, const double *__restrict__ wx,
                                             const double *__restrict__ wy,
                                             const double *__restrict__ wz, double *invD,
-                                            double *Dout, long long c, long long cf)
+                                            double *Dout, long long c, long long cf,
+                                            float *invD32 = nullptr)
 {
     const double D = ((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]);
     if (invD) invD[cf] = rcp64(D);  // NULL: mixed precision, whose FP64 levels never smooth
     if (Dout) Dout[cf] = D;
+    // mixed precision's finest level (no FP64 1/D): the FP32 1/D the
+    // rounding step would write
+    if (W32) invD32[c] = 1.0f / (float)D;
 }
 
 // Every stored weight (and the inverse diagonal) at position (i, j, k) in
@@ -1369,7 +1391,7 @@ __global__ void k_face_weights(int nx, int ny, int nz, int P, long long Q, doubl
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i > nx || j > ny || k > nz) return;
-    face_weights_at(nx, ny, nz, P, Q, inv_h2, bcm, beta, wx, wy, wz, i, j, k);
+    face_weights_at<false>(nx, ny, nz, P, Q, inv_h2, bcm, beta, wx, wy, wz, i, j, k);
 }
 
 __global__ void k_coarsen(int nx, int ny, int nz, int P, long long Q, const double *__restrict__ wx,
@@ -1431,11 +1453,19 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
 
 // ---- every box of a level in one launch (the solver's set-up)
 
+__host__ __device__ inline int setup_kind(int step)
+{
+    return step == 1 ? TK_CFACE : (step == 2 || step == 6) ? TK_CELL : TK_FACE;
+}
+
 // step 0 faces (TK_FACE), 1 coarsen (TK_CFACE), 2 diagonal (TK_CELL),
-// 3 FP32 copies (TK_FACE), 4 faces of a coupled level from betaL (TK_FACE)
+// 3 FP32 copies (TK_FACE), 4 faces of a coupled level from betaL (TK_FACE),
+// 5 faces with their FP32 copies (TK_FACE), 6 diagonal with the FP32 1/D
+// (TK_CELL): 5 and 6 take the place of 0, 2 and 3 on mixed precision's
+// finest level
 __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step, int t0)
 {
-    const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
+    const int kind = setup_kind(step);
     const int t = blockIdx.x + t0;
     const int *ts = S.tstart[kind];
     const int b = find_box(ts, S.nbox, t);
@@ -1445,8 +1475,11 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step, int t0
     tile_extent(kind, B.nx, B.ny, B.nz, ex, ey, ez);
     if (p.x >= ex || p.y >= ey) return;
     if (step == 0)
-        face_weights_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy, B.wz, p.x,
-                        p.y, p.z);
+        face_weights_at<false>(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy,
+                               B.wz, p.x, p.y, p.z);
+    else if (step == 5)
+        face_weights_at<true>(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy,
+                              B.wz, p.x, p.y, p.z, B.wx32, B.wy32, B.wz32);
     else if (step == 1)
         coarsen_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.cP, B.cQ, B.cwx, B.cwy, B.cwz,
                    p.x, p.y, p.z);
@@ -1455,6 +1488,12 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step, int t0
                     (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
                     B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
                          : (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
+    else if (step == 6)
+        inv_diag_at<true>(B.P, B.Q, B.wx, B.wy, B.wz, nullptr, B.D,
+                          (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
+                          B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
+                               : (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
+                          B.invD32);
     else if (step == 4)
         face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.betaL, B.wx, B.wy,
                               B.wz, p.x, p.y, p.z);
@@ -2247,7 +2286,7 @@ cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, cons
 
 cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st)
 {
-    const int kind = step == 1 ? TK_CFACE : step == 2 ? TK_CELL : TK_FACE;
+    const int kind = setup_kind(step);
     if (S.ntiles[kind] == 0) return cudaSuccess;
     k_setup<<<S.ntiles[kind], block2d(), 0, st>>>(S, step, 0);
     return counted(cudaGetLastError());

@@ -359,7 +359,7 @@ int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy
 }
 
 int mg_op_refine(const int n[3], const double *wx, const double *wy, const double *wz,
-                 const double *D, const double *f, double *x, const float *e, float *r32,
+                 const double *D, const double *f, double *x, float *e, float *r32,
                  const double *c_e, const double *c_r, double *partials, double *out,
                  void *stream)
 {

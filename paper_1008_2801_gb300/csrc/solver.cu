@@ -1032,6 +1032,10 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     // (face positions of planes [a, b) read beta planes a-1 .. b-1)
     const int nx = s->n[0][0], ny = s->n[0][1], nz = s->n[0][2];
     const long long plane = (long long)nx * ny;
+    // mixed precision's finest level takes its FP32 copies with its faces
+    // (step 5) and its FP32 1/D with its diagonal (step 6); a coupled level's
+    // faces come from step 4, and its copies from step 3
+    const int face_step = s->has32 ? 5 : 0;
     int slabs = (int)std::max<long long>(
         1, std::min<long long>(Solver::kBetaSlabs, (long long)sizeof(double) * nbeta >> 22));  // >= 4 MiB each
     if (s->xmode || !(s->nbox == 1 || s->shared) || !is_pinned_host(beta) || nz < 2 * slabs)
@@ -1052,7 +1056,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         for (int c = 0, a = 0; a < nz; ++c, a += zs) {
             const int b = a + zs >= nz ? nz + 1 : a + zs;  // the last slab takes the top faces
             CK(cudaStreamWaitEvent(st, s->ev_slab[c], 0));
-            CK(launch_setup_tiles(s->setup_lv[0], 0, a * per_plane, b * per_plane, st));
+            CK(launch_setup_tiles(s->setup_lv[0], face_step, a * per_plane, b * per_plane, st));
         }
     } else {
         CK(cudaMemcpyAsync(s->beta, beta, sizeof(double) * nbeta, cudaMemcpyDefault, st));
@@ -1067,7 +1071,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         CK(launch_setup(s->setup_lv[0], 4, st));
     } else if (slabs == 1) {
         // one launch per step and level over every box
-        CK(launch_setup(s->setup_lv[0], 0, st));
+        CK(launch_setup(s->setup_lv[0], face_step, st));
     }
     for (size_t l = 0; l < s->setup_coarsen.size(); ++l) CK(launch_setup(s->setup_coarsen[l], 1, st));
     // the dense coarsest inverses need the coarsest weights only: forked to
@@ -1080,8 +1084,9 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         CK(cudaEventRecord(s->ev_join, s->side));
     }
     for (int l = 0; l < s->maxlev; ++l) {
-        CK(launch_setup(s->setup_lv[l], 2, st));
-        if (s->has32) CK(launch_setup(s->setup_lv[l], 3, st));
+        const bool fused32 = s->has32 && l == 0 && !s->xmode;
+        CK(launch_setup(s->setup_lv[l], fused32 ? 6 : 2, st));
+        if (s->has32 && !fused32) CK(launch_setup(s->setup_lv[l], 3, st));
     }
     if (s->xmode) {
         CK(launch_union_inverse(s->setup_bottom, s->ub, s->work, s->h64.uinv,
@@ -1321,11 +1326,11 @@ static cudaError_t enqueue_tail64(Solver *s, cudaStream_t st)
     return enqueue_vcycle(s, s->h64, st, true);
 }
 
-// Mixed: zero the FP32 correction, inner_cycles FP32 V-cycles on r32.
+// Mixed: inner_cycles FP32 V-cycles on r32, from e = 0 (zeroed by the
+// prologue, and after that by each refinement update once it has used e).
 static cudaError_t enqueue_step32(Solver *s, cudaStream_t st)
 {
-    cudaError_t e = launch_zero(s->h32.fine, s->active, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     const int inner = s->opts.inner_cycles > 0 ? s->opts.inner_cycles : 2;
     for (int i = 0; i < inner; ++i)
         if ((e = enqueue_vcycle(s, s->h32, st)) != cudaSuccess) return e;

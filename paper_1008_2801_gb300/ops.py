@@ -179,7 +179,7 @@ def residual_norm(w, f, phi, shape, D=None):
 
 
 def refine(w, D, f, x, e32, c_e, c_r, shape):
-    """x += c_e e in place; returns (x, r32 = (f - A x) / c_r, ||f - A x||)."""
+    """x += c_e e in place, then e = 0; returns (x, r32 = (f - A x) / c_r, ||f - A x||)."""
     L = _lib.load()
     r32 = torch.zeros_like(e32)
     m = L.mg_op_norm_scratch(_n(shape))

@@ -267,8 +267,9 @@ def test_refinement_step(cuda_device, shape):
     e = np.random.default_rng(10).uniform(-1, 1, shape).astype(np.float32)
     c_e, c_r = 0.37, 2.5
     xt = _level(shape, x, cuda_device)
-    xo, r32, nrm = K.refine(w, D, _level(shape, f, cuda_device), xt,
-                            _level(shape, e, cuda_device, torch.float32), c_e, c_r, shape)
+    et = _level(shape, e, cuda_device, torch.float32)
+    xo, r32, nrm = K.refine(w, D, _level(shape, f, cuda_device), xt, et, c_e, c_r, shape)
+    assert not et.any()          # the correction is used up: the next cycles start from 0
     faces = O.face_beta(beta)
     want_x = x + c_e * e.astype(np.float64)
     r = O.residual(faces, h, f, want_x)
