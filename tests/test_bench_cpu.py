@@ -23,3 +23,28 @@ def test_reference_arm_json_line():
     assert "16^3" in d["config"]["workload"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_stored_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    # a DRAM figure from an ncu capture is reported only while the kernel's
+    # source region (and the shared header) is the one it was taken on
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.stored_traffic("rbgs_pass_f64") is not None
+    assert bench.stored_traffic("rbgs_sweep_f32") is not None
+    src = tmp_path / "paper_1008_2801_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for f in ("kernels.cu", "common.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_1008_2801_gb300", "csrc", f), src / f)
+    shutil.copytree(os.path.join(ROOT, "profiles"), tmp_path / "profiles")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.stored_traffic("rbgs_pass_f64") is not None
+    text = (src / "kernels.cu").read_text()
+    a, b = bench.TRAFFIC_REGIONS["rbgs_sweep_f32"]
+    i = text.index(a) + len(a)
+    (src / "kernels.cu").write_text(text[:i] + "\n// edited\n" + text[i:])
+    assert bench.stored_traffic("rbgs_sweep_f32") is None      # its region changed
+    assert bench.stored_traffic("rbgs_pass_f64") is not None   # the other did not
+    (src / "common.cuh").write_text((src / "common.cuh").read_text() + "\n")
+    assert bench.stored_traffic("rbgs_pass_f64") is None       # the shared header changed
