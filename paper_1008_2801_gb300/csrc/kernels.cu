@@ -1274,7 +1274,7 @@ struct SymStore {
 };
 
 // Packed FP64 / FP32 matrices up to this size are inverted in shared memory
-// (n <= 231 in FP64, n <= 328 in FP32).
+// (n <= 225 in FP64, n <= 319 in FP32).
 constexpr int kPackedBottomBytes = 200 * 1024;
 
 // The upper triangle of the block of M = -A of one box, rows and columns

@@ -78,3 +78,19 @@ def test_invalid_shapes_are_rejected(cuda_device):
     with pytest.raises(MGError) as e:
         Solver((33, 33, 33), 0.1, device=cuda_device)    # a 35937-cell coarsest level
     assert e.value.name == "unsupported"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(15, 5, 3), (11, 7, 3), (9, 7, 5), (13, 5, 5)])
+def test_coarsest_inverse_either_side_of_shared_memory(cuda_device, shape, precision):
+    # one-level boxes (odd sides) whose dense inverse is packed in shared
+    # memory or kept in global scratch: 225 and 231 cells straddle the FP64
+    # limit (n <= 225), 315 and 325 the FP32 one (n <= 319)
+    beta, f, h = _case(shape, 70)
+    with Solver(shape, h, precision=precision, device=cuda_device) as s:
+        s.set_beta(_t(beta, cuda_device))
+        phi, st = s.solve(_t(f, cuda_device), tol=TOL)
+    assert st["status"] == "ok", st
+    ref, info = O.solve(beta, f, h, tol=1e-13)
+    assert info["status"] == "ok"
+    assert np.linalg.norm(phi.cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
