@@ -19,7 +19,7 @@ TOL = 1e-10
 
 
 def _dev(a, dev):
-    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    return torch.from_numpy(np.array(a, order="C", copy=True)).to(dev)   # writable copy
 
 
 def _rel_resid(beta, f, phi, h):
