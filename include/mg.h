@@ -142,7 +142,14 @@ typedef struct {
                          not apply: a CG residual is not monotone). */
     int max_norm;     /* 1: also report rel_resid_max in mg_stats (one more
                          pass over the level after the solve); 0 (default) */
-    int reserved[4];
+    int wait_limit;   /* bounded device waits (the TMA sweep's tile-copy
+                         waits): polls of the barrier before a wait gives
+                         up, sets the context's error word and the solve
+                         returns MG_ERR_TIMEOUT.  0 (default): 2^22 polls;
+                         n > 0: n polls; -1: give up at the first wait
+                         (exercises the timeout path; the CTA still drains
+                         the copies it issued before it exits) */
+    int reserved[3];
     /* Device memory of the context (its arena, launch descriptors and host
      * staging buffers) comes from dev_alloc(bytes, alloc_user) when set (NULL
      * on failure: MG_ERR_OOM) and goes back through dev_free(ptr,

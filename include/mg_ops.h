@@ -156,7 +156,10 @@ int mg_op_residual_norm(int prec, const int n[3], const void *wx, const void *wy
  * MG_ERR_INVALID_ARG before anything runs.
  * The first call on a device, with that device current, looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call reuses the array and overwrites the slots it
+ * stream capture.  The address is cached per device for the life of the
+ * process: do not use this entry point after a cudaDeviceReset (the
+ * module, and with it the array, may then sit elsewhere).  Every call
+ * reuses the array and overwrites the slots it
  * reads, so nothing needs clearing, but calls that overlap on the GPU race on
  * it: order them (same stream, or synchronise).  Arguments as
  * mg_op_residual_norm without `partials`. */

@@ -45,7 +45,8 @@ class mg_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("max_cycles", c_int),
                 ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
                 ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
-                ("krylov", c_int), ("max_norm", c_int), ("reserved", c_int * 4),
+                ("krylov", c_int), ("max_norm", c_int), ("wait_limit", c_int),
+                ("reserved", c_int * 3),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_user", c_void_p)]
 
 

@@ -33,9 +33,14 @@ bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_
                        const float *wy_base, const float *wz_base);
 int sweep_tma_ctas_per_sm();
 // Same result as launch_rbgs_sweep<float>; *err is set to 1 if a bounded
-// wait on a tile copy gave up (the CTA then stops).
+// wait on a tile copy gave up after wait_polls polls (the CTA then waits,
+// with the default bound, for the copies it issued and stops).
 cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps,
-                                  const int *active, int src_is_phi2, int *err, cudaStream_t st);
+                                  const int *active, int src_is_phi2, int *err, cudaStream_t st,
+                                  long long wait_polls);
+// Polls of a tile-copy wait for mg_opts.wait_limit (0: the default bound;
+// -1: none, the first wait gives up).
+long long sweep_wait_polls(int wait_limit);
 
 // Resident CTAs per SM of the fused sweep kernel (occupancy query).
 template <class T>

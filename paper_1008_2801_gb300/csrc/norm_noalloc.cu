@@ -20,6 +20,10 @@
 // device with cudaGetSymbolAddress, with that device current, on the first
 // call made while it is current.  That first call therefore does a runtime
 // query; make it before any stream capture that should contain the call.
+// The cached address belongs to the device's primary context as it was at
+// that first call: after cudaDeviceReset (or any other teardown of that
+// context) the module is loaded afresh and the address may change, so the
+// entry point must not be used across a device reset in one process.
 #include <mutex>
 
 #include "common.cuh"

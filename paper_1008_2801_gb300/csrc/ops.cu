@@ -228,7 +228,8 @@ int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const
     int *err = reinterpret_cast<int *>(dev + sweep_maps_size());
     CKO(cudaMemcpyAsync(dev, m, sweep_maps_size(), cudaMemcpyHostToDevice, st));
     CKO(cudaMemsetAsync(err, 0, sizeof(int), st));
-    CKO(launch_rbgs_sweep_tma(ts.S, reinterpret_cast<const SweepMaps *>(dev), nullptr, 0, err, st));
+    CKO(launch_rbgs_sweep_tma(ts.S, reinterpret_cast<const SweepMaps *>(dev), nullptr, 0, err, st,
+                              sweep_wait_polls(0)));
     int herr = 0;
     CKO(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKO(cudaStreamSynchronize(st));

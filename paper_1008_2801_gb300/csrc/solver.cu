@@ -407,6 +407,7 @@ static int validate_opts(const mg_opts *o)
     if (o->inner_cycles < 0 || o->inner_cycles > 8)
         return set_error(MG_ERR_INVALID_ARG, "inner_cycles must be in 0..8");
     if (o->krylov < 0 || o->krylov > 1) return set_error(MG_ERR_INVALID_ARG, "krylov must be 0 or 1");
+    if (o->wait_limit < -1) return set_error(MG_ERR_INVALID_ARG, "wait_limit must be >= -1");
     if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr))
         return set_error(MG_ERR_INVALID_ARG, "dev_alloc and dev_free come together");
     return MG_OK;
@@ -1172,7 +1173,9 @@ static cudaError_t sweep_launch(Solver *s, const BoxSet<double> &S, const SweepM
 static cudaError_t sweep_launch(Solver *s, const BoxSet<float> &S, const SweepMaps *maps, int src,
                                 cudaStream_t st)
 {
-    if (maps) return launch_rbgs_sweep_tma(S, maps, s->active, src, s->derr, st);
+    if (maps)
+        return launch_rbgs_sweep_tma(S, maps, s->active, src, s->derr, st,
+                                     sweep_wait_polls(s->opts.wait_limit));
     return launch_rbgs_sweep(S, s->active, src, st);
 }
 

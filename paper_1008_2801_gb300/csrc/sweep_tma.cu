@@ -48,7 +48,7 @@ constexpr unsigned kTxBytes = kSrcBytes + 3 * kOpBytes + kWyBytes;  // bytes lan
 constexpr int kRedBytes = 3 * (kSweepTY + 2) * (2 * kTX + 2) * 4;
 constexpr int kSmemBytes = kStages * kStageBytes + pad128(kRedBytes) + 128;
 
-constexpr long long kWaitLimit = 1ll << 22;  // try_wait polls before giving up
+constexpr long long kWaitLimit = 1ll << 22;  // default try_wait polls before giving up
 
 __device__ __forceinline__ unsigned smem_addr(const void *p)
 {
@@ -78,10 +78,11 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of the barrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+// Bounded wait for phase `parity` of the barrier: at most `polls` polls;
+// false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long polls)
 {
-    for (long long i = 0; i < kWaitLimit; ++i)
+    for (long long i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -114,7 +115,8 @@ namespace {
 
 __global__ void __launch_bounds__(kTX * kSweepTY, 3)
     k_rbgs_sweep_tma(BoxSet<float> S, const SweepMaps *__restrict__ maps,
-                     const int *__restrict__ active, int src_is_phi2, int *__restrict__ err)
+                     const int *__restrict__ active, int src_is_phi2, int *__restrict__ err,
+                     long long polls)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -207,11 +209,12 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 3)
     // give-up takes every thread out of the loop together.
     bool ok = true;
     for (int p = pfirst; p <= pfirst + 1 && ok; ++p)
-        ok = __syncthreads_and(mbar_wait(smem_addr(&bars[stage_of(p)]), phase_of(p)));
+        ok = __syncthreads_and(mbar_wait(smem_addr(&bars[stage_of(p)]), phase_of(p), polls));
 
     int k = z0 - 1;
     for (; k <= z1 && ok; ++k) {
-        if (!__syncthreads_and(mbar_wait(smem_addr(&bars[stage_of(k + 1)]), phase_of(k + 1)))) {
+        if (!__syncthreads_and(
+                mbar_wait(smem_addr(&bars[stage_of(k + 1)]), phase_of(k + 1), polls))) {
             ok = false;
             break;
         }
@@ -278,13 +281,16 @@ __global__ void __launch_bounds__(kTX * kSweepTY, 3)
         if (tid == 0 && k + 3 <= plast && k - 1 >= pfirst) issue(k + 3);
     }
     if (!ok) {
-        // report, then wait (bounded) for every copy this CTA issued
+        // report, then wait (with the default bound, whatever `polls` was)
+        // for every copy this CTA issued: planes pfirst .. k + 2 (the loop
+        // stopped at step k, whose copies up to plane k + 2 were issued; at
+        // most the first kStages planes if it stopped before its first step)
         if (tid == 0) atomicExch(err, 1);
         __syncthreads();
         if (tid == 0) {
             const int last = min(plast, k + 2);
-            for (int p = pfirst; p <= last; ++p) mbar_wait(smem_addr(&bars[stage_of(p)]),
-                                                            phase_of(p));
+            for (int p = pfirst; p <= last; ++p)
+                mbar_wait(smem_addr(&bars[stage_of(p)]), phase_of(p), kWaitLimit);
         }
         __syncthreads();
     }
@@ -344,13 +350,26 @@ bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_
 size_t sweep_maps_size() { return sizeof(SweepMaps); }
 
 // The ring's dynamic shared memory, and the largest shared-memory carveout so
-// that three CTAs fit on an SM.
+// that three CTAs fit on an SM.  Function attributes are per device: they
+// are set once on each device, the first time a launch or an occupancy
+// query runs with that device current.
 static void set_smem_attributes()
 {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && done[dev]) return;
     cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kSmemBytes);
     cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
+    if (dev >= 0) done[dev] = true;
 }
 
 // Levels whose rows and planes hold a whole copy box (72 x 12).
@@ -368,14 +387,18 @@ int sweep_tma_ctas_per_sm()
     return n > 0 ? n : 1;
 }
 
+long long sweep_wait_polls(int wait_limit)
+{
+    return wait_limit == 0 ? kWaitLimit : wait_limit < 0 ? 0 : (long long)wait_limit;
+}
+
 cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps, const int *active,
-                                  int src_is_phi2, int *err, cudaStream_t st)
+                                  int src_is_phi2, int *err, cudaStream_t st, long long wait_polls)
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
-    static std::once_flag once;
-    std::call_once(once, [] { set_smem_attributes(); });
+    set_smem_attributes();
     k_rbgs_sweep_tma<<<S.ntiles[TK_SWEEP], dim3(kTX, kSweepTY), kSmemBytes, st>>>(
-        S, maps, active, src_is_phi2, err);
+        S, maps, active, src_is_phi2, err, wait_polls);
     return cudaGetLastError();
 }
 

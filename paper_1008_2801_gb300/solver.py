@@ -15,6 +15,7 @@ Non-zero wall values enter through ``bc_lift``.
 from __future__ import annotations
 
 import ctypes
+import warnings
 
 import torch
 
@@ -66,7 +67,8 @@ def _torch_allocator(device):
 
 
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
-          full_residual=False, tma=False, krylov=False, max_norm=False, hooks=None):
+          full_residual=False, tma=False, krylov=False, max_norm=False, hooks=None,
+          wait_limit=0):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -79,6 +81,7 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.tma = 1 if tma else 0
     o.krylov = 1 if krylov else 0
     o.max_norm = 1 if max_norm else 0
+    o.wait_limit = int(wait_limit)
     if hooks is not None:
         o.dev_alloc, o.dev_free = hooks
     return o
@@ -144,13 +147,15 @@ class Solver:
     symmetric V-cycle per iteration instead of plain V-cycles, for
     high-contrast beta (with "mixed" the V-cycle runs in FP32, CG in FP64).
     allocator: "torch" takes the context's device memory from PyTorch's
-    caching allocator instead of cudaMalloc.  Not thread-safe.
+    caching allocator instead of cudaMalloc.  wait_limit: polls of a bounded
+    device wait before it gives up (mg_opts.wait_limit; 0 default, -1 gives
+    up at once).  Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
                  full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
-                 allocator=None):
+                 allocator=None, wait_limit=0):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -162,7 +167,7 @@ class Solver:
         self._h = ctypes.c_void_p()
         self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov, max_norm, self._hooks)
+                  full_residual, tma, krylov, max_norm, self._hooks, wait_limit)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
@@ -241,8 +246,10 @@ class Solver:
         return phi, (stats[0] if nrhs == 1 else stats)
 
     def adjoint(self, phi: torch.Tensor, g: torch.Tensor, tol: float = 1e-10,
-                dbeta: torch.Tensor | None = None):
-        """Returns (dL/df = lambda, dL/dbeta) for dL/dphi = g (see mg_adjoint)."""
+                dbeta: torch.Tensor | None = None, stats: bool = False):
+        """Returns (dL/df = lambda, dL/dbeta) for dL/dphi = g (see mg_adjoint),
+        and the adjoint solve's stats (a list for several right-hand sides)
+        as a third item when ``stats`` is set."""
         _check_tensor(phi, "phi", device=self.device)
         _check_tensor(g, "g", phi.numel(), self.device)
         nrhs = phi.numel() // self.numel
@@ -256,6 +263,9 @@ class Solver:
                                         _ptr(dbeta), float(tol), st, _stream_of(phi))
         if rc not in _SOFT:
             raise MGError(rc, "mg_adjoint")
+        if stats:
+            sd = [_stats_dict(s) for s in st]
+            return lam, dbeta, (sd[0] if nrhs == 1 else sd)
         return lam, dbeta
 
     # ---- projection steps around the solve (the velocity constraint)
@@ -536,12 +546,21 @@ class MGSolve(torch.autograd.Function):
     Forward: set beta, solve (f may carry a leading right-hand-side dim).
     Backward: the adjoint solve A lambda = dL/dphi gives dL/df = lambda and
     the face products give dL/dbeta (summed over right-hand sides).
+
+
+    A solve or adjoint solve that stops short of tol (cycle cap or stalled
+    residual) raises MGError when ``strict`` is set on the solver
+    (``solver.strict = True``); otherwise it emits a RuntimeWarning naming the
+    residual reached, so that a gradient is never returned silently from an
+    unconverged solve.  Hard failures (non-finite values, divergence, CUDA
+    errors) always raise.
     """
 
     @staticmethod
     def forward(ctx, f, beta, solver: Solver, tol: float = 1e-10):
         solver.set_beta(beta)
-        phi, _ = solver.solve(f.contiguous(), tol=tol)
+        phi, st = solver.solve(f.contiguous(), tol=tol)
+        _unconverged(solver, "forward solve", st)
         ctx.solver, ctx.tol = solver, tol
         ctx.save_for_backward(phi, beta)
         return phi
@@ -552,8 +571,24 @@ class MGSolve(torch.autograd.Function):
         solver = ctx.solver
         if solver._beta is not beta:
             solver.set_beta(beta)
-        lam, dbeta = solver.adjoint(phi, grad_phi.contiguous(), tol=ctx.tol)
+        lam, dbeta, st = solver.adjoint(phi, grad_phi.contiguous(), tol=ctx.tol, stats=True)
+        _unconverged(solver, "adjoint solve", st)
         return lam, dbeta, None, None
+
+
+def _unconverged(solver, what, stats):
+    """Warn (or raise, with solver.strict) if any right-hand side of a solve
+    did not reach its tolerance."""
+    stats = stats if isinstance(stats, list) else [stats]
+    bad = [s for s in stats if s["status"] != "ok"]
+    if not bad:
+        return
+    worst = max(s["rel_resid"] for s in bad)
+    msg = (f"MGSolve {what}: {len(bad)} of {len(stats)} right-hand sides stopped at "
+           f"status {bad[0]['status']} (relative residual {worst:.3e})")
+    if getattr(solver, "strict", False):
+        raise MGError(_lib.MG_ERR_NOT_CONVERGED, msg)
+    warnings.warn(msg, RuntimeWarning, stacklevel=3)
 
 
 _cache: dict = {}

@@ -25,26 +25,44 @@ def test_reference_arm_json_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 
 
+def test_reference_and_gpu_arms_name_the_same_config():
+    # the two arms print identical config dicts for one size, so that their
+    # lines compare like for like
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    want = ('"config": {"workload": WORKLOAD.format(n=n), "cells": N, "tol": TOL, '
+            '"l2": L2_NOTE}')
+    assert src.count(want) == 2, "both arms build config the same way"
+    assert bench.workload_seed(512) == 3 and bench.workload_seed(256) == 2
+
+
 def test_stored_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     # a DRAM figure from an ncu capture is reported only while the kernel's
-    # source region (and the shared header) is the one it was taken on
+    # source region (and the shared header) is the one it was taken on; a
+    # capture on another size is scaled by the cell count
     import shutil
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.stored_traffic("rbgs_pass_f64") is not None
-    assert bench.stored_traffic("rbgs_sweep_f32") is not None
+    n256 = 256 ** 3
+    t256, note = bench.stored_traffic("rbgs_pass_f64", n256)
+    assert t256 is not None and "this size" in note
+    t512, note = bench.stored_traffic("rbgs_pass_f64", 8 * n256)
+    if "scaled" in note:
+        assert abs(t512 - 8 * t256) <= 8
+    assert bench.stored_traffic("rbgs_sweep_f32", n256)[0] is not None
     src = tmp_path / "paper_1008_2801_gb300" / "csrc"
     src.mkdir(parents=True)
     for f in ("kernels.cu", "common.cuh"):
         shutil.copy(os.path.join(ROOT, "paper_1008_2801_gb300", "csrc", f), src / f)
     shutil.copytree(os.path.join(ROOT, "profiles"), tmp_path / "profiles")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.stored_traffic("rbgs_pass_f64") is not None
+    assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is not None
     text = (src / "kernels.cu").read_text()
     a, b = bench.TRAFFIC_REGIONS["rbgs_sweep_f32"]
     i = text.index(a) + len(a)
     (src / "kernels.cu").write_text(text[:i] + "\n// edited\n" + text[i:])
-    assert bench.stored_traffic("rbgs_sweep_f32") is None      # its region changed
-    assert bench.stored_traffic("rbgs_pass_f64") is not None   # the other did not
+    assert bench.stored_traffic("rbgs_sweep_f32", n256)[0] is None      # its region changed
+    assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is not None   # the other did not
     (src / "common.cuh").write_text((src / "common.cuh").read_text() + "\n")
-    assert bench.stored_traffic("rbgs_pass_f64") is None       # the shared header changed
+    assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is None       # the shared header changed

@@ -153,16 +153,23 @@ def test_levels_rule():
 
 
 def test_manufactured_second_order():
+    # 16^3 -> 128^3: the discrete L2 error falls by 4x per halving of h
+    # (observed orders 1.97, 1.99, 2.00; a first-order wall treatment or a
+    # dropped term in f would pull them well below 1.95).  The max-norm
+    # error converges at second order too, approached from below (1.83,
+    # 1.92, 1.96): the walls' O(1) truncation error weighs more on coarse grids.
     errs = []
-    for n in (16, 32, 64):
+    for n in (16, 32, 64, 128):
         d = inputs.manufactured(n)
         phi, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-12)
         assert info["status"] == "ok"
         e = phi - d["phi_exact"]
         errs.append((np.sqrt(np.mean(e ** 2)), np.max(np.abs(e))))
-    for (l2a, mxa), (l2b, mxb) in zip(errs, errs[1:]):
-        assert np.log2(l2a / l2b) >= 1.8
-        assert np.log2(mxa / mxb) >= 1.8
+    orders = [(np.log2(a[0] / b[0]), np.log2(a[1] / b[1])) for a, b in zip(errs, errs[1:])]
+    for l2, mx in orders:
+        assert l2 >= 1.95, orders
+        assert mx >= 1.8, orders
+    assert orders[-1][1] >= 1.9, orders
 
 
 def test_rbgs_pass_solves_own_colour():

@@ -73,6 +73,10 @@ def test_stellar_256_full_size(cuda_device, precision):
 
 
 def test_stellar_512_full_size_mixed_and_fp64(cuda_device):
+    # the 512^3 workload the benchmark times (seed 3), in both precisions, in
+    # the launch configuration the benchmark uses (graph-captured loop,
+    # default options): each solution against the oracle's, element by
+    # element, and its residual by the oracle's own operator
     d = inputs.config(3)
     out = {}
     for precision in ("mixed", "fp64"):
@@ -80,6 +84,11 @@ def test_stellar_512_full_size_mixed_and_fp64(cuda_device):
         assert st["status"] == "ok", st
         assert _rel_resid(d["beta"], d["f"], phi, d["dx"]) <= TOL * 1.01
         out[precision] = phi
+    ref, info = O.solve(d["beta"], d["f"], d["dx"], tol=1e-13)
+    assert info["status"] == "ok"
+    nr = np.linalg.norm(ref)
+    for precision, phi in out.items():
+        assert np.linalg.norm(phi - ref) <= 1e-9 * nr, precision
     # two independent solves at 1e-10 agree far below the 1e-9 bar
     diff = np.linalg.norm(out["mixed"] - out["fp64"]) / np.linalg.norm(out["fp64"])
     assert diff <= 1e-9
@@ -273,18 +282,22 @@ def test_batched_reduced_vs_oracle(cuda_device, precision):
 
 
 def test_batched_full_size(cuda_device):
+    # the 64 uneven boxes of the batched workload, every box against its own
+    # oracle solution and by the oracle's operator, in both precisions
     d = inputs.config(4)
     shapes = [tuple(int(v) for v in dims[::-1]) for dims in d["dims"]]
+    refs = [O.solve(d["beta"][b], d["f"][b], d["dx"], tol=1e-13)[0] for b in range(len(shapes))]
     for precision in ("fp64", "mixed"):
         bs = BatchSolver(shapes, d["dx"], precision=precision, device=cuda_device)
         bs.set_beta(_dev(np.concatenate([b.ravel() for b in d["beta"]]), cuda_device))
         f = _dev(np.concatenate([x.ravel() for x in d["f"]]), cuda_device)
         phi, sts = bs.solve(f, tol=TOL)
         parts = bs.unpack(phi.cpu())
-        for b in range(0, len(shapes), 7):
-            assert sts[b]["status"] == "ok"
-            assert _rel_resid(d["beta"][b], d["f"][b], parts[b].numpy(), d["dx"]) <= TOL * 1.01
         assert all(s["status"] == "ok" for s in sts)
+        for b in range(len(shapes)):
+            got = parts[b].numpy()
+            assert _rel_resid(d["beta"][b], d["f"][b], got, d["dx"]) <= TOL * 1.01
+            assert np.linalg.norm(got - refs[b]) <= 1e-9 * np.linalg.norm(refs[b]), (b, precision)
         bs.close()
 
 
