@@ -502,19 +502,30 @@ def run_extra(dev, args):
     fp = torch.from_numpy(np.concatenate([x.ravel() for x in d["f"]])).to(dev)
     N = fp.numel()
     res = {"boxes": len(shapes), "cells": N}
+    from paper_1008_2801_gb300 import autotune
     for prec in ("fp64", "mixed"):
-        bs = BatchSolver(shapes, d["dx"], precision=prec, device=dev)
-        phi = torch.zeros_like(fp)
+        # options and tile shapes measured on this GPU for these shapes (a
+        # synthetic problem of the same shapes), then the workload timed with
+        # them and with the library's defaults
+        t0 = time.perf_counter()
+        tuned, _, _ = autotune.tune(shapes, d["dx"], prec, device=dev, trials=1, report=True)
+        tune_s = time.perf_counter() - t0
+        for name, opts in (("batched", tuned), ("batched_default", {})):
+            bs = BatchSolver(shapes, d["dx"], precision=prec, device=dev, **opts)
+            phi = torch.zeros_like(fp)
 
-        def go():
-            bs.set_beta(bp)
-            return bs.solve(fp, phi, tol=TOL, zero_guess=True)[1]
-        ms, sts = time_once(go)
-        res[f"batched_{prec}"] = {"cells_per_s": N / (ms / 1e3), "ms": ms,
-                                  "setup_ms": round(sts[0]["t_setup_ms"], 3),
-                                  "max_cycles": max(s["cycles"] for s in sts),
-                                  "all_ok": all(s["status"] == "ok" for s in sts)}
-        bs.close()
+            def go():
+                bs.set_beta(bp)
+                return bs.solve(fp, phi, tol=TOL, zero_guess=True)[1]
+            ms, sts = time_once(go)
+            res[f"{name}_{prec}"] = {"cells_per_s": N / (ms / 1e3), "ms": ms,
+                                     "setup_ms": round(sts[0]["t_setup_ms"], 3),
+                                     "max_cycles": max(s["cycles"] for s in sts),
+                                     "all_ok": all(s["status"] == "ok" for s in sts)}
+            if opts:
+                res[f"{name}_{prec}"]["autotuned"] = opts
+                res[f"{name}_{prec}"]["tuning_s"] = round(tune_s, 1)
+            bs.close()
     solvers = [Solver(sh, d["dx"], precision="fp64", device=dev) for sh in shapes]
     offs = np.cumsum([0] + [int(np.prod(sh)) for sh in shapes])
 

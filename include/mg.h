@@ -149,7 +149,25 @@ typedef struct {
                          n > 0: n polls; -1: give up at the first wait
                          (exercises the timeout path; the CTA still drains
                          the copies it issued before it exits) */
-    int reserved[3];
+    int persistent;   /* 0 (default): one launch per stage and level;
+                         1: every level smoothed with single-colour passes
+                         runs as two persistent launches per V-cycle, one
+                         going down (pre-smoothing, residual, restriction)
+                         and one coming up (prolongation, post-smoothing),
+                         each CTA walking the tiles of all active boxes of a
+                         stage and a bounded grid barrier between stages
+                         (a cooperative launch of at most the resident CTA
+                         count; a barrier that gives up after wait_limit
+                         polls returns MG_ERR_TIMEOUT).  Levels smoothed
+                         with fused FP32 sweeps keep their own launches. */
+    int sweep_zc;     /* tile depth of the fused FP32 sweep: planes of z a
+                         CTA marches through (its tile is 64 x 8 cells in
+                         x, y).  0 (default): chosen by a model that fills
+                         whole waves of resident CTAs; n in 1..4096: n */
+    int level_ctas;   /* persistent = 1: CTAs per SM of the persistent
+                         launches.  0 (default): as many as can be
+                         resident; n in 1..64: at most n */
+    int reserved[2];
     /* Device memory of the context (its arena, launch descriptors and host
      * staging buffers) comes from dev_alloc(bytes, alloc_user) when set (NULL
      * on failure: MG_ERR_OOM) and goes back through dev_free(ptr,
@@ -347,6 +365,8 @@ enum {
     MG_PROF_COARSE = 5,    /* every coarser level and the coarsest solve */
     MG_PROF_REFINE = 6,    /* mixed precision: FP64 refinement step */
     MG_PROF_KRYLOV = 7,    /* krylov = 1: the CG vector updates and dot products */
+    MG_PROF_LEVEL = 8,     /* persistent = 1: the finest level's persistent launches
+                              (each a whole level sweep, down or up) */
     MG_PROF_NKIND = 16
 };
 typedef struct {

@@ -46,7 +46,8 @@ class mg_opts(ctypes.Structure):
                 ("use_graph", c_int), ("smoother", c_int), ("coarse_cells", c_int),
                 ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
                 ("krylov", c_int), ("max_norm", c_int), ("wait_limit", c_int),
-                ("reserved", c_int * 3),
+                ("persistent", c_int), ("sweep_zc", c_int), ("level_ctas", c_int),
+                ("reserved", c_int * 2),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_user", c_void_p)]
 
 
@@ -58,7 +59,8 @@ class mg_stats(ctypes.Structure):
 
 
 MG_PROF_NKIND = 16
-PROF_NAMES = ["sweep", "pass", "restrict", "prolong", "norm", "coarse", "refine", "krylov"]
+PROF_NAMES = ["sweep", "pass", "restrict", "prolong", "norm", "coarse", "refine", "krylov",
+              "level"]
 
 
 class mg_profile(ctypes.Structure):

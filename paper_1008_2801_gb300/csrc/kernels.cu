@@ -455,11 +455,12 @@ k_rbgs_sweep(BoxSet<T> S, const int *__restrict__ active, int src_is_phi2)
 
 // ------------------------------------------- residual + restriction ----
 
+// One coarse cell per thread, one tile of TK_COARSE: fc = mean over the 8
+// children of f - A phi, phic = 0.
 template <class T, bool FC>
-__global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const int *__restrict__ active)
+__device__ __forceinline__ void restrict_tile(const BoxSet<T> &S, const int *__restrict__ active,
+                                              int t)
 {
-    pdl_wait();
-    const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
@@ -491,6 +492,13 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
     B.phic[cc] = T(0);
 }
 
+template <class T, bool FC>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const int *__restrict__ active)
+{
+    pdl_wait();
+    restrict_tile<T, FC>(S, active, blockIdx.x);
+}
+
 // After a red-black sweep every black cell satisfies its own equation (its
 // residual is rounding-level), so right after smoothing the residual is
 // carried by the red cells alone.  This variant restricts the residual of the
@@ -498,11 +506,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
 // stencil work of k_resid_restrict, the same coarse right-hand side to
 // rounding.  Valid only when the last operation on phi was a black pass.
 template <class T, bool FC>
-__global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
-                                                                 const int *__restrict__ active)
+__device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
+                                                  const int *__restrict__ active, int t)
 {
-    pdl_wait();
-    const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
@@ -540,15 +546,22 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
     B.phic[cc] = T(0);
 }
 
+template <class T, bool FC>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
+                                                                 const int *__restrict__ active)
+{
+    pdl_wait();
+    restrict_red_tile<T, FC>(S, active, blockIdx.x);
+}
+
 // --------------------------------------------------------- prolongation ----
 
 // One thread per coarse cell: its correction is added to the 8 children (two
 // rows of two planes, each child pair one vector store when nx allows).
 template <class T, bool FC>
-__global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__restrict__ active)
+__device__ __forceinline__ void prolong_tile(const BoxSet<T> &S, const int *__restrict__ active,
+                                             int t)
 {
-    pdl_wait();
-    const int t = blockIdx.x;
     const int *ts = S.tstart[TK_COARSE];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
@@ -569,6 +582,13 @@ __global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__
             v.y += e;
             *q = v;
         }
+}
+
+template <class T, bool FC>
+__global__ void __launch_bounds__(kThreads) k_prolong(BoxSet<T> S, const int *__restrict__ active)
+{
+    pdl_wait();
+    prolong_tile<T, FC>(S, active, blockIdx.x);
 }
 
 // -------------------------------------------------------- residual field ----
@@ -2029,6 +2049,181 @@ __global__ void k_norm_combine(int nbox, double *__restrict__ norm)
     for (int b = threadIdx.x; b < nbox; b += blockDim.x) norm[b] = tot;
 }
 
+// ------------------------------------------- persistent level sweeps ----
+//
+// The many boxes of a batch (the grids of one MultiFAB level, paper Sec. 2)
+// walk a level's stages together.  Instead of one launch per stage, a level
+// is smoothed by one launch going down (the pre-smoothing passes, then the
+// residual and restriction) and one coming up (prolongation, then the
+// post-smoothing passes).  The launch is persistent: its grid is at most the
+// number of CTAs that can be resident at once (a cooperative launch, so the
+// runtime refuses a grid that could not be), each CTA walks the tiles of
+// every active box of a stage with a grid-sized stride, and a grid-wide
+// barrier separates consecutive stages.  The barrier is bounded: a CTA that
+// has polled it `polls` times without seeing it complete sets the error
+// word and returns, so a failure (or a forced time-out) ends the launch with
+// an error the host reports as MG_ERR_TIMEOUT, never a hang.
+
+// The barrier (GridSync, kernels.h): one 32-bit word in device memory, zero
+// when a solve starts.  Every CTA adds 1 except CTA 0, which adds
+// 2^31 - (G - 1): when all G have arrived the word has grown by exactly
+// 2^31, so its top bit has flipped and its low bits are back where they
+// were -- the next barrier starts from there without a reset.
+__device__ __forceinline__ bool grid_sync(const GridSync &g)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        __threadfence();   // this CTA's stage results before its arrival
+        const unsigned old = atomicAdd(g.word, add);
+        const volatile unsigned *w = g.word;
+        int ok = 1;
+        long long i = 0;
+        while (((old ^ *w) & 0x80000000u) == 0u) {
+            if (i++ >= g.polls) {
+                ok = 0;
+                atomicExch(g.err, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();   // the other CTAs' results after the barrier
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// One tile of an in-place single-colour pass (as k_rbgs_pass).
+template <class T>
+__device__ __forceinline__ void pass_tile(const BoxSet<T> &S, const int *__restrict__ active,
+                                          int color, int t)
+{
+    const int *ts = S.tstart[TK_PAIR];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<T> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    const int P = B.P;
+    const long long Q = B.Q;
+    const TilePos p = tile_pos(TK_PAIR, B.nx, B.ny, B.nz, t - ts[b]);
+    const int j = p.y, k = p.z;
+    const int i = 2 * p.x + ((j + k + color + B.par) & 1);
+    if (j >= B.ny || i >= B.nx) return;
+    const long long c = (long long)k * Q + (long long)j * P + i;
+    const long long cf =
+        split_on(B) ? (long long)k * Q + (long long)j * P + (color ? (P >> 1) : 0) + p.x : c;
+    B.phi[c] = gs_value<T>(B.phi, B.f, B.invD, B.wx, B.wy, B.wz, c, cf, P, Q);
+}
+
+// One tile of the black pass out of place, phi2 -> phi (the rest of the
+// finest level's first sweep after the look-ahead red pass).
+template <class T>
+__device__ __forceinline__ void pass_oop_tile(const BoxSet<T> &S, const int *__restrict__ active,
+                                              int t)
+{
+    const int *ts = S.tstart[TK_PAIR];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<T> &B = S.boxes[b];
+    if (active && !active[B.box]) return;
+    const TilePos p = tile_pos(TK_PAIR, B.nx, B.ny, B.nz, t - ts[b]);
+    double unused = 0.0;
+    if (p.y < B.ny && 2 * p.x < B.nx) oop_pair(B, 1, 1, p.y, p.z, 2 * p.x, false, unused);
+}
+
+// Work item q of a ghost exchange: record q % nrec, chunk q / nrec of
+// `chunks` (as k_exchange with gridDim.y = chunks).
+template <class T>
+__device__ __forceinline__ void exchange_item(const BoxSet<T> &S, const ExchRec *__restrict__ rec,
+                                              int nrec, int chunks, int q, int second)
+{
+    const ExchRec R = rec[q % nrec];
+    const int chunk = q / nrec;
+    const Box<T> &D = S.boxes[R.dst];
+    const Box<T> &F = S.boxes[R.src];
+    T *__restrict__ dphi = second ? D.phi2 : D.phi;
+    const T *__restrict__ fphi = second ? F.phi2 : F.phi;
+    const int n = R.ex * R.ey * R.ez;
+    const int stride = kThreads * chunks;
+    for (int e = chunk * kThreads + threadIdx.y * kTX + threadIdx.x; e < n; e += stride) {
+        const int a = e % R.ex, r = e / R.ex;
+        const int bb = r % R.ey, c = r / R.ey;
+        dphi[(long long)(R.dk + c) * D.Q + (long long)(R.dj + bb) * D.P + R.di + a] =
+            fphi[(long long)(R.sk + c) * F.Q + (long long)(R.sj + bb) * F.P + R.si + a];
+    }
+}
+
+// A launch that finds the error word set (a barrier of an earlier launch in
+// this solve gave up, leaving the barrier word mid-count) does nothing.
+__device__ __forceinline__ bool grid_failed(const GridSync &g)
+{
+    return *reinterpret_cast<const volatile int *>(g.err) != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, 3) k_level_down(BoxSet<T> S, const int *__restrict__ active,
+                                                         LevelOps op, GridSync g)
+{
+    if (grid_failed(g)) return;
+    auto each = [&](int n, auto &&work) {
+        for (int t = blockIdx.x; t < n; t += gridDim.x) work(t);
+    };
+    auto exchange = [&](int second) -> bool {
+        if (op.nrec == 0) return true;
+        each(op.nrec * op.chunks,
+             [&](int q) { exchange_item(S, op.rec, op.nrec, op.chunks, q, second); });
+        return grid_sync(g);
+    };
+    const int npair = S.ntiles[TK_PAIR];
+    int sweeps = op.nu;
+    if (op.head_done) {
+        if (!exchange(1)) return;
+        each(npair, [&](int t) { pass_oop_tile(S, active, t); });
+        if (!grid_sync(g)) return;
+        --sweeps;
+    }
+    for (int sw = 0; sw < sweeps; ++sw)
+        for (int color = 0; color < 2; ++color) {
+            if (!exchange(0)) return;
+            each(npair, [&](int t) { pass_tile(S, active, color, t); });
+            if (!grid_sync(g)) return;
+        }
+    if (!exchange(0)) return;
+    const int nc = S.ntiles[TK_COARSE];
+    if (op.red) {
+        if (op.flat) each(nc, [&](int t) { restrict_red_tile<T, true>(S, active, t); });
+        else each(nc, [&](int t) { restrict_red_tile<T, false>(S, active, t); });
+    } else {
+        if (op.flat) each(nc, [&](int t) { restrict_tile<T, true>(S, active, t); });
+        else each(nc, [&](int t) { restrict_tile<T, false>(S, active, t); });
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, 4) k_level_up(BoxSet<T> S, const int *__restrict__ active,
+                                                       LevelOps op, GridSync g)
+{
+    if (grid_failed(g)) return;
+    auto each = [&](int n, auto &&work) {
+        for (int t = blockIdx.x; t < n; t += gridDim.x) work(t);
+    };
+    const int nc = S.ntiles[TK_COARSE];
+    if (op.flat) each(nc, [&](int t) { prolong_tile<T, true>(S, active, t); });
+    else each(nc, [&](int t) { prolong_tile<T, false>(S, active, t); });
+    const int npair = S.ntiles[TK_PAIR];
+    for (int sw = 0; sw < op.nu; ++sw)
+        for (int c = 0; c < 2; ++c) {
+            if (!grid_sync(g)) return;
+            if (op.nrec) {
+                each(op.nrec * op.chunks,
+                     [&](int q) { exchange_item(S, op.rec, op.nrec, op.chunks, q, 0); });
+                if (!grid_sync(g)) return;
+            }
+            const int color = op.reverse ? 1 - c : c;
+            each(npair, [&](int t) { pass_tile(S, active, color, t); });
+        }
+}
+
 // ----------------------------------------------------------- launchers ----
 
 static inline dim3 block2d() { return dim3(kTX, kTY); }
@@ -2363,6 +2558,49 @@ cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec
     const int chunks = std::max(1, std::min(1024, (max_cells + 4 * kThreads - 1) / (4 * kThreads)));
     return pdl_launch(k_exchange<T>, dim3(nrec, chunks), block2d(), 0, st, S, active, rec, second);
 }
+
+template <class T>
+int level_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_level_down<T>, kThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int m = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_level_up<T>, kThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, std::min(n, m));
+}
+template int level_ctas_per_sm<double>();
+template int level_ctas_per_sm<float>();
+
+template <class T>
+cudaError_t launch_level(const BoxSet<T> &S, const int *active, int up, const LevelOps &op,
+                         const GridSync &g, int grid, cudaStream_t st)
+{
+    if (S.nbox == 0 || grid < 1) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = block2d();
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident at once
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return counted(up ? cudaLaunchKernelEx(&cfg, k_level_up<T>, S, active, op, g)
+                      : cudaLaunchKernelEx(&cfg, k_level_down<T>, S, active, op, g));
+}
+template cudaError_t launch_level<double>(const BoxSet<double> &, const int *, int,
+                                          const LevelOps &, const GridSync &, int, cudaStream_t);
+template cudaError_t launch_level<float>(const BoxSet<float> &, const int *, int,
+                                         const LevelOps &, const GridSync &, int, cudaStream_t);
 
 template <class T>
 cudaError_t launch_guard_fill(const BoxSet<T> &S, T v, cudaStream_t st)

@@ -114,6 +114,37 @@ cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int 
                          const JudgeState &J, cudaGraphConditionalHandle handle, int use_handle,
                          cudaStream_t st);
 
+// ---- persistent level sweeps (one launch per level and direction) -------
+// Bounded grid-wide barrier of a persistent launch: `word` (device, zero when
+// a solve starts) is shared by every barrier of the solve; a CTA that polls
+// it `polls` times without seeing it complete sets *err to 1 and returns.
+struct GridSync {
+    unsigned *word;
+    int *err;
+    long long polls;
+};
+// What one level's persistent launch does.  Down (k_level_down): nu sweeps
+// of single-colour passes (red, black), then the residual and restriction.
+// Up (k_level_up): prolongation, then nu sweeps.  A grid barrier separates
+// consecutive stages.
+struct LevelOps {
+    int nu;              // sweeps (each a red and a black pass)
+    int head_done;       // down, finest level after the look-ahead red pass (phi -> phi2): the
+                         // first sweep ends with the black pass phi2 -> phi
+    int red;             // down: restrict the residual of the red children only
+    int reverse;         // up: black before red in each sweep (symmetric cycle)
+    const ExchRec *rec;  // ghost exchange before every pass and the residual (nrec = 0: none)
+    int nrec, chunks;    // records, and CTAs' worth of work per record
+    int flat;            // the set tiles TK_COARSE flat (its flat bit)
+};
+// Resident CTAs per SM of the persistent level kernels (occupancy query).
+template <class T>
+int level_ctas_per_sm();
+// One cooperative launch of `grid` CTAs (at most level_ctas_per_sm x SMs).
+template <class T>
+cudaError_t launch_level(const BoxSet<T> &S, const int *active, int up, const LevelOps &op,
+                         const GridSync &g, int grid, cudaStream_t st);
+
 // ---- moving data between packed user arrays and the level layout --------
 // user[off[b] + (k*ny + j)*nx + i] -> level 0 f (to_f) or phi of box b.
 cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,

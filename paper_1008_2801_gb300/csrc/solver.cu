@@ -371,7 +371,12 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
             if (l < H.lc[b]) set.push_back(make_box(s, H, b, l));
         if (!set.empty()) {
             double score = 0.0;
-            const int zc = choose_zc(set, slots, &score);
+            int zc = choose_zc(set, slots, &score);
+            if (s->opts.sweep_zc > 0) {   // the tile depth given (autotuned) instead
+                int maxnz = 1;
+                for (const auto &B : set) maxnz = std::max(maxnz, B.nz);
+                zc = std::min(s->opts.sweep_zc, maxnz);
+            }
             for (auto &B : set) B.zc = zc;
             // fused sweeps when the grid can keep the GPU busy, and only in
             // FP32: FP64 smoothing is bound by the FP64 pipe, where the red
@@ -392,6 +397,11 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
     }
     H.njobs = (int)jobs.size();
     *jobs_off = blob.put(jobs.data(), jobs.size() * sizeof(CoarseJob<T>));
+    if (s->opts.persistent) {
+        int per_sm = level_ctas_per_sm<T>();
+        if (s->opts.level_ctas > 0) per_sm = std::min(per_sm, s->opts.level_ctas);
+        H.pgrid = per_sm * s->sms;
+    }
 }
 
 static int validate_opts(const mg_opts *o)
@@ -408,6 +418,12 @@ static int validate_opts(const mg_opts *o)
         return set_error(MG_ERR_INVALID_ARG, "inner_cycles must be in 0..8");
     if (o->krylov < 0 || o->krylov > 1) return set_error(MG_ERR_INVALID_ARG, "krylov must be 0 or 1");
     if (o->wait_limit < -1) return set_error(MG_ERR_INVALID_ARG, "wait_limit must be >= -1");
+    if (o->persistent < 0 || o->persistent > 1)
+        return set_error(MG_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (o->sweep_zc < 0 || o->sweep_zc > 4096)
+        return set_error(MG_ERR_INVALID_ARG, "sweep_zc must be in 0..4096");
+    if (o->level_ctas < 0 || o->level_ctas > 64)
+        return set_error(MG_ERR_INVALID_ARG, "level_ctas must be in 0..64");
     if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr))
         return set_error(MG_ERR_INVALID_ARG, "dev_alloc and dev_free come together");
     return MG_OK;
@@ -644,6 +660,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     for (int i = 0; i < 7; ++i) bump.take<double>(nbox);
     bump.take<int>(nbox);
     bump.take<int>(1);  // error word
+    bump.take<unsigned>(1);  // grid-barrier word
     // judge block: hist | rel0 | best | tol | status | cycles | stall | step
     const size_t jbytes = sizeof(double) * ((size_t)nbox * MG_MAX_HIST + 2 * nbox + 1) +
                           sizeof(int) * (3 * (size_t)nbox + 1);
@@ -686,6 +703,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->dmean = real.take<double>(nbox);
     s->active = real.take<int>(nbox);
     s->derr = real.take<int>(1);
+    s->gbar = real.take<unsigned>(1);
     s->jbytes = jbytes;
     s->jblock = real.take<char>(jbytes);
     {
@@ -1228,6 +1246,42 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
     return e;
 }
 
+// CTAs of work per exchange record (as launch_exchange: about 4 cells per
+// thread on the largest record).
+static int exch_chunks(int max_cells)
+{
+    return std::max(1, std::min(1024, (max_cells + 4 * kThreads - 1) / (4 * kThreads)));
+}
+
+// Level l of H as one persistent launch (mg_opts.persistent): going down,
+// nu pre-smoothing sweeps then the residual and restriction; coming up,
+// prolongation then nu post-smoothing sweeps (sym: black before red).
+template <class T>
+static cudaError_t level_launch(Solver *s, const Hier<T> &H, int l, bool up, int nu,
+                                bool head_done, bool sym, cudaStream_t st)
+{
+    const BoxSet<T> &S = H.smooth[l];
+    LevelOps op{};
+    op.nu = nu;
+    op.head_done = head_done ? 1 : 0;
+    op.red = (!up && s->opts.nu1 > 0 && !s->opts.full_residual) ? 1 : 0;
+    op.reverse = sym ? 1 : 0;
+    if (s->xmode && s->nxrec[l] > 0) {
+        op.rec = s->xrec[l];
+        op.nrec = s->nxrec[l];
+        op.chunks = exch_chunks(s->xmax[l]);
+    }
+    op.flat = (S.flat >> TK_COARSE) & 1;
+    GridSync g{s->gbar, s->derr, sweep_wait_polls(s->opts.wait_limit)};
+    const long long work = std::max<long long>(
+        std::max(S.ntiles[TK_PAIR], S.ntiles[TK_COARSE]), (long long)op.nrec * op.chunks);
+    const int grid = (int)std::min<long long>(work, H.pgrid);
+    const int sl = l == 0 ? prof_begin(s, MG_PROF_LEVEL, st) : -1;
+    cudaError_t e = launch_level(S, s->active, up ? 1 : 0, op, g, grid, st);
+    prof_end(s, sl, st);
+    return e;
+}
+
 // head_done: the finest level's first red pass already ran out of place
 // (phi -> phi2, look-ahead); the cycle goes on with the black pass phi2 -> phi.
 // sym: post-smoothing sweeps run black then red, the adjoint of the
@@ -1243,6 +1297,13 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
     for (int l = 0; l < nl; ++l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
+        if (H.pgrid > 0 && !H.fused[l]) {
+            if ((e = level_launch(s, H, l, false, s->opts.nu1, l == 0 && head_done, false, st)) !=
+                cudaSuccess)
+                return e;
+            if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
+            continue;
+        }
         int nu1 = s->opts.nu1;
         if (l == 0 && head_done) {
             int sl = prof_begin(s, MG_PROF_PASS, st);
@@ -1276,6 +1337,11 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (l == 0) {
             prof_end(s, coarse, st);
             coarse = -1;
+        }
+        if (H.pgrid > 0 && !H.fused[l]) {
+            if ((e = level_launch(s, H, l, true, s->opts.nu2, false, sym, st)) != cudaSuccess)
+                return e;
+            continue;
         }
         int sl = l == 0 ? prof_begin(s, MG_PROF_PROLONG, st) : -1;
         if ((e = launch_prolong(S, s->active, st)) != cudaSuccess) return e;
@@ -1654,6 +1720,9 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     if (s->singular) CK(launch_remove_mean(H.fine, 0, s->partials, s->dmean, stream));
     for (int b = 0; b < nbox; ++b) s->hactive[b] = 1;
     CK(cudaMemcpyAsync(s->active, s->hactive, sizeof(int) * nbox, cudaMemcpyHostToDevice, stream));
+    // the persistent launches' barrier word starts every solve at zero (a
+    // barrier that gave up in an earlier solve may have left it mid-count)
+    if (s->opts.persistent) CK(cudaMemsetAsync(s->gbar, 0, sizeof(unsigned), stream));
     if (zero_guess) {
         CK(launch_zero(H.fine, nullptr, stream));
     } else {

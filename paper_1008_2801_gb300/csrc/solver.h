@@ -38,6 +38,7 @@ struct Hier {
     cudaGraphExec_t graph = nullptr;            // captured V-cycle (+ fine norm for FP64)
     cudaGraphExec_t head = nullptr;             // look-ahead: first red pass + norm
     T *uinv = nullptr;                          // coupled level: dense inverse of the union bottom
+    int pgrid = 0;                              // resident CTAs of the persistent level kernels
 };
 
 // A timed stretch of one stage class: events recorded before and after it.
@@ -136,6 +137,7 @@ struct Solver {
     int bottom_packed = 0;                // dynamic shared memory of k_setup_bottom (packed matrices)
 
     int *derr = nullptr;                  // device error word (bounded waits that gave up)
+    unsigned *gbar = nullptr;             // device grid-barrier word of the persistent launches
     int bc = 0;                           // wall mask: bit w set = wall w Neumann
     bool singular = false;                // every wall Neumann: A has the constants as null space
     double *dmean = nullptr;              // [nbox] scratch: removed means

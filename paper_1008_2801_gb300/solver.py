@@ -68,7 +68,7 @@ def _torch_allocator(device):
 
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
           full_residual=False, tma=False, krylov=False, max_norm=False, hooks=None,
-          wait_limit=0):
+          wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -82,6 +82,9 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.krylov = 1 if krylov else 0
     o.max_norm = 1 if max_norm else 0
     o.wait_limit = int(wait_limit)
+    o.persistent = 1 if persistent else 0
+    o.sweep_zc = int(sweep_zc)
+    o.level_ctas = int(level_ctas)
     if hooks is not None:
         o.dev_alloc, o.dev_free = hooks
     return o
@@ -149,13 +152,16 @@ class Solver:
     allocator: "torch" takes the context's device memory from PyTorch's
     caching allocator instead of cudaMalloc.  wait_limit: polls of a bounded
     device wait before it gives up (mg_opts.wait_limit; 0 default, -1 gives
-    up at once).  Not thread-safe.
+    up at once).  persistent: one persistent launch per level and direction
+    (mg_opts.persistent); sweep_zc, level_ctas: tile depth of the fused FP32
+    sweep and CTAs per SM of the persistent launches (0: the library's
+    model; see mg_opts and ``autotune``).  Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
                  full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
-                 allocator=None, wait_limit=0):
+                 allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -167,7 +173,8 @@ class Solver:
         self._h = ctypes.c_void_p()
         self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov, max_norm, self._hooks, wait_limit)
+                  full_residual, tma, krylov, max_norm, self._hooks, wait_limit, persistent,
+                  sweep_zc, level_ctas)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
@@ -338,12 +345,14 @@ class Solver:
 class BatchSolver:
     """Independent boxes of uneven size solved together (one launch per stage
     over the tiles of every active box).  shapes: list of (nz, ny, nx); arrays
-    are packed back to back in box order (see ``pack``/``unpack``)."""
+    are packed back to back in box order (see ``pack``/``unpack``).
+    persistent: each level smoothed with passes runs as one persistent
+    launch per direction over all boxes (mg_opts.persistent)."""
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
                  full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
-                 allocator=None):
+                 allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
         L = _lib.load()
         self.bc = bc_mask(bc)
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -356,7 +365,8 @@ class BatchSolver:
         self._h = ctypes.c_void_p()
         self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
-                  full_residual, tma, krylov, max_norm, self._hooks)
+                  full_residual, tma, krylov, max_norm, self._hooks, wait_limit, persistent,
+                  sweep_zc, level_ctas)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, self.bc, ctypes.byref(o)),
                   "mg_batch_create")
@@ -456,7 +466,7 @@ class LevelSolver:
     boundary has Dirichlet walls (phi = 0)."""
 
     def __init__(self, los, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
-                 use_graph=True, device=None, inner_cycles=0):
+                 use_graph=True, device=None, inner_cycles=0, persistent=False, wait_limit=0):
         L = _lib.load()
         self.los = [tuple(int(v) for v in c) for c in los]
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -466,7 +476,8 @@ class LevelSolver:
         lo = (ctypes.c_int * (3 * nb))(*[v for c in self.los for v in c])
         n = (ctypes.c_int * (3 * nb))(*[v for s in self.shapes for v in (s[2], s[1], s[0])])
         self._h = ctypes.c_void_p()
-        o = _opts(precision, nu1, nu2, max_cycles, use_graph, "passes", 0, inner_cycles)
+        o = _opts(precision, nu1, nu2, max_cycles, use_graph, "passes", 0, inner_cycles,
+                  wait_limit=wait_limit, persistent=persistent)
         with torch.cuda.device(self.device):
             check(L.mg_level_create(ctypes.byref(self._h), nb, lo, n, float(dx), 0,
                                     ctypes.byref(o)), "mg_level_create")

@@ -305,7 +305,7 @@ def test_autotune_picks_a_working_option_set(cuda_device, tmp_path, monkeypatch)
     from paper_1008_2801_gb300 import autotune
     monkeypatch.setenv("MG_TUNE_CACHE", str(tmp_path / "tune.json"))
     opts = autotune.tune([(16, 24, 32)], 1 / 32, "mixed", device=cuda_device, trials=1)
-    assert set(opts) == {"smoother", "coarse_cells", "inner_cycles"}
+    assert set(opts) == set(autotune.DEFAULTS)   # options and tile shapes
     hit = autotune.lookup(torch.cuda.get_device_name(cuda_device), [(16, 24, 32)], "mixed")
     assert hit["opts"] == opts and hit["ms"] > 0
     d = inputs.stellar((32, 24, 16), 16)
