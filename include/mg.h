@@ -149,8 +149,8 @@ typedef struct {
                          n > 0: n polls; -1: give up at the first wait
                          (exercises the timeout path; the CTA still drains
                          the copies it issued before it exits) */
-    int persistent;   /* 0 (default): one launch per stage and level;
-                         1: every level smoothed with single-colour passes
+    int persistent;   /* 0 (default): one launch per stage and level.
+                         2: every level smoothed with single-colour passes
                          runs as two persistent launches per V-cycle, one
                          going down (pre-smoothing, residual, restriction)
                          and one coming up (prolongation, post-smoothing),
@@ -158,8 +158,11 @@ typedef struct {
                          stage and a bounded grid barrier between stages
                          (a cooperative launch of at most the resident CTA
                          count; a barrier that gives up after wait_limit
-                         polls returns MG_ERR_TIMEOUT).  Levels smoothed
-                         with fused FP32 sweeps keep their own launches. */
+                         polls returns MG_ERR_TIMEOUT).  1: only the levels
+                         whose largest stage fits in one wave of resident
+                         CTAs (the launch-bound ones); larger levels keep
+                         per-stage launches.  Levels smoothed with fused
+                         FP32 sweeps keep their own launches. */
     int sweep_zc;     /* tile depth of the fused FP32 sweep: planes of z a
                          CTA marches through (its tile is 64 x 8 cells in
                          x, y).  0 (default): chosen by a model that fills
@@ -349,6 +352,49 @@ void mg_level_destroy(mg_level *lv);
  * checking).  INVALID_ARG if two boxes overlap. */
 int mg_level_intersections(int nbox, const int (*lo)[3], const int (*n)[3], int brute,
                            int *nrec, int *out, int cap);
+
+/* ---- one box split in z into slabs, one GPU per slab ----------------------
+ * The paper's codes distribute a level's grids over MPI ranks and fill their
+ * ghost cells from the neighbouring grids before each stencil (paper Sec. 2);
+ * the linear solves are what limits MAESTRO's scaling (Sec. 3).  This is the
+ * same for one large box over several GPUs.  Slab r holds planes
+ * z0[r] .. z0[r+1]-1 (equal slabs: nz must be a multiple of nslab) on
+ * device devices[r].  Levels are smoothed slab by slab, each slab pulling its
+ * neighbours' boundary planes of phi into its guard planes before every
+ * single-colour pass and residual (peer copies into a local halo buffer);
+ * the first level with at most 32^3 cells (or where a slab or the box stops
+ * halving) is gathered: the slabs' restriction writes into one coarse
+ * context on devices[0], which runs the rest of the V-cycle, and their
+ * prolongation reads its correction from there (slabs on other devices reach
+ * it by peer access, which mg_slab_create enables).  The residual norm is the
+ * sum of the slabs' squares, judged on the host once per cycle.  The result
+ * is the single-box solution of the same operator (interface faces are
+ * harmonic means across the two slabs' cells).  FP64 V-cycles only
+ * (opts->precision, krylov and persistent must be 0: MG_ERR_UNSUPPORTED).
+ * All arrays are device memory of the slab's device, (nz_r, ny, nx) C order;
+ * the calls synchronise before they return (their own streams: the
+ * caller's work producing the inputs must be complete when they are made). */
+typedef struct mg_slab mg_slab;
+/* Host only: the slab plan of an n = {nx, ny, nz} box in nslab slabs: z0
+ * (nullable) receives nslab + 1 plane offsets, *gather_level (nullable) the
+ * level solved by the coarse context (levels 0 .. gather_level - 1 are
+ * smoothed slab by slab).  UNSUPPORTED when nz is not a multiple of nslab or
+ * no level can be smoothed slab by slab. */
+int mg_slab_plan(const int n[3], int nslab, int *z0, int *gather_level);
+/* Host only: the halo copies of slab level `level` (< gather_level): *nrec
+ * records of 4 ints into out (nullable; at most cap records): source slab,
+ * its plane (local k), destination slab, its guard plane (-1 below, the
+ * slab's thickness at that level above). */
+int mg_slab_halo(const int n[3], int nslab, int level, int *nrec, int *out, int cap);
+int mg_slab_create(mg_slab **out, const int n[3], double dx, int nslab, const int *devices,
+                   const mg_opts *opts);
+/* beta[r]: slab r's cell beta. */
+int mg_slab_set_beta(mg_slab *sl, const double *const *beta);
+/* f[r], phi[r]: slab r's right-hand side and solution (initial guess unless
+ * flags has MG_ZERO_GUESS); st (nullable) gets the whole box's history. */
+int mg_slab_solve(mg_slab *sl, const double *const *f, double *const *phi, double tol, int flags,
+                  mg_stats *st);
+void mg_slab_destroy(mg_slab *sl);
 
 /* ---- measurement -------------------------------------------------------
  * With profiling on, the solver records CUDA events around each stage class

@@ -9,8 +9,9 @@ an error, never a fallback.
 """
 from __future__ import annotations
 
-__all__ = ["Solver", "BatchSolver", "LevelSolver", "MGSolve", "solve", "bc_mask", "wall_shapes",
-           "level_intersections", "MGError", "build", "inputs", "ops"]
+__all__ = ["Solver", "BatchSolver", "LevelSolver", "SlabSolver", "MGSolve", "solve", "bc_mask",
+           "wall_shapes", "level_intersections", "slab_plan", "slab_halo", "MGError", "build",
+           "inputs", "ops"]
 
 
 def build(force: bool = False) -> str:
@@ -19,8 +20,8 @@ def build(force: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Solver", "BatchSolver", "LevelSolver", "MGSolve", "solve", "bc_mask", "wall_shapes",
-                "level_intersections"):
+    if name in ("Solver", "BatchSolver", "LevelSolver", "SlabSolver", "MGSolve", "solve",
+                "bc_mask", "wall_shapes", "level_intersections", "slab_plan", "slab_halo"):
         from . import solver
         return getattr(solver, name)
     if name == "MGError":

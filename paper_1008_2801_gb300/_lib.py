@@ -110,6 +110,14 @@ _SIGS = {
     "mg_batch_profile_read": (c_int, [c_void_p, ctypes.POINTER(mg_profile), c_int]),
     "mg_level_profile_enable": (c_int, [c_void_p, c_int]),
     "mg_level_profile_read": (c_int, [c_void_p, ctypes.POINTER(mg_profile), c_int]),
+    "mg_slab_plan": (c_int, [c_int3, c_int, c_void_p, c_void_p]),
+    "mg_slab_halo": (c_int, [c_int3, c_int, c_int, c_void_p, c_void_p, c_int]),
+    "mg_slab_create": (c_int, [ctypes.POINTER(c_void_p), c_int3, c_double, c_int, c_void_p,
+                               ctypes.POINTER(mg_opts)]),
+    "mg_slab_set_beta": (c_int, [c_void_p, c_void_p]),
+    "mg_slab_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int,
+                              ctypes.POINTER(mg_stats)]),
+    "mg_slab_destroy": (None, [c_void_p]),
     "mg_error_string": (ctypes.c_char_p, [c_int]),
     "mg_last_error": (ctypes.c_char_p, []),
     # mg_ops.h

@@ -32,7 +32,7 @@ _lock = threading.Lock()
 SMOOTHERS = ("auto", "passes", "fused")
 COARSE = (0, 512, 2048, 8192)
 INNER = (1, 2, 3)
-PERSISTENT = (False, True)
+PERSISTENT = (False, "small", "all")
 SWEEP_ZC = (0, 8, 16, 32, 64)      # 0: the library's wave model
 LEVEL_CTAS = (0, 1, 2)             # 0: every resident CTA
 DEFAULTS = {"smoother": "auto", "coarse_cells": 0, "inner_cycles": 0, "persistent": False,

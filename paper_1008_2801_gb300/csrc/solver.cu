@@ -418,8 +418,8 @@ static int validate_opts(const mg_opts *o)
         return set_error(MG_ERR_INVALID_ARG, "inner_cycles must be in 0..8");
     if (o->krylov < 0 || o->krylov > 1) return set_error(MG_ERR_INVALID_ARG, "krylov must be 0 or 1");
     if (o->wait_limit < -1) return set_error(MG_ERR_INVALID_ARG, "wait_limit must be >= -1");
-    if (o->persistent < 0 || o->persistent > 1)
-        return set_error(MG_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (o->persistent < 0 || o->persistent > 2)
+        return set_error(MG_ERR_INVALID_ARG, "persistent must be 0, 1 or 2");
     if (o->sweep_zc < 0 || o->sweep_zc > 4096)
         return set_error(MG_ERR_INVALID_ARG, "sweep_zc must be in 0..4096");
     if (o->level_ctas < 0 || o->level_ctas > 64)
@@ -479,7 +479,7 @@ static bool create_events(cudaEvent_t *e, int n)
 }
 
 int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
-                  const mg_opts *opts, bool shared_weights, const int (*lo)[3])
+                  const mg_opts *opts, bool shared_weights, const int (*lo)[3], int cut)
 {
     if (!out) return set_error(MG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -541,10 +541,22 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         if (level_check_disjoint(bricks, &a, &c))
             return set_error(MG_ERR_INVALID_ARG, "boxes %d and %d overlap", a, c);
         clev = coupled_levels(nbox, lo, n, cdims, clos);
+        if (cut > 0) {
+            // levels 0 .. cut - 1 only; the last one is solved elsewhere
+            if (clev < cut)
+                return set_error(MG_ERR_UNSUPPORTED, "the boxes halve %d times, %d wanted",
+                                 clev - 1, cut - 1);
+            clev = cut;
+            for (int b = 0; b < nbox; ++b) {
+                cdims[b].resize(cut);
+                clos[b].resize(cut);
+            }
+        }
         for (int b = 0; b < nbox; ++b) {
             const auto &d = cdims[b][clev - 1];
             ucells += d[0] * d[1] * d[2];
         }
+        if (cut > 0) ucells = 0;   // no dense bottom of its own
         if (ucells > MG_MAX_BOTTOM)
             return set_error(MG_ERR_UNSUPPORTED,
                              "coarsest level of the union has %d cells (> %d): box dims and "
@@ -570,6 +582,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     for (int d = 0; d < 3; ++d)
         if (!((bc >> (6 + d)) & 1) && ((bc >> (2 * d)) & 3) != 3) s->singular = false;
     s->coupled = coupled;
+    s->cut = cut;
     s->xmode = coupled || periodic;
     s->wide = s->xmode;
     if (coupled) {
@@ -1121,6 +1134,23 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     return MG_OK;
 }
 
+int solver_setup_from_weights(Solver *s, cudaStream_t st)
+{
+    if (!s || s->xmode || s->has32)
+        return set_error(MG_ERR_INVALID_ARG, "set-up from weights: one FP64 box context");
+    DeviceGuard g(s->dev);
+    CK(cudaEventRecord(s->ev_setup0, st));
+    const long long k0 = launch_counter();
+    for (size_t l = 0; l < s->setup_coarsen.size(); ++l) CK(launch_setup(s->setup_coarsen[l], 1, st));
+    CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, st));
+    for (int l = 0; l < s->maxlev; ++l) CK(launch_setup(s->setup_lv[l], 2, st));
+    CK(cudaEventRecord(s->ev_setup1, st));
+    s->kernels += launch_counter() - k0;
+    s->beta_set = true;
+    s->setup_pending = true;
+    return MG_OK;
+}
+
 // ------------------------------------------------------------ profiling ----
 
 static cudaEvent_t take_event(Solver *s)
@@ -1282,6 +1312,18 @@ static cudaError_t level_launch(Solver *s, const Hier<T> &H, int l, bool up, int
     return e;
 }
 
+// Level l of H runs as persistent launches: persistent = 2 every level
+// smoothed with passes; 1 only those whose largest stage fits in one wave
+// of the persistent grid.
+template <class T>
+static bool level_persistent(const Solver *s, const Hier<T> &H, int l)
+{
+    if (H.pgrid <= 0 || H.fused[l]) return false;
+    if (s->opts.persistent == 2) return true;
+    const BoxSet<T> &S = H.smooth[l];
+    return std::max(S.ntiles[TK_PAIR], S.ntiles[TK_COARSE]) <= H.pgrid;
+}
+
 // head_done: the finest level's first red pass already ran out of place
 // (phi -> phi2, look-ahead); the cycle goes on with the black pass phi2 -> phi.
 // sym: post-smoothing sweeps run black then red, the adjoint of the
@@ -1297,7 +1339,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
     for (int l = 0; l < nl; ++l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
-        if (H.pgrid > 0 && !H.fused[l]) {
+        if (level_persistent(s, H, l)) {
             if ((e = level_launch(s, H, l, false, s->opts.nu1, l == 0 && head_done, false, st)) !=
                 cudaSuccess)
                 return e;
@@ -1338,7 +1380,7 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
             prof_end(s, coarse, st);
             coarse = -1;
         }
-        if (H.pgrid > 0 && !H.fused[l]) {
+        if (level_persistent(s, H, l)) {
             if ((e = level_launch(s, H, l, true, s->opts.nu2, false, sym, st)) != cudaSuccess)
                 return e;
             continue;
@@ -1352,6 +1394,11 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
     }
     prof_end(s, coarse, st);
     return cudaSuccess;
+}
+
+cudaError_t solver_enqueue_vcycle64(Solver *s, cudaStream_t st)
+{
+    return enqueue_vcycle(s, s->h64, st);
 }
 
 // FP64: V-cycle followed by the fine residual norm into dnorm.

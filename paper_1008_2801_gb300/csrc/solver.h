@@ -122,6 +122,8 @@ struct Solver {
     bool lookahead = false;
     // coupled level (the boxes solved as one domain; mg_level)
     bool coupled = false;                            // one norm for all boxes (mg_level)
+    int cut = 0;                                     // levels kept when the coarsest is solved
+                                                     // elsewhere (slab-decomposed box), else 0
     bool xmode = false;                              // ghost exchanges: coupled level or periodic axes
     bool wide = false;                               // wide-guard layout (xmode)
     std::vector<std::vector<std::array<int, 3>>> lo;  // [box][level] lower corners (coupled)
@@ -164,9 +166,19 @@ struct Solver {
 // dx and beta); weights, diagonals and the coarsest inverse exist once.
 // lo (nullable): lower corners of the boxes of a coupled level (one domain;
 // all dx equal, bc 0); NULL: independent boxes.
+// cut > 0 (coupled levels only): keep levels 0 .. cut - 1; the last of them
+// has no dense inverse of its own (its problem is solved by another context,
+// as the coarse end of a slab-decomposed box).
 int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, int bc,
                   const mg_opts *opts, bool shared_weights = false,
-                  const int (*lo)[3] = nullptr);
+                  const int (*lo)[3] = nullptr, int cut = 0);
+// Set-up of a one-box FP64 context whose level-0 face weights were written
+// into its arrays by the caller: coarse weights, diagonals and the dense
+// coarsest inverse, on st.
+int solver_setup_from_weights(Solver *s, cudaStream_t st);
+// One FP64 V-cycle of every active box from its level-0 f and phi (phi is the
+// initial guess), enqueued on st.
+cudaError_t solver_enqueue_vcycle64(Solver *s, cudaStream_t st);
 void solver_destroy(Solver *s);
 int solver_set_beta(Solver *s, const double *beta_packed, cudaStream_t st);
 // Solve every box; f/phi packed.  zero_guess ignores phi's input.

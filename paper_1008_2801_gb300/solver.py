@@ -82,7 +82,7 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.krylov = 1 if krylov else 0
     o.max_norm = 1 if max_norm else 0
     o.wait_limit = int(wait_limit)
-    o.persistent = 1 if persistent else 0
+    o.persistent = {False: 0, True: 2, "all": 2, "small": 1}.get(persistent, persistent)
     o.sweep_zc = int(sweep_zc)
     o.level_ctas = int(level_ctas)
     if hooks is not None:
@@ -153,7 +153,8 @@ class Solver:
     caching allocator instead of cudaMalloc.  wait_limit: polls of a bounded
     device wait before it gives up (mg_opts.wait_limit; 0 default, -1 gives
     up at once).  persistent: one persistent launch per level and direction
-    (mg_opts.persistent); sweep_zc, level_ctas: tile depth of the fused FP32
+    (mg_opts.persistent: True or "all" on every level smoothed with passes,
+    "small" on those whose stages fit in one wave of resident CTAs); sweep_zc, level_ctas: tile depth of the fused FP32
     sweep and CTAs per SM of the persistent launches (0: the library's
     model; see mg_opts and ``autotune``).  Not thread-safe.
     """
@@ -347,7 +348,8 @@ class BatchSolver:
     over the tiles of every active box).  shapes: list of (nz, ny, nx); arrays
     are packed back to back in box order (see ``pack``/``unpack``).
     persistent: each level smoothed with passes runs as one persistent
-    launch per direction over all boxes (mg_opts.persistent)."""
+    launch per direction over all boxes (mg_opts.persistent; True/"all" or
+    "small", as for ``Solver``)."""
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
@@ -615,3 +617,121 @@ def solve(f: torch.Tensor, beta: torch.Tensor, dx: float, tol: float = 1e-10,
     if s is None:
         s = _cache[key] = Solver(shape, dx, precision=precision, device=f.device, bc=bc)
     return MGSolve.apply(f, beta, s, tol)
+
+
+def slab_plan(shape, nslab):
+    """Host only: (z0, gather_level) of an (nz, ny, nx) box split into nslab
+    slabs (mg_slab_plan): slab r holds planes z0[r] .. z0[r+1]-1; levels below
+    gather_level are smoothed slab by slab."""
+    nz, ny, nx = (int(v) for v in shape)
+    z0 = (ctypes.c_int * (nslab + 1))()
+    g = ctypes.c_int()
+    check(_lib.load().mg_slab_plan(_lib.c_int3(nx, ny, nz), int(nslab), z0, ctypes.byref(g)),
+          "mg_slab_plan")
+    return list(z0), g.value
+
+
+def slab_halo(shape, nslab, level):
+    """Host only: the halo copies of one slab level (mg_slab_halo), as dicts
+    src, src_k, dst, dst_k (local plane indices; -1 and the slab's thickness
+    are its guard planes)."""
+    nz, ny, nx = (int(v) for v in shape)
+    L = _lib.load()
+    n = ctypes.c_int()
+    check(L.mg_slab_halo(_lib.c_int3(nx, ny, nz), int(nslab), int(level), ctypes.byref(n),
+                         None, 0), "mg_slab_halo")
+    buf = (ctypes.c_int * (4 * max(n.value, 1)))()
+    check(L.mg_slab_halo(_lib.c_int3(nx, ny, nz), int(nslab), int(level), ctypes.byref(n), buf,
+                         n.value), "mg_slab_halo")
+    return [{"src": buf[4 * i], "src_k": buf[4 * i + 1], "dst": buf[4 * i + 2],
+             "dst_k": buf[4 * i + 3]} for i in range(n.value)]
+
+
+class SlabSolver:
+    """One (nz, ny, nx) box split in z into ``nslab`` equal slabs, slab r on
+    CUDA device ``devices[r]`` (mg_slab_*): the levels down to the gather
+    level are smoothed slab by slab with halo exchanges of one plane, the
+    rest of the V-cycle runs on ``devices[0]``.  FP64 V-cycles.  Arrays are
+    full-box tensors; each slab's part is a view when the tensor already sits
+    on that slab's device, else a copy."""
+
+    def __init__(self, shape, dx, nslab, devices=None, nu1=2, nu2=2, max_cycles=100):
+        L = _lib.load()
+        self.shape = tuple(int(v) for v in shape)
+        nz, ny, nx = self.shape
+        self.nslab = int(nslab)
+        if devices is None:
+            devices = [torch.cuda.current_device()] * self.nslab
+        self.devices = [torch.device("cuda", torch.device("cuda", d).index
+                                     if isinstance(d, int) else torch.device(d).index)
+                        for d in devices]
+        if len(self.devices) != self.nslab:
+            raise ValueError("one device per slab")
+        self.z0, self.gather = slab_plan(self.shape, self.nslab)
+        o = _opts("fp64", nu1, nu2, max_cycles, False, "passes")
+        devs = (ctypes.c_int * self.nslab)(*[d.index for d in self.devices])
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.devices[0]):
+            check(L.mg_slab_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), float(dx),
+                                   self.nslab, devs, ctypes.byref(o)), "mg_slab_create")
+
+    def _parts(self, t, name):
+        _check_tensor(t, name, self.shape[0] * self.shape[1] * self.shape[2])
+        t = t.reshape(self.shape)
+        out = []
+        for r, d in enumerate(self.devices):
+            part = t[self.z0[r]:self.z0[r + 1]]
+            out.append(part if part.device == d else part.to(d).contiguous())
+        return out
+
+    def _ptrs(self, parts):
+        return (ctypes.c_void_p * self.nslab)(*[p.data_ptr() for p in parts])
+
+    def _sync(self):
+        for d in set(self.devices):
+            torch.cuda.synchronize(d)
+
+    def set_beta(self, beta: torch.Tensor):
+        parts = self._parts(beta, "beta")
+        self._sync()
+        check(_lib.load().mg_slab_set_beta(self._h, self._ptrs(parts)), "mg_slab_set_beta")
+
+    def solve(self, f: torch.Tensor, phi: torch.Tensor | None = None, tol: float = 1e-10,
+              zero_guess: bool | None = None):
+        """Returns (phi, stats); phi is a full-box tensor on devices[0]."""
+        if zero_guess is None:
+            zero_guess = phi is None
+        if phi is None:
+            phi = torch.zeros(self.shape, dtype=torch.float64, device=self.devices[0])
+        fp = self._parts(f, "f")
+        pp = self._parts(phi, "phi")
+        self._sync()
+        st = _lib.mg_stats()
+        flags = _lib.MG_ZERO_GUESS if zero_guess else 0
+        rc = _lib.load().mg_slab_solve(self._h, self._ptrs(fp), self._ptrs(pp), float(tol), flags,
+                                       ctypes.byref(st))
+        if rc not in _SOFT:
+            raise MGError(rc, "mg_slab_solve")
+        out = phi.reshape(self.shape)
+        for r, p in enumerate(pp):
+            dst = out[self.z0[r]:self.z0[r + 1]]
+            if p.data_ptr() != dst.data_ptr():
+                dst.copy_(p)
+        return out, _stats_dict(st)
+
+    def close(self):
+        if self._h:
+            _lib.load().mg_slab_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

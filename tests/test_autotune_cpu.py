@@ -20,11 +20,11 @@ def test_candidates_cover_the_options():
     c64 = list(autotune.candidates("fp64"))
     cmx = list(autotune.candidates("mixed"))
     # FP64 levels always use passes: no smoother choice there
-    assert len(cmx) == 3 * 3 * len(c64)
+    assert len(cmx) == 3 * 3 * len(c64) and len(c64) == 4 * 3
     assert {c["smoother"] for c in c64} == {"auto"}
     assert {c["smoother"] for c in cmx} == {"auto", "passes", "fused"}
     assert {c["inner_cycles"] for c in cmx} == {1, 2, 3}
-    assert {c["persistent"] for c in c64} == {False, True}
+    assert {c["persistent"] for c in c64} == {False, "small", "all"}
     for c in c64 + cmx:
         assert set(c) == set(autotune.DEFAULTS)
     assert autotune.key("G", [(2, 3, 4), (5, 6, 7)], "fp64") == "G|fp64|2x3x4;5x6x7"
@@ -37,9 +37,9 @@ def test_tile_candidates_follow_the_options():
     assert {c["sweep_zc"] for c in t} == set(autotune.SWEEP_ZC)
     assert {c["level_ctas"] for c in t} == {0}
     # passes only and persistent launches: their CTAs per SM
-    t = list(autotune.tile_candidates(dict(base, smoother="passes", persistent=True), "mixed"))
+    t = list(autotune.tile_candidates(dict(base, smoother="passes", persistent="all"), "mixed"))
     assert {c["sweep_zc"] for c in t} == {0}
     assert {c["level_ctas"] for c in t} == set(autotune.LEVEL_CTAS)
     # FP64: no fused sweep
-    t = list(autotune.tile_candidates(dict(base, persistent=True), "fp64"))
+    t = list(autotune.tile_candidates(dict(base, persistent="small"), "fp64"))
     assert {c["sweep_zc"] for c in t} == {0}

@@ -33,7 +33,7 @@ def test_batched_persistent_is_bitwise_the_per_stage_solve(cuda_device, precisio
     beta = _dev(np.concatenate([b.ravel() for b in d["beta"]]), cuda_device)
     f = _dev(np.concatenate([x.ravel() for x in d["f"]]), cuda_device)
     out = {}
-    for persistent in (False, True):
+    for persistent in (False, "small", True):
         bs = BatchSolver(shapes, d["dx"], precision=precision, device=cuda_device,
                          persistent=persistent, use_graph=use_graph, smoother="passes")
         bs.set_beta(beta)
@@ -41,8 +41,9 @@ def test_batched_persistent_is_bitwise_the_per_stage_solve(cuda_device, precisio
         assert all(s["status"] == "ok" for s in sts)
         out[persistent] = (phi.cpu(), [s["cycles"] for s in sts])
         bs.close()
-    assert out[True][1] == out[False][1]
-    assert torch.equal(out[True][0], out[False][0])
+    for mode in ("small", True):
+        assert out[mode][1] == out[False][1]
+        assert torch.equal(out[mode][0], out[False][0])
     flat = out[True][0].numpy()
     o = 0
     for b, sh in enumerate(shapes):
