@@ -2224,6 +2224,125 @@ __global__ void __launch_bounds__(kThreads, 4) k_level_up(BoxSet<T> S, const int
         }
 }
 
+// ----------------------------------- coarsest level by conjugate gradients ----
+//
+// A box whose halving stops at a level too large for a dense inverse (more
+// than MG_MAX_BOTTOM cells: a 33^3 box, or 100^3, whose coarsest level is
+// 25^3) solves that level by conjugate gradients preconditioned with its
+// diagonal, on M = -A (symmetric positive definite): x = phi, r = phi2, and
+// two more level arrays p, q.  One persistent cooperative launch runs the
+// whole iteration; each of its three stages per iteration ends at the
+// bounded grid barrier of the persistent level sweeps, and every dot product
+// is summed in a fixed order (per-CTA partial sums, then each CTA adds the
+// partials 0 .. G-1), so every CTA takes the same decisions and the result
+// is reproducible.  It stops when <r, D^-1 r> has fallen by tol^2, after
+// maxit iterations, or if <p, M p> is not positive.
+
+// (M v)_c = D_c v_c - sum_f w_f v_nbr: minus the operator, zero outside.
+template <class T>
+__device__ __forceinline__ T neg_apply(const Box<T> &B, const T *__restrict__ v, long long c,
+                                       long long cf)
+{
+    const T a = B.wx[c], b = B.wx[c + 1], d = B.wy[c], e = B.wy[c + B.P], g = B.wz[c],
+            h = B.wz[c + B.Q];
+    const T D = B.D ? B.D[cf] : ((a + b) + (d + e)) + (g + h);
+    T s = D * v[c];
+    s = fmadd(-a, v[c - 1], s);
+    s = fmadd(-b, v[c + 1], s);
+    s = fmadd(-d, v[c - B.P], s);
+    s = fmadd(-e, v[c + B.P], s);
+    s = fmadd(-g, v[c - B.Q], s);
+    return fmadd(-h, v[c + B.Q], s);
+}
+
+// Fixed-order sum of the G partials (every CTA gets the same bits).
+__device__ __forceinline__ double sum_partials(const double *__restrict__ part, int G)
+{
+    __shared__ double tot;
+    double v = 0.0;
+    if (threadIdx.y == 0) {
+        for (int i = threadIdx.x; i < G; i += kTX) v += part[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) tot = v;
+    }
+    __syncthreads();
+    const double r = tot;
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_cg_bottom(BoxSet<T> S, const int *__restrict__ active,
+                                                        T *p, T *q, double *part, GridSync g,
+                                                        double tol, int maxit)
+{
+    const Box<T> &B = S.boxes[0];
+    if ((active && !active[B.box]) || grid_failed(g)) return;
+    const int nt = S.ntiles[TK_CELL], G = gridDim.x;
+    double *pa = part, *pb = part + G;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    T *__restrict__ x = B.phi;
+    T *__restrict__ r = B.phi2;
+    // each stage walks the level's cells tile by tile
+    auto cells = [&](auto &&body) {
+        for (int t = blockIdx.x; t < nt; t += G) {
+            const TilePos tp = tile_pos(TK_CELL, nx, ny, nz, t);
+            if (tp.x < nx && tp.y < ny)
+                body((long long)tp.z * B.Q + (long long)tp.y * B.P + tp.x, fidx(B, tp.x, tp.y, tp.z));
+        }
+    };
+    auto put = [&](double *dst, double v) {
+        const double bs = block_sum(v);
+        if (threadIdx.x == 0 && threadIdx.y == 0) dst[blockIdx.x] = bs;
+    };
+    // x = 0, r = -f, p = D^-1 r, partial <r, D^-1 r>
+    double acc = 0.0;
+    cells([&](long long c, long long cf) {
+        const T rv = -B.f[cf];
+        const T zv = rv * B.invD[cf];
+        x[c] = T(0);
+        r[c] = rv;
+        p[c] = zv;
+        acc += (double)rv * (double)zv;
+    });
+    put(pb, acc);
+    if (!grid_sync(g)) return;
+    double rz = sum_partials(pb, G);
+    const double rz0 = rz, stop = tol * tol * rz0;
+    if (!(rz0 > 0.0)) return;   // f = 0 on this level: x = 0
+    for (int it = 0; it < maxit; ++it) {
+        // q = M p, partial <p, q>
+        acc = 0.0;
+        cells([&](long long c, long long cf) {
+            const T qv = neg_apply(B, p, c, cf);
+            q[c] = qv;
+            acc += (double)p[c] * (double)qv;
+        });
+        put(pa, acc);
+        if (!grid_sync(g)) return;
+        const double pq = sum_partials(pa, G);
+        if (!(pq > 0.0)) return;
+        const T alpha = (T)(rz / pq);
+        // x += alpha p, r -= alpha q, partial <r, D^-1 r>
+        acc = 0.0;
+        cells([&](long long c, long long cf) {
+            x[c] = fmadd(alpha, p[c], x[c]);
+            const T rv = fmadd(-alpha, q[c], r[c]);
+            r[c] = rv;
+            acc += (double)rv * (double)(rv * B.invD[cf]);
+        });
+        put(pb, acc);
+        if (!grid_sync(g)) return;
+        const double rz1 = sum_partials(pb, G);
+        if (rz1 <= stop) return;
+        const T beta = (T)(rz1 / rz);
+        rz = rz1;
+        // p = D^-1 r + beta p
+        cells([&](long long c, long long cf) { p[c] = fmadd(beta, p[c], r[c] * B.invD[cf]); });
+        if (!grid_sync(g)) return;
+    }
+}
+
 // ----------------------------------------------------------- launchers ----
 
 static inline dim3 block2d() { return dim3(kTX, kTY); }
@@ -2601,6 +2720,43 @@ template cudaError_t launch_level<double>(const BoxSet<double> &, const int *, i
                                           const LevelOps &, const GridSync &, int, cudaStream_t);
 template cudaError_t launch_level<float>(const BoxSet<float> &, const int *, int,
                                          const LevelOps &, const GridSync &, int, cudaStream_t);
+
+template <class T>
+int cg_bottom_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cg_bottom<T>, kThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, n);
+}
+template int cg_bottom_ctas_per_sm<double>();
+template int cg_bottom_ctas_per_sm<float>();
+
+template <class T>
+cudaError_t launch_cg_bottom(const BoxSet<T> &S, const int *active, T *p, T *q, double *part,
+                             const GridSync &g, int grid, double tol, int maxit, cudaStream_t st)
+{
+    if (S.nbox == 0 || grid < 1) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = block2d();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return counted(cudaLaunchKernelEx(&cfg, k_cg_bottom<T>, S, active, p, q, part, g, tol, maxit));
+}
+template cudaError_t launch_cg_bottom<double>(const BoxSet<double> &, const int *, double *,
+                                              double *, double *, const GridSync &, int, double,
+                                              int, cudaStream_t);
+template cudaError_t launch_cg_bottom<float>(const BoxSet<float> &, const int *, float *, float *,
+                                             double *, const GridSync &, int, double, int,
+                                             cudaStream_t);
 
 template <class T>
 cudaError_t launch_guard_fill(const BoxSet<T> &S, T v, cudaStream_t st)

@@ -145,6 +145,18 @@ template <class T>
 cudaError_t launch_level(const BoxSet<T> &S, const int *active, int up, const LevelOps &op,
                          const GridSync &g, int grid, cudaStream_t st);
 
+// ---- coarsest level too large for a dense inverse: conjugate gradients ----
+// One cooperative launch over box 0 of S (its coarsest level): diagonally
+// preconditioned CG on -A from x = 0 into phi (r in phi2; p, q level arrays
+// of that level with zero guards; part: 2 x grid doubles of scratch), until
+// <r, D^-1 r> falls by tol^2 or maxit iterations; stages separated by the
+// bounded grid barrier g.
+template <class T>
+int cg_bottom_ctas_per_sm();
+template <class T>
+cudaError_t launch_cg_bottom(const BoxSet<T> &S, const int *active, T *p, T *q, double *part,
+                             const GridSync &g, int grid, double tol, int maxit, cudaStream_t st);
+
 // ---- moving data between packed user arrays and the level layout --------
 // user[off[b] + (k*ny + j)*nx + i] -> level 0 f (to_f) or phi of box b.
 cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,

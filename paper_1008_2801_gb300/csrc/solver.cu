@@ -86,6 +86,15 @@ static std::vector<std::array<int, 3>> level_dims(int nx, int ny, int nz)
     return d;
 }
 
+// CG on a coarsest level too large for a dense inverse: stop when
+// <r, D^-1 r> has fallen by tol^2 or after the iteration cap (FP64 / FP32
+// levels; FP32 rounding stalls the residual near sqrt(cond) x 6e-8, so the
+// FP32 cycles of mixed precision stop earlier, which only costs cycles);
+// kCgPartials bounds the CTAs of its launch.
+constexpr double kCgTol64 = 1e-13, kCgTol32 = 1e-5;
+constexpr int kCgMaxIt64 = 20000, kCgMaxIt32 = 3000;
+constexpr int kCgPartials = 4096;
+
 // ------------------------------------------------------------ building ----
 
 // Device memory of a context: the caller's allocator when given, else
@@ -157,7 +166,16 @@ static void carve(Solver *s, Hier<T> &H, Bump &bump, bool full)
         }
         const auto &db = s->dims[b][s->nlev[b] - 1];
         const size_t nb = (size_t)db[0] * db[1] * db[2];
-        if (!s->xmode) H.ainv[b] = (s->shared && b > 0) ? H.ainv[0] : bump.take<T>(nb * nb);
+        if (s->cg_bottom) {
+            // no dense inverse: p and q of the CG on the coarsest level
+            const long long E = level_elems(db[0], db[1], db[2]);
+            const long long Q = pitch_plane(db[0], db[1]);
+            T *pp = bump.take<T>((size_t)E), *qq = bump.take<T>((size_t)E);
+            H.cgp = pp ? pp + Q : nullptr;
+            H.cgq = qq ? qq + Q : nullptr;
+        } else if (!s->xmode) {
+            H.ainv[b] = (s->shared && b > 0) ? H.ainv[0] : bump.take<T>(nb * nb);
+        }
     }
     if (s->xmode) H.uinv = bump.take<T>((size_t)s->ub.n * s->ub.n);
 }
@@ -341,7 +359,7 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
         // first level small enough for the coarse kernel (the coarsest level
         // always is: it is solved there when the kernel is off)
         int lc = s->nlev[b] - 1;
-        if (lim > 0) {
+        if (lim > 0 && !s->cg_bottom) {
             for (int l = 0; l < s->nlev[b]; ++l) {
                 const auto &d = s->dims[b][l];
                 if ((long long)d[0] * d[1] * d[2] <= lim && s->nlev[b] - l <= kMaxCoarse) {
@@ -397,6 +415,11 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
     }
     H.njobs = (int)jobs.size();
     *jobs_off = blob.put(jobs.data(), jobs.size() * sizeof(CoarseJob<T>));
+    if (s->cg_bottom) {
+        const auto &db = s->dims[0][s->nlev[0] - 1];
+        H.cggrid = std::max(1, std::min({cg_bottom_ctas_per_sm<T>() * s->sms, kCgPartials,
+                                         tiles_of(TK_CELL, db[0], db[1], db[2])}));
+    }
     if (s->opts.persistent) {
         int per_sm = level_ctas_per_sm<T>();
         if (s->opts.level_ctas > 0) per_sm = std::min(per_sm, s->opts.level_ctas);
@@ -609,11 +632,18 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         const std::array<int, 3> db = s->dims.back().back();
         const int cells = db[0] * db[1] * db[2];
         if (!coupled && cells > MG_MAX_BOTTOM) {
-            delete s;
-            return set_error(MG_ERR_UNSUPPORTED,
-                             "box %d: coarsest level %dx%dx%d has %d cells (> %d); the dims "
-                             "must halve down to a small level",
-                             b, db[0], db[1], db[2], cells, MG_MAX_BOTTOM);
+            // too large for a dense inverse: one box with a Dirichlet wall
+            // solves its coarsest level by conjugate gradients
+            if (nbox == 1 && !periodic && !s->singular) {
+                s->cg_bottom = true;
+            } else {
+                delete s;
+                return set_error(MG_ERR_UNSUPPORTED,
+                                 "box %d: coarsest level %dx%dx%d has %d cells (> %d); with "
+                                 "several boxes, periodic axes or every wall Neumann the dims "
+                                 "must halve down to a small level",
+                                 b, db[0], db[1], db[2], cells, MG_MAX_BOTTOM);
+            }
         }
         s->max_bottom = std::max(s->max_bottom, cells);
         s->off[b + 1] = s->off[b] + (long long)nx * ny * nz;
@@ -634,7 +664,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     std::vector<size_t> work_off(nbox, 0);
     for (int b = 0; b < nbox; ++b) {
         const auto &db = s->dims[b].back();
-        const size_t nb = (size_t)db[0] * db[1] * db[2];
+        const size_t nb = s->cg_bottom ? 0 : (size_t)db[0] * db[1] * db[2];
         work_off[b] = work_elems;
         work_elems += nb * nb;
         ntiles0 += (size_t)tiles_of(TK_CELL, s->n[b][0], s->n[b][1], s->n[b][2]);
@@ -674,6 +704,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     bump.take<int>(nbox);
     bump.take<int>(1);  // error word
     bump.take<unsigned>(1);  // grid-barrier word
+    if (s->cg_bottom) bump.take<double>(2 * kCgPartials);   // CG partial sums
     // judge block: hist | rel0 | best | tol | status | cycles | stall | step
     const size_t jbytes = sizeof(double) * ((size_t)nbox * MG_MAX_HIST + 2 * nbox + 1) +
                           sizeof(int) * (3 * (size_t)nbox + 1);
@@ -717,6 +748,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->active = real.take<int>(nbox);
     s->derr = real.take<int>(1);
     s->gbar = real.take<unsigned>(1);
+    if (s->cg_bottom) s->cgpart = real.take<double>(2 * kCgPartials);
     s->jbytes = jbytes;
     s->jblock = real.take<char>(jbytes);
     {
@@ -1112,7 +1144,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     if (!s->xmode) {
         CK(cudaEventRecord(s->ev_fork, st));
         CK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-        CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, s->side));
+        if (!s->cg_bottom) CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, s->side));
         CK(cudaEventRecord(s->ev_join, s->side));
     }
     for (int l = 0; l < s->maxlev; ++l) {
@@ -1142,7 +1174,7 @@ int solver_setup_from_weights(Solver *s, cudaStream_t st)
     CK(cudaEventRecord(s->ev_setup0, st));
     const long long k0 = launch_counter();
     for (size_t l = 0; l < s->setup_coarsen.size(); ++l) CK(launch_setup(s->setup_coarsen[l], 1, st));
-    CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, st));
+    if (!s->cg_bottom) CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, st));
     for (int l = 0; l < s->maxlev; ++l) CK(launch_setup(s->setup_lv[l], 2, st));
     CK(cudaEventRecord(s->ev_setup1, st));
     s->kernels += launch_counter() - k0;
@@ -1369,6 +1401,11 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
     if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     if (s->coupled)
         e = launch_union_bottom(H.bottom, s->ub, H.uinv, s->active, st);
+    else if (s->cg_bottom)
+        e = launch_cg_bottom(H.bottom, s->active, H.cgp, H.cgq, s->cgpart,
+                             GridSync{s->gbar, s->derr, sweep_wait_polls(s->opts.wait_limit)},
+                             H.cggrid, sizeof(T) == sizeof(double) ? kCgTol64 : kCgTol32,
+                             sizeof(T) == sizeof(double) ? kCgMaxIt64 : kCgMaxIt32, st);
     else
         e = launch_coarse_vcycle(H.jobs, H.njobs, s->active, s->opts.nu1, s->opts.nu2, st,
                                  sym ? 1 : 0);
@@ -1769,7 +1806,8 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     CK(cudaMemcpyAsync(s->active, s->hactive, sizeof(int) * nbox, cudaMemcpyHostToDevice, stream));
     // the persistent launches' barrier word starts every solve at zero (a
     // barrier that gave up in an earlier solve may have left it mid-count)
-    if (s->opts.persistent) CK(cudaMemsetAsync(s->gbar, 0, sizeof(unsigned), stream));
+    if (s->opts.persistent || s->cg_bottom)
+        CK(cudaMemsetAsync(s->gbar, 0, sizeof(unsigned), stream));
     if (zero_guess) {
         CK(launch_zero(H.fine, nullptr, stream));
     } else {

@@ -39,6 +39,8 @@ struct Hier {
     cudaGraphExec_t head = nullptr;             // look-ahead: first red pass + norm
     T *uinv = nullptr;                          // coupled level: dense inverse of the union bottom
     int pgrid = 0;                              // resident CTAs of the persistent level kernels
+    T *cgp = nullptr, *cgq = nullptr;           // CG coarsest level: p and q (level arrays)
+    int cggrid = 0;                             // CG coarsest level: CTAs of its launch
 };
 
 // A timed stretch of one stage class: events recorded before and after it.
@@ -140,6 +142,10 @@ struct Solver {
 
     int *derr = nullptr;                  // device error word (bounded waits that gave up)
     unsigned *gbar = nullptr;             // device grid-barrier word of the persistent launches
+    // one box whose coarsest level is too large for a dense inverse: solved
+    // there by conjugate gradients (p, q in the hierarchies; partial sums)
+    bool cg_bottom = false;
+    double *cgpart = nullptr;
     int bc = 0;                           // wall mask: bit w set = wall w Neumann
     bool singular = false;                // every wall Neumann: A has the constants as null space
     double *dmean = nullptr;              // [nbox] scratch: removed means

@@ -76,7 +76,8 @@ def test_invalid_shapes_are_rejected(cuda_device):
         BatchSolver([], 0.1, device=cuda_device)
     assert e.value.name == "invalid_arg"
     with pytest.raises(MGError) as e:
-        Solver((33, 33, 33), 0.1, device=cuda_device)    # a 35937-cell coarsest level
+        # 35937-cell coarsest levels in a batch (one box at a time solves them by CG)
+        BatchSolver([(33, 33, 33), (8, 8, 8)], 0.1, device=cuda_device)
     assert e.value.name == "unsupported"
 
 

@@ -244,7 +244,8 @@ def test_faults_are_reported_not_raised_on_device(cuda_device):
             s.solve(f, tol=0.0)
         assert ei.value.name == "invalid_arg"
     with pytest.raises(MGError) as ei:
-        Solver((33, 33, 33), 1 / 33, device=cuda_device)
+        # a 35937-cell coarsest level with every wall Neumann (singular A)
+        Solver((33, 33, 33), 1 / 33, bc=63, device=cuda_device)
     assert ei.value.name == "unsupported" and "33x33x33" in str(ei.value)
     with pytest.raises(MGError) as ei:
         Solver((8, 8, 8), -1.0, device=cuda_device)
