@@ -2049,6 +2049,102 @@ __global__ void k_norm_combine(int nbox, double *__restrict__ norm)
     for (int b = threadIdx.x; b < nbox; b += blockDim.x) norm[b] = tot;
 }
 
+// ------------------------------------ right-hand sides of one box ----
+//
+// A batch whose boxes are right-hand sides of one box (mg_solve_multi,
+// mg_adjoint with several right-hand sides) has one set of weights, 1/D and
+// D for all of them.  These pass variants take a tile of box 0's index
+// space and update the same cells in every active right-hand side, so the
+// six weights and 1/D of a cell are read once for all of them: an FP64 pass
+// then moves 16 + 28 / nrhs bytes a cell and right-hand side (phi's sectors,
+// half of f, half of phi written) instead of 44.  The arithmetic per cell is
+// that of k_rbgs_pass / k_rbgs_pass_oop, in the same order.
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_rbgs_pass_multi(BoxSet<T> S,
+                                                              const int *__restrict__ active,
+                                                              int color)
+{
+    pdl_wait();
+    const Box<T> &B0 = S.boxes[0];
+    const int P = B0.P;
+    const long long Q = B0.Q;
+    const TilePos p = tile_pos(TK_PAIR, B0.nx, B0.ny, B0.nz, blockIdx.x);
+    const int j = p.y, k = p.z;
+    const int i = 2 * p.x + ((j + k + color + B0.par) & 1);
+    if (j >= B0.ny || i >= B0.nx) return;
+    const long long c = (long long)k * Q + (long long)j * P + i;
+    const long long cf =
+        split_on(B0) ? (long long)k * Q + (long long)j * P + (color ? (P >> 1) : 0) + p.x : c;
+    const T wxa = B0.wx[c], wxb = B0.wx[c + 1], wya = B0.wy[c], wyb = B0.wy[c + P],
+            wza = B0.wz[c], wzb = B0.wz[c + Q], id = B0.invD[cf];
+#pragma unroll 2
+    for (int r = 0; r < S.nbox; ++r) {
+        const Box<T> &B = S.boxes[r];
+        if (active && !active[B.box]) continue;
+        const T *__restrict__ ph = B.phi;
+        T s = fmadd(wxa, ph[c - 1], -B.f[cf]);
+        s = fmadd(wxb, ph[c + 1], s);
+        s = fmadd(wya, ph[c - P], s);
+        s = fmadd(wyb, ph[c + P], s);
+        s = fmadd(wza, ph[c - Q], s);
+        B.phi[c] = fmadd(wzb, ph[c + Q], s) * id;
+    }
+}
+
+// One colour out of place (as k_rbgs_pass_oop) in every right-hand side.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_rbgs_pass_oop_multi(BoxSet<T> S,
+                                                                  const int *__restrict__ active,
+                                                                  int color, int from2)
+{
+    pdl_wait();
+    const Box<T> &B0 = S.boxes[0];
+    const int P = B0.P;
+    const long long Q = B0.Q;
+    const TilePos p = tile_pos(TK_PAIR, B0.nx, B0.ny, B0.nz, blockIdx.x);
+    const int j = p.y, k = p.z, x0 = 2 * p.x;
+    if (j >= B0.ny || x0 >= B0.nx) return;
+    typedef typename Vec2<T>::type V2;
+    const long long c0 = (long long)k * Q + (long long)j * P + x0;
+    const int odd = (j + k + color + B0.par) & 1;
+    const bool upd = x0 + odd < B0.nx;
+    const long long c = c0 + odd;
+    const long long cf =
+        split_on(B0) ? (long long)k * Q + (long long)j * P + (color ? (P >> 1) : 0) + (x0 >> 1)
+                     : c;
+    T wxa = 0, wxb = 0, wya = 0, wyb = 0, wza = 0, wzb = 0, id = 0;
+    if (upd) {
+        wxa = B0.wx[c];
+        wxb = B0.wx[c + 1];
+        wya = B0.wy[c];
+        wyb = B0.wy[c + P];
+        wza = B0.wz[c];
+        wzb = B0.wz[c + Q];
+        id = B0.invD[cf];
+    }
+#pragma unroll 2
+    for (int r = 0; r < S.nbox; ++r) {
+        const Box<T> &B = S.boxes[r];
+        if (active && !active[B.box]) continue;
+        const T *__restrict__ src = from2 ? B.phi2 : B.phi;
+        T *__restrict__ dst = from2 ? B.phi : B.phi2;
+        V2 pair = *reinterpret_cast<const V2 *>(src + c0);
+        if (upd) {
+            T s = fmadd(wxa, src[c - 1], -B.f[cf]);
+            s = fmadd(wxb, src[c + 1], s);
+            s = fmadd(wya, src[c - P], s);
+            s = fmadd(wyb, src[c + P], s);
+            s = fmadd(wza, src[c - Q], s);
+            s = fmadd(wzb, src[c + Q], s);
+            const T nv = s * id;
+            if (odd) pair.y = nv;
+            else pair.x = nv;
+        }
+        *reinterpret_cast<V2 *>(dst + c0) = pair;
+    }
+}
+
 // ------------------------------------------- persistent level sweeps ----
 //
 // The many boxes of a batch (the grids of one MultiFAB level, paper Sec. 2)
@@ -2236,7 +2332,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_level_up(BoxSet<T> S, const int
 // is summed in a fixed order (per-CTA partial sums, then each CTA adds the
 // partials 0 .. G-1), so every CTA takes the same decisions and the result
 // is reproducible.  It stops when <r, D^-1 r> has fallen by tol^2, after
-// maxit iterations, or if <p, M p> is not positive.
+// maxit iterations, when 200 iterations in a row have not lowered it below
+// its smallest value so far (rounding has stalled it), or if <p, M p> is
+// not positive.
 
 // (M v)_c = D_c v_c - sum_f w_f v_nbr: minus the operator, zero outside.
 template <class T>
@@ -2310,6 +2408,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_bottom(BoxSet<T> S, const int *
     double rz = sum_partials(pb, G);
     const double rz0 = rz, stop = tol * tol * rz0;
     if (!(rz0 > 0.0)) return;   // f = 0 on this level: x = 0
+    double best = rz0;
+    int since = 0;
     for (int it = 0; it < maxit; ++it) {
         // q = M p, partial <p, q>
         acc = 0.0;
@@ -2335,6 +2435,12 @@ __global__ void __launch_bounds__(kThreads) k_cg_bottom(BoxSet<T> S, const int *
         if (!grid_sync(g)) return;
         const double rz1 = sum_partials(pb, G);
         if (rz1 <= stop) return;
+        if (rz1 < best) {
+            best = rz1;
+            since = 0;
+        } else if (++since >= 200) {
+            return;
+        }
         const T beta = (T)(rz1 / rz);
         rz = rz1;
         // p = D^-1 r + beta p
@@ -2677,6 +2783,22 @@ cudaError_t launch_exchange(const BoxSet<T> &S, const int *active, const ExchRec
     const int chunks = std::max(1, std::min(1024, (max_cells + 4 * kThreads - 1) / (4 * kThreads)));
     return pdl_launch(k_exchange<T>, dim3(nrec, chunks), block2d(), 0, st, S, active, rec, second);
 }
+
+template <class T>
+cudaError_t launch_rbgs_pass_multi(const BoxSet<T> &S, const int *active, int color, int oop,
+                                   int from2, cudaStream_t st)
+{
+    if (S.nbox == 0 || S.ntiles[TK_PAIR] == 0) return cudaSuccess;
+    const int per = S.ntiles[TK_PAIR] / S.nbox;   // tiles of one right-hand side
+    if (oop)
+        return pdl_launch(k_rbgs_pass_oop_multi<T>, dim3(per), block2d(), 0, st, S, active, color,
+                          from2);
+    return pdl_launch(k_rbgs_pass_multi<T>, dim3(per), block2d(), 0, st, S, active, color);
+}
+template cudaError_t launch_rbgs_pass_multi<double>(const BoxSet<double> &, const int *, int, int,
+                                                    int, cudaStream_t);
+template cudaError_t launch_rbgs_pass_multi<float>(const BoxSet<float> &, const int *, int, int,
+                                                   int, cudaStream_t);
 
 template <class T>
 int level_ctas_per_sm()

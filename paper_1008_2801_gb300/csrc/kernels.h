@@ -21,6 +21,15 @@ template <class T>
 cudaError_t launch_rbgs_pass_oop(const BoxSet<T> &S, const int *active, int color, int from2,
                                  double *partials, cudaStream_t st);
 
+// The boxes of S are right-hand sides of one box (same dims, one set of
+// weights, 1/D and D): one colour pass in every active box, in place
+// (oop = 0) or out of place (oop = 1, from2 as launch_rbgs_pass_oop), each
+// cell's weights read once for all of them.  Same arithmetic per cell as
+// the per-box passes.
+template <class T>
+cudaError_t launch_rbgs_pass_multi(const BoxSet<T> &S, const int *active, int color, int oop,
+                                   int from2, cudaStream_t st);
+
 // ---- FP32 fused sweep fed by the Tensor Memory Accelerator (sweep_tma.cu)
 struct SweepMaps;  // six tensor maps of one box level (device memory, 64-B aligned)
 size_t sweep_maps_size();

@@ -91,7 +91,7 @@ static std::vector<std::array<int, 3>> level_dims(int nx, int ny, int nz)
 // levels; FP32 rounding stalls the residual near sqrt(cond) x 6e-8, so the
 // FP32 cycles of mixed precision stop earlier, which only costs cycles);
 // kCgPartials bounds the CTAs of its launch.
-constexpr double kCgTol64 = 1e-13, kCgTol32 = 1e-5;
+constexpr double kCgTol64 = 1e-12, kCgTol32 = 1e-5;
 constexpr int kCgMaxIt64 = 20000, kCgMaxIt32 = 3000;
 constexpr int kCgPartials = 4096;
 
@@ -1278,6 +1278,17 @@ static cudaError_t combine(Solver *s, double *norm, cudaStream_t st)
     return launch_norm_combine(s->nbox, norm, st);
 }
 
+// The boxes are right-hand sides of one box (shared weights): passes read
+// each cell's weights once for all of them.
+static bool rhs_shared(const Solver *s) { return s->shared && s->nbox > 1 && !s->xmode; }
+
+template <class T>
+static cudaError_t pass_launch(Solver *s, const BoxSet<T> &S, int color, cudaStream_t st)
+{
+    if (rhs_shared(s)) return launch_rbgs_pass_multi(S, s->active, color, 0, 0, st);
+    return launch_rbgs_pass(S, s->active, color, st);
+}
+
 // reverse: black before red in each sweep (single-colour passes only).
 template <class T>
 static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool fused,
@@ -1299,8 +1310,7 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
         for (int color = 0; color < 2; ++color) {
             int sl = fine ? prof_begin(s, MG_PROF_PASS, st) : -1;
             if ((e = exch(s, S, lvl, st)) != cudaSuccess) return e;
-            if ((e = launch_rbgs_pass(S, s->active, reverse ? 1 - color : color, st)) !=
-                cudaSuccess)
+            if ((e = pass_launch(s, S, reverse ? 1 - color : color, st)) != cudaSuccess)
                 return e;
             prof_end(s, sl, st);
         }
@@ -1382,8 +1392,9 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (l == 0 && head_done) {
             int sl = prof_begin(s, MG_PROF_PASS, st);
             if ((e = exch(s, S, 0, st, true)) != cudaSuccess) return e;
-            if ((e = launch_rbgs_pass_oop(S, s->active, 1, 1, nullptr, st)) != cudaSuccess)
-                return e;
+            e = rhs_shared(s) ? launch_rbgs_pass_multi(S, s->active, 1, 1, 1, st)
+                              : launch_rbgs_pass_oop(S, s->active, 1, 1, nullptr, st);
+            if (e != cudaSuccess) return e;
             prof_end(s, sl, st);
             --nu1;
         }

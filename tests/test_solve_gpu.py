@@ -265,6 +265,34 @@ def test_multi_rhs_matches_single(cuda_device):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multi_rhs_that_stop_at_different_cycles(cuda_device, precision):
+    # the right-hand sides of one box share one weight set and their passes
+    # read it once for all of them; boxes leave at different cycles (a zero
+    # right-hand side at once, one started from its own solution, the others
+    # when they converge) and each result stays bitwise its single solve
+    d = inputs.stellar((40, 24, 32), 19, nrhs=4)
+    shape = d["f"].shape
+    with Solver(shape, d["dx"], precision=precision, device=cuda_device) as s:
+        s.set_beta(_dev(d["beta"], cuda_device))
+        fb = _dev(d["f_batch"], cuda_device)
+        fb[1].zero_()
+        fb[3] *= 1e-3
+        sol3, _ = s.solve(fb[3].contiguous())
+        guess = torch.zeros_like(fb)
+        guess[3] = sol3
+        phis, sts = s.solve(fb, phi=guess.clone(), zero_guess=False)
+        assert all(st["status"] == "ok" for st in sts)
+        assert sts[1]["cycles"] == 0 and sts[3]["cycles"] == 0
+        assert not phis[1].any()
+        for b in range(4):
+            one, st1 = s.solve(fb[b].contiguous(), phi=guess[b].clone(), zero_guess=False)
+            assert st1["cycles"] == sts[b]["cycles"]
+            assert torch.equal(one, phis[b]), b
+        ref, _ = O.solve(d["beta"], d["f_batch"][0], d["dx"], tol=1e-13)
+        assert np.linalg.norm(phis[0].cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batched_reduced_vs_oracle(cuda_device, precision):
     d = inputs.batched(12, 40, sizes=(8, 12, 16, 24, 32), dx=1 / 32)
     shapes = [tuple(int(v) for v in dims[::-1]) for dims in d["dims"]]
