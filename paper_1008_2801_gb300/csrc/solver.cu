@@ -1278,14 +1278,25 @@ static cudaError_t combine(Solver *s, double *norm, cudaStream_t st)
     return launch_norm_combine(s->nbox, norm, st);
 }
 
-// The boxes are right-hand sides of one box (shared weights): passes read
-// each cell's weights once for all of them.
+// The boxes are right-hand sides of one box (shared weights): on a level
+// whose one box alone fills the GPU (at least 4 tiles per SM), passes read
+// each cell's weights once for all of them.  On smaller levels the
+// per-box launch keeps more CTAs in flight, which matters more there
+// (measured at 128^3 x 8: the multi-RHS passes took the finest level's
+// passes from 10.4 to 9.7 ms, but made the coarser levels 50% slower).
 static bool rhs_shared(const Solver *s) { return s->shared && s->nbox > 1 && !s->xmode; }
+
+template <class T>
+static bool rhs_shared_level(const Solver *s, const BoxSet<T> &S)
+{
+    return rhs_shared(s) && S.nbox == s->nbox &&
+           S.ntiles[TK_PAIR] / S.nbox >= 4 * s->sms;
+}
 
 template <class T>
 static cudaError_t pass_launch(Solver *s, const BoxSet<T> &S, int color, cudaStream_t st)
 {
-    if (rhs_shared(s)) return launch_rbgs_pass_multi(S, s->active, color, 0, 0, st);
+    if (rhs_shared_level(s, S)) return launch_rbgs_pass_multi(S, s->active, color, 0, 0, st);
     return launch_rbgs_pass(S, s->active, color, st);
 }
 
@@ -1392,8 +1403,8 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (l == 0 && head_done) {
             int sl = prof_begin(s, MG_PROF_PASS, st);
             if ((e = exch(s, S, 0, st, true)) != cudaSuccess) return e;
-            e = rhs_shared(s) ? launch_rbgs_pass_multi(S, s->active, 1, 1, 1, st)
-                              : launch_rbgs_pass_oop(S, s->active, 1, 1, nullptr, st);
+            e = rhs_shared_level(s, S) ? launch_rbgs_pass_multi(S, s->active, 1, 1, 1, st)
+                                       : launch_rbgs_pass_oop(S, s->active, 1, 1, nullptr, st);
             if (e != cudaSuccess) return e;
             prof_end(s, sl, st);
             --nu1;
