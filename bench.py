@@ -652,6 +652,49 @@ def run_extra(dev, args):
     ex["krylov_256^3"] = res
     del beta, f, cases
 
+    # the 256^3 workload split in z into 2 and 4 slabs (each slab its own
+    # context and stream, halo planes by peer copies; on one GPU here, so
+    # this is the decomposition's overhead, not multi-GPU scaling), next to
+    # the single box
+    from paper_1008_2801_gb300 import SlabSolver
+    d = inputs.config(2)
+    n = d["f"].shape[0]
+    beta = torch.from_numpy(d["beta"]).to(dev)
+    f = torch.from_numpy(d["f"]).to(dev)
+    res = {}
+    for nslab in (1, 2, 4):
+        sl = SlabSolver((n, n, n), d["dx"], nslab)
+
+        def slab_step():
+            sl.set_beta(beta)
+            return sl.solve(f, tol=TOL)
+        ms, (_, st) = time_once(slab_step)
+        res[f"slabs_{nslab}"] = {"cells_per_s": n ** 3 / (ms / 1e3), "ms": ms,
+                                 "cycles": st["cycles"], "status": st["status"],
+                                 "gather_level": sl.gather}
+        sl.close()
+    ex["slab_256^3_one_gpu"] = res
+
+    # boxes whose coarsest level is too large for a dense inverse (conjugate
+    # gradients there): 100^3 (coarsest 25^3) and 33^3 (no halving at all)
+    res = {}
+    for shape in ((100, 100, 100), (33, 33, 33)):
+        dd = inputs.stellar(shape[::-1], 60)
+        bb = torch.from_numpy(dd["beta"]).to(dev)
+        ff = torch.from_numpy(dd["f"]).to(dev)
+        for prec in ("fp64", "mixed"):
+            s = Solver(shape, dd["dx"], precision=prec, device=dev)
+
+            def cg_step():
+                s.set_beta(bb)
+                return s.solve(ff, tol=TOL)
+            ms, (_, st) = time_once(cg_step)
+            res[f"{shape[0]}^3_{prec}"] = {"cells_per_s": ff.numel() / (ms / 1e3), "ms": ms,
+                                           "cycles": st["cycles"], "status": st["status"],
+                                           "coarsest": list(s.levels()[-1])}
+            s.close()
+    ex["cg_coarsest_level"] = res
+
     # adjoint, 128^3 x 8 right-hand sides
     d = inputs.config(5)
     beta = torch.from_numpy(d["beta"]).to(dev).requires_grad_(True)

@@ -269,8 +269,10 @@ def test_multi_rhs_that_stop_at_different_cycles(cuda_device, precision):
     # the right-hand sides of one box share one weight set and their passes
     # read it once for all of them; boxes leave at different cycles (a zero
     # right-hand side at once, one started from its own solution, the others
-    # when they converge) and each result stays bitwise its single solve
-    d = inputs.stellar((40, 24, 32), 19, nrhs=4)
+    # when they converge) and each result stays bitwise its single solve.
+    # 128 x 64 x 64 fills the GPU with one right-hand side (1024 pair tiles),
+    # so the finest level takes the multi-RHS passes.
+    d = inputs.stellar((128, 64, 64), 19, nrhs=4)
     shape = d["f"].shape
     with Solver(shape, d["dx"], precision=precision, device=cuda_device) as s:
         s.set_beta(_dev(d["beta"], cuda_device))
