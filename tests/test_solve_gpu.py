@@ -269,7 +269,10 @@ def test_multi_rhs_that_stop_at_different_cycles(cuda_device, precision):
     # the right-hand sides of one box share one weight set and their passes
     # read it once for all of them; boxes leave at different cycles (a zero
     # right-hand side at once, one started from its own solution, the others
-    # when they converge) and each result stays bitwise its single solve.
+    # when they converge) and each result is its single solve: bitwise in
+    # FP64; in mixed precision the batch of four may fuse the FP32 sweeps
+    # where one right-hand side alone does not (more tiles fill the GPU),
+    # which rounds 1/D differently, so there the two agree to the tolerance.
     # 128 x 64 x 64 fills the GPU with one right-hand side (1024 pair tiles),
     # so the finest level takes the multi-RHS passes.
     d = inputs.stellar((128, 64, 64), 19, nrhs=4)
@@ -288,8 +291,12 @@ def test_multi_rhs_that_stop_at_different_cycles(cuda_device, precision):
         assert not phis[1].any()
         for b in range(4):
             one, st1 = s.solve(fb[b].contiguous(), phi=guess[b].clone(), zero_guess=False)
-            assert st1["cycles"] == sts[b]["cycles"]
-            assert torch.equal(one, phis[b]), b
+            if precision == "fp64":
+                assert st1["cycles"] == sts[b]["cycles"]
+                assert torch.equal(one, phis[b]), b
+            else:
+                assert abs(st1["cycles"] - sts[b]["cycles"]) <= 1
+                assert (one - phis[b]).norm() <= 1e-9 * max(one.norm().item(), 1e-300), b
         ref, _ = O.solve(d["beta"], d["f_batch"][0], d["dx"], tol=1e-13)
         assert np.linalg.norm(phis[0].cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
 
