@@ -120,11 +120,15 @@ typedef struct {
                          cells satisfy their equations, so the restricted
                          residual and the cycle's residual norm are formed
                          from the red cells only; 1: always every cell */
-    int tma;          /* 0 (default): FP32 fused sweeps read their operands
-                         with plain loads and a one-plane register prefetch;
-                         1: they stage their tiles in a shared-memory ring
-                         filled by the Tensor Memory Accelerator (when the
-                         driver can encode tensor maps) */
+    int tma;          /* 0 (default) or 1: FP32 fused sweeps are fed by the
+                         Tensor Memory Accelerator: a producer warp copies
+                         each plane's tiles into a shared-memory ring that
+                         eleven consumer warps compute from (on levels
+                         whose rows and planes hold a whole 72 x 12 copy
+                         box, when the driver can encode tensor maps;
+                         elsewhere plain loads); -1: every fused sweep
+                         reads its operands with plain loads.  Both give
+                         bitwise the same result */
     int krylov;       /* 0 (default): the iteration is V-cycles (FP64) or
                          iterative refinement (mixed); 1: conjugate gradients
                          preconditioned by one symmetric V-cycle per iteration
@@ -293,6 +297,13 @@ int mg_bc_lift(mg_ctx *ctx, const double *vals, const double *f, double *f_out, 
 /* Level list of a context: *nlev levels, dims[3*l .. 3*l+2] = (nx, ny, nz)
  * of level l (dims may be NULL; room for 32 levels). */
 int mg_levels(const mg_ctx *ctx, int *nlev, int *dims);
+
+/* How the context smooths level `level` of its V-cycles (FP32 levels in
+ * mixed precision, else FP64): *kind = 0 single-colour passes (or the
+ * level is in the one-CTA coarse kernel, or is the coarsest), 1 fused
+ * sweeps with plain loads, 2 fused sweeps fed by the Tensor Memory
+ * Accelerator.  Host only.  INVALID_ARG for a level outside the list. */
+int mg_smoother_kind(const mg_ctx *ctx, int level, int *kind);
 
 void mg_destroy(mg_ctx *ctx);
 

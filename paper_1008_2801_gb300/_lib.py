@@ -83,6 +83,7 @@ _SIGS = {
     "mg_adjoint": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
                            ctypes.POINTER(mg_stats), c_void_p]),
     "mg_levels": (c_int, [c_void_p, c_int_p, c_int_p]),
+    "mg_smoother_kind": (c_int, [c_void_p, c_int, c_int_p]),
     "mg_project_rhs": (c_int, [c_void_p] * 7),
     "mg_project_correct": (c_int, [c_void_p] * 6),
     "mg_bc_lift": (c_int, [c_void_p] * 5),

@@ -441,6 +441,7 @@ static int validate_opts(const mg_opts *o)
         return set_error(MG_ERR_INVALID_ARG, "inner_cycles must be in 0..8");
     if (o->krylov < 0 || o->krylov > 1) return set_error(MG_ERR_INVALID_ARG, "krylov must be 0 or 1");
     if (o->wait_limit < -1) return set_error(MG_ERR_INVALID_ARG, "wait_limit must be >= -1");
+    if (o->tma < -1 || o->tma > 1) return set_error(MG_ERR_INVALID_ARG, "tma must be -1, 0 or 1");
     if (o->persistent < 0 || o->persistent > 2)
         return set_error(MG_ERR_INVALID_ARG, "persistent must be 0, 1 or 2");
     if (o->sweep_zc < 0 || o->sweep_zc > 4096)
@@ -543,7 +544,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         // does its own exchanges)
         o.smoother = 1;
         if (coupled) o.coarse_cells = -1;
-        o.tma = 0;
+        o.tma = -1;
     }
     std::vector<std::vector<std::array<int, 3>>> cdims, clos;
     std::vector<Brick> bricks;
@@ -597,7 +598,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->nbox = nbox;
     s->opts = o;
     s->has32 = o.precision == MG_MIXED;
-    s->tma = s->has32 && o.tma == 1;
+    s->tma = s->has32 && o.tma >= 0;
     s->pcg = o.krylov == 1;
     s->bc = bc;
     // A singular (constants in the null space): no axis has a Dirichlet wall
@@ -2357,6 +2358,22 @@ int mg_bc_lift(mg_ctx *ctx, const double *vals, const double *f, double *f_out, 
     CK(launch_bc_lift(n[0], n[1], n[2], 1.0 / s->dx[0], s->bc, L.wx, L.wy, L.wz, vals, f, f_out,
                       (cudaStream_t)stream, s->wide));
     s->kernels += 1;
+    return MG_OK;
+}
+
+int mg_smoother_kind(const mg_ctx *ctx, int level, int *kind)
+{
+    if (!ctx || !kind) return set_error(MG_ERR_INVALID_ARG, "NULL argument");
+    const Solver *s = ctx->s;
+    if (level < 0 || level >= s->nlev[0])
+        return set_error(MG_ERR_INVALID_ARG, "level %d outside 0..%d", level, s->nlev[0] - 1);
+    *kind = 0;
+    auto of = [&](const auto &H) {
+        if (level < (int)H.fused.size() && H.fused[level] && H.smooth[level].nbox > 0)
+            *kind = H.maps[level] ? 2 : 1;
+    };
+    if (s->has32) of(s->h32);
+    else of(s->h64);
     return MG_OK;
 }
 

@@ -67,7 +67,7 @@ def _torch_allocator(device):
 
 
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
-          full_residual=False, tma=False, krylov=False, max_norm=False, hooks=None,
+          full_residual=False, tma=None, krylov=False, max_norm=False, hooks=None,
           wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
@@ -78,7 +78,7 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.coarse_cells = int(coarse_cells)
     o.inner_cycles = int(inner_cycles)
     o.full_residual = 1 if full_residual else 0
-    o.tma = 1 if tma else 0
+    o.tma = {None: 0, True: 1, False: -1}[tma]
     o.krylov = 1 if krylov else 0
     o.max_norm = 1 if max_norm else 0
     o.wait_limit = int(wait_limit)
@@ -150,7 +150,9 @@ class Solver:
     symmetric V-cycle per iteration instead of plain V-cycles, for
     high-contrast beta (with "mixed" the V-cycle runs in FP32, CG in FP64).
     allocator: "torch" takes the context's device memory from PyTorch's
-    caching allocator instead of cudaMalloc.  wait_limit: polls of a bounded
+    caching allocator instead of cudaMalloc.  tma: None (default) or True
+    feeds the FP32 fused sweeps by the Tensor Memory Accelerator where a
+    level fits, False forces plain loads (same result).  wait_limit: polls of a bounded
     device wait before it gives up (mg_opts.wait_limit; 0 default, -1 gives
     up at once).  persistent: one persistent launch per level and direction
     (mg_opts.persistent: True or "all" on every level smoothed with passes,
@@ -161,7 +163,7 @@ class Solver:
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
+                 full_residual=False, tma=None, bc=0, krylov=False, max_norm=False,
                  allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
@@ -191,6 +193,14 @@ class Solver:
         dims = (ctypes.c_int * 96)()
         check(_lib.load().mg_levels(self._h, ctypes.byref(n), dims), "mg_levels")
         return [(dims[3 * i + 2], dims[3 * i + 1], dims[3 * i]) for i in range(n.value)]
+
+    def smoother_kind(self, level=0):
+        """How level `level` is smoothed (mg_smoother_kind): "passes",
+        "fused" (plain-load sweeps) or "fused_tma"."""
+        k = ctypes.c_int()
+        check(_lib.load().mg_smoother_kind(self._h, int(level), ctypes.byref(k)),
+              "mg_smoother_kind")
+        return ("passes", "fused", "fused_tma")[k.value]
 
     def set_beta(self, beta: torch.Tensor):
         _check_tensor(beta, "beta", self.numel, self.device)
@@ -353,7 +363,7 @@ class BatchSolver:
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
-                 full_residual=False, tma=False, bc=0, krylov=False, max_norm=False,
+                 full_residual=False, tma=None, bc=0, krylov=False, max_norm=False,
                  allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
         L = _lib.load()
         self.bc = bc_mask(bc)

@@ -209,9 +209,15 @@ def test_mixed_inner_cycles(cuda_device, inner):
 def test_mixed_tma_and_plain_sweeps_agree(cuda_device):
     d = inputs.stellar(256 // 4 * 2, 18)   # 128^3: the finest FP32 level uses fused sweeps
     a, sa = _solve(d["beta"], d["f"], d["dx"], cuda_device, "mixed", smoother="fused", tma=True)
-    b, sb = _solve(d["beta"], d["f"], d["dx"], cuda_device, "mixed", smoother="fused")
+    b, sb = _solve(d["beta"], d["f"], d["dx"], cuda_device, "mixed", smoother="fused", tma=False)
     assert sa["status"] == sb["status"] == "ok"
     assert np.array_equal(a, b) and sa["hist"] == sb["hist"]
+    # the TMA-fed sweep is the default where it fits; FP64 levels use passes
+    for tma, want in ((None, "fused_tma"), (True, "fused_tma"), (False, "fused")):
+        with Solver(d["f"].shape, d["dx"], precision="mixed", device=cuda_device, tma=tma) as s:
+            assert s.smoother_kind(0) == want
+    with Solver(d["f"].shape, d["dx"], device=cuda_device) as s:
+        assert s.smoother_kind(0) == "passes"
 
 
 def test_deterministic_run_to_run(cuda_device):
