@@ -411,7 +411,9 @@ void mg_slab_destroy(mg_slab *sl);
  * With profiling on, the solver records CUDA events around each stage class
  * below (as event nodes inside the captured V-cycle graph, so the times are
  * those of the real solve) and accumulates the device time between them.
- * `kernels` counts every kernel launched by the context (graph nodes count
+ * Back-to-back launches of one class (the ν sweeps or the 2ν passes of a
+ * smoothing step) share one pair of events, and `launches` counts each of
+ * them, so ms / launches is a launch's average time.  `kernels` counts every kernel launched by the context (graph nodes count
  * once per replay).  Profiling takes effect at the next solve. */
 enum {
     MG_PROF_SWEEP = 0,     /* finest level: fused red+black sweeps */

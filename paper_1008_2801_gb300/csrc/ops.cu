@@ -214,8 +214,8 @@ int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const
     cudaStream_t st = (cudaStream_t)stream;
     Box<float> B = level_box<float>(n, wx, wy, wz, nullptr, f, phi_in, phi_out);
     B.zc = zc > 0 ? zc : kSweepZ;
-    std::vector<char> host(sweep_maps_size() + 64);
-    SweepMaps *m = reinterpret_cast<SweepMaps *>(round_up((long long)(uintptr_t)host.data(), 64));
+    std::vector<char> host(sweep_maps_size() + 128);   // tensor maps are 128-byte aligned
+    SweepMaps *m = reinterpret_cast<SweepMaps *>(round_up((long long)(uintptr_t)host.data(), 128));
     if (!sweep_tma_fits(n[0], n[1]))
         return set_error(MG_ERR_UNSUPPORTED, "level too small for the TMA sweep (nx >= 64, ny >= 11)");
     if (!encode_sweep_maps(m, n[0], n[1], n[2], phi_in, phi_out, f, wx, wy, wz))

@@ -228,9 +228,9 @@ static Box<T> make_box(const Solver *s, const Hier<T> &H, int b, int l)
 // after upload.
 struct DescBlob {
     std::vector<char> bytes;
-    size_t put(const void *p, size_t n)
+    size_t put(const void *p, size_t n, int align = 64)
     {
-        size_t o = (size_t)round_up((long long)bytes.size(), 64);
+        size_t o = (size_t)round_up((long long)bytes.size(), align);
         bytes.resize(o + n);
         if (n) memcpy(bytes.data() + o, p, n);
         return o;
@@ -329,8 +329,8 @@ static bool plan_maps(const std::vector<Box<T>> &set, DescBlob &blob, size_t *of
     for (const Box<T> &B : set)
         if (!sweep_tma_fits(B.nx, B.ny)) return false;
     const size_t one = sweep_maps_size();
-    std::vector<char> bytes(one * set.size() + 64);
-    char *base = reinterpret_cast<char *>(round_up((long long)(uintptr_t)bytes.data(), 64));
+    std::vector<char> bytes(one * set.size() + 128);   // tensor maps are 128-byte aligned
+    char *base = reinterpret_cast<char *>(round_up((long long)(uintptr_t)bytes.data(), 128));
     for (size_t i = 0; i < set.size(); ++i) {
         const Box<T> &B = set[i];
         const long long Q = B.Q;
@@ -339,7 +339,7 @@ static bool plan_maps(const std::vector<Box<T>> &set, DescBlob &blob, size_t *of
                                lb(B.phi), lb(B.phi2), lb(B.f), lb(B.wx), lb(B.wy), lb(B.wz)))
             return false;
     }
-    *off = blob.put(base, one * set.size());
+    *off = blob.put(base, one * set.size(), 128);
     return true;
 }
 
@@ -1204,11 +1204,12 @@ static cudaError_t record(Solver *s, cudaEvent_t ev, cudaStream_t st)
                         : cudaEventRecord(ev, st);
 }
 
-// Open a timed stretch of stage class `kind`; returns its slot or -1.
-static int prof_begin(Solver *s, int kind, cudaStream_t st)
+// Open a timed stretch of stage class `kind` holding `launches` launches of
+// that class back to back; returns its slot or -1.
+static int prof_begin(Solver *s, int kind, cudaStream_t st, int launches = 1)
 {
     if (!s->prof || !s->rec) return -1;
-    ProfSlot sl{kind, take_event(s), take_event(s)};
+    ProfSlot sl{kind, take_event(s), take_event(s), launches};
     if (record(s, sl.b, st) != cudaSuccess) return -1;
     s->rec->push_back(sl);
     return (int)s->rec->size() - 1;
@@ -1228,7 +1229,7 @@ static void prof_collect(Solver *s)
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, sl.b, sl.e) == cudaSuccess) {
                 s->prof_ms[sl.kind] += ms;
-                s->prof_n[sl.kind] += 1;
+                s->prof_n[sl.kind] += sl.launches;
             }
         }
     };
@@ -1307,25 +1308,28 @@ static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool
                           const SweepMaps *maps, cudaStream_t st, int lvl = 0,
                           bool reverse = false)
 {
+    // one timed stretch per group of back-to-back launches, so that the
+    // event records between launches do not count in each launch's time
     cudaError_t e = cudaSuccess;
     int left = nu;
-    if (fused && !reverse) {
+    if (fused && !reverse && left >= 2) {
+        const int sl = fine ? prof_begin(s, MG_PROF_SWEEP, st, left / 2 * 2) : -1;
         for (; left >= 2; left -= 2) {
-            for (int src = 0; src < 2; ++src) {
-                int sl = fine ? prof_begin(s, MG_PROF_SWEEP, st) : -1;
+            for (int src = 0; src < 2; ++src)
                 if ((e = sweep_launch(s, S, maps, src, st)) != cudaSuccess) return e;
-                prof_end(s, sl, st);
+        }
+        prof_end(s, sl, st);
+    }
+    if (left > 0) {
+        const int sl = fine ? prof_begin(s, MG_PROF_PASS, st, 2 * left) : -1;
+        for (; left > 0; --left) {
+            for (int color = 0; color < 2; ++color) {
+                if ((e = exch(s, S, lvl, st)) != cudaSuccess) return e;
+                if ((e = pass_launch(s, S, reverse ? 1 - color : color, st)) != cudaSuccess)
+                    return e;
             }
         }
-    }
-    for (; left > 0; --left) {
-        for (int color = 0; color < 2; ++color) {
-            int sl = fine ? prof_begin(s, MG_PROF_PASS, st) : -1;
-            if ((e = exch(s, S, lvl, st)) != cudaSuccess) return e;
-            if ((e = pass_launch(s, S, reverse ? 1 - color : color, st)) != cudaSuccess)
-                return e;
-            prof_end(s, sl, st);
-        }
+        prof_end(s, sl, st);
     }
     return e;
 }

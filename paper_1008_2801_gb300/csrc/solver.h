@@ -47,6 +47,7 @@ struct Hier {
 struct ProfSlot {
     int kind;
     cudaEvent_t b, e;
+    int launches;   // launches of the stage class the stretch holds
 };
 
 struct Solver {

@@ -8,7 +8,7 @@
 // split over warps:
 //   - warp 0, the producer: one thread issues, per plane, five tiled bulk
 //     tensor copies (phi with a 2-cell halo, f and the three face-weight
-//     arrays with a 1-cell halo, 15.3 KB) into a 4-stage shared-memory ring,
+//     arrays with a 1-cell halo, 15.5 KB) into a 6-stage shared-memory ring,
 //     each stage guarded by a "full" mbarrier (the bytes landed) and an
 //     "empty" one (every consumer warp has read it);
 //   - warps 1..11, the consumers (8 row warps, 2 ring-row warps, 1
@@ -17,12 +17,15 @@
 //     release a plane's stage when they have read it.
 // Every operand address is a per-thread offset fixed at start plus a
 // compile-time stage and region constant: the plane loop is unrolled by the
-// four stages, so a step's stage slots, ring slot and colour parity are
-// constants and the consumers issue few instructions per cell.  56
-// registers and 71 KB of shared memory keep 3 CTAs (36 warps) per SM; the
-// copies of the next planes are in flight while a plane is computed, so
-// DRAM latency stays off the critical path (measured at 512^3: 664 us per
-// sweep, 72% of HBM, against 798 us for the plain-load sweep).
+// number of stages, so a step's stage slots, ring slot and colour parity are
+// constants and the consumers issue few instructions per cell.  A step holds
+// three stages (planes k-1, k, k+1), so the other three are copies in
+// flight: 106 KB of shared memory and 71 registers give 2 CTAs (24 warps)
+// and six planes in flight per SM.  Measured at 512^3 (one launch, CUDA
+// events): 636 us per sweep, 75% of HBM, against 677 us with 4 stages and 3
+// CTAs per SM (one plane in flight per CTA), 980 us with 8 or 12 stages and
+// one CTA per SM (too few warps to hide the update chain) and 798 us for
+// the plain-load sweep.
 // Waits are bounded: a wait that gives up sets the error word and the
 // threads go on (no consumer may leave the loop while the others meet at
 // the named barrier); the producer stops issuing, and before it exits it
@@ -46,8 +49,6 @@ constexpr int kTileW = 72;                 // x0 - 4 .. x0 + 67
 constexpr int kSrcRows = kSweepTY + 4;     // y0 - 2 .. y0 + 9
 constexpr int kOpRows = kSweepTY + 2;      // y0 - 1 .. y0 + 8
 constexpr int kWyRows = kSweepTY + 3;      // y0 - 1 .. y0 + 9 (faces)
-constexpr int kStages = 4;                 // the plane loop is unrolled by this
-static_assert(kStages == 4, "the consumers' step unroll assumes 4 stages");
 constexpr int kConsumers = kSweepTY + 3;   // row warps, 2 ring-row warps, 1 ring-column warp
 constexpr int kTmaThreads = 32 * (kConsumers + 1);
 
@@ -63,8 +64,18 @@ constexpr int kWzOff = kWyOff + pad128(kWyBytes);
 constexpr int kStageBytes = kWzOff + pad128(kOpBytes);
 constexpr unsigned kTxBytes = kSrcBytes + 3 * kOpBytes + kWyBytes;  // bytes landing per stage
 constexpr int kRedSW = 2 * kTX + 2, kRedPlane = (kSweepTY + 2) * kRedSW;   // red ring, floats
-constexpr int kRedBytes = 4 * kRedPlane * 4;
-constexpr int kSmemBytes = kStages * kStageBytes + pad128(kRedBytes) + 128;
+
+// NS stages in the ring; the plane loop is unrolled by NS, so that every
+// stage and red-ring slot is a compile-time constant.  The red ring needs at
+// least 4 slots (planes k, k-1 and k-2 are read while the next step writes
+// the fourth) and a slot count dividing the unroll.
+__host__ __device__ constexpr int red_slots(int ns) { return ns % 4 == 0 ? 4 : ns; }
+constexpr int smem_bytes(int ns)
+{
+    return ns * kStageBytes + pad128(red_slots(ns) * kRedPlane * 4) + 128;
+}
+// the configuration the library launches: 6 stages, 2 CTAs (24 warps) per SM
+constexpr int kStages = 6, kMinCtas = 2;
 
 constexpr long long kWaitLimit = 1ll << 22;  // default try_wait polls before giving up
 
@@ -134,8 +145,9 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map)
 
 }  // namespace
 
-// Tensor maps of one box at one level: phi, phi2, f, wx, wy, wz.
-struct alignas(64) SweepMaps {
+// Tensor maps of one box at one level: phi, phi2, f, wx, wy, wz (each
+// 128-byte aligned, as CUtensorMap is).
+struct SweepMaps {
     CUtensorMap m[6];
 };
 
@@ -156,20 +168,32 @@ __device__ __forceinline__ float red_update(float sw, float se, float ss, float 
     return s * __frcp_rn(((wxa + wxb) + (wya + wyb)) + (wza + wzb));
 }
 
-__global__ void __launch_bounds__(kTmaThreads, 3)
+// step(kb, J) for J = I .. U-1 while kb + J <= z1 (step 0 always runs).
+template <int I, int U, class F>
+__device__ __forceinline__ void unroll_steps(F &step, int kb, int z1)
+{
+    if constexpr (I < U) {
+        if (I == 0 || kb + I <= z1) step(kb, std::integral_constant<int, I>{});
+        unroll_steps<I + 1, U>(step, kb, z1);
+    }
+}
+
+template <int NS, int MINB>
+__global__ void __launch_bounds__(kTmaThreads, MINB)
     k_rbgs_sweep_tma(BoxSet<float> S, const SweepMaps *__restrict__ maps,
                      const int *__restrict__ active, int src_is_phi2, int *__restrict__ err,
                      long long polls)
 {
     constexpr int STG = kStageBytes / 4;   // stage stride, floats
+    constexpr int NR = red_slots(NS);
     constexpr int PHI = kSrcOff / 4, FF = kFOff / 4, WX = kWxOff / 4, WY = kWyOff / 4,
                   WZ = kWzOff / 4, TW = kTileW, SW = kRedSW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *const sm = reinterpret_cast<float *>(smem);
-    float *const red = sm + kStages * STG;
-    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+    float *const red = sm + NS * STG;
+    __shared__ __align__(8) unsigned long long full[NS], empty[NS];
 
     const int t = blockIdx.x;
     const int *ts = S.tstart[TK_SWEEP];
@@ -195,7 +219,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
     const int pfirst = z0 - 2, plast = z1 + 1;   // planes this CTA reads
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
             mbar_init(smem_addr(&empty[s]), kConsumers);
         }
@@ -204,16 +228,16 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
     __syncthreads();
 
     if (warp == 0) {
-        // producer: plane p goes to stage (p - pfirst) % 4; from the fifth
-        // plane on it waits until the consumers have released the stage
+        // producer: plane p goes to stage (p - pfirst) % NS; from plane
+        // pfirst + NS on it waits until the consumers have released the stage
         if (lane == 0) {
             for (int i = 0; i < 6; ++i) tensormap_acquire(&M.m[i]);
             const CUtensorMap *msrc = &M.m[src_is_phi2 ? 1 : 0];
             int last = pfirst - 1;
             for (int p = pfirst; p <= plast; ++p) {
-                const int i = p - pfirst, s = i & (kStages - 1);
-                if (i >= kStages &&
-                    !mbar_wait(smem_addr(&empty[s]), (unsigned)(((i / kStages) - 1) & 1), polls)) {
+                const int i = p - pfirst, s = i % NS;
+                if (i >= NS &&
+                    !mbar_wait(smem_addr(&empty[s]), (unsigned)(((i / NS) - 1) & 1), polls)) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -230,9 +254,9 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
             }
             // every copy issued has landed before this thread exits (the
             // earlier planes' stages were waited on before their reuse)
-            for (int p = max(pfirst, last - kStages + 1); p <= last; ++p)
-                if (!mbar_wait(smem_addr(&full[(p - pfirst) & (kStages - 1)]),
-                               (unsigned)(((p - pfirst) / kStages) & 1), kWaitLimit))
+            for (int p = max(pfirst, last - NS + 1); p <= last; ++p)
+                if (!mbar_wait(smem_addr(&full[(p - pfirst) % NS]),
+                               (unsigned)(((p - pfirst) / NS) & 1), kWaitLimit))
                     atomicExch(err, 1);
         }
         return;
@@ -285,10 +309,10 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
     auto step = [&](int kb, auto J) {
         constexpr int j = decltype(J)::value;
         // plane k = kb + j: stages of planes k-1, k, k+1, ring slots of k, k-1, k-2
-        constexpr int sM = j & 3, s0 = (j + 1) & 3, sP = (j + 2) & 3;
-        constexpr int r0 = j & 3, rm = (j + 3) & 3, rmm = (j + 2) & 3;
+        constexpr int sM = j % NS, s0 = (j + 1) % NS, sP = (j + 2) % NS;
+        constexpr int r0 = j % NR, rm = (j + NR - 1) % NR, rmm = (j + NR - 2) % NR;
         const int k = kb + j;
-        if (!mbar_wait(smem_addr(&full[sP]), (unsigned)(((k + 1 - pfirst) / kStages) & 1),
+        if (!mbar_wait(smem_addr(&full[sP]), (unsigned)(((k + 1 - pfirst) / NS) & 1),
                        polls) &&
             lane == 0)
             atomicExch(err, 1);
@@ -347,12 +371,8 @@ __global__ void __launch_bounds__(kTmaThreads, 3)
     if (!(mbar_wait(smem_addr(&full[0]), 0u, polls) && mbar_wait(smem_addr(&full[1]), 0u, polls)) &&
         lane == 0)
         atomicExch(err, 1);
-    for (int kb = z0 - 1; kb <= z1; kb += kStages, gdst += kStages * Q) {
-        step(kb, std::integral_constant<int, 0>{});
-        if (kb + 1 <= z1) step(kb, std::integral_constant<int, 1>{});
-        if (kb + 2 <= z1) step(kb, std::integral_constant<int, 2>{});
-        if (kb + 3 <= z1) step(kb, std::integral_constant<int, 3>{});
-    }
+    for (int kb = z0 - 1; kb <= z1; kb += NS, gdst += NS * Q)
+        unroll_steps<0, NS>(step, kb, z1);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -409,9 +429,10 @@ bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_
 size_t sweep_maps_size() { return sizeof(SweepMaps); }
 
 // The ring's dynamic shared memory, and the largest shared-memory carveout so
-// that three CTAs fit on an SM.  Function attributes are per device: they
+// that two CTAs fit on an SM.  Function attributes are per device: they
 // are set once on each device, the first time a launch or an occupancy
 // query runs with that device current.
+template <int NS, int MINB>
 static void set_smem_attributes()
 {
     constexpr int kMaxDevices = 64;
@@ -424,9 +445,10 @@ static void set_smem_attributes()
     }
     std::lock_guard<std::mutex> lk(mu);
     if (dev >= 0 && done[dev]) return;
-    cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSmemBytes);
-    cudaFuncSetAttribute(k_rbgs_sweep_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_rbgs_sweep_tma<NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_bytes(NS));
+    cudaFuncSetAttribute(k_rbgs_sweep_tma<NS, MINB>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     if (dev >= 0) done[dev] = true;
 }
@@ -437,9 +459,10 @@ bool sweep_tma_fits(int nx, int ny) { return pitch_row(nx) >= kTileW && ny + 1 >
 int sweep_tma_ctas_per_sm()
 {
     int n = 0;
-    set_smem_attributes();
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep_tma, kTmaThreads,
-                                                      kSmemBytes) != cudaSuccess) {
+    set_smem_attributes<kStages, kMinCtas>();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep_tma<kStages, kMinCtas>,
+                                                      kTmaThreads,
+                                                      smem_bytes(kStages)) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -455,9 +478,10 @@ cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps,
                                   int src_is_phi2, int *err, cudaStream_t st, long long wait_polls)
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
-    set_smem_attributes();
-    k_rbgs_sweep_tma<<<S.ntiles[TK_SWEEP], kTmaThreads, kSmemBytes, st>>>(
-        S, maps, active, src_is_phi2, err, wait_polls);
+    set_smem_attributes<kStages, kMinCtas>();
+    k_rbgs_sweep_tma<kStages, kMinCtas>
+        <<<S.ntiles[TK_SWEEP], kTmaThreads, smem_bytes(kStages), st>>>(S, maps, active,
+                                                                      src_is_phi2, err, wait_polls);
     return cudaGetLastError();
 }
 
