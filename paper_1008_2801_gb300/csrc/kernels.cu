@@ -129,6 +129,60 @@ struct Vec2<double> { typedef double2 type; };
 template <>
 struct Vec2<float> { typedef float2 type; };
 
+// FP64 <-> FP32 conversions by integer moves of the IEEE 754 fields
+// (binary64: sign, 11-bit exponent biased by 1023, 52-bit fraction;
+// binary32: sign, 8-bit exponent biased by 127, 23-bit fraction).  GB300
+// executes the conversion instructions on its narrow FP64 pipe, where one
+// conversion costs as much as an FMA; these use the integer pipe.
+
+// exact widening of a float in FP32's normal range (exponent field 1..254):
+// exponent + (1023 - 127), the fraction's top 20 bits in the high word, its
+// low 3 bits at the top of the low word
+__device__ __forceinline__ double normal_f32_to_f64(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    return __hiloint2double((int)((b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20))),
+                            (int)(b << 29));
+}
+
+// the float nearest to x, ties to even (IEEE round-to-nearest)
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned h = hi & 0x7fffffffu;
+    // biased exponent 897..1150: FP32 exponent 1..254 (a round-up out of 254
+    // carries into the exponent and gives infinity, as the rounding does)
+    if (h - (897u << 20) >= (254u << 20)) return __double2float_rn(x);
+    unsigned m = ((h - (896u << 20)) << 3) | (lo >> 29);   // truncated to 23 fraction bits
+    const unsigned rest = lo & 0x1fffffffu;                 // the 29 bits dropped
+    m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(m | (hi & 0x80000000u));
+}
+
+// 1/d in FP64 without an FP64 division, whose iterations occupy GB300's
+// narrow FP64 pipe: Newton-Raphson for the reciprocal (Muller et al.,
+// Handbook of Floating-Point Arithmetic, on iterations for 1/d) from an FP32
+// seed.  The seed: d's fraction truncated to 23 bits (relative error below
+// 2^-23) and its FP32 reciprocal by the approximate instruction (at most one
+// FP32 ulp), widened exactly, both by integer moves; then d y0 = 1 - e with
+// |e| < 2^-21.9, and one cubic step y = y0 (1 + e + e^2) = (1 - e^3) / d,
+// e computed by a fused multiply-add, is within 2^-65 of 1/d before its one
+// rounding, hence within one ulp (and nearly always the correctly rounded
+// value).  A d outside 2^-125 <= |d| < 2^126 (so that the seed and its
+// reciprocal are normal FP32 numbers; d = 0, inf, NaN) takes the division.
+__device__ __forceinline__ double rcp64(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned h = hi & 0x7fffffffu;
+    if ((h >> 20) - 898u > 250u) return 1.0 / d;   // FP32 exponent of d outside 2..252
+    const float f = __uint_as_float((((h - (896u << 20)) << 3) | (lo >> 29)) | (hi & 0x80000000u));
+    float s;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(f));
+    const double y = normal_f32_to_f64(s);   // s is normal: 2^-126 < |1/f| <= 2^125
+    const double e = fma(-d, y, 1.0);
+    return fma(fma(e, e, e), y, y);
+}
+
 // ---------------------------------------------- single-colour GS pass ----
 
 template <class T>
@@ -269,24 +323,6 @@ template <class T>
 struct SweepRed { T sw, se, ss, sn, sd, su, wxa, wxb, wya, wyb, wza, wzb, f; };
 template <class T>
 struct SweepBlack { T wxa, wxb, wya, wyb, wza, wzb, f; };
-
-// 1/d in FP64 without an FP64 division, whose iterations occupy GB300's
-// narrow FP64 pipe: Newton-Raphson for the reciprocal (Muller et al.,
-// Handbook of Floating-Point Arithmetic, on iterations for 1/d) from an FP32
-// seed.  With y0 = the FP32 reciprocal of d rounded to FP32, d y0 = 1 - e
-// with |e| < 2^-22; one cubic step y = y0 (1 + e + e^2) = (1 - e^3) / d,
-// e computed by a fused multiply-add, is within 2^-66 of 1/d before its one
-// rounding, hence within one ulp (and nearly always the correctly rounded
-// value).  A d whose FP32 reciprocal is not a normal finite number (d = 0,
-// |d| beyond FP32's normal range, NaN) takes the division.
-__device__ __forceinline__ double rcp64(double d)
-{
-    const float s = __frcp_rn(__double2float_rn(d));
-    if (!(fabsf(s) >= 1.17549435e-38f && fabsf(s) <= 3.40282347e38f)) return 1.0 / d;
-    const double y = (double)s;
-    const double e = fma(-d, y, 1.0);
-    return fma(fma(e, e, e), y, y);
-}
 
 __device__ __forceinline__ float rcp_rn(float d) { return __frcp_rn(d); }
 __device__ __forceinline__ double rcp_rn(double d) { return rcp64(d); }
@@ -1124,11 +1160,12 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 // every box of a level in one launch (the solver).
 
 // weight of a face between cells with coefficients a and b: the harmonic mean
-// 2 a b / (a + b) times 1/h^2 (c2 = 2 / h^2), the quotient taken through
+// 2 a b / (a + b) times 1/h^2, given cb = (2 / h^2) b (the upper cell's
+// factor, shared by the three faces below it), the quotient taken through
 // rcp64 (within a few ulp of the correctly rounded quotient)
-__device__ __forceinline__ double harmonic_w(double a, double b, double c2)
+__device__ __forceinline__ double harmonic_w(double a, double b, double cb)
 {
-    return (c2 * a) * b * rcp64(a + b);
+    return (a * cb) * rcp64(a + b);
 }
 
 // Wall w (0..5 = x-, x+, y-, y+, z-, z+) is Neumann when bit w of the mask is
@@ -1154,27 +1191,30 @@ __device__ __forceinline__ void face_weights_at(int nx, int ny, int nz, int P, l
 {
     auto bc = [&](int a, int bb, int c) { return beta[((long long)c * ny + bb) * nx + a]; };
     const long long q = (long long)k * Q + (long long)j * P + i;
-    const double c2 = 2.0 * inv_h2;
+    // cell (i, j, k) is the upper cell of all three faces at this position
+    // (every inner face lies below a cell of the box)
+    const double b = (i < nx && j < ny && k < nz) ? bc(i, j, k) : 0.0;
+    const double cb = (2.0 * inv_h2) * b;
     if (j < ny && k < nz) {
         const double v = (i == 0) ? wall_beta(bcm, 0, bc(0, j, k)) * inv_h2
                        : (i == nx) ? wall_beta(bcm, 1, bc(nx - 1, j, k)) * inv_h2
-                                   : harmonic_w(bc(i - 1, j, k), bc(i, j, k), c2);
+                                   : harmonic_w(bc(i - 1, j, k), b, cb);
         wx[q] = v;
-        if (W32) wx32[q] = (float)v;
+        if (W32) wx32[q] = f64_to_f32_rn(v);
     }
     if (i < nx && k < nz) {
         const double v = (j == 0) ? wall_beta(bcm, 2, bc(i, 0, k)) * inv_h2
                        : (j == ny) ? wall_beta(bcm, 3, bc(i, ny - 1, k)) * inv_h2
-                                   : harmonic_w(bc(i, j - 1, k), bc(i, j, k), c2);
+                                   : harmonic_w(bc(i, j - 1, k), b, cb);
         wy[q] = v;
-        if (W32) wy32[q] = (float)v;
+        if (W32) wy32[q] = f64_to_f32_rn(v);
     }
     if (i < nx && j < ny) {
         const double v = (k == 0) ? wall_beta(bcm, 4, bc(i, j, 0)) * inv_h2
                        : (k == nz) ? wall_beta(bcm, 5, bc(i, j, nz - 1)) * inv_h2
-                                   : harmonic_w(bc(i, j, k - 1), bc(i, j, k), c2);
+                                   : harmonic_w(bc(i, j, k - 1), b, cb);
         wz[q] = v;
-        if (W32) wz32[q] = (float)v;
+        if (W32) wz32[q] = f64_to_f32_rn(v);
     }
 }
 
@@ -1189,17 +1229,19 @@ __device__ __forceinline__ void face_weights_level_at(int nx, int ny, int nz, in
                                                       double *wy, double *wz, int i, int j, int k)
 {
     const long long q = (long long)k * Q + (long long)j * P + i;
-    const double c2 = 2.0 * inv_h2;
-    // a below / left of the face, b above / right; lo/hi: the walls on either
-    // side of axis d (their Dirichlet or Neumann condition from bcm)
-    auto face = [&](double a, double b, int d) {
+    // a below / left of the face, b = bl[q] above / right (the same cell for
+    // all three faces); lo/hi: the walls on either side of axis d (their
+    // Dirichlet or Neumann condition from bcm)
+    const double b = bl[q];
+    const double cb = (2.0 * inv_h2) * b;
+    auto face = [&](double a, int d) {
         if (a < 0.0) return wall_beta(bcm, 2 * d, b) * inv_h2;
         if (b < 0.0) return wall_beta(bcm, 2 * d + 1, a) * inv_h2;
-        return harmonic_w(a, b, c2);
+        return harmonic_w(a, b, cb);
     };
-    if (j < ny && k < nz) wx[q] = face(bl[q - 1], bl[q], 0);
-    if (i < nx && k < nz) wy[q] = face(bl[q - P], bl[q], 1);
-    if (i < nx && j < ny) wz[q] = face(bl[q - Q], bl[q], 2);
+    if (j < ny && k < nz) wx[q] = face(bl[q - 1], 0);
+    if (i < nx && k < nz) wy[q] = face(bl[q - P], 1);
+    if (i < nx && j < ny) wz[q] = face(bl[q - Q], 2);
 }
 
 // Coarse position (I, J, K) in [0, cx] x [0, cy] x [0, cz]; coarse face
@@ -1237,7 +1279,7 @@ __device__ __forceinline__ void inv_diag_at(int P, long long Q, const double *__
     if (Dout) Dout[cf] = D;
     // mixed precision's finest level (no FP64 1/D): the FP32 1/D the
     // rounding step would write
-    if (W32) invD32[c] = 1.0f / (float)D;
+    if (W32) invD32[c] = 1.0f / f64_to_f32_rn(D);
 }
 
 // Every stored weight (and the inverse diagonal) at position (i, j, k) in
@@ -1254,12 +1296,12 @@ __device__ __forceinline__ void round_at(int nx, int ny, int nz, int P, long lon
                                          const double *__restrict__ D = nullptr)
 {
     const long long q = (long long)k * Q + (long long)j * P + i;
-    if (j < ny && k < nz) wx32[q] = (float)wx[q];
-    if (i < nx && k < nz) wy32[q] = (float)wy[q];
-    if (i < nx && j < ny) wz32[q] = (float)wz[q];
+    if (j < ny && k < nz) wx32[q] = f64_to_f32_rn(wx[q]);
+    if (i < nx && k < nz) wy32[q] = f64_to_f32_rn(wy[q]);
+    if (i < nx && j < ny) wz32[q] = f64_to_f32_rn(wz[q]);
     if (i < nx && j < ny && k < nz) {
         const long long cf = rb ? split_at(i, j, k, par, P, Q) : q;
-        invD32[q] = invD ? (float)invD[cf] : 1.0f / (float)D[cf];
+        invD32[q] = invD ? f64_to_f32_rn(invD[cf]) : 1.0f / f64_to_f32_rn(D[cf]);
     }
 }
 

@@ -50,19 +50,24 @@ def test_stored_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     t512, note = bench.stored_traffic("rbgs_pass_f64", 8 * n256)
     if "scaled" in note:
         assert abs(t512 - 8 * t256) <= 8
-    assert bench.stored_traffic("rbgs_sweep_f32", n256)[0] is not None
+    assert bench.stored_traffic("rbgs_sweep_tma_f32", n256)[0] is not None
     src = tmp_path / "paper_1008_2801_gb300" / "csrc"
     src.mkdir(parents=True)
-    for f in ("kernels.cu", "common.cuh"):
+    for f in ("kernels.cu", "sweep_tma.cu", "common.cuh"):
         shutil.copy(os.path.join(ROOT, "paper_1008_2801_gb300", "csrc", f), src / f)
     shutil.copytree(os.path.join(ROOT, "profiles"), tmp_path / "profiles")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is not None
+    assert bench.stored_traffic("rbgs_sweep_tma_f32", n256)[0] is not None
     text = (src / "kernels.cu").read_text()
-    a, b = bench.TRAFFIC_REGIONS["rbgs_sweep_f32"]
+    a, b = bench.TRAFFIC_REGIONS["rbgs_pass_f64"]
     i = text.index(a) + len(a)
     (src / "kernels.cu").write_text(text[:i] + "\n// edited\n" + text[i:])
-    assert bench.stored_traffic("rbgs_sweep_f32", n256)[0] is None      # its region changed
-    assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is not None   # the other did not
+    assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is None           # its region changed
+    assert bench.stored_traffic("rbgs_sweep_tma_f32", n256)[0] is not None  # the other did not
+    (src / "kernels.cu").write_text(text)
+    (src / "sweep_tma.cu").write_text((src / "sweep_tma.cu").read_text() + "\n")
+    assert bench.stored_traffic("rbgs_sweep_tma_f32", n256)[0] is None      # its file changed
+    assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is not None
     (src / "common.cuh").write_text((src / "common.cuh").read_text() + "\n")
     assert bench.stored_traffic("rbgs_pass_f64", n256)[0] is None       # the shared header changed

@@ -93,6 +93,69 @@ def test_inverse_diagonal_over_the_fp64_range(cuda_device):
     np.testing.assert_array_equal(got[exact], want[exact])
 
 
+def _rounding_cases(m, rng):
+    """Doubles that exercise float rounding: random magnitudes 1e-50..1e50
+    (FP32 subnormals, zeros and overflow among them), exact midpoints between
+    neighbouring floats and the doubles just either side of them, the ends
+    of FP32's normal range, and signed zeros."""
+    v = np.sign(rng.uniform(-1, 1, m)) * 10.0 ** rng.uniform(-50, 50, m)
+    f = (rng.uniform(1, 2, m) * 2.0 ** rng.integers(-120, 120, m)).astype(np.float32)
+    f = f.astype(np.float64)
+    half = np.spacing(f.astype(np.float32)).astype(np.float64) / 2
+    k = m // 8
+    v[:k] = f[:k] + half[:k]                                   # ties: to the even neighbour
+    v[k:2 * k] = np.nextafter(f[k:2 * k] + half[k:2 * k], 0)   # just below a midpoint
+    v[2 * k:3 * k] = np.nextafter(f[2 * k:3 * k] + half[2 * k:3 * k], np.inf)  # just above
+    v[3 * k:4 * k] *= -1
+    fmax = float(np.finfo(np.float32).max)
+    tiny = float(np.finfo(np.float32).tiny)
+    v[4 * k:4 * k + 12] = [fmax, fmax + 2.0 ** 103, np.nextafter(fmax + 2.0 ** 103, 0),
+                           fmax + 2.0 ** 104, tiny, np.nextafter(tiny, 0),
+                           tiny * (1 - 2.0 ** -25), -tiny, 0.0, -0.0, 1.0, -3.0]
+    return v
+
+
+def test_fp32_rounding_is_round_to_nearest_even(cuda_device):
+    # the FP32 copies of the weights and of 1/D (mg_op_round_f32) are the
+    # IEEE round-to-nearest-even images of the FP64 values, bit for bit
+    # (numpy's float64 -> float32 conversion is that rounding)
+    m = 4096
+    shape = (1, m, 1)
+    rng = np.random.default_rng(21)
+    vals = {"x": _rounding_cases(2 * m, rng).reshape(1, m, 2),
+            "y": _rounding_cases(m + 1, rng).reshape(1, m + 1, 1),
+            "z": _rounding_cases(2 * m, rng).reshape(2, m, 1),
+            "cell": _rounding_cases(m, rng).reshape(1, m, 1)}
+    w = [_level(shape, vals[k], cuda_device, kind=k) for k in "xyz"]
+    invD = _level(shape, vals["cell"], cuda_device)
+    w32, inv32 = K.round_f32(w, invD, shape)
+    with np.errstate(over="ignore"):
+        for t, k in zip(list(w32) + [inv32], "xyz" + "c"):
+            kind = "cell" if k == "c" else k
+            got = K.get(t, shape, kind).cpu().numpy()
+            want = vals[kind].astype(np.float32)
+            np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_refinement_update_widens_exactly(cuda_device):
+    # x += 1 * e from x = 0 (mg_op_refine): every FP32 correction, zeros,
+    # subnormals and the ends of the range included, lands in x unchanged
+    m = 4096
+    shape = (1, m, 1)
+    rng = np.random.default_rng(22)
+    e = (np.sign(rng.uniform(-1, 1, m)) * 10.0 ** rng.uniform(-45, 38, m)).astype(np.float32)
+    fi = np.finfo(np.float32)
+    e[:8] = [0.0, -0.0, fi.tiny, fi.tiny / 8, -fi.tiny / 3, fi.max, -fi.max, 1.0]
+    dims = {"x": (1, m, 2), "y": (1, m + 1, 1), "z": (2, m, 1), "cell": (1, m, 1)}
+    zero = lambda kind: _level(shape, np.zeros(dims[kind]), cuda_device, kind=kind)
+    w = [zero(k) for k in "xyz"]
+    x = _level(shape, np.zeros((1, m, 1)), cuda_device)
+    et = _level(shape, e.reshape(1, m, 1), cuda_device, torch.float32)
+    xo, _, _ = K.refine(w, zero("cell"), zero("cell"), x, et, 1.0, 1.0, shape)
+    got = K.get(xo, shape).cpu().numpy().ravel()
+    np.testing.assert_array_equal(got, e.astype(np.float64))
+
+
 @pytest.mark.parametrize("shape", EVEN)
 def test_coarsened_weights(cuda_device, shape):
     beta, _, _, h = _case(shape, 2)
