@@ -114,8 +114,19 @@ typedef struct {
                          per box (the coarse end of the V-cycle as a single
                          launch); 0 default (4096 in FP32 V-cycles, 1024 in
                          FP64 ones, whose FP64 rate per SM is low), -1 off */
-    int inner_cycles; /* MG_MIXED: FP32 V-cycles per FP64 refinement step
-                         (0 default = 2; 1..8) */
+    int inner_cycles; /* MG_MIXED: FP32 V-cycles per FP64 refinement step.
+                         1..8: that many.  0 (default): adaptive, up to 8:
+                         the step solves A e = r32 for a scaled copy r32 of
+                         the FP64 residual r, and the finest level's
+                         restriction after pre-smoothing also gives
+                         ||r32 - A e|| of the smoothed iterate; a box leaves
+                         the step's cycles there (its e is that iterate)
+                         once the update is expected to bring ||r|| to
+                         tol ||f|| / 2, or the step has reduced ||r32 - A e||
+                         by 1e6, the most asked of FP32 arithmetic.  With
+                         nu1 = 0 or
+                         full_residual = 1 (no red-only restriction) the
+                         default is 2 fixed cycles */
     int full_residual;/* 0 (default): right after a red-black sweep the black
                          cells satisfy their equations, so the restricted
                          residual and the cycle's residual norm are formed

@@ -535,31 +535,20 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(BoxSet<T> S, const 
     restrict_tile<T, FC>(S, active, blockIdx.x);
 }
 
-// After a red-black sweep every black cell satisfies its own equation (its
-// residual is rounding-level), so right after smoothing the residual is
-// carried by the red cells alone.  This variant restricts the residual of the
-// 4 red children of each coarse cell (the black 4 count as zero): half the
-// stencil work of k_resid_restrict, the same coarse right-hand side to
-// rounding.  Valid only when the last operation on phi was a black pass.
-template <class T, bool FC>
-__device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
-                                                  const int *__restrict__ active, int t)
+// The red-children restriction of coarse cell (I, J, K); returns the sum of
+// the squared red residuals when NORM.
+template <class T, bool NORM>
+__device__ __forceinline__ T restrict_red_cell(const Box<T> &B, int I, int J, int K)
 {
-    const int *ts = S.tstart[TK_COARSE];
-    const int b = find_box(ts, S.nbox, t);
-    const Box<T> &B = S.boxes[b];
-    if (active && !active[B.box]) return;
-    const int nx = B.nx, ny = B.ny, nz = B.nz, P = B.P;
+    const int P = B.P;
     const long long Q = B.Q;
-    TilePos p = tile_pos<FC>(TK_COARSE, nx, ny, nz, t - ts[b]);
-    const int I = p.x, J = p.y, K = p.z;
-    if (I >= nx / 2 || J >= ny / 2) return;
     // red children of the 2x2x2 block at (2I, 2J, 2K): (a+b+c+par) even,
     // par the parity of the box's lower corner in the level's index space
     const long long o = (long long)(2 * K) * Q + (long long)(2 * J) * P + 2 * I;
     // colour-split f and D: a red child (i, j, k) of this block sits at
     // element I of row (j, k)'s red half
     const long long of = (long long)(2 * K) * Q + (long long)(2 * J) * P + I;
+    T r2 = T(0);
     auto red4 = [&](auto has_d, auto odd) {
         constexpr bool HD = decltype(has_d)::value, OD = decltype(odd)::value;
         const long long c0 = OD ? o + 1 : o, c1 = OD ? o + P : o + P + 1,
@@ -567,11 +556,12 @@ __device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
         const bool sp = split_on(B);
         const long long f0 = sp ? of : c0, f1 = sp ? of + P : c1, f2 = sp ? of + Q : c2,
                         f3 = sp ? of + Q + P : c3;
-        T sum = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c0, f0, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c1, f1, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c2, f2, P, Q);
-        sum += residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c3, f3, P, Q);
-        return sum;
+        const T a0 = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c0, f0, P, Q);
+        const T a1 = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c1, f1, P, Q);
+        const T a2 = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c2, f2, P, Q);
+        const T a3 = residual_at<T, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c3, f3, P, Q);
+        if (NORM) r2 = fmadd(a3, a3, fmadd(a2, a2, fmadd(a1, a1, a0 * a0)));
+        return ((a0 + a1) + a2) + a3;
     };
     const T sum = B.D ? (B.par ? red4(std::true_type{}, std::true_type{})
                                : red4(std::true_type{}, std::false_type{}))
@@ -580,14 +570,50 @@ __device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
     const long long cc = (long long)K * B.cQ + (long long)J * B.cP + I;
     B.fc[cfidx(B, I, J, K)] = sum * T(0.125);
     B.phic[cc] = T(0);
+    return r2;
 }
 
-template <class T, bool FC>
+// After a red-black sweep every black cell satisfies its own equation (its
+// residual is rounding-level), so right after smoothing the residual is
+// carried by the red cells alone.  This variant restricts the residual of the
+// 4 red children of each coarse cell (the black 4 count as zero): half the
+// stencil work of k_resid_restrict, the same coarse right-hand side to
+// rounding.  Valid only when the last operation on phi was a black pass.
+// NORM: also the tile's sum of the squared red residuals into partials[t]
+// (hence ||f - A phi||^2 of the smoothed iterate, summed per box in fixed
+// order by the caller); every thread of the CTA reaches the block sum.
+template <class T, bool FC, bool NORM = false>
+__device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
+                                                  const int *__restrict__ active, int t,
+                                                  double *__restrict__ partials = nullptr)
+{
+    const int *ts = S.tstart[TK_COARSE];
+    const int b = find_box(ts, S.nbox, t);
+    const Box<T> &B = S.boxes[b];
+    if (active && !active[B.box]) return;   // the whole CTA: its box is skipped
+    const int nx = B.nx, ny = B.ny, nz = B.nz, P = B.P;
+    const long long Q = B.Q;
+    TilePos p = tile_pos<FC>(TK_COARSE, nx, ny, nz, t - ts[b]);
+    const int I = p.x, J = p.y, K = p.z;
+    if (NORM) {
+        T r2 = T(0);
+        if (I < nx / 2 && J < ny / 2) r2 = restrict_red_cell<T, NORM>(B, I, J, K);
+        const double tot = block_sum((double)r2);
+        if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = tot;
+        __syncthreads();   // the block sum's scratch is reused by the next tile
+        return;
+    }
+    if (I >= nx / 2 || J >= ny / 2) return;
+    restrict_red_cell<T, NORM>(B, I, J, K);
+}
+
+template <class T, bool FC, bool NORM>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict_red(BoxSet<T> S,
-                                                                 const int *__restrict__ active)
+                                                                 const int *__restrict__ active,
+                                                                 double *__restrict__ partials)
 {
     pdl_wait();
-    restrict_red_tile<T, FC>(S, active, blockIdx.x);
+    restrict_red_tile<T, FC, NORM>(S, active, blockIdx.x, partials);
 }
 
 // --------------------------------------------------------- prolongation ----
@@ -1151,6 +1177,60 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
         sr[b] = v;
         sr_inv[b] = v > 0.0 ? 1.0 / v : 0.0;
     }
+}
+
+// Exit test of the inner FP32 cycles of a refinement step (mixed precision,
+// adaptive inner cycles).  The step solves A e = r32 with r32 = r_k / se
+// (||r_k|| = sr, so ||r32|| = sr / se); after its update x + se e the FP64
+// residual is se times the inner residual r32 - A e, up to FP32 rounding.
+// Per box still in the inner cycles: ||r32 - A e|| of the just smoothed
+// iterate (the red-children restriction's partial sums over the box's tiles,
+// in fixed order) against max(tol ||f|| / 2, floor_rel sr) / se: at or below
+// it the update is expected to meet tol, or the step has gained the factor
+// floor_rel, and the box leaves the inner cycles of this step (active32 = 0).
+// floor_rel: the most one step asks of FP32 arithmetic.  One CTA.
+__global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__restrict__ active32,
+                                                      const double *__restrict__ partials,
+                                                      const double *__restrict__ se,
+                                                      const double *__restrict__ sr,
+                                                      const double *__restrict__ normf,
+                                                      const double *__restrict__ tol,
+                                                      double floor_rel)
+{
+    pdl_wait();
+    __shared__ double wsum[32];
+    const int *ts = S.tstart[TK_COARSE];
+    for (int b = 0; b < S.nbox; ++b) {
+        const int id = S.boxes[b].box;
+        if (!active32[id]) continue;   // read by every thread before the barrier below
+        double v = 0.0;
+        for (int q = ts[b] + (int)threadIdx.x; q < ts[b + 1]; q += 1024) v += partials[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < 32; ++w) tot += wsum[w];
+            const double e = se[id];
+            const double target =
+                e > 0.0 ? fmax(0.5 * tol[0] * normf[id], floor_rel * sr[id]) / e : 0.0;
+            if (!(sqrt(tot) > target)) active32[id] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// Copy of the per-box flags (the inner cycles start from the step's boxes).
+__global__ void k_copy_flags(int nbox, const int *__restrict__ src, int *__restrict__ dst)
+{
+    pdl_wait();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbox) dst[b] = src[b];
+}
+
+cudaError_t launch_copy_flags(int nbox, const int *src, int *dst, cudaStream_t st)
+{
+    return pdl_launch(k_copy_flags, dim3((nbox + 255) / 256), dim3(256), 0, st, nbox, src, dst);
 }
 
 // ------------------------------------------------------------- set-up ----
@@ -2328,7 +2408,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_level_down(BoxSet<T> S, const i
         }
     if (!exchange(0)) return;
     const int nc = S.ntiles[TK_COARSE];
-    if (op.red) {
+    if (op.red && op.partials) {
+        if (op.flat) each(nc, [&](int t) { restrict_red_tile<T, true, true>(S, active, t, op.partials); });
+        else each(nc, [&](int t) { restrict_red_tile<T, false, true>(S, active, t, op.partials); });
+    } else if (op.red) {
         if (op.flat) each(nc, [&](int t) { restrict_red_tile<T, true>(S, active, t); });
         else each(nc, [&](int t) { restrict_red_tile<T, false>(S, active, t); });
     } else {
@@ -2551,14 +2634,30 @@ cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStr
 }
 
 template <class T>
-cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st)
+cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st,
+                                      double *partials)
 {
     if (S.ntiles[TK_COARSE] == 0) return cudaSuccess;
-    if (S.flat & (1 << TK_COARSE))
-        return pdl_launch(k_resid_restrict_red<T, true>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st,
-                          S, active);
-    return pdl_launch(k_resid_restrict_red<T, false>, dim3(S.ntiles[TK_COARSE]), block2d(), 0, st, S,
-                      active);
+    const dim3 g(S.ntiles[TK_COARSE]);
+    const bool flat = S.flat & (1 << TK_COARSE);
+    if (partials)
+        return flat ? pdl_launch(k_resid_restrict_red<T, true, true>, g, block2d(), 0, st, S,
+                                 active, partials)
+                    : pdl_launch(k_resid_restrict_red<T, false, true>, g, block2d(), 0, st, S,
+                                 active, partials);
+    return flat ? pdl_launch(k_resid_restrict_red<T, true, false>, g, block2d(), 0, st, S, active,
+                             partials)
+                : pdl_launch(k_resid_restrict_red<T, false, false>, g, block2d(), 0, st, S, active,
+                             partials);
+}
+
+cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
+                               const double *se, const double *sr, const double *normf,
+                               const double *tol, double floor_rel, cudaStream_t st)
+{
+    if (S.nbox == 0) return cudaSuccess;
+    return pdl_launch(k_inner_judge, dim3(1), dim3(1024), 0, st, S, active32, partials, se, sr,
+                      normf, tol, floor_rel);
 }
 
 template <class T>
@@ -2996,7 +3095,7 @@ cudaError_t launch_pcg_scalars(int nbox, const int *active, int step, const PcgS
     template cudaError_t launch_rbgs_sweep<T>(const BoxSet<T> &, const int *, int, cudaStream_t); \
     template cudaError_t launch_resid_restrict<T>(const BoxSet<T> &, const int *, cudaStream_t);  \
     template cudaError_t launch_resid_restrict_red<T>(const BoxSet<T> &, const int *,             \
-                                                      cudaStream_t);                              \
+                                                      cudaStream_t, double *);                    \
     template cudaError_t launch_prolong<T>(const BoxSet<T> &, const int *, cudaStream_t);         \
     template cudaError_t launch_residual_field<T>(const BoxSet<T> &, cudaStream_t);               \
     template cudaError_t launch_norm_partials<T>(const BoxSet<T> &, const int *, int, double *,   \

@@ -68,7 +68,14 @@ cudaError_t launch_resid_restrict(const BoxSet<T> &S, const int *active, cudaStr
 // Same, right after a red-black sweep: only the 4 red children carry a
 // residual (black cells satisfy their equations), half the stencil work.
 template <class T>
-cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st);
+cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st,
+                                      double *partials = nullptr);
+// Adaptive inner cycles (mixed precision): the exit test after a restriction
+// with partials, and the copy of the step's box flags into the inner ones.
+cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
+                               const double *se, const double *sr, const double *normf,
+                               const double *tol, double floor_rel, cudaStream_t st);
+cudaError_t launch_copy_flags(int nbox, const int *src, int *dst, cudaStream_t st);
 
 // phi += phic[parent].
 template <class T>
@@ -145,6 +152,7 @@ struct LevelOps {
     const ExchRec *rec;  // ghost exchange before every pass and the residual (nrec = 0: none)
     int nrec, chunks;    // records, and CTAs' worth of work per record
     int flat;            // the set tiles TK_COARSE flat (its flat bit)
+    double *partials;    // down, red restriction: per-tile sums of squared residuals (or null)
 };
 // Resident CTAs per SM of the persistent level kernels (occupancy query).
 template <class T>

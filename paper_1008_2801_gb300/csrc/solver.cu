@@ -94,6 +94,13 @@ static std::vector<std::array<int, 3>> level_dims(int nx, int ny, int nz)
 constexpr double kCgTol64 = 1e-12, kCgTol32 = 1e-5;
 constexpr int kCgMaxIt64 = 20000, kCgMaxIt32 = 3000;
 constexpr int kCgPartials = 4096;
+// Mixed precision with adaptive inner cycles (mg_opts.inner_cycles = 0): at
+// most kInnerMax FP32 V-cycles per refinement step, a box leaving them once
+// its update is expected to meet tol / 2, or its inner residual has dropped
+// by kInnerFloor (the most a step asks of FP32 arithmetic)
+constexpr int kInnerMax = 8;
+constexpr double kInnerFloor = 1e-6;
+constexpr int kInnerFixed = 2;   // inner cycles per step where the test is not available
 
 // ------------------------------------------------------------ building ----
 
@@ -703,6 +710,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     bump.take<double>(ntiles0);       // partials
     for (int i = 0; i < 7; ++i) bump.take<double>(nbox);
     bump.take<int>(nbox);
+    bump.take<int>(nbox);   // inner flags
     bump.take<int>(1);  // error word
     bump.take<unsigned>(1);  // grid-barrier word
     if (s->cg_bottom) bump.take<double>(2 * kCgPartials);   // CG partial sums
@@ -747,6 +755,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->sr_inv = real.take<double>(nbox);
     s->dmean = real.take<double>(nbox);
     s->active = real.take<int>(nbox);
+    s->active32 = real.take<int>(nbox);
     s->derr = real.take<int>(1);
     s->gbar = real.take<unsigned>(1);
     if (s->cg_bottom) s->cgpart = real.take<double>(2 * kCgPartials);
@@ -781,6 +790,12 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     std::vector<std::pair<int, size_t>> maps64, maps32;
     plan_hier(s, s->h64, blob, p64, &jobs64, &maps64);
     if (s->has32) plan_hier(s, s->h32, blob, p32, &jobs32, &maps32);
+    // adaptive inner cycles: the exit test reads the red-only restriction of
+    // the finest FP32 level (after a black pass: nu1 > 0, no full residual),
+    // its per-tile sums in the partials array
+    s->inner_adapt = s->has32 && !s->pcg && o.inner_cycles == 0 && o.nu1 > 0 &&
+                     !o.full_residual && !s->h32.smooth.empty() &&
+                     (size_t)s->h32.smooth[0].ntiles[TK_COARSE] <= ntiles0;
     // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
     // last (nu2 > 0, so black residuals vanish), single-colour passes on every
     // box's finest level, and the red-only residual reading
@@ -1344,6 +1359,25 @@ static int exch_chunks(int max_cells)
 // Level l of H as one persistent launch (mg_opts.persistent): going down,
 // nu pre-smoothing sweeps then the residual and restriction; coming up,
 // prolongation then nu post-smoothing sweeps (sym: black before red).
+// Inner cycles of an adaptive refinement step: the finest FP32 level's
+// restriction also sums squared residuals (into the partials array), and the
+// exit test follows it.  FP64 hierarchies never take part.
+static double *inner_partials(const Solver *s, const Hier<float> &H, int l)
+{
+    return (s->inner_norm && l == 0 && &H == &s->h32) ? s->partials : nullptr;
+}
+static double *inner_partials(const Solver *, const Hier<double> &, int) { return nullptr; }
+
+static cudaError_t inner_judge(Solver *s, const BoxSet<float> &S, cudaStream_t st)
+{
+    return launch_inner_judge(S, s->active, s->partials, s->se, s->sr, s->dnormf, s->J.tol,
+                              kInnerFloor, st);
+}
+static cudaError_t inner_judge(Solver *, const BoxSet<double> &, cudaStream_t)
+{
+    return cudaSuccess;
+}
+
 template <class T>
 static cudaError_t level_launch(Solver *s, const Hier<T> &H, int l, bool up, int nu,
                                 bool head_done, bool sym, cudaStream_t st)
@@ -1360,6 +1394,7 @@ static cudaError_t level_launch(Solver *s, const Hier<T> &H, int l, bool up, int
         op.chunks = exch_chunks(s->xmax[l]);
     }
     op.flat = (S.flat >> TK_COARSE) & 1;
+    op.partials = (!up && op.red) ? inner_partials(s, H, l) : nullptr;
     GridSync g{s->gbar, s->derr, sweep_wait_polls(s->opts.wait_limit)};
     const long long work = std::max<long long>(
         std::max(S.ntiles[TK_PAIR], S.ntiles[TK_COARSE]), (long long)op.nrec * op.chunks);
@@ -1367,6 +1402,7 @@ static cudaError_t level_launch(Solver *s, const Hier<T> &H, int l, bool up, int
     const int sl = l == 0 ? prof_begin(s, MG_PROF_LEVEL, st) : -1;
     cudaError_t e = launch_level(S, s->active, up ? 1 : 0, op, g, grid, st);
     prof_end(s, sl, st);
+    if (e == cudaSuccess && op.partials) e = inner_judge(s, S, st);
     return e;
 }
 
@@ -1418,11 +1454,13 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
             return e;
         int sl = l == 0 ? prof_begin(s, MG_PROF_RESTRICT, st) : -1;
         if ((e = exch(s, S, l, st)) != cudaSuccess) return e;
-        e = (s->opts.nu1 > 0 && !s->opts.full_residual)
-                ? launch_resid_restrict_red(S, s->active, st)
+        const bool red = s->opts.nu1 > 0 && !s->opts.full_residual;
+        double *ip = red ? inner_partials(s, H, l) : nullptr;
+        e = red ? launch_resid_restrict_red(S, s->active, st, ip)
                 : launch_resid_restrict(S, s->active, st);
         if (e != cudaSuccess) return e;
         prof_end(s, sl, st);
+        if (ip && (e = inner_judge(s, S, st)) != cudaSuccess) return e;
         if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     }
     if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
@@ -1506,15 +1544,30 @@ static cudaError_t enqueue_tail64(Solver *s, cudaStream_t st)
     return enqueue_vcycle(s, s->h64, st, true);
 }
 
-// Mixed: inner_cycles FP32 V-cycles on r32, from e = 0 (zeroed by the
-// prologue, and after that by each refinement update once it has used e).
+// Mixed: FP32 V-cycles on r32, from e = 0 (zeroed by the prologue, and after
+// that by each refinement update once it has used e).  inner_cycles > 0: that
+// many.  Adaptive (inner_cycles = 0): up to kInnerMax, run on the inner flags
+// (a copy of the step's); after each cycle's pre-smoothing on the finest level
+// the exit test clears the flag of every box whose inner residual meets its
+// target, so the rest of that cycle and the later ones skip the box, whose e
+// is then the iterate the test measured.
 static cudaError_t enqueue_step32(Solver *s, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
-    const int inner = s->opts.inner_cycles > 0 ? s->opts.inner_cycles : 2;
-    for (int i = 0; i < inner; ++i)
-        if ((e = enqueue_vcycle(s, s->h32, st)) != cudaSuccess) return e;
-    return cudaSuccess;
+    if (!s->inner_adapt) {
+        const int inner = s->opts.inner_cycles > 0 ? s->opts.inner_cycles : kInnerFixed;
+        for (int i = 0; i < inner; ++i)
+            if ((e = enqueue_vcycle(s, s->h32, st)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    if ((e = launch_copy_flags(s->nbox, s->active, s->active32, st)) != cudaSuccess) return e;
+    int *const outer = s->active;
+    s->active = s->active32;
+    s->inner_norm = true;
+    for (int i = 0; i < kInnerMax && e == cudaSuccess; ++i) e = enqueue_vcycle(s, s->h32, st);
+    s->active = outer;
+    s->inner_norm = false;
+    return e;
 }
 
 template <class F>
@@ -2032,9 +2085,12 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
         }
     } else {
         // FP64 iterative refinement around FP32 V-cycles: step k >= 1 runs
-        // inner_cycles FP32 V-cycles on r32, then x += se e, the FP64
-        // residual r_k = f - A x, r32 = r_k / sr for the next step and
-        // ||r_k|| = sr ||r32|| (step 0 ran above).
+        // FP32 V-cycles on r32 (inner_cycles of them, or adaptive), then
+        // x += se e, the FP64 residual r_k = f - A x, r32 = r_k / sr for the
+        // next step and ||r_k|| = sr ||r32|| (step 0 ran above).  The
+        // adaptive exit test reads tol from the judge block, uploaded for
+        // either loop.
+        if (s->inner_adapt && any && !device_loop) CKS(upload_judge(s, bs, tol, stream));
         if (device_loop && any) {
             CKS(upload_judge(s, bs, tol, stream));
             CKS(run_loop(s, &s->loop32, &s->loop_kernels32, enqueue_body32, stream));

@@ -79,6 +79,9 @@ struct Solver {
     double *dinv = nullptr;        // [nbox] scratch reciprocal
     double *se = nullptr, *sr = nullptr, *sr_inv = nullptr;  // mixed scales
     int *active = nullptr;         // [nbox] device flags
+    int *active32 = nullptr;       // [nbox] device flags of a refinement step's inner FP32 cycles
+    bool inner_adapt = false;      // mixed: inner cycles end per box on the inner residual
+    bool inner_norm = false;       // enqueueing inner cycles: restriction with norm + exit test
     const long long *doff = nullptr;  // [nbox + 1] device copy of off
     int *dside = nullptr;          // [nbox] device: 1 if the solution ended in phi2
     double *hnorm = nullptr;       // pinned [2 * nbox]
