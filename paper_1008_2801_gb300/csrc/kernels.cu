@@ -1220,17 +1220,57 @@ __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__re
     }
 }
 
-// Copy of the per-box flags (the inner cycles start from the step's boxes).
-__global__ void k_copy_flags(int nbox, const int *__restrict__ src, int *__restrict__ dst)
+// Start of a refinement step's inner cycles: the inner flags are a copy of
+// the step's; with a loop handle (inner cycles as a graph WHILE node) also
+// the cycle counter to 0 and the loop condition to 1.  One CTA.
+__global__ void __launch_bounds__(256) k_inner_begin(int nbox, const int *__restrict__ src,
+                                                     int *__restrict__ dst, int *__restrict__ count,
+                                                     cudaGraphConditionalHandle handle,
+                                                     int use_handle)
 {
     pdl_wait();
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nbox) dst[b] = src[b];
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) dst[b] = src[b];
+    if (threadIdx.x == 0) {
+        *count = 0;
+        if (use_handle) cudaGraphSetConditional(handle, 1u);
+    }
 }
 
-cudaError_t launch_copy_flags(int nbox, const int *src, int *dst, cudaStream_t st)
+// End of one inner cycle in the WHILE form: the loop goes on while some box
+// is still in the inner cycles and fewer than max_cycles have run (the
+// counter bounds the loop whatever the flags say); count[1] sums the cycles
+// of the whole solve.  One CTA.
+__global__ void __launch_bounds__(256) k_inner_end(int nbox, const int *__restrict__ flags,
+                                                   int *__restrict__ count, int max_cycles,
+                                                   cudaGraphConditionalHandle handle)
 {
-    return pdl_launch(k_copy_flags, dim3((nbox + 255) / 256), dim3(256), 0, st, nbox, src, dst);
+    pdl_wait();
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x)
+        if (flags[b]) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int c = count[0] + 1;
+        count[0] = c;
+        count[1] += 1;   // the solve's total, for the launch count
+        cudaGraphSetConditional(handle, (any && c < max_cycles) ? 1u : 0u);
+    }
+}
+
+cudaError_t launch_inner_begin(int nbox, const int *src, int *dst, int *count,
+                               cudaGraphConditionalHandle handle, int use_handle, cudaStream_t st)
+{
+    return pdl_launch(k_inner_begin, dim3(1), dim3(256), 0, st, nbox, src, dst, count, handle,
+                      use_handle);
+}
+
+cudaError_t launch_inner_end(int nbox, const int *flags, int *count, int max_cycles,
+                             cudaGraphConditionalHandle handle, cudaStream_t st)
+{
+    return pdl_launch(k_inner_end, dim3(1), dim3(256), 0, st, nbox, flags, count, max_cycles,
+                      handle);
 }
 
 // ------------------------------------------------------------- set-up ----

@@ -71,11 +71,15 @@ template <class T>
 cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cudaStream_t st,
                                       double *partials = nullptr);
 // Adaptive inner cycles (mixed precision): the exit test after a restriction
-// with partials, and the copy of the step's box flags into the inner ones.
+// with partials; the start of a step's inner cycles (flags copied, counter
+// reset, loop condition set) and, in the graph WHILE form, the end of each.
 cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
                                const double *se, const double *sr, const double *normf,
                                const double *tol, double floor_rel, cudaStream_t st);
-cudaError_t launch_copy_flags(int nbox, const int *src, int *dst, cudaStream_t st);
+cudaError_t launch_inner_begin(int nbox, const int *src, int *dst, int *count,
+                               cudaGraphConditionalHandle handle, int use_handle, cudaStream_t st);
+cudaError_t launch_inner_end(int nbox, const int *flags, int *count, int max_cycles,
+                             cudaGraphConditionalHandle handle, cudaStream_t st);
 
 // phi += phic[parent].
 template <class T>

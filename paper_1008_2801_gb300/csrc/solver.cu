@@ -711,6 +711,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     for (int i = 0; i < 7; ++i) bump.take<double>(nbox);
     bump.take<int>(nbox);
     bump.take<int>(nbox);   // inner flags
+    bump.take<int>(2);      // inner cycle counters (this step, this solve)
     bump.take<int>(1);  // error word
     bump.take<unsigned>(1);  // grid-barrier word
     if (s->cg_bottom) bump.take<double>(2 * kCgPartials);   // CG partial sums
@@ -756,6 +757,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->dmean = real.take<double>(nbox);
     s->active = real.take<int>(nbox);
     s->active32 = real.take<int>(nbox);
+    s->icount = real.take<int>(2);
     s->derr = real.take<int>(1);
     s->gbar = real.take<unsigned>(1);
     if (s->cg_bottom) s->cgpart = real.take<double>(2 * kCgPartials);
@@ -795,6 +797,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     // its per-tile sums in the partials array
     s->inner_adapt = s->has32 && !s->pcg && o.inner_cycles == 0 && o.nu1 > 0 &&
                      !o.full_residual && !s->h32.smooth.empty() &&
+                     s->h32.smooth[0].nbox > 0 &&
                      (size_t)s->h32.smooth[0].ntiles[TK_COARSE] <= ntiles0;
     // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
     // last (nu2 > 0, so black residuals vanish), single-colour passes on every
@@ -965,6 +968,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         cudaMallocHost(&s->hactive, sizeof(int) * nbox) != cudaSuccess ||
         cudaMallocHost(&s->hside, sizeof(int) * (nbox + 1)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -1008,6 +1012,7 @@ void solver_destroy(Solver *s)
     if (s->hactive) cudaFreeHost(s->hactive);
     if (s->hside) cudaFreeHost(s->hside);
     if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->cap2) cudaStreamDestroy(s->cap2);
     if (s->copy) cudaStreamDestroy(s->copy);
     if (s->side) cudaStreamDestroy(s->side);
     if (s->ev_in) cudaEventDestroy(s->ev_in);
@@ -1560,14 +1565,58 @@ static cudaError_t enqueue_step32(Solver *s, cudaStream_t st)
             if ((e = enqueue_vcycle(s, s->h32, st)) != cudaSuccess) return e;
         return cudaSuccess;
     }
-    if ((e = launch_copy_flags(s->nbox, s->active, s->active32, st)) != cudaSuccess) return e;
     int *const outer = s->active;
+    if (!s->inner_while) {
+        // unrolled: kInnerMax cycles, those after every box has left doing
+        // nothing (each kernel skips inactive boxes)
+        if ((e = launch_inner_begin(s->nbox, outer, s->active32, s->icount, 0, 0, st)) !=
+            cudaSuccess)
+            return e;
+        s->active = s->active32;
+        s->inner_norm = true;
+        for (int i = 0; i < kInnerMax && e == cudaSuccess; ++i) e = enqueue_vcycle(s, s->h32, st);
+        s->active = outer;
+        s->inner_norm = false;
+        return e;
+    }
+    // inside the device loop's captured body: a WHILE node whose body is one
+    // cycle followed by the loop-end kernel (at most kInnerMax iterations)
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd)) != cudaSuccess)
+        return e;
+    if (cs != cudaStreamCaptureStatusActive || !cg) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0)) != cudaSuccess) return e;
+    if ((e = launch_inner_begin(s->nbox, outer, s->active32, s->icount, h, 1, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd)) != cudaSuccess)
+        return e;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return e;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s->cap2, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
     s->active = s->active32;
     s->inner_norm = true;
-    for (int i = 0; i < kInnerMax && e == cudaSuccess; ++i) e = enqueue_vcycle(s, s->h32, st);
+    const long long k0 = launch_counter();
+    e = enqueue_vcycle(s, s->h32, s->cap2);
+    if (e == cudaSuccess) e = launch_inner_end(s->nbox, s->active32, s->icount, kInnerMax, h, s->cap2);
+    s->inner_cycle_kernels = launch_counter() - k0;
     s->active = outer;
     s->inner_norm = false;
-    return e;
+    cudaError_t ee = cudaStreamEndCapture(s->cap2, &body);
+    return e != cudaSuccess ? e : ee;
 }
 
 template <class F>
@@ -1648,7 +1697,9 @@ static cudaError_t enqueue_body64(Solver *s, cudaStream_t st, cudaGraphCondition
 // norm, scales for the next step, decision.
 static cudaError_t enqueue_body32(Solver *s, cudaStream_t st, cudaGraphConditionalHandle h)
 {
+    s->inner_while = s->inner_adapt;
     cudaError_t e = enqueue_step32(s, st);
+    s->inner_while = false;
     if (e != cudaSuccess) return e;
     if ((e = launch_refine_update(s->h64.fine, s->h32.fine, s->active, s->se, st)) != cudaSuccess)
         return e;
@@ -1816,6 +1867,7 @@ static int upload_judge(Solver *s, const std::vector<BoxState> &bs, double tol,
     }
     *tl = tol;
     CK(cudaMemcpyAsync(s->jblock, s->hjblock, s->jbytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s->icount, 0, 2 * sizeof(int), st));
     return MG_OK;
 }
 
@@ -1831,6 +1883,12 @@ static int download_judge(Solver *s, std::vector<BoxState> &bs, long long per_it
     const int *cycles = status + nb;
     const int *step = cycles + 2 * nb;
     s->kernels += per_iter * (long long)(*step + ((s->lookahead && !s->has32) ? 1 : 0));
+    if (s->inner_cycle_kernels > 0 && s->has32) {
+        // the body counted one inner cycle per step; the WHILE node ran more
+        int inner[2] = {0, 0};
+        CK(cudaMemcpy(inner, s->icount, sizeof inner, cudaMemcpyDeviceToHost));
+        s->kernels += s->inner_cycle_kernels * (long long)std::max(inner[1] - *step, 0);
+    }
     for (int b = 0; b < nb; ++b) {
         if (bs[b].done) continue;
         bs[b].status = status[b];

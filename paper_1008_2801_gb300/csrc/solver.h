@@ -82,6 +82,9 @@ struct Solver {
     int *active32 = nullptr;       // [nbox] device flags of a refinement step's inner FP32 cycles
     bool inner_adapt = false;      // mixed: inner cycles end per box on the inner residual
     bool inner_norm = false;       // enqueueing inner cycles: restriction with norm + exit test
+    bool inner_while = false;      // enqueueing the device loop's body: inner cycles as a WHILE node
+    int *icount = nullptr;         // [2] device: inner cycles run in this step, in this solve
+    long long inner_cycle_kernels = 0;  // launches of one inner cycle in the WHILE form
     const long long *doff = nullptr;  // [nbox + 1] device copy of off
     int *dside = nullptr;          // [nbox] device: 1 if the solution ended in phi2
     double *hnorm = nullptr;       // pinned [2 * nbox]
@@ -89,6 +92,7 @@ struct Solver {
     int *hside = nullptr;          // pinned [nbox + 1]; the last is the error word's copy
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;  // packed staging
     cudaStream_t cap = nullptr;    // capture stream
+    cudaStream_t cap2 = nullptr;   // capture stream of a nested conditional body
     // host inputs of a solve are copied in on this stream, concurrently with
     // work already queued on the caller's stream (e.g. mg_set_beta's set-up)
     cudaStream_t copy = nullptr;
