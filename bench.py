@@ -51,8 +51,10 @@ L2_NOTE = "inputs larger than L2 (working set > 1 GB against 129 MB of L2)"
 BYTES_PER_CELL = {("sweep", 8): 48, ("sweep", 4): 24, ("pass", 8): 44, ("pass", 4): 22,
                   ("restrict", 8): 41, ("restrict", 4): 20.5, ("refine", 8): 60}
 # FP64 flops per cell of one launch: a Gauss-Seidel update is 6 FMA + 1 mul =
-# 13 flop; a sweep updates every cell, a single-colour pass half
-FLOPS_PER_CELL = {"sweep": 13, "pass": 6.5}
+# 13 flop; a sweep updates every cell, a single-colour pass half; the
+# red-only restriction forms half the cells' residuals (7 FMA each); the
+# refinement step adds s e (1 FMA) and forms every residual (7 FMA)
+FLOPS_PER_CELL = {"sweep": 13, "pass": 6.5, "restrict": 7, "refine": 16}
 
 
 def workload_seed(n):
@@ -331,6 +333,11 @@ def run_gpu(args):
                     "k_rbgs_pass (FP64 single-colour pass, finest level; average over the "
                     "in-place passes and the cycle's first two out-of-place passes)",
                     "rbgs_pass_f64")
+    # the residual kernel of the FP64 cycle (residual of the red children +
+    # restriction, finest level)
+    roof["fp64_residual_restriction"] = roofline(
+        fine, "restrict", 8, "k_resid_restrict_red<double> (residual of the red children and "
+        "restriction, finest level)", None)
 
     # mixed precision on the same input
     smx = Solver((n, n, n), d["dx"], precision="mixed", device=dev,
@@ -342,8 +349,15 @@ def run_gpu(args):
     _, _, profm, _ = timed(smx, args.steps, 1, True)
     smx.close()
     finem = {k: v for k, v in profm.items() if k != "kernels" and v["launches"]}
+    # FP32 V-cycles per solve, from the finest level's smoothing launches of
+    # the profiled steps (nu1 + nu2 = 4 sweeps a cycle; a cycle whose inner
+    # exit test ends it after pre-smoothing counts one half)
+    nsm = finem["sweep"]["launches"] if "sweep" in finem else finem.get(
+        "pass", {"launches": 0})["launches"] / 2
     mixed = {"value": world * N / (msm / 1e3), "unit": "cells/s", "ms_per_step": msm,
-             "refinement_steps": stm["cycles"], "fp32_vcycles_per_step": 2,
+             "refinement_steps": stm["cycles"],
+             "fp32_vcycles_per_solve": round(nsm / 4 / max(args.steps, 1), 2),
+             "inner_cycles": "adaptive (at most 8 a step)",
              "rel_resid": stm["rel_resid"], "speedup_vs_fp64": ms_max / msm,
              "split": {"setup_ms": round(stm["t_setup_ms"], 4),
                        "solve_ms": round(msm - stm["t_setup_ms"], 4)},
@@ -357,6 +371,14 @@ def run_gpu(args):
                  "k_rbgs_sweep (FP32 fused red-black sweep, finest level, plain loads)")
         mixed["roofline"] = roofline(finem, "sweep", 4, kname,
                                      "rbgs_sweep_tma_f32" if tma else "rbgs_sweep_f32")
+    if "restrict" in finem:
+        mixed["roofline_residual_restriction"] = roofline(
+            finem, "restrict", 4, "k_resid_restrict_red<float> (residual of the red children, "
+            "restriction and the inner exit test's sums, finest level)", None)
+    if "refine" in finem:
+        mixed["roofline_refinement"] = roofline(
+            finem, "refine", 8, "k_refine_update + k_refine_residual (FP64 refinement step: "
+            "x += s e, r = f - A x, r32 and ||r||; one stretch a step)", None)
     roof["mixed_fp32_sweep"] = mixed.get("roofline")
 
     # end to end through the C ABI with host (pinned) buffers

@@ -579,9 +579,9 @@ __device__ __forceinline__ T restrict_red_cell(const Box<T> &B, int I, int J, in
 // 4 red children of each coarse cell (the black 4 count as zero): half the
 // stencil work of k_resid_restrict, the same coarse right-hand side to
 // rounding.  Valid only when the last operation on phi was a black pass.
-// NORM: also the tile's sum of the squared red residuals into partials[t]
-// (hence ||f - A phi||^2 of the smoothed iterate, summed per box in fixed
-// order by the caller); every thread of the CTA reaches the block sum.
+// NORM: also each warp's sum of the squared red residuals into
+// partials[t * kThreads / 32 + warp] (hence ||f - A phi||^2 of the smoothed
+// iterate, summed per box in fixed order by the caller); no block barrier.
 template <class T, bool FC, bool NORM = false>
 __device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
                                                   const int *__restrict__ active, int t,
@@ -598,9 +598,10 @@ __device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
     if (NORM) {
         T r2 = T(0);
         if (I < nx / 2 && J < ny / 2) r2 = restrict_red_cell<T, NORM>(B, I, J, K);
-        const double tot = block_sum((double)r2);
-        if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = tot;
-        __syncthreads();   // the block sum's scratch is reused by the next tile
+        double v = (double)r2;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const int tid = threadIdx.y * kTX + threadIdx.x;
+        if ((tid & 31) == 0) partials[(long long)t * (kThreads / 32) + (tid >> 5)] = v;
         return;
     }
     if (I >= nx / 2 || J >= ny / 2) return;
@@ -1188,7 +1189,7 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 // in fixed order) against max(tol ||f|| / 2, floor_rel sr) / se: at or below
 // it the update is expected to meet tol, or the step has gained the factor
 // floor_rel, and the box leaves the inner cycles of this step (active32 = 0).
-// floor_rel: the most one step asks of FP32 arithmetic.  One CTA.
+// floor_rel: the most one step asks of FP32 arithmetic.  One CTA per box.
 __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__restrict__ active32,
                                                       const double *__restrict__ partials,
                                                       const double *__restrict__ se,
@@ -1199,24 +1200,24 @@ __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__re
 {
     pdl_wait();
     __shared__ double wsum[32];
+    const int b = blockIdx.x;
+    const int id = S.boxes[b].box;
+    if (!active32[id]) return;   // the whole CTA
     const int *ts = S.tstart[TK_COARSE];
-    for (int b = 0; b < S.nbox; ++b) {
-        const int id = S.boxes[b].box;
-        if (!active32[id]) continue;   // read by every thread before the barrier below
-        double v = 0.0;
-        for (int q = ts[b] + (int)threadIdx.x; q < ts[b + 1]; q += 1024) v += partials[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < 32; ++w) tot += wsum[w];
-            const double e = se[id];
-            const double target =
-                e > 0.0 ? fmax(0.5 * tol[0] * normf[id], floor_rel * sr[id]) / e : 0.0;
-            if (!(sqrt(tot) > target)) active32[id] = 0;
-        }
-        __syncthreads();
+    constexpr int W = kThreads / 32;   // partial sums per tile of the restriction
+    const long long lo = (long long)ts[b] * W, hi = (long long)ts[b + 1] * W;
+    double v = 0.0;
+    for (long long q = lo + threadIdx.x; q < hi; q += 1024) v += partials[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 32; ++w) tot += wsum[w];
+        const double e = se[id];
+        const double target =
+            e > 0.0 ? fmax(0.5 * tol[0] * normf[id], floor_rel * sr[id]) / e : 0.0;
+        if (!(sqrt(tot) > target)) active32[id] = 0;
     }
 }
 
@@ -2696,8 +2697,8 @@ cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const doub
                                const double *tol, double floor_rel, cudaStream_t st)
 {
     if (S.nbox == 0) return cudaSuccess;
-    return pdl_launch(k_inner_judge, dim3(1), dim3(1024), 0, st, S, active32, partials, se, sr,
-                      normf, tol, floor_rel);
+    return pdl_launch(k_inner_judge, dim3(S.nbox), dim3(1024), 0, st, S, active32, partials, se,
+                      sr, normf, tol, floor_rel);
 }
 
 template <class T>

@@ -793,12 +793,10 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     plan_hier(s, s->h64, blob, p64, &jobs64, &maps64);
     if (s->has32) plan_hier(s, s->h32, blob, p32, &jobs32, &maps32);
     // adaptive inner cycles: the exit test reads the red-only restriction of
-    // the finest FP32 level (after a black pass: nu1 > 0, no full residual),
-    // its per-tile sums in the partials array
+    // the finest FP32 level (after a black pass: nu1 > 0, no full residual)
     s->inner_adapt = s->has32 && !s->pcg && o.inner_cycles == 0 && o.nu1 > 0 &&
                      !o.full_residual && !s->h32.smooth.empty() &&
-                     s->h32.smooth[0].nbox > 0 &&
-                     (size_t)s->h32.smooth[0].ntiles[TK_COARSE] <= ntiles0;
+                     s->h32.smooth[0].nbox > 0;
     // FP64 look-ahead norm: needs a red pass first (nu1 > 0), a black pass
     // last (nu2 > 0, so black residuals vanish), single-colour passes on every
     // box's finest level, and the red-only residual reading
@@ -926,6 +924,14 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
         solver_destroy(s);
         return set_error(MG_ERR_OOM, "cudaMalloc(descriptors): %s", cudaGetErrorString(e));
     }
+    if (s->inner_adapt) {   // the restriction's per-warp sums of the inner exit test
+        const size_t np = (size_t)s->h32.smooth[0].ntiles[TK_COARSE] * (kThreads / 32);
+        e = dev_malloc(s, reinterpret_cast<void **>(&s->ipart), np * sizeof(double));
+        if (e != cudaSuccess) {
+            solver_destroy(s);
+            return set_error(MG_ERR_OOM, "cudaMalloc(inner sums): %s", cudaGetErrorString(e));
+        }
+    }
     if (periodic) {
         // the coarse jobs' exchange records, now that their address is known
         auto link = [&](size_t at, int lc, auto *tag) {
@@ -966,6 +972,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     if (cudaMallocHost(&s->hjblock, s->jbytes) != cudaSuccess ||
         cudaMallocHost(&s->hnorm, sizeof(double) * 2 * nbox) != cudaSuccess ||
         cudaMallocHost(&s->hactive, sizeof(int) * nbox) != cudaSuccess ||
+        cudaMallocHost(&s->hflags, sizeof(int) * nbox) != cudaSuccess ||
         cudaMallocHost(&s->hside, sizeof(int) * (nbox + 1)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking) != cudaSuccess ||
@@ -992,7 +999,8 @@ void solver_destroy(Solver *s)
     // a caller's allocator may hand the memory out again at once: let the
     // context's queued work (e.g. a set-up without a solve yet) finish first
     if (s->opts.dev_free) cudaDeviceSynchronize();
-    for (auto *v : {&s->slots64, &s->slots32, &s->slots_head, &s->direct})
+    for (auto *v : {&s->slots64, &s->slots32, &s->slots_head, &s->slots_down0, &s->slots_rest,
+                    &s->direct})
         for (auto &sl : *v) {
             cudaEventDestroy(sl.b);
             cudaEventDestroy(sl.e);
@@ -1001,15 +1009,19 @@ void solver_destroy(Solver *s)
     if (s->h64.head) cudaGraphExecDestroy(s->h64.head);
     if (s->h64.graph) cudaGraphExecDestroy(s->h64.graph);
     if (s->h32.graph) cudaGraphExecDestroy(s->h32.graph);
+    if (s->h32.down0) cudaGraphExecDestroy(s->h32.down0);
+    if (s->h32.rest) cudaGraphExecDestroy(s->h32.rest);
     if (s->loop64) cudaGraphExecDestroy(s->loop64);
     if (s->loop32) cudaGraphExecDestroy(s->loop32);
     if (s->loop_pcg) cudaGraphExecDestroy(s->loop_pcg);
     if (s->hjblock) cudaFreeHost(s->hjblock);
     dev_free(s, s->arena);
     dev_free(s, s->desc);
+    dev_free(s, s->ipart);
     dev_free(s, s->stage_a);
     if (s->hnorm) cudaFreeHost(s->hnorm);
     if (s->hactive) cudaFreeHost(s->hactive);
+    if (s->hflags) cudaFreeHost(s->hflags);
     if (s->hside) cudaFreeHost(s->hside);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->cap2) cudaStreamDestroy(s->cap2);
@@ -1369,13 +1381,13 @@ static int exch_chunks(int max_cells)
 // exit test follows it.  FP64 hierarchies never take part.
 static double *inner_partials(const Solver *s, const Hier<float> &H, int l)
 {
-    return (s->inner_norm && l == 0 && &H == &s->h32) ? s->partials : nullptr;
+    return (s->inner_norm && l == 0 && &H == &s->h32) ? s->ipart : nullptr;
 }
 static double *inner_partials(const Solver *, const Hier<double> &, int) { return nullptr; }
 
 static cudaError_t inner_judge(Solver *s, const BoxSet<float> &S, cudaStream_t st)
 {
-    return launch_inner_judge(S, s->active, s->partials, s->se, s->sr, s->dnormf, s->J.tol,
+    return launch_inner_judge(S, s->active, s->ipart, s->se, s->sr, s->dnormf, s->J.tol,
                               kInnerFloor, st);
 }
 static cudaError_t inner_judge(Solver *, const BoxSet<double> &, cudaStream_t)
@@ -1429,20 +1441,22 @@ static bool level_persistent(const Solver *s, const Hier<T> &H, int l)
 // pre-smoother, so that with nu1 = nu2 and a zero start the cycle is a
 // symmetric linear operator (the CG preconditioner).
 template <class T>
+// part: 0 the whole cycle; 1 only the finest level's down leg (smoothing,
+// restriction); 2 the rest (what part 1 leaves out).
 static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
-                                  bool head_done = false, bool sym = false)
+                                  bool head_done = false, bool sym = false, int part = 0)
 {
     cudaError_t e;
     const int nl = (int)H.smooth.size();
-    int coarse = -1;
-    for (int l = 0; l < nl; ++l) {
+    int coarse = part == 2 ? prof_begin(s, MG_PROF_COARSE, st) : -1;
+    for (int l = part == 2 ? 1 : 0; l < (part == 1 ? std::min(nl, 1) : nl); ++l) {
         const BoxSet<T> &S = H.smooth[l];
         if (S.nbox == 0) continue;
         if (level_persistent(s, H, l)) {
             if ((e = level_launch(s, H, l, false, s->opts.nu1, l == 0 && head_done, false, st)) !=
                 cudaSuccess)
                 return e;
-            if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
+            if (l == 0 && part == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
             continue;
         }
         int nu1 = s->opts.nu1;
@@ -1466,9 +1480,10 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
         if (e != cudaSuccess) return e;
         prof_end(s, sl, st);
         if (ip && (e = inner_judge(s, S, st)) != cudaSuccess) return e;
-        if (l == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
+        if (l == 0 && part == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
     }
-    if (nl == 0 || H.smooth[0].nbox == 0) coarse = prof_begin(s, MG_PROF_COARSE, st);
+    if (part == 1) return cudaSuccess;
+    if (part == 0 && (nl == 0 || H.smooth[0].nbox == 0)) coarse = prof_begin(s, MG_PROF_COARSE, st);
     if (s->coupled)
         e = launch_union_bottom(H.bottom, s->ub, H.uinv, s->active, st);
     else if (s->cg_bottom)
@@ -1549,6 +1564,26 @@ static cudaError_t enqueue_tail64(Solver *s, cudaStream_t st)
     return enqueue_vcycle(s, s->h64, st, true);
 }
 
+// Host-judged inner cycles: the parts of one cycle on the inner flags.
+static cudaError_t enqueue_inner_part(Solver *s, cudaStream_t st, int part)
+{
+    int *const outer = s->active;
+    s->active = s->active32;
+    s->inner_norm = true;
+    cudaError_t e = enqueue_vcycle(s, s->h32, st, false, false, part);
+    s->active = outer;
+    s->inner_norm = false;
+    return e;
+}
+static cudaError_t enqueue_inner_down0(Solver *s, cudaStream_t st)
+{
+    return enqueue_inner_part(s, st, 1);
+}
+static cudaError_t enqueue_inner_rest(Solver *s, cudaStream_t st)
+{
+    return enqueue_inner_part(s, st, 2);
+}
+
 // Mixed: FP32 V-cycles on r32, from e = 0 (zeroed by the prologue, and after
 // that by each refinement update once it has used e).  inner_cycles > 0: that
 // many.  Adaptive (inner_cycles = 0): up to kInnerMax, run on the inner flags
@@ -1565,22 +1600,11 @@ static cudaError_t enqueue_step32(Solver *s, cudaStream_t st)
             if ((e = enqueue_vcycle(s, s->h32, st)) != cudaSuccess) return e;
         return cudaSuccess;
     }
+    // adaptive: only inside the device loop's captured body (the host-judged
+    // loop runs run_inner_host instead): a WHILE node whose body is one cycle
+    // followed by the loop-end kernel (at most kInnerMax iterations)
+    if (!s->inner_while) return cudaErrorInvalidValue;
     int *const outer = s->active;
-    if (!s->inner_while) {
-        // unrolled: kInnerMax cycles, those after every box has left doing
-        // nothing (each kernel skips inactive boxes)
-        if ((e = launch_inner_begin(s->nbox, outer, s->active32, s->icount, 0, 0, st)) !=
-            cudaSuccess)
-            return e;
-        s->active = s->active32;
-        s->inner_norm = true;
-        for (int i = 0; i < kInnerMax && e == cudaSuccess; ++i) e = enqueue_vcycle(s, s->h32, st);
-        s->active = outer;
-        s->inner_norm = false;
-        return e;
-    }
-    // inside the device loop's captured body: a WHILE node whose body is one
-    // cycle followed by the loop-end kernel (at most kInnerMax iterations)
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -1638,7 +1662,12 @@ static int run_step(Solver *s, cudaGraphExec_t *graph, std::vector<ProfSlot> *sl
         s->h64.head = nullptr;
         if (s->h32.graph) cudaGraphExecDestroy(s->h32.graph);
         s->h32.graph = nullptr;
-        for (auto *v : {&s->slots64, &s->slots32, &s->slots_head}) {
+        if (s->h32.down0) cudaGraphExecDestroy(s->h32.down0);
+        s->h32.down0 = nullptr;
+        if (s->h32.rest) cudaGraphExecDestroy(s->h32.rest);
+        s->h32.rest = nullptr;
+        for (auto *v : {&s->slots64, &s->slots32, &s->slots_head, &s->slots_down0,
+                        &s->slots_rest}) {
             for (auto &sl : *v) {
                 s->ev_free.push_back(sl.b);
                 s->ev_free.push_back(sl.e);
@@ -1811,6 +1840,29 @@ static int download_judge(Solver *s, std::vector<struct BoxState> &bs, long long
 #define RUN32(s, st) run_step(s, &(s)->h32.graph, &(s)->slots32, &(s)->graph_kernels32, enqueue_step32, st)
 #define RUNHEAD(s, st) run_step(s, &(s)->h64.head, &(s)->slots_head, &(s)->graph_kernels_head, enqueue_head64, st)
 #define RUNTAIL(s, st) run_step(s, &(s)->h64.graph, &(s)->slots64, &(s)->graph_kernels64, enqueue_tail64, st)
+#define RUNDOWN0(s, st) run_step(s, &(s)->h32.down0, &(s)->slots_down0, &(s)->graph_kernels_down0, enqueue_inner_down0, st)
+#define RUNREST(s, st) run_step(s, &(s)->h32.rest, &(s)->slots_rest, &(s)->graph_kernels_rest, enqueue_inner_rest, st)
+
+// Adaptive inner cycles of one refinement step in the host-judged loop: the
+// finest level's down leg (with the exit test), the inner flags read back,
+// and the rest of the cycle only while some box is still in; at most
+// kInnerMax cycles.  The same work on every box as the device loop's WHILE
+// form, whose last cycle runs its rest on no box.
+static int run_inner_host(Solver *s, cudaStream_t st)
+{
+    CK(launch_inner_begin(s->nbox, s->active, s->active32, s->icount, 0, 0, st));
+    for (int i = 0; i < kInnerMax; ++i) {
+        CKS(RUNDOWN0(s, st));
+        CK(cudaMemcpyAsync(s->hflags, s->active32, sizeof(int) * s->nbox, cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int b = 0; b < s->nbox; ++b) any = any || s->hflags[b] != 0;
+        if (!any) break;
+        CKS(RUNREST(s, st));
+    }
+    return MG_OK;
+}
 
 // Per-box bookkeeping of the convergence loop.
 struct BoxState {
@@ -2156,7 +2208,8 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
             any = false;
         }
         for (int k = 1; any; ++k) {
-            CKS(RUN32(s, stream));
+            if (s->inner_adapt) CKS(run_inner_host(s, stream));
+            else CKS(RUN32(s, stream));
             s->rec = &s->direct;
             const int sl = prof_begin(s, MG_PROF_REFINE, stream);
             CK(launch_refine_update(H.fine, s->h32.fine, s->active, s->se, stream));

@@ -37,6 +37,8 @@ struct Hier {
     int njobs = 0;
     cudaGraphExec_t graph = nullptr;            // captured V-cycle (+ fine norm for FP64)
     cudaGraphExec_t head = nullptr;             // look-ahead: first red pass + norm
+    cudaGraphExec_t down0 = nullptr;            // host-judged inner cycles: finest level's down leg
+    cudaGraphExec_t rest = nullptr;             // ... and the rest of the cycle
     T *uinv = nullptr;                          // coupled level: dense inverse of the union bottom
     int pgrid = 0;                              // resident CTAs of the persistent level kernels
     T *cgp = nullptr, *cgq = nullptr;           // CG coarsest level: p and q (level arrays)
@@ -84,11 +86,13 @@ struct Solver {
     bool inner_norm = false;       // enqueueing inner cycles: restriction with norm + exit test
     bool inner_while = false;      // enqueueing the device loop's body: inner cycles as a WHILE node
     int *icount = nullptr;         // [2] device: inner cycles run in this step, in this solve
+    double *ipart = nullptr;       // device: per-warp sums of the finest FP32 restriction
     long long inner_cycle_kernels = 0;  // launches of one inner cycle in the WHILE form
     const long long *doff = nullptr;  // [nbox + 1] device copy of off
     int *dside = nullptr;          // [nbox] device: 1 if the solution ended in phi2
     double *hnorm = nullptr;       // pinned [2 * nbox]
     int *hactive = nullptr;        // pinned [nbox]
+    int *hflags = nullptr;         // pinned [nbox]: inner flags read by the host-judged loop
     int *hside = nullptr;          // pinned [nbox + 1]; the last is the error word's copy
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;  // packed staging
     cudaStream_t cap = nullptr;    // capture stream
@@ -126,6 +130,8 @@ struct Solver {
     long long cap_kernels = 0;            // kernels enqueued into graph captures
     long long graph_kernels64 = 0, graph_kernels32 = 0, graph_kernels_head = 0;
     std::vector<ProfSlot> slots_head;     // event slots of the look-ahead head graph
+    std::vector<ProfSlot> slots_down0, slots_rest;  // ... of the host-judged inner cycle parts
+    long long graph_kernels_down0 = 0, graph_kernels_rest = 0;
     // FP64 look-ahead: each cycle starts with an out-of-place red pass that
     // also yields the previous iterate's residual norm, judged before the
     // rest of the cycle (no separate norm pass)
