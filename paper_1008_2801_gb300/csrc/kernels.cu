@@ -1189,14 +1189,16 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
 // in fixed order) against max(tol ||f|| / 2, floor_rel sr) / se: at or below
 // it the update is expected to meet tol, or the step has gained the factor
 // floor_rel, and the box leaves the inner cycles of this step (active32 = 0).
-// floor_rel: the most one step asks of FP32 arithmetic.  One CTA per box.
+// floor_rel: the most one step asks of FP32 arithmetic.  One CTA per box;
+// coupled (the boxes of a level solved as one domain, whose norms and scales
+// are the domain's): one CTA, one decision for every box.
 __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__restrict__ active32,
                                                       const double *__restrict__ partials,
                                                       const double *__restrict__ se,
                                                       const double *__restrict__ sr,
                                                       const double *__restrict__ normf,
                                                       const double *__restrict__ tol,
-                                                      double floor_rel)
+                                                      double floor_rel, int coupled)
 {
     pdl_wait();
     __shared__ double wsum[32];
@@ -1205,7 +1207,8 @@ __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__re
     if (!active32[id]) return;   // the whole CTA
     const int *ts = S.tstart[TK_COARSE];
     constexpr int W = kThreads / 32;   // partial sums per tile of the restriction
-    const long long lo = (long long)ts[b] * W, hi = (long long)ts[b + 1] * W;
+    const long long lo = coupled ? (long long)ts[0] * W : (long long)ts[b] * W;
+    const long long hi = coupled ? (long long)ts[S.nbox] * W : (long long)ts[b + 1] * W;
     double v = 0.0;
     for (long long q = lo + threadIdx.x; q < hi; q += 1024) v += partials[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1217,7 +1220,12 @@ __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__re
         const double e = se[id];
         const double target =
             e > 0.0 ? fmax(0.5 * tol[0] * normf[id], floor_rel * sr[id]) / e : 0.0;
-        if (!(sqrt(tot) > target)) active32[id] = 0;
+        if (!(sqrt(tot) > target)) {
+            if (coupled)
+                for (int q = 0; q < S.nbox; ++q) active32[S.boxes[q].box] = 0;
+            else
+                active32[id] = 0;
+        }
     }
 }
 
@@ -2694,11 +2702,11 @@ cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cud
 
 cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
                                const double *se, const double *sr, const double *normf,
-                               const double *tol, double floor_rel, cudaStream_t st)
+                               const double *tol, double floor_rel, int coupled, cudaStream_t st)
 {
     if (S.nbox == 0) return cudaSuccess;
-    return pdl_launch(k_inner_judge, dim3(S.nbox), dim3(1024), 0, st, S, active32, partials, se,
-                      sr, normf, tol, floor_rel);
+    return pdl_launch(k_inner_judge, dim3(coupled ? 1 : S.nbox), dim3(1024), 0, st, S, active32,
+                      partials, se, sr, normf, tol, floor_rel, coupled);
 }
 
 template <class T>

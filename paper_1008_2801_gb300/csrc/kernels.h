@@ -75,7 +75,7 @@ cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cud
 // reset, loop condition set) and, in the graph WHILE form, the end of each.
 cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
                                const double *se, const double *sr, const double *normf,
-                               const double *tol, double floor_rel, cudaStream_t st);
+                               const double *tol, double floor_rel, int coupled, cudaStream_t st);
 cudaError_t launch_inner_begin(int nbox, const int *src, int *dst, int *count,
                                cudaGraphConditionalHandle handle, int use_handle, cudaStream_t st);
 cudaError_t launch_inner_end(int nbox, const int *flags, int *count, int max_cycles,

@@ -1388,7 +1388,7 @@ static double *inner_partials(const Solver *, const Hier<double> &, int) { retur
 static cudaError_t inner_judge(Solver *s, const BoxSet<float> &S, cudaStream_t st)
 {
     return launch_inner_judge(S, s->active, s->ipart, s->se, s->sr, s->dnormf, s->J.tol,
-                              kInnerFloor, st);
+                              kInnerFloor, s->coupled ? 1 : 0, st);
 }
 static cudaError_t inner_judge(Solver *, const BoxSet<double> &, cudaStream_t)
 {

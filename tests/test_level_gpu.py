@@ -71,6 +71,20 @@ def test_rectangle_tiled_by_boxes_is_the_single_box_solve(cuda_device, precision
     assert np.linalg.norm(phi - one.cpu().numpy()) <= 1e-9 * np.linalg.norm(phi)
 
 
+def test_mixed_level_leaves_inner_cycles_as_one_domain(cuda_device):
+    # the boxes of a level share ghost cells: the adaptive inner cycles end
+    # for all of them at once, on the domain's inner residual, so the level
+    # takes the refinement steps of the single box it tiles
+    beta, f, h = _domain((96, 96, 96), 4)
+    los = [(i, j, k) for k in (0, 32, 64) for j in (0, 32, 64) for i in (0, 32, 64)]
+    ns = [(32, 32, 32)] * 27
+    st, _ = _check(los, ns, beta, f, h, cuda_device, "mixed")
+    with Solver(beta.shape, h, precision="mixed", device=cuda_device) as s:
+        s.set_beta(_t(beta, cuda_device))
+        _, st1 = s.solve(_t(f, cuda_device), tol=TOL)
+    assert st["cycles"] <= st1["cycles"] + 1, (st["hist"], st1["hist"])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_l_shaped_level(cuda_device, precision):
     beta, f, h = _domain((8, 32, 32), 2)
