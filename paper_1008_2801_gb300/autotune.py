@@ -31,7 +31,7 @@ _lock = threading.Lock()
 
 SMOOTHERS = ("auto", "passes", "fused")
 COARSE = (0, 512, 2048, 8192)
-INNER = (1, 2, 3)
+INNER = (0, 2, 4)   # 0: adaptive (the default)
 PERSISTENT = (False, "small", "all")
 SWEEP_ZC = (0, 8, 16, 32, 64)      # 0: the library's wave model
 LEVEL_CTAS = (0, 1, 2)             # 0: every resident CTA

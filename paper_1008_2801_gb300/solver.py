@@ -145,7 +145,10 @@ class Solver:
     """Multigrid solver for one (nz, ny, nx) box with cubic cells of size dx.
 
     precision: "fp64" (everything FP64) or "mixed" (FP32 V-cycles inside an
-    FP64 iterative-refinement loop).  bc: wall mask or D/N string (see the
+    FP64 iterative-refinement loop; inner_cycles: FP32 V-cycles per
+    refinement step, 0 (default) adaptive, up to 8, each box leaving them
+    once its update is expected to meet tol, or 1..8 fixed).  bc: wall mask
+    or D/N string (see the
     module docstring).  krylov: conjugate gradients preconditioned by one
     symmetric V-cycle per iteration instead of plain V-cycles, for
     high-contrast beta (with "mixed" the V-cycle runs in FP32, CG in FP64).

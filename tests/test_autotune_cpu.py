@@ -23,7 +23,7 @@ def test_candidates_cover_the_options():
     assert len(cmx) == 3 * 3 * len(c64) and len(c64) == 4 * 3
     assert {c["smoother"] for c in c64} == {"auto"}
     assert {c["smoother"] for c in cmx} == {"auto", "passes", "fused"}
-    assert {c["inner_cycles"] for c in cmx} == {1, 2, 3}
+    assert {c["inner_cycles"] for c in cmx} == {0, 2, 4}   # 0: adaptive
     assert {c["persistent"] for c in c64} == {False, "small", "all"}
     for c in c64 + cmx:
         assert set(c) == set(autotune.DEFAULTS)
