@@ -1026,6 +1026,10 @@ __global__ void __launch_bounds__(kThreads) k_refine_update(BoxSet<double> S64, 
     E.phi[c] = 0.f;   // the next step's FP32 cycles start from e = 0
 }
 
+// X_ZERO: x = 0 (a zero initial guess), so r = f exactly (every product in
+// the FMA chain is a signed zero): f is read instead of the stencil formed,
+// with the same roundings and sums after it.
+template <bool X_ZERO>
 __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64, BoxSet<float> S32,
                                                               const int *__restrict__ active,
                                                               const double *__restrict__ c_r_inv,
@@ -1047,8 +1051,10 @@ __global__ void __launch_bounds__(kThreads) k_refine_residual(BoxSet<double> S64
             constexpr bool HD = decltype(has_d)::value;
             for (int k = z0; k < z1; ++k) {
                 const long long c = (long long)k * B.Q + (long long)p.y * B.P + p.x;
-                const double r = residual_at<double, HD>(B.phi, B.f, B.wx, B.wy, B.wz, B.D, c,
-                                                         fidx(B, p.x, p.y, k), B.P, B.Q);
+                const long long cf = fidx(B, p.x, p.y, k);
+                const double r = X_ZERO ? B.f[cf]
+                                        : residual_at<double, HD>(B.phi, B.f, B.wx, B.wy, B.wz,
+                                                                  B.D, c, cf, B.P, B.Q);
                 const float r32 = (float)r * cri;
                 E.f[c] = r32;
                 acc = fmaf(r32, r32, acc);
@@ -1114,19 +1120,28 @@ __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restri
 
 // ------------------------------------------------- packing and helpers ----
 
+// The copies between the caller's packed arrays and the level layout, and
+// the zeroing of a level's phi, take one thread per cell column of kColZ
+// planes (TK_COLZ tiles): kColZ independent loads or stores in flight per
+// thread instead of one per one-plane CTA.
 __global__ void __launch_bounds__(kThreads) k_pack(BoxSet<double> S, const long long *__restrict__ off,
                                                    const double *__restrict__ user, int to_f)
 {
     pdl_wait();
     const int t = blockIdx.x;
-    const int *ts = S.tstart[TK_CELL];
+    const int *ts = S.tstart[TK_COLZ];
     const int b = find_box(ts, S.nbox, t);
     const Box<double> &B = S.boxes[b];
-    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
-    const long long u = off[B.box] + ((long long)p.z * B.ny + p.y) * B.nx + p.x;
-    if (to_f) B.f[fidx(B, p.x, p.y, p.z)] = user[u];
-    else B.phi[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] = user[u];
+    const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+    const long long us = (long long)B.ny * B.nx;
+    const double *src = user + off[B.box] + ((long long)z0 * B.ny + p.y) * B.nx + p.x;
+#pragma unroll 4
+    for (int k = z0; k < z1; ++k, src += us) {
+        if (to_f) B.f[fidx(B, p.x, p.y, k)] = *src;
+        else B.phi[(long long)k * B.Q + (long long)p.y * B.P + p.x] = *src;
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_unpack(BoxSet<double> S, const long long *__restrict__ off,
@@ -1135,15 +1150,18 @@ __global__ void __launch_bounds__(kThreads) k_unpack(BoxSet<double> S, const lon
 {
     pdl_wait();
     const int t = blockIdx.x;
-    const int *ts = S.tstart[TK_CELL];
+    const int *ts = S.tstart[TK_COLZ];
     const int b = find_box(ts, S.nbox, t);
     const Box<double> &B = S.boxes[b];
-    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
-    const long long u = off[B.box] + ((long long)p.z * B.ny + p.y) * B.nx + p.x;
-    const long long c = (long long)p.z * B.Q + (long long)p.y * B.P + p.x;
-    const double *src = (side && side[B.box]) ? B.phi2 : B.phi;
-    user[u] = src[c];
+    const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+    const long long us = (long long)B.ny * B.nx;
+    double *dst = user + off[B.box] + ((long long)z0 * B.ny + p.y) * B.nx + p.x;
+    const double *src = ((side && side[B.box]) ? B.phi2 : B.phi) + (long long)z0 * B.Q +
+                        (long long)p.y * B.P + p.x;
+#pragma unroll 4
+    for (int k = z0; k < z1; ++k, dst += us, src += B.Q) *dst = *src;
 }
 
 template <class T>
@@ -1151,13 +1169,16 @@ __global__ void __launch_bounds__(kThreads) k_zero(BoxSet<T> S, const int *__res
 {
     pdl_wait();
     const int t = blockIdx.x;
-    const int *ts = S.tstart[TK_CELL];
+    const int *ts = S.tstart[TK_COLZ];
     const int b = find_box(ts, S.nbox, t);
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    TilePos p = tile_pos(TK_CELL, B.nx, B.ny, B.nz, t - ts[b]);
+    TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
     if (p.x >= B.nx || p.y >= B.ny) return;
-    B.phi[(long long)p.z * B.Q + (long long)p.y * B.P + p.x] = T(0);
+    const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+    T *dst = B.phi + (long long)z0 * B.Q + (long long)p.y * B.P + p.x;
+#pragma unroll 4
+    for (int k = z0; k < z1; ++k, dst += B.Q) *dst = T(0);
 }
 
 __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
@@ -2777,11 +2798,14 @@ cudaError_t launch_refine_update(const BoxSet<double> &S64, const BoxSet<float> 
 
 cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float> &S32,
                                    const int *active, const double *c_r_inv, double *partials,
-                                   cudaStream_t st)
+                                   cudaStream_t st, bool x_zero)
 {
     if (S64.ntiles[TK_COLZ] == 0) return cudaSuccess;
-    return pdl_launch(k_refine_residual, dim3(S64.ntiles[TK_COLZ]), block2d(), 0, st, S64, S32,
-                      active, c_r_inv, partials);
+    if (x_zero)
+        return pdl_launch(k_refine_residual<true>, dim3(S64.ntiles[TK_COLZ]), block2d(), 0, st,
+                          S64, S32, active, c_r_inv, partials);
+    return pdl_launch(k_refine_residual<false>, dim3(S64.ntiles[TK_COLZ]), block2d(), 0, st, S64,
+                      S32, active, c_r_inv, partials);
 }
 
 cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int *active,
@@ -2796,22 +2820,22 @@ cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int 
 cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,
                         int to_f, cudaStream_t st)
 {
-    if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    return pdl_launch(k_pack, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, off, user, to_f);
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    return pdl_launch(k_pack, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, off, user, to_f);
 }
 
 cudaError_t launch_unpack(const BoxSet<double> &S, const long long *off, double *user,
                           const int *side, cudaStream_t st)
 {
-    if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    return pdl_launch(k_unpack, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, off, user, side);
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    return pdl_launch(k_unpack, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, off, user, side);
 }
 
 template <class T>
 cudaError_t launch_zero(const BoxSet<T> &S, const int *active, cudaStream_t st)
 {
-    if (S.ntiles[TK_CELL] == 0) return cudaSuccess;
-    return pdl_launch(k_zero<T>, dim3(S.ntiles[TK_CELL]), block2d(), 0, st, S, active);
+    if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
+    return pdl_launch(k_zero<T>, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, active);
 }
 
 cudaError_t launch_scales(int nbox, const int *active, int init, const double *norm,

@@ -122,11 +122,12 @@ cudaError_t launch_coarse_vcycle(const CoarseJob<T> *jobs, int njobs, const int 
 // f, weights, D in S64; FP32 phi = e, f = r32 in S32):
 //   update:   x += c_e[b] e
 //   residual: r = f - A x; r32 = r * c_r_inv[b]; partial sums of r32^2
+//   (x_zero: x = 0, so r = f, read without the stencil)
 cudaError_t launch_refine_update(const BoxSet<double> &S64, const BoxSet<float> &S32,
                                  const int *active, const double *c_e, cudaStream_t st);
 cudaError_t launch_refine_residual(const BoxSet<double> &S64, const BoxSet<float> &S32,
                                    const int *active, const double *c_r_inv, double *partials,
-                                   cudaStream_t st);
+                                   cudaStream_t st, bool x_zero = false);
 
 // One convergence decision per active box after a cycle (see k_judge); sets
 // the graph condition to "any box still active" when use_handle is 1.

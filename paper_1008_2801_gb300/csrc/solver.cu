@@ -2023,7 +2023,9 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
         CK(exch(s, H.fine, 0, stream));
         CK(launch_zero(s->h32.fine, nullptr, stream));
         CK(launch_scales(nbox, nullptr, 1, s->dnorm, s->dnormf, s->se, s->sr, s->sr_inv, stream));
-        CK(launch_refine_residual(H.fine, s->h32.fine, nullptr, s->sr_inv, s->partials, stream));
+        // (zero guess: r0 = f, read without forming the stencil)
+        CK(launch_refine_residual(H.fine, s->h32.fine, nullptr, s->sr_inv, s->partials, stream,
+                                  zero_guess));
         CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnorm, nullptr, nullptr, stream,
                               s->sr));
         CK(combine(s, s->dnorm, stream));
