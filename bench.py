@@ -189,6 +189,11 @@ TRAFFIC_REGIONS = {
                        "// ------------------------------------------- residual + restriction ----"),
     # the TMA-fed sweep is the whole of its own file
     "rbgs_sweep_tma_f32": ("sweep_tma.cu", None),
+    # the red-children residual + restriction (FP64; FP32 with the inner exit sums)
+    "resid_restrict_f64": ("// ------------------------------------------- residual + restriction ----",
+                           "// --------------------------------------------------------- prolongation ----"),
+    "resid_restrict_f32": ("// ------------------------------------------- residual + restriction ----",
+                           "// --------------------------------------------------------- prolongation ----"),
 }
 
 
@@ -337,7 +342,7 @@ def run_gpu(args):
     # restriction, finest level)
     roof["fp64_residual_restriction"] = roofline(
         fine, "restrict", 8, "k_resid_restrict_red<double> (residual of the red children and "
-        "restriction, finest level)", None)
+        "restriction, finest level)", "resid_restrict_f64")
 
     # mixed precision on the same input
     smx = Solver((n, n, n), d["dx"], precision="mixed", device=dev,
@@ -374,7 +379,7 @@ def run_gpu(args):
     if "restrict" in finem:
         mixed["roofline_residual_restriction"] = roofline(
             finem, "restrict", 4, "k_resid_restrict_red<float> (residual of the red children, "
-            "restriction and the inner exit test's sums, finest level)", None)
+            "restriction and the inner exit test's sums, finest level)", "resid_restrict_f32")
     if "refine" in finem:
         mixed["roofline_refinement"] = roofline(
             finem, "refine", 8, "k_refine_update + k_refine_residual (FP64 refinement step: "

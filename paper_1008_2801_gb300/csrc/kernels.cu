@@ -1201,20 +1201,52 @@ __global__ void k_scales(int nbox, const int *__restrict__ active, int init,
     }
 }
 
+// First stage of the inner exit test's sums: chunk c of the set (chunk
+// c - cstart[b] of box b, cstart the per-box chunk prefix) sums the per-warp
+// partials of its kInnerChunk restriction tiles in fixed order.
+__global__ void __launch_bounds__(256) k_inner_sum(BoxSet<float> S, const int *__restrict__ active32,
+                                                   const int *__restrict__ cstart,
+                                                   int chunk_tiles,
+                                                   const double *__restrict__ partials,
+                                                   double *__restrict__ chunks)
+{
+    pdl_wait();
+    __shared__ double wsum[8];
+    const int c = blockIdx.x;
+    const int b = find_box(cstart, S.nbox, c);
+    if (!active32[S.boxes[b].box]) return;   // the whole CTA
+    const int *ts = S.tstart[TK_COARSE];
+    constexpr int W = kThreads / 32;   // partial sums per tile of the restriction
+    const int t0 = ts[b] + (c - cstart[b]) * chunk_tiles;
+    const int t1 = min(t0 + chunk_tiles, ts[b + 1]);
+    double v = 0.0;
+    for (long long q = (long long)t0 * W + threadIdx.x; q < (long long)t1 * W; q += 256)
+        v += partials[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += wsum[w];
+        chunks[c] = tot;
+    }
+}
+
 // Exit test of the inner FP32 cycles of a refinement step (mixed precision,
 // adaptive inner cycles).  The step solves A e = r32 with r32 = r_k / se
 // (||r_k|| = sr, so ||r32|| = sr / se); after its update x + se e the FP64
 // residual is se times the inner residual r32 - A e, up to FP32 rounding.
 // Per box still in the inner cycles: ||r32 - A e|| of the just smoothed
-// iterate (the red-children restriction's partial sums over the box's tiles,
-// in fixed order) against max(tol ||f|| / 2, floor_rel sr) / se: at or below
+// iterate (the red-children restriction's sums, per box and in fixed order:
+// its chunk sums) against max(tol ||f|| / 2, floor_rel sr) / se: at or below
 // it the update is expected to meet tol, or the step has gained the factor
 // floor_rel, and the box leaves the inner cycles of this step (active32 = 0).
 // floor_rel: the most one step asks of FP32 arithmetic.  One CTA per box;
 // coupled (the boxes of a level solved as one domain, whose norms and scales
 // are the domain's): one CTA, one decision for every box.
 __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__restrict__ active32,
-                                                      const double *__restrict__ partials,
+                                                      const int *__restrict__ cstart,
+                                                      const double *__restrict__ chunks,
                                                       const double *__restrict__ se,
                                                       const double *__restrict__ sr,
                                                       const double *__restrict__ normf,
@@ -1226,12 +1258,9 @@ __global__ void __launch_bounds__(1024) k_inner_judge(BoxSet<float> S, int *__re
     const int b = blockIdx.x;
     const int id = S.boxes[b].box;
     if (!active32[id]) return;   // the whole CTA
-    const int *ts = S.tstart[TK_COARSE];
-    constexpr int W = kThreads / 32;   // partial sums per tile of the restriction
-    const long long lo = coupled ? (long long)ts[0] * W : (long long)ts[b] * W;
-    const long long hi = coupled ? (long long)ts[S.nbox] * W : (long long)ts[b + 1] * W;
+    const int lo = coupled ? cstart[0] : cstart[b], hi = coupled ? cstart[S.nbox] : cstart[b + 1];
     double v = 0.0;
-    for (long long q = lo + threadIdx.x; q < hi; q += 1024) v += partials[q];
+    for (int q = lo + threadIdx.x; q < hi; q += 1024) v += chunks[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -2722,12 +2751,16 @@ cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cud
 }
 
 cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
+                               const int *cstart, int nchunks, int chunk_tiles, double *chunks,
                                const double *se, const double *sr, const double *normf,
                                const double *tol, double floor_rel, int coupled, cudaStream_t st)
 {
-    if (S.nbox == 0) return cudaSuccess;
+    if (S.nbox == 0 || nchunks == 0) return cudaSuccess;
+    cudaError_t e = pdl_launch(k_inner_sum, dim3(nchunks), dim3(256), 0, st, S, active32, cstart,
+                               chunk_tiles, partials, chunks);
+    if (e != cudaSuccess) return e;
     return pdl_launch(k_inner_judge, dim3(coupled ? 1 : S.nbox), dim3(1024), 0, st, S, active32,
-                      partials, se, sr, normf, tol, floor_rel, coupled);
+                      cstart, chunks, se, sr, normf, tol, floor_rel, coupled);
 }
 
 template <class T>

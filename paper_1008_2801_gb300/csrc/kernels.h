@@ -74,6 +74,7 @@ cudaError_t launch_resid_restrict_red(const BoxSet<T> &S, const int *active, cud
 // with partials; the start of a step's inner cycles (flags copied, counter
 // reset, loop condition set) and, in the graph WHILE form, the end of each.
 cudaError_t launch_inner_judge(const BoxSet<float> &S, int *active32, const double *partials,
+                               const int *cstart, int nchunks, int chunk_tiles, double *chunks,
                                const double *se, const double *sr, const double *normf,
                                const double *tol, double floor_rel, int coupled, cudaStream_t st);
 cudaError_t launch_inner_begin(int nbox, const int *src, int *dst, int *count,

@@ -101,6 +101,7 @@ constexpr int kCgPartials = 4096;
 constexpr int kInnerMax = 8;
 constexpr double kInnerFloor = 1e-6;
 constexpr int kInnerFixed = 2;   // inner cycles per step where the test is not available
+constexpr int kInnerChunk = 64;  // restriction tiles per first-stage sum of the exit test
 
 // ------------------------------------------------------------ building ----
 
@@ -919,18 +920,36 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     const size_t off_at = blob.put(s->off.data(), s->off.size() * sizeof(long long));
     std::vector<int> zeros(nbox, 0);
     const size_t side_at = blob.put(zeros.data(), zeros.size() * sizeof(int));
+    // adaptive inner cycles: chunks of kInnerChunk restriction tiles of one
+    // box each (the first stage of the exit test's sums), their start per box
+    size_t icst_at = 0;
+    if (s->inner_adapt) {
+        const SetPlan<Box<float>> *p0 = nullptr;
+        for (const auto &p : p32)
+            if (p.target == &s->h32.smooth[0]) p0 = &p;
+        const int nb = s->h32.smooth[0].nbox;
+        std::vector<int> ts(nb + 1), cst(nb + 1, 0);
+        memcpy(ts.data(), blob.bytes.data() + p0->ts_off[TK_COARSE], sizeof(int) * (nb + 1));
+        for (int b = 0; b < nb; ++b)
+            cst[b + 1] = cst[b] + (ts[b + 1] - ts[b] + kInnerChunk - 1) / kInnerChunk;
+        s->inner_chunks = cst[nb];
+        icst_at = blob.put(cst.data(), cst.size() * sizeof(int));
+    }
     e = dev_malloc(s, reinterpret_cast<void **>(&s->desc), blob.bytes.size());
     if (e != cudaSuccess) {
         solver_destroy(s);
         return set_error(MG_ERR_OOM, "cudaMalloc(descriptors): %s", cudaGetErrorString(e));
     }
-    if (s->inner_adapt) {   // the restriction's per-warp sums of the inner exit test
+    if (s->inner_adapt) {   // the restriction's per-warp sums and their chunk sums
         const size_t np = (size_t)s->h32.smooth[0].ntiles[TK_COARSE] * (kThreads / 32);
-        e = dev_malloc(s, reinterpret_cast<void **>(&s->ipart), np * sizeof(double));
+        e = dev_malloc(s, reinterpret_cast<void **>(&s->ipart),
+                       (np + (size_t)s->inner_chunks) * sizeof(double));
         if (e != cudaSuccess) {
             solver_destroy(s);
             return set_error(MG_ERR_OOM, "cudaMalloc(inner sums): %s", cudaGetErrorString(e));
         }
+        s->ichunk = s->ipart + np;
+        s->icstart = reinterpret_cast<const int *>(s->desc + icst_at);
     }
     if (periodic) {
         // the coarse jobs' exchange records, now that their address is known
@@ -1387,8 +1406,9 @@ static double *inner_partials(const Solver *, const Hier<double> &, int) { retur
 
 static cudaError_t inner_judge(Solver *s, const BoxSet<float> &S, cudaStream_t st)
 {
-    return launch_inner_judge(S, s->active, s->ipart, s->se, s->sr, s->dnormf, s->J.tol,
-                              kInnerFloor, s->coupled ? 1 : 0, st);
+    return launch_inner_judge(S, s->active, s->ipart, s->icstart, s->inner_chunks, kInnerChunk,
+                              s->ichunk, s->se, s->sr, s->dnormf, s->J.tol, kInnerFloor,
+                              s->coupled ? 1 : 0, st);
 }
 static cudaError_t inner_judge(Solver *, const BoxSet<double> &, cudaStream_t)
 {

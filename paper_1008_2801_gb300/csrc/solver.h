@@ -87,6 +87,9 @@ struct Solver {
     bool inner_while = false;      // enqueueing the device loop's body: inner cycles as a WHILE node
     int *icount = nullptr;         // [2] device: inner cycles run in this step, in this solve
     double *ipart = nullptr;       // device: per-warp sums of the finest FP32 restriction
+    double *ichunk = nullptr;      // device: their sums over chunks of tiles of one box
+    const int *icstart = nullptr;  // device [nbox + 1]: first chunk of each box of that set
+    int inner_chunks = 0;
     long long inner_cycle_kernels = 0;  // launches of one inner cycle in the WHILE form
     const long long *doff = nullptr;  // [nbox + 1] device copy of off
     int *dside = nullptr;          // [nbox] device: 1 if the solution ended in phi2
