@@ -49,7 +49,9 @@ L2_NOTE = "inputs larger than L2 (working set > 1 GB against 129 MB of L2)"
 # phi; the fused sweep reads phi, f and the three weights, computes 1/D from
 # the weights, and writes phi')
 BYTES_PER_CELL = {("sweep", 8): 48, ("sweep", 4): 24, ("pass", 8): 44, ("pass", 4): 22,
-                  ("restrict", 8): 41, ("restrict", 4): 20.5, ("refine", 8): 60}
+                  ("restrict", 8): 41, ("restrict", 4): 20.5, ("refine", 8): 60,
+                  # the first post-smoothing sweep also reads the coarse correction
+                  ("sweep_prolong", 4): 24.5}
 # FP64 flops per cell of one launch: a Gauss-Seidel update is 6 FMA + 1 mul =
 # 13 flop; a sweep updates every cell, a single-colour pass half; the
 # red-only restriction forms half the cells' residuals (7 FMA each); the
@@ -187,8 +189,9 @@ TRAFFIC_REGIONS = {
                       "// -------------------------------------- fused red+black sweep (z-march) ----"),
     "rbgs_sweep_f32": ("// -------------------------------------- fused red+black sweep (z-march) ----",
                        "// ------------------------------------------- residual + restriction ----"),
-    # the TMA-fed sweep is the whole of its own file
+    # the TMA-fed sweep is the whole of its own file (both variants)
     "rbgs_sweep_tma_f32": ("sweep_tma.cu", None),
+    "rbgs_sweep_tma_prol_f32": ("sweep_tma.cu", None),
     # the red-children residual + restriction (FP64; FP32 with the inner exit sums)
     "resid_restrict_f64": ("// ------------------------------------------- residual + restriction ----",
                            "// --------------------------------------------------------- prolongation ----"),
@@ -357,8 +360,8 @@ def run_gpu(args):
     # FP32 V-cycles per solve, from the finest level's smoothing launches of
     # the profiled steps (nu1 + nu2 = 4 sweeps a cycle; a cycle whose inner
     # exit test ends it after pre-smoothing counts one half)
-    nsm = finem["sweep"]["launches"] if "sweep" in finem else finem.get(
-        "pass", {"launches": 0})["launches"] / 2
+    nsm = (finem["sweep"]["launches"] + finem.get("sweep_prolong", {"launches": 0})["launches"]
+           if "sweep" in finem else finem.get("pass", {"launches": 0})["launches"] / 2)
     mixed = {"value": world * N / (msm / 1e3), "unit": "cells/s", "ms_per_step": msm,
              "refinement_steps": stm["cycles"],
              "fp32_vcycles_per_solve": round(nsm / 4 / max(args.steps, 1), 2),
@@ -376,6 +379,11 @@ def run_gpu(args):
                  "k_rbgs_sweep (FP32 fused red-black sweep, finest level, plain loads)")
         mixed["roofline"] = roofline(finem, "sweep", 4, kname,
                                      "rbgs_sweep_tma_f32" if tma else "rbgs_sweep_f32")
+    if "sweep_prolong" in finem:
+        mixed["roofline_sweep_with_prolongation"] = roofline(
+            finem, "sweep_prolong", 4, "k_rbgs_sweep_tma with the prolongation (the first "
+            "post-smoothing sweep, finest level: the coarse correction added to the neighbours "
+            "it reads)", "rbgs_sweep_tma_prol_f32")
     if "restrict" in finem:
         mixed["roofline_residual_restriction"] = roofline(
             finem, "restrict", 4, "k_resid_restrict_red<float> (residual of the red children, "

@@ -437,6 +437,8 @@ enum {
     MG_PROF_KRYLOV = 7,    /* krylov = 1: the CG vector updates and dot products */
     MG_PROF_LEVEL = 8,     /* persistent = 1: the finest level's persistent launches
                               (each a whole level sweep, down or up) */
+    MG_PROF_SWEEP_PROLONG = 9, /* finest level: the first post-smoothing fused sweep
+                              with the prolongation applied to what it reads */
     MG_PROF_NKIND = 16
 };
 typedef struct {

@@ -60,7 +60,7 @@ class mg_stats(ctypes.Structure):
 
 MG_PROF_NKIND = 16
 PROF_NAMES = ["sweep", "pass", "restrict", "prolong", "norm", "coarse", "refine", "krylov",
-              "level"]
+              "level", "sweep_prolong"]
 
 
 class mg_profile(ctypes.Structure):

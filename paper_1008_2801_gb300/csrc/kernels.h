@@ -31,22 +31,29 @@ cudaError_t launch_rbgs_pass_multi(const BoxSet<T> &S, const int *active, int co
                                    int from2, cudaStream_t st);
 
 // ---- FP32 fused sweep fed by the Tensor Memory Accelerator (sweep_tma.cu)
-struct SweepMaps;  // six tensor maps of one box level (device memory, 64-B aligned)
+struct SweepMaps;  // seven tensor maps of one box level (device memory, 128-B aligned)
 size_t sweep_maps_size();
 // The TMA sweep serves levels whose rows and planes hold a whole copy box.
 bool sweep_tma_fits(int nx, int ny);
+// The fused prolongation also needs the coarse level to hold its copy box.
+bool sweep_tma_prol_fits(int nx, int ny, int cx, int cy);
 // Encode the maps from the arrays' allocation bases (logical (0, 0, -1));
-// false if the driver offers no encoder.
+// phic_base (or null): the coarse level's phi, cx x cy x cz, for the fused
+// prolongation.  False if the driver offers no encoder or a box does not fit.
 bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_base,
                        const float *phi2_base, const float *f_base, const float *wx_base,
-                       const float *wy_base, const float *wz_base);
+                       const float *wy_base, const float *wz_base,
+                       const float *phic_base = nullptr, int cx = 0, int cy = 0, int cz = 0);
 int sweep_tma_ctas_per_sm();
 // Same result as launch_rbgs_sweep<float>; *err is set to 1 if a bounded
 // wait on a tile copy gave up after wait_polls polls (the CTA then waits,
 // with the default bound, for the copies it issued and stops).
+// prolong: first apply the level's prolongation phi += e(parent) (the coarse
+// correction in each box's phic) to the tiles read, as launch_prolong would
+// (maps encoded with the coarse level's phi).
 cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps,
                                   const int *active, int src_is_phi2, int *err, cudaStream_t st,
-                                  long long wait_polls);
+                                  long long wait_polls, bool prolong = false);
 // Polls of a tile-copy wait for mg_opts.wait_limit (0: the default bound;
 // -1: none, the first wait gives up).
 long long sweep_wait_polls(int wait_limit);

@@ -330,12 +330,19 @@ static long long coarse_limit(const mg_opts &o)
 
 // Tensor maps of every box of an FP32 level set (TMA sweep); false if the
 // driver cannot encode them.
+// TMA maps of a level's boxes; *prol: they also hold each box's coarse phi
+// (the fused prolongation), which every box's coarse level must allow.
 template <class T>
-static bool plan_maps(const std::vector<Box<T>> &set, DescBlob &blob, size_t *off)
+static bool plan_maps(const std::vector<Box<T>> &set, DescBlob &blob, size_t *off, bool *prol)
 {
+    *prol = false;
     if (sizeof(T) != sizeof(float)) return false;
-    for (const Box<T> &B : set)
+    bool cp = true;
+    for (const Box<T> &B : set) {
         if (!sweep_tma_fits(B.nx, B.ny)) return false;
+        cp = cp && B.phic && sweep_tma_prol_fits(B.nx, B.ny, B.nx / 2, B.ny / 2) &&
+             B.nz % 2 == 0;
+    }
     const size_t one = sweep_maps_size();
     std::vector<char> bytes(one * set.size() + 128);   // tensor maps are 128-byte aligned
     char *base = reinterpret_cast<char *>(round_up((long long)(uintptr_t)bytes.data(), 128));
@@ -343,11 +350,14 @@ static bool plan_maps(const std::vector<Box<T>> &set, DescBlob &blob, size_t *of
         const Box<T> &B = set[i];
         const long long Q = B.Q;
         auto lb = [&](const T *p) { return reinterpret_cast<const float *>(p - Q); };
+        const float *pc = cp ? reinterpret_cast<const float *>(B.phic - B.cQ) : nullptr;
         if (!encode_sweep_maps(reinterpret_cast<SweepMaps *>(base + i * one), B.nx, B.ny, B.nz,
-                               lb(B.phi), lb(B.phi2), lb(B.f), lb(B.wx), lb(B.wy), lb(B.wz)))
+                               lb(B.phi), lb(B.phi2), lb(B.f), lb(B.wx), lb(B.wy), lb(B.wz), pc,
+                               B.nx / 2, B.ny / 2, B.nz / 2))
             return false;
     }
     *off = blob.put(base, one * set.size(), 128);
+    *prol = cp;
     return true;
 }
 
@@ -388,6 +398,7 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
     plans.push_back(plan_set(blob, &H.bottom, bottom));
     H.fused.assign(H.smooth.size(), 0);
     H.maps.assign(H.smooth.size(), nullptr);
+    H.prol.assign(H.smooth.size(), 0);
     const bool tma = sizeof(T) == sizeof(float) && s->tma;
     const long long slots =
         (long long)s->sms * (tma ? sweep_tma_ctas_per_sm() : sweep_ctas_per_sm<T>());
@@ -416,8 +427,11 @@ static void plan_hier(Solver *s, Hier<T> &H, DescBlob &blob,
             H.fused[l] = small && sizeof(T) == sizeof(float) &&
                          (s->opts.smoother == 2 || (s->opts.smoother == 0 && ok));
             size_t moff = 0;
-            if (H.fused[l] && tma && s->tma && plan_maps(set, blob, &moff))
+            bool prol = false;
+            if (H.fused[l] && tma && s->tma && plan_maps(set, blob, &moff, &prol)) {
                 map_offs->push_back({l, moff});  // else: plain-load sweeps on this level
+                H.prol[l] = prol ? 1 : 0;
+            }
         }
         plans.push_back(plan_set(blob, &H.smooth[l], set));
     }
@@ -1297,18 +1311,20 @@ static void prof_collect(Solver *s)
 
 // ------------------------------------------------------------ the cycle ----
 
+// prolong: the TMA sweep applies the level's prolongation to what it reads
+// (only with maps that hold the coarse phi)
 static cudaError_t sweep_launch(Solver *s, const BoxSet<double> &S, const SweepMaps *,
-                                int src, cudaStream_t st)
+                                int src, cudaStream_t st, bool = false)
 {
     return launch_rbgs_sweep(S, s->active, src, st);
 }
 
 static cudaError_t sweep_launch(Solver *s, const BoxSet<float> &S, const SweepMaps *maps, int src,
-                                cudaStream_t st)
+                                cudaStream_t st, bool prolong = false)
 {
     if (maps)
         return launch_rbgs_sweep_tma(S, maps, s->active, src, s->derr, st,
-                                     sweep_wait_polls(s->opts.wait_limit));
+                                     sweep_wait_polls(s->opts.wait_limit), prolong);
     return launch_rbgs_sweep(S, s->active, src, st);
 }
 
@@ -1354,22 +1370,30 @@ static cudaError_t pass_launch(Solver *s, const BoxSet<T> &S, int color, cudaStr
 }
 
 // reverse: black before red in each sweep (single-colour passes only).
+// prolong_first: the first sweep also applies the level's prolongation
+// (fused TMA sweeps whose maps hold the coarse phi, nu >= 2).
 template <class T>
 static cudaError_t smooth(Solver *s, const BoxSet<T> &S, int nu, bool fine, bool fused,
                           const SweepMaps *maps, cudaStream_t st, int lvl = 0,
-                          bool reverse = false)
+                          bool reverse = false, bool prolong_first = false)
 {
     // one timed stretch per group of back-to-back launches, so that the
     // event records between launches do not count in each launch's time
     cudaError_t e = cudaSuccess;
     int left = nu;
     if (fused && !reverse && left >= 2) {
-        const int sl = fine ? prof_begin(s, MG_PROF_SWEEP, st, left / 2 * 2) : -1;
-        for (; left >= 2; left -= 2) {
-            for (int src = 0; src < 2; ++src)
-                if ((e = sweep_launch(s, S, maps, src, st)) != cudaSuccess) return e;
+        int nsw = left / 2 * 2;
+        if (prolong_first) {   // timed as its own class: it also does the prolongation
+            const int sl = fine ? prof_begin(s, MG_PROF_SWEEP_PROLONG, st) : -1;
+            if ((e = sweep_launch(s, S, maps, 0, st, true)) != cudaSuccess) return e;
+            prof_end(s, sl, st);
+            --nsw;
         }
+        const int sl = fine ? prof_begin(s, MG_PROF_SWEEP, st, nsw) : -1;
+        for (int i = prolong_first ? 1 : 0; i < left / 2 * 2; ++i)
+            if ((e = sweep_launch(s, S, maps, i & 1, st)) != cudaSuccess) return e;
         prof_end(s, sl, st);
+        left -= left / 2 * 2;
     }
     if (left > 0) {
         const int sl = fine ? prof_begin(s, MG_PROF_PASS, st, 2 * left) : -1;
@@ -1527,11 +1551,16 @@ static cudaError_t enqueue_vcycle(Solver *s, const Hier<T> &H, cudaStream_t st,
                 return e;
             continue;
         }
-        int sl = l == 0 ? prof_begin(s, MG_PROF_PROLONG, st) : -1;
-        if ((e = launch_prolong(S, s->active, st)) != cudaSuccess) return e;
-        prof_end(s, sl, st);
-        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, H.maps[l], st, l, sym)) !=
-            cudaSuccess)
+        // fused TMA sweeps whose maps hold the coarse phi take the
+        // prolongation into their first post-smoothing sweep
+        const bool fuse = H.fused[l] && H.maps[l] && H.prol[l] && !sym && s->opts.nu2 >= 2;
+        if (!fuse) {
+            int sl = l == 0 ? prof_begin(s, MG_PROF_PROLONG, st) : -1;
+            if ((e = launch_prolong(S, s->active, st)) != cudaSuccess) return e;
+            prof_end(s, sl, st);
+        }
+        if ((e = smooth(s, S, s->opts.nu2, l == 0, H.fused[l] != 0, H.maps[l], st, l, sym,
+                        fuse)) != cudaSuccess)
             return e;
     }
     prof_end(s, coarse, st);

@@ -30,6 +30,8 @@ struct Hier {
     std::vector<BoxSet<T>> smooth;              // [level]: boxes not yet at their bottom
     std::vector<char> fused;                    // [level]: smooth with fused sweeps
     std::vector<const SweepMaps *> maps;        // [level]: TMA maps of the level's boxes (or null)
+    std::vector<char> prol;                     // [level]: the maps hold the coarse phi (fused
+                                                //   prolongation in the first post-smoothing sweep)
     BoxSet<T> fine{};                           // level 0 of every box
     BoxSet<T> bottom{};                         // coarsest level of every box
     std::vector<int> lc;                        // [box] first level run by the coarse kernel

@@ -63,6 +63,13 @@ constexpr int kWyOff = kWxOff + pad128(kOpBytes);
 constexpr int kWzOff = kWyOff + pad128(kWyBytes);
 constexpr int kStageBytes = kWzOff + pad128(kOpBytes);
 constexpr unsigned kTxBytes = kSrcBytes + 3 * kOpBytes + kWyBytes;  // bytes landing per stage
+// With the prolongation fused (the first post-smoothing sweep): the coarse
+// correction under the phi tile, coarse columns x0/2 - 4 .. x0/2 + 35 and
+// rows y0/2 - 1 .. y0/2 + 4 of coarse plane p/2, after the stage's regions
+constexpr int kEcW = 40, kEcRows = kSweepTY / 2 + 2;
+constexpr int kEcOff = kStageBytes;
+constexpr int kEcBytes = kEcW * kEcRows * 4;
+constexpr int kStageBytesP = kEcOff + pad128(kEcBytes);
 constexpr int kRedSW = 2 * kTX + 2, kRedPlane = (kSweepTY + 2) * kRedSW;   // red ring, floats
 
 // NS stages in the ring; the plane loop is unrolled by NS, so that every
@@ -70,10 +77,11 @@ constexpr int kRedSW = 2 * kTX + 2, kRedPlane = (kSweepTY + 2) * kRedSW;   // re
 // least 4 slots (planes k, k-1 and k-2 are read while the next step writes
 // the fourth) and a slot count dividing the unroll.
 __host__ __device__ constexpr int red_slots(int ns) { return ns % 4 == 0 ? 4 : ns; }
-constexpr int smem_bytes(int ns)
+constexpr int smem_bytes(int ns, bool prol = false)
 {
-    return ns * kStageBytes + pad128(red_slots(ns) * kRedPlane * 4) + 128;
+    return ns * (prol ? kStageBytesP : kStageBytes) + pad128(red_slots(ns) * kRedPlane * 4) + 128;
 }
+
 // the configuration the library launches: 6 stages, 2 CTAs (24 warps) per SM
 constexpr int kStages = 6, kMinCtas = 2;
 
@@ -145,10 +153,11 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map)
 
 }  // namespace
 
-// Tensor maps of one box at one level: phi, phi2, f, wx, wy, wz (each
-// 128-byte aligned, as CUtensorMap is).
+// Tensor maps of one box at one level: phi, phi2, f, wx, wy, wz and the
+// coarse level's phi (the correction; absent where it is not encoded), each
+// 128-byte aligned, as CUtensorMap is.
 struct SweepMaps {
-    CUtensorMap m[6];
+    CUtensorMap m[7];
 };
 
 namespace {
@@ -178,16 +187,24 @@ __device__ __forceinline__ void unroll_steps(F &step, int kb, int z1)
     }
 }
 
-template <int NS, int MINB>
+// PROL: the level's prolongation phi += e(parent) (the coarse correction,
+// in the coarse level's phi) enters the sweep: each stage also holds the
+// coarse tile under its plane, and a red update adds a neighbour's parent
+// correction to the neighbour's staged value before using it, the FP32 sum
+// the prolongation kernel would have stored.  A red update reads only black
+// neighbours and a black update only the new red values, so the sweep's
+// result is bitwise that of prolongation then sweep; the level's phi in
+// memory stays unprolonged, which the out-of-place sweep never reads again.
+template <int NS, int MINB, bool PROL>
 __global__ void __launch_bounds__(kTmaThreads, MINB)
     k_rbgs_sweep_tma(BoxSet<float> S, const SweepMaps *__restrict__ maps,
                      const int *__restrict__ active, int src_is_phi2, int *__restrict__ err,
                      long long polls)
 {
-    constexpr int STG = kStageBytes / 4;   // stage stride, floats
+    constexpr int STG = (PROL ? kStageBytesP : kStageBytes) / 4;   // stage stride, floats
     constexpr int NR = red_slots(NS);
     constexpr int PHI = kSrcOff / 4, FF = kFOff / 4, WX = kWxOff / 4, WY = kWyOff / 4,
-                  WZ = kWzOff / 4, TW = kTileW, SW = kRedSW;
+                  WZ = kWzOff / 4, EC = kEcOff / 4, TW = kTileW, SW = kRedSW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -231,7 +248,7 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
         // producer: plane p goes to stage (p - pfirst) % NS; from plane
         // pfirst + NS on it waits until the consumers have released the stage
         if (lane == 0) {
-            for (int i = 0; i < 6; ++i) tensormap_acquire(&M.m[i]);
+            for (int i = 0; i < (PROL ? 7 : 6); ++i) tensormap_acquire(&M.m[i]);
             const CUtensorMap *msrc = &M.m[src_is_phi2 ? 1 : 0];
             int last = pfirst - 1;
             for (int p = pfirst; p <= plast; ++p) {
@@ -242,15 +259,20 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
                     break;
                 }
                 last = p;
-                unsigned char *base = smem + s * kStageBytes;
+                unsigned char *base = smem + s * (STG * 4);
                 const unsigned bar = smem_addr(&full[s]);
-                mbar_expect_tx(bar, kTxBytes);
+                mbar_expect_tx(bar, kTxBytes + (PROL ? kEcBytes : 0));
                 const int zt = p + 1;  // tensor z of logical plane p (guard plane first)
                 tma_load_3d(smem_addr(base + kSrcOff), msrc, bar, x0 - 4, y0 - 2, zt);
                 tma_load_3d(smem_addr(base + kFOff), &M.m[2], bar, x0 - 4, y0 - 1, zt);
                 tma_load_3d(smem_addr(base + kWxOff), &M.m[3], bar, x0 - 4, y0 - 1, zt);
                 tma_load_3d(smem_addr(base + kWyOff), &M.m[4], bar, x0 - 4, y0 - 1, zt);
                 tma_load_3d(smem_addr(base + kWzOff), &M.m[5], bar, x0 - 4, y0 - 1, zt);
+                // the coarse correction under plane p: coarse plane p >> 1
+                // (planes -1, -2: the coarse guard plane, zero)
+                if (PROL)
+                    tma_load_3d(smem_addr(base + kEcOff), &M.m[6], bar, x0 / 2 - 4, y0 / 2 - 1,
+                                (p >> 1) + 1);
             }
             // every copy issued has landed before this thread exits (the
             // earlier planes' stages were waited on before their reuse)
@@ -261,6 +283,7 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
         }
         return;
     }
+
 
     // consumers
     const int cw = warp - 1;           // 0..7 row warps, 8 / 9 ring rows, 10 ring column
@@ -274,6 +297,20 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
     int phiC[2], opC[2], ringC[2];
     bool valid[2];
     bool ractive;
+    // PROL: offsets in the coarse tile of the parents of the red cell's
+    // west, east, south and north neighbours and of its own column (the
+    // parent of its z neighbours, in their planes' tiles)
+    int eW[2], eE[2], eS[2], eN[2], eC[2];
+    auto ecoarse = [&](int x, int y) {
+        return ((y >> 1) - (y0 >> 1) + 1) * kEcW + (x >> 1) - (x0 >> 1) + 4;
+    };
+    auto parents = [&](int q, int x, int y) {
+        eW[q] = ecoarse(x - 1, y);
+        eE[q] = ecoarse(x + 1, y);
+        eS[q] = ecoarse(x, y - 1);
+        eN[q] = ecoarse(x, y + 1);
+        eC[q] = ecoarse(x, y);
+    };
     if (!colw) {
         const int y = own ? y0 + cw : cw == kSweepTY ? y0 - 1 : y0 + kSweepTY;
         const int srow = own ? cw + 1 : cw == kSweepTY ? 0 : kSweepTY + 1;
@@ -284,6 +321,7 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
             opC[q] = (y - y0 + 1) * TW + (x - x0 + 4);
             ringC[q] = srow * SW + x - x0 + 1;
             valid[q] = y >= 0 && y < ny && x < nx;
+            parents(q, x, y);
         }
         ractive = true;
     } else {
@@ -295,6 +333,7 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
             opC[q] = (yy - y0 + 1) * TW + (xc - x0 + 4);
             ringC[q] = (yy - y0 + 1) * SW + xc - x0 + 1;
             valid[q] = lane < kSweepTY && xc >= 0 && xc < nx && yy < ny;
+            parents(q, xc, yy);
         }
         ractive = lane < kSweepTY;
     }
@@ -324,10 +363,19 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
             const int c = q ? phiC[1] : phiC[0];
             const int o = q ? opC[1] : opC[0];
             const bool v = (q ? valid[1] : valid[0]) && k >= 0 && k < nz;
-            const float val = red_update(
-                S0[PHI + c - 1], S0[PHI + c + 1], S0[PHI + c - TW], S0[PHI + c + TW],
-                SM_[PHI + c], SP[PHI + c], S0[WX + o], S0[WX + o + 1], S0[WY + o],
-                S0[WY + o + TW], S0[WZ + o], SP[WZ + o], S0[FF + o]);
+            float nw = S0[PHI + c - 1], ne = S0[PHI + c + 1], ns = S0[PHI + c - TW],
+                  nn = S0[PHI + c + TW], nd = SM_[PHI + c], nu = SP[PHI + c];
+            if (PROL) {   // the neighbours as the prolongation leaves them
+                nw += S0[EC + (q ? eW[1] : eW[0])];
+                ne += S0[EC + (q ? eE[1] : eE[0])];
+                ns += S0[EC + (q ? eS[1] : eS[0])];
+                nn += S0[EC + (q ? eN[1] : eN[0])];
+                nd += SM_[EC + (q ? eC[1] : eC[0])];
+                nu += SP[EC + (q ? eC[1] : eC[0])];
+            }
+            const float val = red_update(nw, ne, ns, nn, nd, nu, S0[WX + o], S0[WX + o + 1],
+                                         S0[WY + o], S0[WY + o + TW], S0[WZ + o], SP[WZ + o],
+                                         S0[FF + o]);
             R0[q ? ringC[1] : ringC[0]] = v ? val : 0.f;
         }
         named_barrier(1, 32 * kConsumers);
@@ -368,7 +416,8 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
         if (lane == 0) mbar_arrive(smem_addr(&empty[sM]));
     };
     // the first step also needs planes pfirst and pfirst + 1
-    if (!(mbar_wait(smem_addr(&full[0]), 0u, polls) && mbar_wait(smem_addr(&full[1]), 0u, polls)) &&
+    if (!(mbar_wait(smem_addr(&full[0]), 0u, polls) &&
+          mbar_wait(smem_addr(&full[1]), 0u, polls)) &&
         lane == 0)
         atomicExch(err, 1);
     for (int kb = z0 - 1; kb <= z1; kb += NS, gdst += NS * Q)
@@ -398,32 +447,50 @@ EncodeTiledFn encoder()
 
 }  // namespace
 
-// Encode the six maps of a box level (arrays given by their allocation
-// base = logical (0, 0, -1)).  Returns false if the driver cannot.
+// Encode the maps of a box level (arrays given by their allocation base =
+// logical (0, 0, -1)): phi, phi2, f, wx, wy, wz, and with phic_base the
+// coarse level's phi (cx x cy x cz cells) for the fused prolongation.
+// Returns false if the driver cannot (or a box does not fit).
 bool encode_sweep_maps(SweepMaps *out, int nx, int ny, int nz, const float *phi_base,
                        const float *phi2_base, const float *f_base, const float *wx_base,
-                       const float *wy_base, const float *wz_base)
+                       const float *wy_base, const float *wz_base, const float *phic_base,
+                       int cx, int cy, int cz)
 {
     EncodeTiledFn fn = encoder();
     if (!fn) return false;
-    const long long P = pitch_row(nx), Q = pitch_plane(nx, ny);
     if (!sweep_tma_fits(nx, ny)) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)(ny + 1), (cuuint64_t)(nz + 2)};
-    const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)Q * 4};
     const cuuint32_t ones[3] = {1, 1, 1};
+    auto enc = [&](CUtensorMap *m, const float *base, int mx, int my, int mz,
+                   const cuuint32_t *box) {
+        const long long P = pitch_row(mx), Q = pitch_plane(mx, my);
+        const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)(my + 1), (cuuint64_t)(mz + 2)};
+        const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)Q * 4};
+        return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
+                  strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
     const cuuint32_t box_src[3] = {kTileW, kSrcRows, 1};
     const cuuint32_t box_op[3] = {kTileW, kOpRows, 1};
     const cuuint32_t box_wy[3] = {kTileW, kWyRows, 1};
     const float *base[6] = {phi_base, phi2_base, f_base, wx_base, wy_base, wz_base};
     const cuuint32_t *box[6] = {box_src, box_src, box_op, box_op, box_wy, box_op};
-    for (int i = 0; i < 6; ++i) {
-        CUresult r = fn(&out->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                        const_cast<float *>(base[i]), dims, strides, box[i], ones,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return false;
+    for (int i = 0; i < 6; ++i)
+        if (!enc(&out->m[i], base[i], nx, ny, nz, box[i])) return false;
+    memset(&out->m[6], 0, sizeof(CUtensorMap));
+    if (phic_base) {
+        if (!sweep_tma_prol_fits(nx, ny, cx, cy)) return false;
+        const cuuint32_t box_ec[3] = {kEcW, kEcRows, 1};
+        if (!enc(&out->m[6], phic_base, cx, cy, cz, box_ec)) return false;
     }
     return true;
+}
+
+// The fused prolongation reads a 40 x 6 coarse tile: the coarse rows and
+// planes hold it, and the level is twice the coarse one in x and y.
+bool sweep_tma_prol_fits(int nx, int ny, int cx, int cy)
+{
+    return nx == 2 * cx && ny == 2 * cy && pitch_row(cx) >= kEcW && cy + 1 >= kEcRows;
 }
 
 size_t sweep_maps_size() { return sizeof(SweepMaps); }
@@ -432,7 +499,7 @@ size_t sweep_maps_size() { return sizeof(SweepMaps); }
 // that two CTAs fit on an SM.  Function attributes are per device: they
 // are set once on each device, the first time a launch or an occupancy
 // query runs with that device current.
-template <int NS, int MINB>
+template <int NS, int MINB, bool PROL>
 static void set_smem_attributes()
 {
     constexpr int kMaxDevices = 64;
@@ -445,9 +512,9 @@ static void set_smem_attributes()
     }
     std::lock_guard<std::mutex> lk(mu);
     if (dev >= 0 && done[dev]) return;
-    cudaFuncSetAttribute(k_rbgs_sweep_tma<NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_bytes(NS));
-    cudaFuncSetAttribute(k_rbgs_sweep_tma<NS, MINB>,
+    cudaFuncSetAttribute(k_rbgs_sweep_tma<NS, MINB, PROL>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(NS, PROL));
+    cudaFuncSetAttribute(k_rbgs_sweep_tma<NS, MINB, PROL>,
                          cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     if (dev >= 0) done[dev] = true;
@@ -459,8 +526,8 @@ bool sweep_tma_fits(int nx, int ny) { return pitch_row(nx) >= kTileW && ny + 1 >
 int sweep_tma_ctas_per_sm()
 {
     int n = 0;
-    set_smem_attributes<kStages, kMinCtas>();
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep_tma<kStages, kMinCtas>,
+    set_smem_attributes<kStages, kMinCtas, false>();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rbgs_sweep_tma<kStages, kMinCtas, false>,
                                                       kTmaThreads,
                                                       smem_bytes(kStages)) != cudaSuccess) {
         cudaGetLastError();
@@ -475,13 +542,21 @@ long long sweep_wait_polls(int wait_limit)
 }
 
 cudaError_t launch_rbgs_sweep_tma(const BoxSet<float> &S, const SweepMaps *maps, const int *active,
-                                  int src_is_phi2, int *err, cudaStream_t st, long long wait_polls)
+                                  int src_is_phi2, int *err, cudaStream_t st, long long wait_polls,
+                                  bool prolong)
 {
     if (S.ntiles[TK_SWEEP] == 0) return cudaSuccess;
-    set_smem_attributes<kStages, kMinCtas>();
-    k_rbgs_sweep_tma<kStages, kMinCtas>
-        <<<S.ntiles[TK_SWEEP], kTmaThreads, smem_bytes(kStages), st>>>(S, maps, active,
-                                                                      src_is_phi2, err, wait_polls);
+    if (prolong) {
+        set_smem_attributes<kStages, kMinCtas, true>();
+        k_rbgs_sweep_tma<kStages, kMinCtas, true>
+            <<<S.ntiles[TK_SWEEP], kTmaThreads, smem_bytes(kStages, true), st>>>(
+                S, maps, active, src_is_phi2, err, wait_polls);
+    } else {
+        set_smem_attributes<kStages, kMinCtas, false>();
+        k_rbgs_sweep_tma<kStages, kMinCtas, false>
+            <<<S.ntiles[TK_SWEEP], kTmaThreads, smem_bytes(kStages), st>>>(
+                S, maps, active, src_is_phi2, err, wait_polls);
+    }
     return cudaGetLastError();
 }
 
