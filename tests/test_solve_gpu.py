@@ -173,14 +173,18 @@ def test_device_loop_matches_host_loop(cuda_device, precision, max_cycles):
     assert sa["cycles"] == sb["cycles"] and sa["hist"] == sb["hist"]
 
 
-def test_batched_device_loop_matches_host_loop(cuda_device):
-    d = inputs.batched(6, 41, sizes=(8, 12, 16, 24), dx=1 / 32)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_device_loop_matches_host_loop(cuda_device, precision):
+    # mixed: the boxes leave each step's adaptive inner cycles at their own
+    # cycle, inside a nested graph loop on the device and after host reads
+    # of the inner flags on the host; the same bits either way
+    d = inputs.batched(6, 41, sizes=(8, 12, 16, 24, 64, 96), dx=1 / 32)
     shapes = [tuple(int(v) for v in dims[::-1]) for dims in d["dims"]]
     bp = _dev(np.concatenate([b.ravel() for b in d["beta"]]), cuda_device)
     fp = _dev(np.concatenate([x.ravel() for x in d["f"]]), cuda_device)
     res = []
     for prof in (False, True):
-        bs = BatchSolver(shapes, d["dx"], device=cuda_device)
+        bs = BatchSolver(shapes, d["dx"], precision=precision, device=cuda_device)
         bs.profile(prof)
         bs.set_beta(bp)
         phi, sts = bs.solve(fp)
