@@ -93,6 +93,17 @@ int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const
                          const float *f, const float *phi_in, float *phi_out, int zc,
                          void *stream);
 
+/* The TMA-fed sweep with the level's prolongation fused (the V-cycle's
+ * first post-smoothing sweep): the result is bitwise that of
+ * mg_op_prolong_add(phic, phi_in) followed by mg_op_rbgs_sweep_tma, but
+ * phi_in is left as it is.  phic: the coarse level's phi (n / 2 cells, level
+ * layout); n must be even.  Same errors as mg_op_rbgs_sweep_tma, and
+ * UNSUPPORTED if the coarse level is too small for its copy box (n / 2 >= 32
+ * in x, >= 5 in y). */
+int mg_op_rbgs_sweep_tma_prolong(const int n[3], const float *wx, const float *wy,
+                                 const float *wz, const float *f, const float *phic,
+                                 const float *phi_in, float *phi_out, int zc, void *stream);
+
 /* In the residual stages below, D (nullable) is the stored diagonal of
  * mg_op_inv_diag in the stage precision; when NULL it is summed from the six
  * weights of each cell. */

@@ -131,6 +131,7 @@ _SIGS = {
     "mg_op_rbgs_pass": (c_int, [c_int, c_int3] + [c_void_p] * 6 + [c_int, c_void_p]),
     "mg_op_rbgs_sweep": (c_int, [c_int, c_int3] + [c_void_p] * 6 + [c_int, c_void_p]),
     "mg_op_rbgs_sweep_tma": (c_int, [c_int3] + [c_void_p] * 6 + [c_int, c_void_p]),
+    "mg_op_rbgs_sweep_tma_prolong": (c_int, [c_int3] + [c_void_p] * 7 + [c_int, c_void_p]),
     "mg_op_residual": (c_int, [c_int, c_int3] + [c_void_p] * 8),
     "mg_op_residual_restrict": (c_int, [c_int, c_int3] + [c_void_p] * 9),
     "mg_op_residual_restrict_red": (c_int, [c_int, c_int3] + [c_void_p] * 9),

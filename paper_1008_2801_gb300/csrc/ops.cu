@@ -203,22 +203,34 @@ int mg_op_rbgs_sweep(int prec, const int n[3], const void *wx, const void *wy, c
     });
 }
 
-int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const float *wz,
-                         const float *f, const float *phi_in, float *phi_out, int zc,
-                         void *stream)
+// The TMA sweep through a one-box set; phic (or null): the coarse level's
+// phi, for the fused prolongation.
+static int sweep_tma_op(const int n[3], const float *wx, const float *wy, const float *wz,
+                        const float *f, const float *phic, const float *phi_in, float *phi_out,
+                        int zc, void *stream)
 {
     if (bad_dims(n) || !wx || !wy || !wz || !f || !phi_in || !phi_out ||
-        phi_in == phi_out)
-        return set_error(MG_ERR_INVALID_ARG, "bad argument (phi_in and phi_out must differ)");
+        phi_in == phi_out || (phic && !all_even(n)))
+        return set_error(MG_ERR_INVALID_ARG,
+                         "bad argument (phi_in and phi_out must differ; with phic n even)");
     cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
+    const int c[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
     Box<float> B = level_box<float>(n, wx, wy, wz, nullptr, f, phi_in, phi_out);
     B.zc = zc > 0 ? zc : kSweepZ;
+    if (phic) {
+        B.phic = logical<float>(phic, c);
+        B.cP = (int)pitch_row(c[0]);
+        B.cQ = pitch_plane(c[0], c[1]);
+    }
     std::vector<char> host(sweep_maps_size() + 128);   // tensor maps are 128-byte aligned
     SweepMaps *m = reinterpret_cast<SweepMaps *>(round_up((long long)(uintptr_t)host.data(), 128));
     if (!sweep_tma_fits(n[0], n[1]))
         return set_error(MG_ERR_UNSUPPORTED, "level too small for the TMA sweep (nx >= 64, ny >= 11)");
-    if (!encode_sweep_maps(m, n[0], n[1], n[2], phi_in, phi_out, f, wx, wy, wz))
+    if (phic && !sweep_tma_prol_fits(n[0], n[1], c[0], c[1]))
+        return set_error(MG_ERR_UNSUPPORTED, "coarse level too small for its copy box");
+    if (!encode_sweep_maps(m, n[0], n[1], n[2], phi_in, phi_out, f, wx, wy, wz, phic, c[0], c[1],
+                           c[2]))
         return set_error(MG_ERR_UNSUPPORTED, "tensor maps cannot be encoded on this driver");
     TempSet<float> ts;
     int rc = ts.make(B, st);
@@ -229,13 +241,28 @@ int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const
     CKO(cudaMemcpyAsync(dev, m, sweep_maps_size(), cudaMemcpyHostToDevice, st));
     CKO(cudaMemsetAsync(err, 0, sizeof(int), st));
     CKO(launch_rbgs_sweep_tma(ts.S, reinterpret_cast<const SweepMaps *>(dev), nullptr, 0, err, st,
-                              sweep_wait_polls(0)));
+                              sweep_wait_polls(0), phic != nullptr));
     int herr = 0;
     CKO(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKO(cudaStreamSynchronize(st));
     CKO(cudaFreeAsync(dev, st));
     if (herr) return set_error(MG_ERR_TIMEOUT, "a tile-copy wait gave up");
     return MG_OK;
+}
+
+int mg_op_rbgs_sweep_tma(const int n[3], const float *wx, const float *wy, const float *wz,
+                         const float *f, const float *phi_in, float *phi_out, int zc,
+                         void *stream)
+{
+    return sweep_tma_op(n, wx, wy, wz, f, nullptr, phi_in, phi_out, zc, stream);
+}
+
+int mg_op_rbgs_sweep_tma_prolong(const int n[3], const float *wx, const float *wy,
+                                 const float *wz, const float *f, const float *phic,
+                                 const float *phi_in, float *phi_out, int zc, void *stream)
+{
+    if (!phic) return set_error(MG_ERR_INVALID_ARG, "bad argument (phic)");
+    return sweep_tma_op(n, wx, wy, wz, f, phic, phi_in, phi_out, zc, stream);
 }
 
 int mg_op_residual(int prec, const int n[3], const void *wx, const void *wy, const void *wz,

@@ -125,6 +125,18 @@ def rbgs_sweep_tma(w, f, phi_in, shape, phi_out=None, zc=0):
     return phi_out
 
 
+def rbgs_sweep_tma_prolong(w, f, phic, phi_in, shape, phi_out=None, zc=0):
+    """The TMA sweep with the prolongation phi_in += phic(parent) fused
+    (phi_in itself left unchanged)."""
+    if phi_out is None:
+        phi_out = torch.zeros_like(phi_in)
+    check(_lib.load().mg_op_rbgs_sweep_tma_prolong(_n(shape), *map(_p, w), _p(f), _p(phic),
+                                                   _p(phi_in), _p(phi_out), int(zc),
+                                                   _s(phi_in)),
+          "mg_op_rbgs_sweep_tma_prolong")
+    return phi_out
+
+
 def residual(w, f, phi, shape, D=None):
     r = torch.zeros_like(phi)
     check(_lib.load().mg_op_residual(_PREC[phi.dtype], _n(shape), *map(_p, w), _p(D), _p(f),

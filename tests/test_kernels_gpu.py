@@ -232,6 +232,34 @@ def test_tma_sweep_is_bitwise_the_plain_sweep(cuda_device, shape, zc):
     assert not full[0].any() and not full[-1].any() and not full[:, :, shape[2]:].any()
 
 
+@pytest.mark.parametrize("zc", [0, 3, 8])
+@pytest.mark.parametrize("shape", [(12, 12, 64), (70, 20, 130), (34, 40, 136)])
+def test_tma_sweep_with_prolongation_is_prolongation_then_sweep(cuda_device, shape, zc):
+    # the fused form adds each red update's neighbours' parent corrections to
+    # their staged values: bitwise the prolongation kernel followed by the
+    # sweep, and phi_in itself stays unprolonged
+    beta, f, phi, h = _case(shape, 15)
+    w, _ = _weights(beta, h, shape, cuda_device, torch.float32)
+    ft = _level(shape, f, cuda_device, torch.float32)
+    pin = _level(shape, phi, cuda_device, torch.float32)
+    c = tuple(s // 2 for s in shape)
+    e = np.random.default_rng(16).uniform(-1, 1, c).astype(np.float32)
+    pc = _level(c, e, cuda_device, torch.float32)
+    before = pin.clone()
+    fused = K.rbgs_sweep_tma_prolong(w, ft, pc, pin, shape, zc=zc)
+    assert torch.equal(pin, before)
+    prolonged = K.prolong_add(pc, pin.clone(), shape)
+    want = K.rbgs_sweep(w, ft, prolonged, shape, zc=zc)
+    assert torch.equal(fused, want)
+    # against the oracle: a red-black sweep of the prolonged iterate
+    faces = O.face_beta(beta)
+    up = phi.astype(np.float64) + np.repeat(np.repeat(np.repeat(e, 2, 0), 2, 1), 2, 2)
+    ref = O.rbgs_pass(faces, h, f, O.rbgs_pass(faces, h, f, up, 0), 1)
+    got = K.get(fused, shape).cpu().double().numpy()
+    scale = np.max(np.abs(ref)) + np.max(np.abs(f)) * h * h / np.min(faces[0])
+    assert np.max(np.abs(got - ref)) <= _tol(torch.float32) * scale
+
+
 @pytest.mark.parametrize("stored_diag", [False, True])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("shape", SHAPES)
