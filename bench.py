@@ -397,6 +397,7 @@ def run_gpu(args):
     # end to end through the C ABI with host (pinned) buffers
     se = Solver((n, n, n), d["dx"], precision="fp64", device=dev)
     tot = tset = 0.0
+    per_step = []
     for it in range(warm + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -407,6 +408,7 @@ def run_gpu(args):
         if it >= warm:
             tot += t1 - t0
             tset += ts - t0
+            per_step.append((t1 - t0) * 1e3)
     e2e_ms = max_over_ranks(tot / args.steps * 1e3, dev)
     se.close()
     del bh, fh, ph
@@ -414,7 +416,10 @@ def run_gpu(args):
            "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N,
            "path": "mg_set_beta + mg_solve_ex (MG_ZERO_GUESS), FP64, on pinned host buffers "
                    "(beta and f copied in, phi out, inside the calls)",
-           "host_ms_in_set_beta_call": round(tset / args.steps * 1e3, 3)}
+           "host_ms_in_set_beta_call": round(tset / args.steps * 1e3, 3),
+           "step_ms": {"min": round(min(per_step), 2),
+                       "median": round(sorted(per_step)[len(per_step) // 2], 2),
+                       "max": round(max(per_step), 2)}}
 
     out = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
            "steps": args.steps, "warmup": warm, "ms_per_step": ms_max,
