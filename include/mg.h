@@ -185,7 +185,13 @@ typedef struct {
     int level_ctas;   /* persistent = 1: CTAs per SM of the persistent
                          launches.  0 (default): as many as can be
                          resident; n in 1..64: at most n */
-    int reserved[2];
+    int fp32_setup;   /* MG_MIXED on independent boxes: 0 (default): the
+                         finest level's FP32 weights are its FP64 ones rounded,
+                         every coarser level is set up in FP32 only (averages
+                         of the finer FP32 weights, 1/D from its own), since
+                         the FP64 levels below the finest are never read;
+                         1: every level is set up in FP64 and rounded */
+    int reserved;
     /* Device memory of the context (its arena, launch descriptors and host
      * staging buffers) comes from dev_alloc(bytes, alloc_user) when set (NULL
      * on failure: MG_ERR_OOM) and goes back through dev_free(ptr,
@@ -205,7 +211,7 @@ typedef struct {
     double rel_resid0;         /* ||f - A phi0|| / ||f|| before the first cycle */
     double rel_resid;          /* ||f - A phi|| / ||f|| at return */
     double hist[MG_MAX_HIST];  /* rel_resid after cycle c (hist[0] = rel_resid0) */
-    float t_setup_ms;          /* mg_set_beta wall time of the last set-up */
+    float t_setup_ms;          /* device time of the last mg_set_beta set-up on its stream */
     float t_solve_ms;          /* wall time of this call */
     double rel_resid_max;      /* max |f - A phi| / max |f| at return (opts.max_norm = 1;
                                   else 0) */

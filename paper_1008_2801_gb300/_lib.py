@@ -47,7 +47,7 @@ class mg_opts(ctypes.Structure):
                 ("inner_cycles", c_int), ("full_residual", c_int), ("tma", c_int),
                 ("krylov", c_int), ("max_norm", c_int), ("wait_limit", c_int),
                 ("persistent", c_int), ("sweep_zc", c_int), ("level_ctas", c_int),
-                ("reserved", c_int * 2),
+                ("fp32_setup", c_int), ("reserved", c_int),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_user", c_void_p)]
 
 

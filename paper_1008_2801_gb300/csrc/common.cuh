@@ -201,6 +201,11 @@ struct SetupBox {
     const double *betaL;                // coupled level 0: beta in the level layout, guards
                                         // holding the neighbour box's beta or -1 (no neighbour)
     int par, rb;                        // colour parity; invD and D colour-split (split_at)
+    // mixed precision with the coarser FP32 levels averaged in FP32: the
+    // next-coarser level's FP32 weights, and w32src = 1 when the bottom
+    // inverse assembles from the FP32 weights
+    float *cwx32, *cwy32, *cwz32;
+    int w32src;
 };
 typedef DescSet<SetupBox> SetupSet;
 

@@ -145,6 +145,12 @@ __device__ __forceinline__ double normal_f32_to_f64(float x)
                             (int)(b << 29));
 }
 
+// The conversion instruction for the values the integer path below leaves
+// out (zero, subnormal results, overflow, infinity, NaN): a call, so that the
+// compiler cannot run it under a predicate for every value, which would put
+// one FP64-pipe conversion into each call of f64_to_f32_rn.
+__device__ __noinline__ float f64_to_f32_by_cvt(double x) { return __double2float_rn(x); }
+
 // the float nearest to x, ties to even (IEEE round-to-nearest)
 __device__ __forceinline__ float f64_to_f32_rn(double x)
 {
@@ -152,7 +158,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x)
     const unsigned h = hi & 0x7fffffffu;
     // biased exponent 897..1150: FP32 exponent 1..254 (a round-up out of 254
     // carries into the exponent and gives infinity, as the rounding does)
-    if (h - (897u << 20) >= (254u << 20)) return __double2float_rn(x);
+    if (h - (897u << 20) >= (254u << 20)) return f64_to_f32_by_cvt(x);
     unsigned m = ((h - (896u << 20)) << 3) | (lo >> 29);   // truncated to 23 fraction bits
     const unsigned rest = lo & 0x1fffffffu;                 // the 29 bits dropped
     m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
@@ -778,14 +784,14 @@ __global__ void __launch_bounds__(1024) k_norm_finish(BoxSet<T> S, const int *__
                                                       double *__restrict__ out,
                                                       double *__restrict__ copy,
                                                       double *__restrict__ inv,
-                                                      const double *__restrict__ mult, int kind)
+                                                      const double *__restrict__ mult,
+                                                      const int *__restrict__ ts)
 {
     pdl_wait();
     __shared__ double wsum[32];
     const int b = blockIdx.x;
     const Box<T> &B = S.boxes[b];
     if (active && !active[B.box]) return;
-    const int *ts = S.tstart[kind];
     const int lo = ts[b], hi = ts[b + 1];
     double s = 0.0;
     for (int q = lo + (int)threadIdx.x; q < hi; q += 1024) s += partials[q];
@@ -1425,25 +1431,41 @@ __device__ __forceinline__ void face_weights_level_at(int nx, int ny, int nz, in
 
 // Coarse position (I, J, K) in [0, cx] x [0, cy] x [0, cz]; coarse face
 // beta = mean of the 4 fine faces, coarse h = 2h: w_c = (sum of 4 w) / 16.
+template <class T>
 __device__ __forceinline__ void coarsen_at(int nx, int ny, int nz, int P, long long Q,
-                                           const double *__restrict__ wx,
-                                           const double *__restrict__ wy,
-                                           const double *__restrict__ wz, int cP, long long cQ,
-                                           double *cwx, double *cwy, double *cwz, int I, int J,
-                                           int K)
+                                           const T *__restrict__ wx, const T *__restrict__ wy,
+                                           const T *__restrict__ wz, int cP, long long cQ,
+                                           T *cwx, T *cwy, T *cwz, int I, int J, int K)
 {
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
     auto at = [&](int i, int j, int k) { return (long long)k * Q + (long long)j * P + i; };
     const long long cq = (long long)K * cQ + (long long)J * cP + I;
+    const T q = T(0.0625);
     if (J < cy && K < cz)
         cwx[cq] = (wx[at(2 * I, 2 * J, 2 * K)] + wx[at(2 * I, 2 * J + 1, 2 * K)] +
-                   wx[at(2 * I, 2 * J, 2 * K + 1)] + wx[at(2 * I, 2 * J + 1, 2 * K + 1)]) * 0.0625;
+                   wx[at(2 * I, 2 * J, 2 * K + 1)] + wx[at(2 * I, 2 * J + 1, 2 * K + 1)]) * q;
     if (I < cx && K < cz)
         cwy[cq] = (wy[at(2 * I, 2 * J, 2 * K)] + wy[at(2 * I + 1, 2 * J, 2 * K)] +
-                   wy[at(2 * I, 2 * J, 2 * K + 1)] + wy[at(2 * I + 1, 2 * J, 2 * K + 1)]) * 0.0625;
+                   wy[at(2 * I, 2 * J, 2 * K + 1)] + wy[at(2 * I + 1, 2 * J, 2 * K + 1)]) * q;
     if (I < cx && J < cy)
         cwz[cq] = (wz[at(2 * I, 2 * J, 2 * K)] + wz[at(2 * I + 1, 2 * J, 2 * K)] +
-                   wz[at(2 * I, 2 * J + 1, 2 * K)] + wz[at(2 * I + 1, 2 * J + 1, 2 * K)]) * 0.0625;
+                   wz[at(2 * I, 2 * J + 1, 2 * K)] + wz[at(2 * I + 1, 2 * J + 1, 2 * K)]) * q;
+}
+
+// ---- mixed precision's coarser FP32 levels, averaged in FP32
+//
+// Only the finest level's FP32 weights (the rounded FP64 ones) and the
+// coarser FP32 levels are read by mixed precision's cycles: the coarser
+// levels are averaged from the finer FP32 weights (coarsen_at<float>) and
+// take their FP32 1/D from their own weights, with no FP64 coarse level.
+
+// FP32 1/D of cell c from the level's FP32 weights.
+__device__ __forceinline__ void inv_diag32_at(int P, long long Q, const float *__restrict__ wx,
+                                              const float *__restrict__ wy,
+                                              const float *__restrict__ wz, float *invD,
+                                              long long c)
+{
+    invD[c] = 1.0f / (((wx[c] + wx[c + 1]) + (wy[c] + wy[c + P])) + (wz[c] + wz[c + Q]));
 }
 
 template <bool W32 = false>
@@ -1522,19 +1544,19 @@ constexpr int kPackedBottomBytes = 200 * 1024;
 // from `at` on (the box's cells in C order): diagonal = sum of the six
 // weights, -w to each later neighbour inside the box (the earlier ones are
 // the mirrors).  Called by every thread of the CTA.
-template <class S>
+template <class S, class W>
 __device__ __forceinline__ void assemble_box_block(int nx, int ny, int nz, int P, long long Q,
-                                                   const double *__restrict__ wx,
-                                                   const double *__restrict__ wy,
-                                                   const double *__restrict__ wz, S a, int at)
+                                                   const W *__restrict__ wx,
+                                                   const W *__restrict__ wy,
+                                                   const W *__restrict__ wz, S a, int at)
 {
     using R = typename std::remove_reference<decltype(*a.a)>::type;
     const int m = nx * ny * nz;
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
         const int i = r % nx, j = (r / nx) % ny, k = r / (nx * ny);
         const long long c = (long long)k * Q + (long long)j * P + i;
-        const double ww = wx[c], we = wx[c + 1], ws = wy[c], wn = wy[c + P], wd = wz[c],
-                     wu = wz[c + Q];
+        const W ww = wx[c], we = wx[c + 1], ws = wy[c], wn = wy[c + P], wd = wz[c],
+                wu = wz[c + Q];
         R *row = a.row(at + r);
         row[0] = (R)(((ww + we) + (ws + wn)) + (wd + wu));
         if (i < nx - 1) row[1] = (R)-we;
@@ -1551,11 +1573,11 @@ __device__ __forceinline__ void gauss_jordan_cta(S a, int n, bool singular, doub
 // its rounding to inv32; float, when no FP64 inverse is wanted: inv32 only).
 // a: the matrix storage (SymStore of R, n = the box's cells); col: 2n of R
 // (shared memory).
-template <class R, class S>
+template <class R, class S, class W>
 __device__ __forceinline__ void bottom_inverse_cta(int nx, int ny, int nz, int P, long long Q,
-                                                   const double *__restrict__ wx,
-                                                   const double *__restrict__ wy,
-                                                   const double *__restrict__ wz, bool singular,
+                                                   const W *__restrict__ wx,
+                                                   const W *__restrict__ wy,
+                                                   const W *__restrict__ wz, bool singular,
                                                    S a, double *inv64, float *inv32, R *col)
 {
     for (long long e = threadIdx.x; e < a.size(); e += blockDim.x) a.a[e] = R(0);
@@ -1694,19 +1716,62 @@ __global__ void __launch_bounds__(1024) k_bottom_inverse(int nx, int ny, int nz,
 
 // ---- every box of a level in one launch (the solver's set-up)
 
-__host__ __device__ inline int setup_kind(int step)
+__host__ __device__ constexpr int setup_kind(int step)
 {
-    return step == 1 ? TK_CFACE : (step == 2 || step == 6) ? TK_CELL : TK_FACE;
+    return (step == 1 || step == 9) ? TK_CFACE
+         : (step == 2 || step == 6 || step == 8) ? TK_CELL : TK_FACE;
+}
+
+// One set-up step at one position of box B (see k_setup for the steps).
+template <int step>
+__device__ __forceinline__ void setup_step(const SetupBox &B, const TilePos &p)
+{
+    if constexpr (step == 0)
+        face_weights_at<false>(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy,
+                               B.wz, p.x, p.y, p.z);
+    else if constexpr (step == 5)
+        face_weights_at<true>(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy,
+                              B.wz, p.x, p.y, p.z, B.wx32, B.wy32, B.wz32);
+    else if constexpr (step == 1)
+        coarsen_at<double>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.cP, B.cQ, B.cwx,
+                           B.cwy, B.cwz, p.x, p.y, p.z);
+    else if constexpr (step == 2)
+        inv_diag_at(B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.D,
+                    (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
+                    B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
+                         : (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
+    else if constexpr (step == 6)
+        inv_diag_at<true>(B.P, B.Q, B.wx, B.wy, B.wz, nullptr, B.D,
+                          (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
+                          B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
+                               : (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
+                          B.invD32);
+    else if constexpr (step == 4)
+        face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.betaL, B.wx, B.wy,
+                              B.wz, p.x, p.y, p.z);
+    else if constexpr (step == 8)
+        inv_diag32_at(B.P, B.Q, B.wx32, B.wy32, B.wz32, B.invD32,
+                      (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
+    else if constexpr (step == 9)
+        coarsen_at<float>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx32, B.wy32, B.wz32, B.cP, B.cQ,
+                          B.cwx32, B.cwy32, B.cwz32, p.x, p.y, p.z);
+    else
+        round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
+                 B.invD32, p.x, p.y, p.z, B.rb, B.par, B.D);
 }
 
 // step 0 faces (TK_FACE), 1 coarsen (TK_CFACE), 2 diagonal (TK_CELL),
 // 3 FP32 copies (TK_FACE), 4 faces of a coupled level from betaL (TK_FACE),
 // 5 faces with their FP32 copies (TK_FACE), 6 diagonal with the FP32 1/D
 // (TK_CELL): 5 and 6 take the place of 0, 2 and 3 on mixed precision's
-// finest level
-__global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step, int t0)
+// finest level; 8 FP32 1/D (TK_CELL) and 9 FP32 coarsening (TK_CFACE) set
+// up its coarser FP32 levels from the finer FP32 ones.  The step is a
+// template argument: a run-time index into the set's tstart array
+// (a kernel parameter) would make every thread copy the set to local memory.
+template <int STEP>
+__global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int t0)
 {
-    const int kind = setup_kind(step);
+    constexpr int kind = setup_kind(STEP);
     const int t = blockIdx.x + t0;
     const int *ts = S.tstart[kind];
     const int b = find_box(ts, S.nbox, t);
@@ -1715,32 +1780,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupSet S, int step, int t0
     int ex, ey, ez;
     tile_extent(kind, B.nx, B.ny, B.nz, ex, ey, ez);
     if (p.x >= ex || p.y >= ey) return;
-    if (step == 0)
-        face_weights_at<false>(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy,
-                               B.wz, p.x, p.y, p.z);
-    else if (step == 5)
-        face_weights_at<true>(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.beta, B.wx, B.wy,
-                              B.wz, p.x, p.y, p.z, B.wx32, B.wy32, B.wz32);
-    else if (step == 1)
-        coarsen_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.cP, B.cQ, B.cwx, B.cwy, B.cwz,
-                   p.x, p.y, p.z);
-    else if (step == 2)
-        inv_diag_at(B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.D,
-                    (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
-                    B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
-                         : (long long)p.z * B.Q + (long long)p.y * B.P + p.x);
-    else if (step == 6)
-        inv_diag_at<true>(B.P, B.Q, B.wx, B.wy, B.wz, nullptr, B.D,
-                          (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
-                          B.rb ? split_at(p.x, p.y, p.z, B.par, B.P, B.Q)
-                               : (long long)p.z * B.Q + (long long)p.y * B.P + p.x,
-                          B.invD32);
-    else if (step == 4)
-        face_weights_level_at(B.nx, B.ny, B.nz, B.P, B.Q, B.inv_h2, B.bc, B.betaL, B.wx, B.wy,
-                              B.wz, p.x, p.y, p.z);
-    else
-        round_at(B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, B.invD, B.wx32, B.wy32, B.wz32,
-                 B.invD32, p.x, p.y, p.z, B.rb, B.par, B.D);
+    setup_step<STEP>(B, p);
 }
 
 // One CTA per box: the coarsest level's dense inverse, in FP64 when an FP64
@@ -1756,7 +1796,20 @@ __global__ void __launch_bounds__(1024) k_setup_bottom(SetupSet S, int packed_by
     const bool singular = (B.bc & 63) == 63;
     const int n = B.nx * B.ny * B.nz;
     const long long tri = (long long)n * (n + 1) / 2;
-    if (B.inv64) {
+    if (B.w32src) {
+        // coarser FP32 levels averaged in FP32: assembled from their weights
+        float *colf = reinterpret_cast<float *>(col);
+        if (tri * (long long)sizeof(float) <= packed_bytes)
+            bottom_inverse_cta<float>(
+                B.nx, B.ny, B.nz, B.P, B.Q, B.wx32, B.wy32, B.wz32, singular,
+                SymStore<float, true>{reinterpret_cast<float *>(bottom_packed), n}, nullptr,
+                B.inv32, colf);
+        else
+            bottom_inverse_cta<float>(B.nx, B.ny, B.nz, B.P, B.Q, B.wx32, B.wy32, B.wz32,
+                                      singular,
+                                      SymStore<float, false>{reinterpret_cast<float *>(B.work), n},
+                                      nullptr, B.inv32, colf);
+    } else if (B.inv64) {
         if (tri * (long long)sizeof(double) <= packed_bytes)
             bottom_inverse_cta<double>(
                 B.nx, B.ny, B.nz, B.P, B.Q, B.wx, B.wy, B.wz, singular,
@@ -2798,9 +2851,11 @@ cudaError_t launch_norm_finish(const BoxSet<T> &S, const int *active, const doub
                                const double *mult, int mode)
 {
     if (S.nbox == 0) return cudaSuccess;
-    const int kind = mode == 2 ? TK_PCOLZ : TK_COLZ;
+    // the partials' tile starts (the host picks the kind: a run-time index
+    // into the kernel's parameter set would copy it to local memory)
+    const int *ts = S.tstart[mode == 2 ? TK_PCOLZ : TK_COLZ];
     return pdl_launch(k_norm_finish<T>, dim3(S.nbox), dim3(1024), 0, st, S, active, partials, out,
-                      copy, inv, mult, kind);
+                      copy, inv, mult, ts);
 }
 
 template <class T>
@@ -2951,19 +3006,29 @@ cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, cons
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st)
-{
-    const int kind = setup_kind(step);
-    if (S.ntiles[kind] == 0) return cudaSuccess;
-    k_setup<<<S.ntiles[kind], block2d(), 0, st>>>(S, step, 0);
-    return counted(cudaGetLastError());
-}
-
 cudaError_t launch_setup_tiles(const SetupSet &S, int step, int t0, int t1, cudaStream_t st)
 {
     if (t1 <= t0) return cudaSuccess;
-    k_setup<<<t1 - t0, block2d(), 0, st>>>(S, step, t0);
+    const dim3 g(t1 - t0), b = block2d();
+    switch (step) {
+    case 0: k_setup<0><<<g, b, 0, st>>>(S, t0); break;
+    case 1: k_setup<1><<<g, b, 0, st>>>(S, t0); break;
+    case 2: k_setup<2><<<g, b, 0, st>>>(S, t0); break;
+    case 3: k_setup<3><<<g, b, 0, st>>>(S, t0); break;
+    case 4: k_setup<4><<<g, b, 0, st>>>(S, t0); break;
+    case 5: k_setup<5><<<g, b, 0, st>>>(S, t0); break;
+    case 6: k_setup<6><<<g, b, 0, st>>>(S, t0); break;
+    case 8: k_setup<8><<<g, b, 0, st>>>(S, t0); break;
+    case 9: k_setup<9><<<g, b, 0, st>>>(S, t0); break;
+    default: return cudaErrorInvalidValue;
+    }
     return counted(cudaGetLastError());
+}
+
+cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st)
+{
+    if (step < 0 || step > 9 || step == 7) return cudaErrorInvalidValue;
+    return launch_setup_tiles(S, step, 0, S.ntiles[setup_kind(step)], st);
 }
 
 cudaError_t launch_setup_bottom(const SetupSet &S, int packed_bytes, cudaStream_t st)

@@ -222,7 +222,9 @@ cudaError_t launch_bottom_inverse(int nx, int ny, int nz, const double *wx, cons
                                   float *inv32, cudaStream_t st);
 // ---- set-up of every box of a level in one launch ------------------------
 // step 0: face weights from beta; 1: coarse weights; 2: D and 1/D; 3: FP32
-// copies.
+// copies; 4: coupled faces from betaL; 5: faces with their FP32 copies; 6: D
+// with the FP32 1/D; 8: FP32 1/D from the FP32 weights; 9: FP32 coarse
+// weights from the finer FP32 ones.
 cudaError_t launch_setup(const SetupSet &S, int step, cudaStream_t st);
 // Tiles [t0, t1) of one step (tiles are numbered plane by plane, so a range
 // of whole planes of a one-box set is a range of tiles).

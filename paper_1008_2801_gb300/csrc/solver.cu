@@ -470,6 +470,8 @@ static int validate_opts(const mg_opts *o)
         return set_error(MG_ERR_INVALID_ARG, "sweep_zc must be in 0..4096");
     if (o->level_ctas < 0 || o->level_ctas > 64)
         return set_error(MG_ERR_INVALID_ARG, "level_ctas must be in 0..64");
+    if (o->fp32_setup < 0 || o->fp32_setup > 1)
+        return set_error(MG_ERR_INVALID_ARG, "fp32_setup must be 0 or 1");
     if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr))
         return set_error(MG_ERR_INVALID_ARG, "dev_alloc and dev_free come together");
     return MG_OK;
@@ -631,6 +633,7 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
     s->cut = cut;
     s->xmode = coupled || periodic;
     s->wide = s->xmode;
+    s->coarse32 = s->has32 && !s->xmode && o.fp32_setup == 0;
     if (coupled) {
         s->lo = clos;
         s->ub.n = ucells;
@@ -847,9 +850,16 @@ int solver_create(Solver **out, int nbox, const int (*n)[3], const double *dx, i
             B.wy32 = M.wy;
             B.wz32 = M.wz;
             B.invD32 = M.invD;
+            if (l + 1 < s->nlev[b]) {
+                const LevelBufs<float> &C = s->h32.lv[b][l + 1];
+                B.cwx32 = C.wx;
+                B.cwy32 = C.wy;
+                B.cwz32 = C.wz;
+            }
         }
         B.beta = s->beta + s->off[b];
         B.inv_h2 = 1.0 / (s->dx[b] * s->dx[b]);
+        B.w32src = s->coarse32 ? 1 : 0;
         B.nx = d[0];
         B.ny = d[1];
         B.nz = d[2];
@@ -1164,7 +1174,10 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     const long long plane = (long long)nx * ny;
     // mixed precision's finest level takes its FP32 copies with its faces
     // (step 5) and its FP32 1/D with its diagonal (step 6); a coupled level's
-    // faces come from step 4, and its copies from step 3
+    // faces come from step 4, and its copies from step 3.  With coarse32 the
+    // coarser levels are FP32 only, averaged from the finer FP32 weights
+    // (step 9) with their 1/D (step 8).
+    const bool c32 = s->coarse32;
     const int face_step = s->has32 ? 5 : 0;
     int slabs = (int)std::max<long long>(
         1, std::min<long long>(Solver::kBetaSlabs, (long long)sizeof(double) * nbeta >> 22));  // >= 4 MiB each
@@ -1203,7 +1216,18 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         // one launch per step and level over every box
         CK(launch_setup(s->setup_lv[0], face_step, st));
     }
-    for (size_t l = 0; l < s->setup_coarsen.size(); ++l) CK(launch_setup(s->setup_coarsen[l], 1, st));
+    if (c32) {
+        // the finest level's D and FP32 1/D; level l's FP32 weights averaged
+        // into l + 1, then its FP32 1/D (no FP64 level below the finest)
+        CK(launch_setup(s->setup_lv[0], 6, st));
+        for (size_t l = 0; l < s->setup_coarsen.size(); ++l) {
+            CK(launch_setup(s->setup_coarsen[l], 9, st));
+            CK(launch_setup(s->setup_lv[l + 1], 8, st));
+        }
+    } else {
+        for (size_t l = 0; l < s->setup_coarsen.size(); ++l)
+            CK(launch_setup(s->setup_coarsen[l], 1, st));
+    }
     // the dense coarsest inverses need the coarsest weights only: forked to
     // the side stream (one CTA per box, on as many SMs), they overlap the
     // diagonal and FP32 steps of the finer levels on the others
@@ -1213,7 +1237,7 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
         if (!s->cg_bottom) CK(launch_setup_bottom(s->setup_bottom, s->bottom_packed, s->side));
         CK(cudaEventRecord(s->ev_join, s->side));
     }
-    for (int l = 0; l < s->maxlev; ++l) {
+    for (int l = 0; l < s->maxlev && !c32; ++l) {
         const bool fused32 = s->has32 && l == 0 && !s->xmode;
         CK(launch_setup(s->setup_lv[l], fused32 ? 6 : 2, st));
         if (s->has32 && !fused32) CK(launch_setup(s->setup_lv[l], 3, st));

@@ -119,6 +119,10 @@ struct Solver {
     bool beta_set = false;
     float t_setup_ms = 0.f;
     bool setup_pending = false;
+    // mixed precision on independent boxes (mg_opts.fp32_setup = 0): the
+    // levels below the finest are FP32 only, averaged from the finer FP32
+    // weights (the finest level's are the rounded FP64 ones)
+    bool coarse32 = false;
 
     // measurement (mg_profile_*)
     bool prof = false;                    // record stage events

@@ -68,7 +68,7 @@ def _torch_allocator(device):
 
 def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, inner_cycles=0,
           full_residual=False, tma=None, krylov=False, max_norm=False, hooks=None,
-          wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
+          wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0, fp32_setup="coarse32"):
     o = _lib.mg_opts()
     _lib.load().mg_default_opts(ctypes.byref(o))
     o.precision = PRECISIONS[precision]
@@ -85,6 +85,7 @@ def _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells=0, 
     o.persistent = {False: 0, True: 2, "all": 2, "small": 1}.get(persistent, persistent)
     o.sweep_zc = int(sweep_zc)
     o.level_ctas = int(level_ctas)
+    o.fp32_setup = {"coarse32": 0, "rounded": 1}[fp32_setup]
     if hooks is not None:
         o.dev_alloc, o.dev_free = hooks
     return o
@@ -161,13 +162,18 @@ class Solver:
     (mg_opts.persistent: True or "all" on every level smoothed with passes,
     "small" on those whose stages fit in one wave of resident CTAs); sweep_zc, level_ctas: tile depth of the fused FP32
     sweep and CTAs per SM of the persistent launches (0: the library's
-    model; see mg_opts and ``autotune``).  Not thread-safe.
+    model; see mg_opts and ``autotune``).  fp32_setup ("mixed"): "coarse32"
+    (default) rounds the finest level's FP64 weights to FP32 and sets the
+    coarser levels up in FP32 only (averages of the finer FP32 weights);
+    "rounded" sets every level up in FP64 and rounds it (mg_opts.fp32_setup).
+    Not thread-safe.
     """
 
     def __init__(self, shape, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
                  full_residual=False, tma=None, bc=0, krylov=False, max_norm=False,
-                 allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
+                 allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0,
+                 fp32_setup="coarse32"):
         L = _lib.load()
         self.shape = tuple(int(v) for v in shape)
         nz, ny, nx = self.shape
@@ -180,7 +186,7 @@ class Solver:
         self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
                   full_residual, tma, krylov, max_norm, self._hooks, wait_limit, persistent,
-                  sweep_zc, level_ctas)
+                  sweep_zc, level_ctas, fp32_setup)
         with torch.cuda.device(self.device):
             check(L.mg_create(ctypes.byref(self._h), _lib.c_int3(nx, ny, nz), self.dx, self.bc,
                               ctypes.byref(o)), "mg_create")
@@ -362,12 +368,13 @@ class BatchSolver:
     are packed back to back in box order (see ``pack``/``unpack``).
     persistent: each level smoothed with passes runs as one persistent
     launch per direction over all boxes (mg_opts.persistent; True/"all" or
-    "small", as for ``Solver``)."""
+    "small", as for ``Solver``); fp32_setup as for ``Solver``."""
 
     def __init__(self, shapes, dx, precision="fp64", nu1=2, nu2=2, max_cycles=100,
                  use_graph=True, smoother="auto", device=None, coarse_cells=0, inner_cycles=0,
                  full_residual=False, tma=None, bc=0, krylov=False, max_norm=False,
-                 allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0):
+                 allocator=None, wait_limit=0, persistent=False, sweep_zc=0, level_ctas=0,
+                 fp32_setup="coarse32"):
         L = _lib.load()
         self.bc = bc_mask(bc)
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -381,7 +388,7 @@ class BatchSolver:
         self._hooks = _torch_allocator(self.device) if allocator == "torch" else None
         o = _opts(precision, nu1, nu2, max_cycles, use_graph, smoother, coarse_cells, inner_cycles,
                   full_residual, tma, krylov, max_norm, self._hooks, wait_limit, persistent,
-                  sweep_zc, level_ctas)
+                  sweep_zc, level_ctas, fp32_setup)
         with torch.cuda.device(self.device):
             check(L.mg_batch_create(ctypes.byref(self._h), nb, n, d, self.bc, ctypes.byref(o)),
                   "mg_batch_create")

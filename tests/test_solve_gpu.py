@@ -61,6 +61,30 @@ def test_stellar_reduced(cuda_device, shape, precision):
     assert np.linalg.norm(phi - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("shape", [(24, 40, 56), (64, 64, 64)])
+def test_mixed_fp32_setup_forms(cuda_device, shape):
+    # the coarser FP32 levels averaged in FP32 (default) or every level
+    # rounded from FP64: both are FP32 cycles inside FP64 refinement, so both
+    # meet the FP64 residual and land on the oracle's solution; each is
+    # reproducible bit for bit
+    nz, ny, nx = shape
+    d = inputs.stellar((nx, ny, nz), 5)
+    ref, _ = O.solve(d["beta"], d["f"], d["dx"], tol=1e-13)
+    out = {}
+    for fs in ("coarse32", "rounded"):
+        phi, st = _solve(d["beta"], d["f"], d["dx"], cuda_device, "mixed", fp32_setup=fs)
+        again, _ = _solve(d["beta"], d["f"], d["dx"], cuda_device, "mixed", fp32_setup=fs)
+        assert st["status"] == "ok" and st["cycles"] <= 3, st
+        assert np.array_equal(phi, again)
+        assert _rel_resid(d["beta"], d["f"], phi, d["dx"]) <= TOL * 1.01
+        assert np.linalg.norm(phi - ref) <= 1e-9 * np.linalg.norm(ref)
+        out[fs] = phi
+    # the forms differ only in the coarse FP32 operators, i.e. in the path
+    assert np.linalg.norm(out["coarse32"] - out["rounded"]) <= 2e-9 * np.linalg.norm(ref)
+    with pytest.raises(KeyError):
+        Solver(shape, d["dx"], precision="mixed", device=cuda_device, fp32_setup="beta")
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_stellar_256_full_size(cuda_device, precision):
     d = inputs.config(2)
