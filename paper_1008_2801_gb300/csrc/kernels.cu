@@ -602,12 +602,13 @@ __device__ __forceinline__ void restrict_red_tile(const BoxSet<T> &S,
     TilePos p = tile_pos<FC>(TK_COARSE, nx, ny, nz, t - ts[b]);
     const int I = p.x, J = p.y, K = p.z;
     if (NORM) {
+        // the warp's sum in T (for FP32 no FP64 adds on the narrow pipe; an
+        // exit test's sum needs no more), widened once
         T r2 = T(0);
         if (I < nx / 2 && J < ny / 2) r2 = restrict_red_cell<T, NORM>(B, I, J, K);
-        double v = (double)r2;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
         const int tid = threadIdx.y * kTX + threadIdx.x;
-        if ((tid & 31) == 0) partials[(long long)t * (kThreads / 32) + (tid >> 5)] = v;
+        if ((tid & 31) == 0) partials[(long long)t * (kThreads / 32) + (tid >> 5)] = (double)r2;
         return;
     }
     if (I >= nx / 2 || J >= ny / 2) return;
