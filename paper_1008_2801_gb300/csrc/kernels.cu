@@ -1130,9 +1130,12 @@ __global__ void __launch_bounds__(1024) k_judge(int nbox, const double *__restri
 // The copies between the caller's packed arrays and the level layout, and
 // the zeroing of a level's phi, take one thread per cell column of kColZ
 // planes (TK_COLZ tiles): kColZ independent loads or stores in flight per
-// thread instead of one per one-plane CTA.
+// thread instead of one per one-plane CTA.  partials (f only, or NULL): also
+// the CTA's sum of f^2, as k_norm_partials in mode 1 forms it (the column's
+// FMAs in plane order, then block_sum), so that ||f|| needs no pass of its own.
 __global__ void __launch_bounds__(kThreads) k_pack(BoxSet<double> S, const long long *__restrict__ off,
-                                                   const double *__restrict__ user, int to_f)
+                                                   const double *__restrict__ user, int to_f,
+                                                   double *__restrict__ partials)
 {
     pdl_wait();
     const int t = blockIdx.x;
@@ -1140,14 +1143,25 @@ __global__ void __launch_bounds__(kThreads) k_pack(BoxSet<double> S, const long 
     const int b = find_box(ts, S.nbox, t);
     const Box<double> &B = S.boxes[b];
     TilePos p = tile_pos(TK_COLZ, B.nx, B.ny, B.nz, t - ts[b]);
-    if (p.x >= B.nx || p.y >= B.ny) return;
-    const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
-    const long long us = (long long)B.ny * B.nx;
-    const double *src = user + off[B.box] + ((long long)z0 * B.ny + p.y) * B.nx + p.x;
+    double v = 0.0;
+    if (p.x < B.nx && p.y < B.ny) {
+        const int z0 = p.z * kColZ, z1 = min(z0 + kColZ, B.nz);
+        const long long us = (long long)B.ny * B.nx;
+        const double *src = user + off[B.box] + ((long long)z0 * B.ny + p.y) * B.nx + p.x;
 #pragma unroll 4
-    for (int k = z0; k < z1; ++k, src += us) {
-        if (to_f) B.f[fidx(B, p.x, p.y, k)] = *src;
-        else B.phi[(long long)k * B.Q + (long long)p.y * B.P + p.x] = *src;
+        for (int k = z0; k < z1; ++k, src += us) {
+            const double u = *src;
+            if (to_f) {
+                B.f[fidx(B, p.x, p.y, k)] = u;
+                if (partials) v = fma(u, u, v);
+            } else {
+                B.phi[(long long)k * B.Q + (long long)p.y * B.P + p.x] = u;
+            }
+        }
+    }
+    if (partials) {   // uniform over the launch
+        const double sum = block_sum(v);
+        if (threadIdx.x == 0 && threadIdx.y == 0) partials[t] = sum;
     }
 }
 
@@ -2907,10 +2921,11 @@ cudaError_t launch_judge(int nbox, const double *norm, const double *normf, int 
 }
 
 cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,
-                        int to_f, cudaStream_t st)
+                        int to_f, cudaStream_t st, double *partials)
 {
     if (S.ntiles[TK_COLZ] == 0) return cudaSuccess;
-    return pdl_launch(k_pack, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, off, user, to_f);
+    return pdl_launch(k_pack, dim3(S.ntiles[TK_COLZ]), block2d(), 0, st, S, off, user, to_f,
+                      to_f ? partials : nullptr);
 }
 
 cudaError_t launch_unpack(const BoxSet<double> &S, const long long *off, double *user,

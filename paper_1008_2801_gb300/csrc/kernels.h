@@ -189,8 +189,10 @@ cudaError_t launch_cg_bottom(const BoxSet<T> &S, const int *active, T *p, T *q, 
 
 // ---- moving data between packed user arrays and the level layout --------
 // user[off[b] + (k*ny + j)*nx + i] -> level 0 f (to_f) or phi of box b.
+// partials (f only): also the TK_COLZ partial sums of f^2 that
+// launch_norm_partials(S, NULL, 1, partials) would write, bit for bit.
 cudaError_t launch_pack(const BoxSet<double> &S, const long long *off, const double *user,
-                        int to_f, cudaStream_t st);
+                        int to_f, cudaStream_t st, double *partials = nullptr);
 // level 0 phi (side[b] == 0, or side == NULL) or phi2 (side[b] == 1) -> user.
 cudaError_t launch_unpack(const BoxSet<double> &S, const long long *off, double *user,
                           const int *side, cudaStream_t st);

@@ -2062,7 +2062,10 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     const double *fd = nullptr, *pd = nullptr;
     bool fst = false, pst = false;
     CKS(device_view(s, f, 0, true, stream, &fd, &fst, -1, side_in));
-    CK(launch_pack(H.fine, s->doff, fd, 1, stream));
+    // the pack also leaves the partial sums of ||f||^2 (bitwise those of the
+    // norm pass), unless the mean of f is removed next
+    const bool norm_in_pack = !s->singular;
+    CK(launch_pack(H.fine, s->doff, fd, 1, stream, norm_in_pack ? s->partials : nullptr));
     // every wall Neumann: only the zero-mean part of f is in the range of A
     if (s->singular) CK(launch_remove_mean(H.fine, 0, s->partials, s->dmean, stream));
     for (int b = 0; b < nbox; ++b) s->hactive[b] = 1;
@@ -2080,7 +2083,7 @@ int solver_solve(Solver *s, const double *f, double *phi, double tol, mg_stats *
     // ||f|| and the starting residual r0 = f - A phi0.  In mixed precision
     // r0 comes from refinement step 0 (FP64 residual, no update), which also
     // leaves r32 = r0 / ||f|| and the scales for the first FP32 cycles.
-    CK(launch_norm_partials(H.fine, nullptr, 1, s->partials, stream));
+    if (!norm_in_pack) CK(launch_norm_partials(H.fine, nullptr, 1, s->partials, stream));
     CK(launch_norm_finish(H.fine, nullptr, s->partials, s->dnormf, nullptr, nullptr, stream));
     CK(combine(s, s->dnormf, stream));
     if (!mixed && zero_guess) {
