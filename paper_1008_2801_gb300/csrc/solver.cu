@@ -1230,7 +1230,8 @@ int solver_set_beta(Solver *s, const double *beta, cudaStream_t st)
     }
     // the dense coarsest inverses need the coarsest weights only: forked to
     // the side stream (one CTA per box, on as many SMs), they overlap the
-    // diagonal and FP32 steps of the finer levels on the others
+    // diagonal and FP32 steps of the finer levels on the others (with
+    // coarse32 those came first: the coarsest FP32 weights end that chain)
     if (!s->xmode) {
         CK(cudaEventRecord(s->ev_fork, st));
         CK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
